@@ -1,0 +1,91 @@
+"""Planted mistakes in the oracle must trip at least one pin (CPU only).
+
+Each case patches one plausible slip into a copy of an oracle function — a transposed
+overlap, a dropped commutator term, a wrong sign — and checks that the pin built for it
+fails.  This guards the pins themselves.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import kernel as ok
+from oracle import model as om
+from oracle import propagate as op
+
+
+@pytest.fixture(scope="module")
+def m4():
+    return om.Model(wl.small_model(4, 2))
+
+
+def _kernel_transposed_hole(model):
+    """Slip: (U_k^+ U_k')_{m m'} instead of (U_k'^+ U_k)_{m' m} in the hole factor."""
+    p, Nk, Nb = model.p, model.Nk, model.Nb
+    W = ok.W_matrix(p)
+    O = np.einsum("kin,qip->kqnp", model.U.conj(), model.U)
+    K = -W[:, :, None, None, None, None] * O[:, :, :, None, :, None] * O[:, :, None, :, None, :]
+    return np.transpose(K, (0, 2, 3, 1, 4, 5)).reshape(Nk * Nb * Nb, Nk * Nb * Nb)
+
+
+def test_transposed_hole_overlap_breaks_gauge_covariance(m4):
+    rng = np.random.default_rng(11)
+    ph = rng.uniform(0, 2 * np.pi, (m4.Nk, m4.Nb))
+    K1, K2 = _kernel_transposed_hole(m4), _kernel_transposed_hole(m4.rephased(ph))
+    e = np.exp(1j * ph)
+    pair = (e.conj()[:, :, None] * e[:, None, :]).reshape(-1)
+    assert np.abs(K2 - pair[:, None] * K1 * pair.conj()[None, :]).max() > 1e-6
+
+
+def test_transposed_hole_overlap_breaks_fft_identity(m4):
+    x = wl.random_state(m4.N, 3)
+    a, b = _kernel_transposed_hole(m4) @ x, ok.apply_fft(m4, x)
+    assert np.abs(a - b).max() > 1e-3 * np.abs(b).max()
+
+
+def test_wrong_commutator_sign_breaks_rabi(monkeypatch):
+    p = wl.small_model(1, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    good = op.rhs
+
+    def bad_rhs(model, apply_K, Ex, Ey, X):
+        return -good(model, apply_K, Ex, Ey, X).conj()   # i[H, rho] instead of -i[H, rho] (conj flips i)
+    monkeypatch.setattr(op, "rhs", bad_rhs)
+    import scipy.linalg
+    E, Ttot, dt = 0.01, 40.0, 0.2
+    T = int(Ttot / dt)
+    _, x = op.rk4(mdl, lambda v: K @ v, op.half_step_samples(wl.Pulse(E0=E, kind=1), dt, T), dt, T)
+    W0 = -K[0, 0].real
+    rho0 = mdl.rho0()[0]
+    Ut = scipy.linalg.expm(-1j * (np.diag(mdl.eps[0]) + E * mdl.dx[0] + W0 * rho0) * Ttot)
+    exact = Ut @ rho0 @ Ut.conj().T
+    assert np.abs(rho0 + x.reshape(2, 2) - exact).max() > 1e-4
+
+
+def test_dropped_kernel_term_breaks_rabi():
+    """Without dSigma the Rabi frequency misses the W0 rho0 shift."""
+    p = wl.small_model(1, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    import scipy.linalg
+    E, Ttot, dt = 0.01, 40.0, 0.2
+    T = int(Ttot / dt)
+    _, x = op.rk4(mdl, lambda v: 0 * v, op.half_step_samples(wl.Pulse(E0=E, kind=1), dt, T), dt, T)
+    W0 = -K[0, 0].real
+    rho0 = mdl.rho0()[0]
+    Ut = scipy.linalg.expm(-1j * (np.diag(mdl.eps[0]) + E * mdl.dx[0] + W0 * rho0) * Ttot)
+    exact = Ut @ rho0 @ Ut.conj().T
+    assert np.abs(rho0 + x.reshape(2, 2) - exact).max() > 1e-4
+
+
+def test_wrong_W0_breaks_quadrature_pin():
+    import scipy.integrate
+    p = wl.small_model(12, 1)
+    A = p.Nk * p.a ** 2
+    h = np.pi / (p.L * p.a)
+    f = lambda y, x: ok.coulomb_W(np.hypot(x, y), A, p.r0)
+    v, _ = scipy.integrate.dblquad(f, 0, h, lambda x: 0.0, lambda x: x, epsabs=0, epsrel=1e-12)
+    brute = 8.0 * v / (4.0 * h * h)
+    # slip: average over the disc of radius h instead of the square
+    disc = (2 * np.pi / (A * p.r0)) * 2 * np.pi * np.log1p(p.r0 * h) / (np.pi * h * h)
+    assert abs(disc - brute) / brute > 1e-3

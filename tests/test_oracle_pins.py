@@ -1,0 +1,302 @@
+"""Pins of the FP64 oracle against closed forms, invariants and independent routines.
+
+Each test fixes a part of the oracle with something other than the oracle itself, so
+that a dropped term, a wrong sign or index, or a transposed operand fails one of them.
+No GPU.
+"""
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+import workloads as wl
+from oracle import kernel as ok
+from oracle import lowrank as olr
+from oracle import model as om
+from oracle import propagate as op
+
+
+@pytest.fixture(scope="module")
+def m2():
+    return om.Model(wl.small_model(6, 1))
+
+
+@pytest.fixture(scope="module")
+def m4():
+    return om.Model(wl.small_model(4, 2))
+
+
+# ---------------------------------------------------------------- model -------------
+
+@pytest.mark.parametrize("nc", [1, 2])
+def test_eigenpairs_closed_form(nc):
+    """Eigenvalues are off_c +- |d(k)| (textbook 2x2); eigenvectors diagonalise h."""
+    p = wl.small_model(5, nc)
+    k = om.kgrid(p.L, p.a) + 0.013
+    eps, U = om.eigensystem(k, p)
+    kx, ky = k[:, 0] * p.a, k[:, 1] * p.a
+    d = np.sqrt((p.t * np.sin(kx)) ** 2 + (p.t * np.sin(ky)) ** 2
+                + (p.Delta + p.m * (2 - np.cos(kx) - np.cos(ky))) ** 2)
+    want = np.sort(np.concatenate([np.stack([p.offsets[c] - d, p.offsets[c] + d], 1)
+                                   for c in range(nc)], 1), axis=1)
+    np.testing.assert_allclose(eps, want, atol=1e-14)
+    H = om.h_orbital(k, p)
+    np.testing.assert_allclose(H @ U, U * eps[:, None, :], atol=1e-14)
+    # gauge rule: largest-modulus component real and positive
+    idx = np.argmax(np.abs(U), axis=1)
+    piv = np.take_along_axis(U, idx[:, None, :], axis=1)
+    assert np.all(piv.real > 0) and np.abs(piv.imag).max() < 1e-15
+
+
+def test_dh_dk_matches_numerical_derivative():
+    p = wl.small_model(3, 2)
+    k = om.kgrid(p.L, p.a) + 0.02
+    for ax in (0, 1):
+        e = np.zeros(2)
+        e[ax] = 1e-6
+        num = (om.h_orbital(k + e, p) - om.h_orbital(k - e, p)) / 2e-6
+        np.testing.assert_allclose(om.dh_dk(k, p, ax), num, atol=1e-8)
+
+
+@pytest.mark.parametrize("nc", [1, 2])
+def test_dipole_matches_interband_formula(nc):
+    """i<n|du_m> = i <n|dh|m> / (eps_m - eps_n) for n != m; diagonal zero after transport."""
+    p = wl.small_model(5, nc)
+    mdl = om.Model(p)
+    for ax, d in ((0, mdl.dx), (1, mdl.dy)):
+        dh = np.einsum("kin,kij,kjm->knm", mdl.U.conj(), om.dh_dk(mdl.k, p, ax), mdl.U)
+        de = mdl.eps[:, None, :] - mdl.eps[:, :, None]          # eps_m - eps_n
+        off = ~np.eye(p.Nb, dtype=bool)
+        want = np.zeros_like(dh)
+        want[:, off] = 1j * dh[:, off] / de[:, off]
+        np.testing.assert_allclose(d, want, atol=2e-8)
+        assert np.abs(np.diagonal(d, axis1=1, axis2=2)).max() < 1e-9
+        np.testing.assert_allclose(d, np.conj(np.swapaxes(d, 1, 2)), atol=1e-15)
+
+
+def test_velocity_diagonal_is_band_slope(m4):
+    """Hellmann-Feynman: v_nn = d eps_n / dk_x (central difference of eigenvalues)."""
+    p = m4.p
+    e = np.array([1e-6, 0.0])
+    slope = (om.eigensystem(m4.k + e, p)[0] - om.eigensystem(m4.k - e, p)[0]) / 2e-6
+    np.testing.assert_allclose(np.diagonal(m4.vx, axis1=1, axis2=2).real, slope, atol=1e-8)
+
+
+def test_four_band_copies_decouple(m4):
+    """Bands of different copies have zero overlap, dipole and velocity."""
+    # bands 0, 2 are copy 0 (lower/upper); 1, 3 are copy 1 (offset 0.03)
+    U = m4.U
+    w0 = np.abs(U[:, 0:2, :]) ** 2
+    copy = (w0.sum(axis=1) < 0.5).astype(int)                  # (Nk, Nb)
+    assert np.all(copy == np.array([0, 1, 0, 1]))
+    for X in (m4.dx, m4.dy, m4.vx):
+        cross = X[:, copy[0][:, None] != copy[0][None, :]]
+        assert np.abs(cross).max() < 1e-9
+
+
+# ---------------------------------------------------------------- W(q) ---------------
+
+def test_cell_average_against_2d_quadrature():
+    """W0 = mean of W over the mini-cell, checked by adaptive Cartesian 2D quadrature."""
+    p = wl.small_model(12, 1)
+    A = p.Nk * p.a ** 2
+    h = np.pi / (p.L * p.a)
+    f = lambda y, x: ok.coulomb_W(np.hypot(x, y), A, p.r0)
+    # quarter square [0,h]^2 (W is even in qx, qy); split the integrable corner singularity
+    val1, _ = scipy.integrate.dblquad(f, 0, h, lambda x: 0.0, lambda x: x, epsabs=0, epsrel=1e-12)
+    brute = 8.0 * val1 / (4.0 * h * h)
+    assert abs(ok.cell_average_W0(h, A, p.r0) - brute) / brute < 1e-9
+
+
+def test_cell_average_unscreened_limit():
+    """r0 -> 0: mean of 1/|q| over the square of half-side h is 2 ln(1 + sqrt 2) / h."""
+    A, h = 3.7, 0.05
+    got = ok.cell_average_W0(h, A, 1e-10)
+    want = (2 * np.pi / A) * 2 * np.log1p(np.sqrt(2.0)) / h
+    assert abs(got - want) / want < 1e-8
+
+
+# ---------------------------------------------------------------- kernel -------------
+
+@pytest.mark.parametrize("name", ["m2", "m4"])
+def test_kernel_hermitian_and_diag(name, request):
+    mdl = request.getfixturevalue(name)
+    K = ok.dense_kernel(mdl)
+    assert np.abs(K - K.conj().T).max() == 0.0
+    W0 = ok.cell_average_W0(np.pi / (mdl.p.L * mdl.p.a), mdl.Nk * mdl.p.a ** 2, mdl.p.r0)
+    np.testing.assert_allclose(np.diag(K), -W0, rtol=1e-14)
+    np.testing.assert_allclose(ok.kernel_diag(mdl), np.diag(K), rtol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["m2", "m4"])
+def test_kernel_dense_equals_fft_convolution(name, request):
+    """Dense K.x == the independent FFT-convolution form, to rounding."""
+    mdl = request.getfixturevalue(name)
+    K = ok.dense_kernel(mdl)
+    x = wl.random_state(mdl.N, 3)
+    a, b = ok.apply_dense(K, x), ok.apply_fft(mdl, x)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+def test_kernel_entries_by_scalar_loops(m4):
+    """Sampled entries and rows of the dense matrix against the entry formula."""
+    K = ok.dense_kernel(m4)
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        r, c = rng.integers(0, m4.N, 2)
+        assert abs(K[r, c] - ok.kernel_entry(m4, int(r), int(c))) < 1e-16
+    for r in rng.integers(0, m4.N, 5):
+        np.testing.assert_allclose(ok.kernel_row(m4, int(r)), K[r], atol=1e-17)
+
+
+def test_kernel_gauge_covariance(m4):
+    """Rephasing bands multiplies K entries by the matching pair phases (index check)."""
+    rng = np.random.default_rng(11)
+    ph = rng.uniform(0, 2 * np.pi, (m4.Nk, m4.Nb))
+    K1, K2 = ok.dense_kernel(m4), ok.dense_kernel(m4.rephased(ph))
+    e = np.exp(1j * ph)
+    pair = (e.conj()[:, :, None] * e[:, None, :]).reshape(-1)     # phase of rho_nm,k
+    np.testing.assert_allclose(K2, pair[:, None] * K1 * pair.conj()[None, :], atol=1e-16)
+
+
+def test_single_k_kernel_is_minus_W0_identity():
+    p = wl.small_model(1, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    W0 = ok.cell_average_W0(np.pi / p.a, p.a ** 2, p.r0)
+    np.testing.assert_allclose(K, -W0 * np.eye(4), atol=1e-15)
+
+
+# ---------------------------------------------------------------- SVD ----------------
+
+def test_svd_full_rank_and_eckart_young(m2):
+    K = ok.dense_kernel(m2)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, m2.N)
+    assert np.abs(olr.reconstruct(d, U, S, V) - K).max() < 1e-14 * np.abs(K).max() * m2.N
+    sv = olr.singular_values(Koff)
+    # Hermitian K^off: singular values are |eigenvalues| (independent LAPACK routine)
+    np.testing.assert_allclose(np.sort(np.abs(scipy.linalg.eigvalsh(Koff)))[::-1], sv, atol=1e-15)
+    for r in (5, 40, 200):
+        U, S, V = olr.truncated_svd(Koff, r)
+        err = np.linalg.norm(Koff - (U * S) @ V.conj().T)
+        assert abs(err - np.sqrt(np.sum(sv[r:] ** 2))) < 1e-12 * np.linalg.norm(Koff)
+
+
+def test_lowrank_apply_matches_reconstruction(m2):
+    K = ok.dense_kernel(m2)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, 30)
+    x = wl.random_state(m2.N, 5)
+    np.testing.assert_allclose(olr.apply_lowrank(d, U, S, V, x),
+                               olr.reconstruct(d, U, S, V) @ x, atol=1e-16)
+
+
+def test_r_squared_definition():
+    y = np.array([1.0, 2.0, 3.0, 4.0])
+    assert olr.r_squared(y, y) == 1.0
+    assert abs(olr.r_squared(y, np.full(4, y.mean()))) < 1e-15
+
+
+# ---------------------------------------------------------------- dynamics -----------
+
+def _rabi_exact(mdl, E, t):
+    W0 = -ok.dense_kernel(mdl)[0, 0].real
+    rho0 = mdl.rho0()[0]
+    Heff = np.diag(mdl.eps[0]) + E * mdl.dx[0] + W0 * rho0
+    Ut = scipy.linalg.expm(-1j * Heff * t)
+    return Ut @ rho0 @ Ut.conj().T
+
+
+def test_rabi_closed_form_single_k():
+    """Nk = 1, constant field: K = -W0 I, so rho(t) = e^{-iHt} rho0 e^{iHt} with
+    H = H0 + E d + W0 rho0 exactly; RK4 error must shrink ~16x when dt halves."""
+    p = wl.small_model(1, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    E = 0.01
+    pulse = wl.Pulse(E0=E, kind=1)
+    Ttot = 40.0
+    errs = []
+    for dt in (0.4, 0.2, 0.1):
+        T = int(round(Ttot / dt))
+        s = op.half_step_samples(pulse, dt, T)
+        _, x = op.rk4(mdl, lambda v: K @ v, s, dt, T)
+        rho = mdl.rho0()[0] + x.reshape(2, 2)
+        errs.append(np.abs(rho - _rabi_exact(mdl, E, Ttot)).max())
+    assert errs[1] < 3e-7
+    for a, b in zip(errs, errs[1:]):
+        assert 12.0 < a / b < 20.0
+
+
+def test_stationary_without_field(m4):
+    K = ok.dense_kernel(m4)
+    s = np.zeros(2 * 20 + 1)
+    obs, x = op.rk4(m4, lambda v: K @ v, s, 0.2, 20)
+    assert np.all(x == 0)
+    assert np.all(obs[:, 0] == 0) and np.all(obs[:, 2] == 0)
+
+
+def test_trace_and_hermiticity_conserved(m4):
+    K = ok.dense_kernel(m4)
+    pulse = wl.Pulse(E0=5e-3, omega=0.1, t0=10.0, sigma=5.0)
+    T = 100
+    _, x = op.rk4(m4, lambda v: K @ v, op.half_step_samples(pulse, 0.2, T), 0.2, T)
+    X = x.reshape(m4.Nk, 4, 4)
+    assert np.abs(np.trace(X, axis1=1, axis2=2)).max() < 1e-15
+    assert np.abs(X - np.conj(np.swapaxes(X, 1, 2))).max() < 1e-15
+    assert np.abs(X).max() > 1e-5
+
+
+def test_gauge_invariance_of_observables(m4):
+    """Random per-k band phases change K, d, v and rho, but not P, J, occupation."""
+    rng = np.random.default_rng(2)
+    m4b = m4.rephased(rng.uniform(0, 2 * np.pi, (m4.Nk, m4.Nb)))
+    pulse = wl.Pulse(E0=5e-3, omega=0.1, t0=10.0, sigma=5.0)
+    T = 60
+    s = op.half_step_samples(pulse, 0.2, T)
+    K1, K2 = ok.dense_kernel(m4), ok.dense_kernel(m4b)
+    o1, _ = op.rk4(m4, lambda v: K1 @ v, s, 0.2, T)
+    o2, _ = op.rk4(m4b, lambda v: K2 @ v, s, 0.2, T)
+    assert np.abs(o1[:, 0]).max() > 1e-5
+    np.testing.assert_allclose(o1, o2, atol=1e-15)
+
+
+def test_lowrank_full_rank_propagation_equals_full(m2):
+    K = ok.dense_kernel(m2)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, m2.N)
+    pulse = wl.Pulse(E0=5e-3, omega=0.1, t0=10.0, sigma=5.0)
+    T = 80
+    s = op.half_step_samples(pulse, 0.2, T)
+    o1, _ = op.rk4(m2, lambda v: K @ v, s, 0.2, T)
+    o2, _ = op.rk4(m2, lambda v: olr.apply_lowrank(d, U, S, V, v), s, 0.2, T)
+    assert op.rel_l2(o2[:, 0], o1[:, 0]) < 1e-12
+
+
+def test_truncation_error_shrinks_with_rank():
+    """Paper trend (Fig. abs_linear): P(t) error vs the full kernel falls as rank grows."""
+    mdl = om.Model(wl.small_model(8, 1))
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    pulse = wl.Pulse(E0=1e-3, omega=0.1, t0=40.0, sigma=12.0)
+    T = 300
+    s = op.half_step_samples(pulse, 0.2, T)
+    ref, _ = op.rk4(mdl, lambda v: K @ v, s, 0.2, T)
+    errs = []
+    for r in (2, 13, 51, 128):
+        U, S, V = olr.truncated_svd(Koff, r)
+        o, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), s, 0.2, T)
+        errs.append(op.rel_l2(o[:, 0], ref[:, 0]))
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+
+
+def test_linear_response_scaling(m2):
+    """Weak field: P(t) is linear in E0 to O(E0^2) (linear-response limit of Eq. tdagw)."""
+    K = ok.dense_kernel(m2)
+    T = 150
+    outs = []
+    for E0 in (1e-5, 2e-5):
+        s = op.half_step_samples(wl.Pulse(E0=E0, omega=0.1, t0=10.0, sigma=5.0), 0.2, T)
+        outs.append(op.rk4(m2, lambda v: K @ v, s, 0.2, T)[0][:, 0])
+    assert op.rel_l2(outs[1], 2 * outs[0]) < 1e-4
