@@ -1,0 +1,166 @@
+/*
+ * tdagw.h -- C ABI of the GB300 (sm_103a) TD-aGW kernel-contraction library.
+ *
+ * The library propagates the one-body density matrix of a crystal under a driving field,
+ * Eq. tdagw of arXiv:2502.05635 ("Data-driven low-rank approximation for electron-hole
+ * kernel and acceleration of time-dependent GW calculations"):
+ *
+ *     i d/dt rho_k = [ H^QP_k + dSigma_k(t) + E(t).d_k , rho_k ]
+ *     dSigma_{nmk} = sum_{n'm'k'} K_{nmk,n'm'k'} drho_{n'm'k'}        (Eq. sigma-from-k)
+ *
+ * with the kernel applied either densely (cost Nb^4 Nk^2 per evaluation, Sec. "SVD
+ * acceleration", Appendix A.1) or in the truncated-SVD form of Eq. svd_diag_offdiag /
+ * Eq. svd_acc, dSigma = K^diag drho + U diag(S) (V^H drho) (cost Nb^2 Nk 2z).
+ *
+ * Conventions shared by every call
+ *   - N = Nb^2 Nk; pair index i = (k Nb + n) Nb + m; k = ix L + iy on the L x L grid.
+ *   - Complex numbers are interleaved (re, im).  "c64" = 2 x float, "c128" = 2 x double.
+ *     The context's dtype (TDAGW_C64 or TDAGW_C128) fixes the device storage and the
+ *     arithmetic of the propagation path; host-side exchange arrays are always c128/double.
+ *   - Return value: TDAGW_OK (0) or a negative TDAGW_ERR_* code; tdagw_last_error() gives a
+ *     message for the calling thread.  No C++ exception or abort crosses this boundary.
+ *   - Device pointers passed in are borrowed for the duration of the call and used on the
+ *     context's stream; all device work is stream-ordered on that stream.  Calls that write
+ *     to host memory synchronise the stream before returning.
+ *   - Memory the library allocates is owned by the context and freed by tdagw_destroy.
+ */
+#ifndef TDAGW_H
+#define TDAGW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TDAGW_OK = 0,
+    TDAGW_ERR_INVALID_ARG = -1,
+    TDAGW_ERR_OOM = -2,
+    TDAGW_ERR_CUDA = -3,
+    TDAGW_ERR_NOT_BUILT = -4,     /* tdagw_build_kernel has not run */
+    TDAGW_ERR_NO_FACTORS = -5,    /* low-rank mode without factors */
+    TDAGW_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    TDAGW_ERR_UNSUPPORTED = -7
+};
+
+enum { TDAGW_C64 = 0, TDAGW_C128 = 1 };
+enum { TDAGW_FULL = 0, TDAGW_LOWRANK = 1 };
+enum {
+    TDAGW_FIELD_GAUSS_COS = 0,    /* E0 exp(-(t-t0)^2 / (2 sigma^2)) cos(omega t)          */
+    TDAGW_FIELD_CONST = 1,        /* E0                                                     */
+    TDAGW_FIELD_SIN2_SIN = 2,     /* E0 sin^2(pi t / T_pulse) sin(omega t) on [0, T_pulse]  */
+    TDAGW_FIELD_TABLE = 3         /* caller samples E(j dt/2), j = 0 .. 2 steps              */
+};
+/* propagate flags */
+enum {
+    TDAGW_FLAG_RESET = 1,         /* start from drho = 0 and t = 0 (else continue)          */
+    TDAGW_FLAG_NO_GRAPH = 2,      /* launch stage by stage instead of replaying a CUDA graph */
+    TDAGW_FLAG_NO_KAHAN = 4       /* plain (uncompensated) RK4 accumulation                 */
+};
+
+typedef struct tdagw_ctx tdagw_ctx;
+
+/* Lattice stand-in for the paper's first-principles bands (Appendix A): nb_copies copies of
+ * h(k) = Delta sz + t (sin(kx a) sx + sin(ky a) sy) + m (2 - cos kx a - cos ky a) sz,
+ * copy c shifted by offsets[c]; Nb = 2 nb_copies bands, lower half occupied.  W(q) is the
+ * 2D Rytova-Keldysh interaction 2 pi / (A |q| (1 + r0 |q|)), A = Nk a^2, with W(0) the
+ * mean over the grid's mini-cell (Appendix B). */
+typedef struct {
+    int L;                /* grid is L x L, 1 <= L <= 4096                                */
+    int nb_copies;        /* 1 (Nb = 2) or 2 (Nb = 4)                                     */
+    double offsets[4];    /* energy offset of each copy (Ha)                              */
+    double Delta, t, m;   /* model parameters (Ha)                                        */
+    double a;             /* lattice constant (bohr)                                      */
+    double r0;            /* screening length (bohr)                                      */
+    int dtype;            /* TDAGW_C64 or TDAGW_C128                                      */
+} tdagw_model_desc;
+
+/* One driving pulse (atomic units).  The field is E(t) (dir_x, dir_y) and couples as
+ * E(t).d_k with the k-local dipoles d (Eq. tdagw, length gauge). */
+typedef struct {
+    int kind;             /* TDAGW_FIELD_*                                                */
+    double E0, omega, t0, sigma, T_pulse;
+    double dir_x, dir_y;
+    const double* table;  /* kind TABLE: host array of 2*steps+1 samples, else NULL       */
+} tdagw_field;
+
+/* Create a context for one model.  stream: a cudaStream_t (may be NULL for the legacy
+ * default stream).  *out receives the context.  Allocates nothing on the device yet. */
+int tdagw_create(const tdagw_model_desc* desc, void* stream, tdagw_ctx** out);
+
+/* Build the model (bands, gauge-fixed eigenvectors, dipoles d^x, d^y, velocity v^x) on the
+ * host in FP64 and the dense kernel K (N x N, row-major, context dtype) on the device
+ * (Eq. bse-direct-def for the model:
+ *   K_{(k n m),(k' n' m')} = -W(k - k') (U_k^+ U_k')_{n n'} (U_k'^+ U_k)_{m' m}).
+ * Errors: TDAGW_ERR_OOM if K does not fit. */
+int tdagw_build_kernel(tdagw_ctx* ctx);
+
+/* Sizes: N = Nb^2 Nk, Nb, Nk.  Any pointer may be NULL. */
+int tdagw_model_info(const tdagw_ctx* ctx, int64_t* N, int* Nb, int* Nk);
+
+/* Copy the host-side model out (for checks).  eps: Nk*Nb doubles; dx, dy, vx: Nk*Nb*Nb c128;
+ * U: Nk*Norb*Nb c128 (column n of U_k is band n in the orbital basis).  Any may be NULL. */
+int tdagw_get_model(const tdagw_ctx* ctx, double* eps, double* dx, double* dy, double* vx,
+                    double* U);
+
+/* Sampled kernel entries K[rows[i], cols[i]] as stored on the device, written to out as
+ * n c128 values (host).  Synchronises. */
+int tdagw_get_kernel_entries(tdagw_ctx* ctx, const int64_t* rows, const int64_t* cols,
+                             int64_t n, double* out);
+
+/* Randomised truncated SVD of K^off = K - diag(K) (Eq. svd_diag_offdiag) to rank `rank`
+ * (Halko-Martinsson-Tropp range finder with `oversample` extra columns and `power_iters`
+ * power iterations, Gaussian test matrix from `seed`; FP64 orthogonalisation and core
+ * eigen-solve on the device, K^off being Hermitian).  Replaces any factors present.
+ * precision: 0 = factors stored in the context dtype.  Errors: INVALID_ARG if
+ * rank + oversample > N. */
+int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
+                       uint64_t seed, int precision);
+
+/* Install factors K^off ~ U diag(S) V^H from the host (c128 U, V: N x rank row-major;
+ * S: rank doubles; diag: N c128 or NULL to keep diag(K) of the built kernel). */
+int tdagw_set_factors(tdagw_ctx* ctx, int rank, const double* U, const double* S,
+                      const double* V, const double* diag);
+
+/* Copy the installed factors to the host in c128 (U, V: N x rank; S: rank; diag: N).
+ * *rank receives the rank; any array pointer may be NULL. */
+int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V, double* diag);
+
+/* One kernel application y = K x (mode FULL) or y = K^diag x + U (S (V^H x)) (LOWRANK)
+ * on device vectors of N elements in the context dtype. */
+int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
+
+/* Propagate B trajectories (B = 1 here) by classical RK4 (four stages per step, dSigma
+ * re-evaluated at every stage, Kahan-compensated state accumulation) for steps[b] steps of
+ * dt.  fields: B host structs.  Observables (P_x, J_x, occupation of the first conduction
+ * band; Sec. "SVD acceleration") are recorded at every step including t = 0 of this call.
+ * Errors: NO_FACTORS for LOWRANK without factors; NOT_BUILT before tdagw_build_kernel. */
+int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
+                    double dt, int mode, int flags);
+
+/* Copy the observables recorded by the last tdagw_propagate: rows (steps+1) x B x 3 FP64,
+ * row-major.  host != 0: out is host memory (synchronises); else device memory.
+ * max_rows bounds the rows written; *rows receives the rows available. */
+int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* rows, int host);
+
+/* State of trajectory 0: drho (N c128, host) = compensated sum + carry, the carry alone
+ * (N c128, the low-order part kept by the compensated RK4 accumulation; may be NULL) and
+ * the steps taken since the last reset.  set_state installs them (carry NULL = zero);
+ * get_state followed by set_state resumes a run bit for bit.  Synchronises. */
+int tdagw_get_state(tdagw_ctx* ctx, double* drho, double* carry, int64_t* step);
+int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int64_t step);
+
+/* Wait for all work queued on the context's stream. */
+int tdagw_sync(tdagw_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* tdagw_last_error(void);
+
+void tdagw_destroy(tdagw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDAGW_H */

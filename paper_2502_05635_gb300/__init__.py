@@ -1,0 +1,261 @@
+"""Python binding of the GB300 TD-aGW library (libtdagw.so, C ABI in include/tdagw.h).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels.  The
+module-level functions carry the C names one-to-one; ``Context`` is a small convenience
+wrapper over them.  Host arrays are numpy (complex128 / float64, C-contiguous); device
+arrays are torch CUDA tensors (passed by data pointer).  There is no fallback: if the
+library is missing, importing the names works but every call raises ``TdagwError``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdagw.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_BUILT, ERR_NO_FACTORS, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+C64, C128 = 0, 1
+FULL, LOWRANK = 0, 1
+FIELD_GAUSS_COS, FIELD_CONST, FIELD_SIN2_SIN, FIELD_TABLE = 0, 1, 2, 3
+FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN = 1, 2, 4
+
+
+class TdagwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tdagw error {code}: {msg}")
+        self.code = code
+
+
+class ModelDesc(ct.Structure):
+    _fields_ = [("L", ct.c_int), ("nb_copies", ct.c_int), ("offsets", ct.c_double * 4),
+                ("Delta", ct.c_double), ("t", ct.c_double), ("m", ct.c_double),
+                ("a", ct.c_double), ("r0", ct.c_double), ("dtype", ct.c_int)]
+
+
+class Field(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("E0", ct.c_double), ("omega", ct.c_double),
+                ("t0", ct.c_double), ("sigma", ct.c_double), ("T_pulse", ct.c_double),
+                ("dir_x", ct.c_double), ("dir_y", ct.c_double),
+                ("table", ct.POINTER(ct.c_double))]
+
+
+_P = ct.c_void_p
+_D = ct.POINTER(ct.c_double)
+_I64 = ct.POINTER(ct.c_int64)
+_SIGS = {
+    "tdagw_create": [ct.POINTER(ModelDesc), _P, ct.POINTER(_P)],
+    "tdagw_build_kernel": [_P],
+    "tdagw_model_info": [_P, _I64, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
+    "tdagw_get_model": [_P, _D, _D, _D, _D, _D],
+    "tdagw_get_kernel_entries": [_P, _I64, _I64, ct.c_int64, _D],
+    "tdagw_compress_svd": [_P, ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, ct.c_int],
+    "tdagw_set_factors": [_P, ct.c_int, _D, _D, _D, _D],
+    "tdagw_get_factors": [_P, ct.POINTER(ct.c_int), _D, _D, _D, _D],
+    "tdagw_apply": [_P, ct.c_int, _P, _P],
+    "tdagw_propagate": [_P, ct.POINTER(Field), ct.c_int, ct.POINTER(ct.c_int), ct.c_double,
+                        ct.c_int, ct.c_int],
+    "tdagw_observables": [_P, _D, ct.c_int64, _I64, ct.c_int],
+    "tdagw_get_state": [_P, _D, _D, _I64],
+    "tdagw_set_state": [_P, _D, _D, ct.c_int64],
+    "tdagw_sync": [_P],
+}
+EXPORTED = sorted(list(_SIGS) + ["tdagw_last_error", "tdagw_destroy"])
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """Load libtdagw.so (built by build.py / __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise TdagwError(ERR_UNSUPPORTED, f"{LIB_PATH} not built; run build.py")
+        L = ct.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ct.c_int
+        L.tdagw_last_error.argtypes = []
+        L.tdagw_last_error.restype = ct.c_char_p
+        L.tdagw_destroy.argtypes = [_P]
+        L.tdagw_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise TdagwError(rc, lib().tdagw_last_error().decode())
+
+
+def _dptr(a):
+    """double* of a C-contiguous numpy float64/complex128 array (or None)."""
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"] and a.dtype in (np.float64, np.complex128)
+    return a.ctypes.data_as(_D)
+
+
+def _devptr(t) -> int:
+    if not t.is_cuda:
+        raise TdagwError(ERR_INVALID_ARG, "expected a CUDA tensor")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- one-to-one names ------
+
+def tdagw_create(desc: ModelDesc, stream: int | None = None) -> int:
+    h = _P()
+    _check(lib().tdagw_create(ct.byref(desc), _P(stream or 0), ct.byref(h)))
+    return h.value
+
+
+def tdagw_build_kernel(ctx: int):
+    _check(lib().tdagw_build_kernel(_P(ctx)))
+
+
+def tdagw_model_info(ctx: int):
+    n, nb, nk = ct.c_int64(), ct.c_int(), ct.c_int()
+    _check(lib().tdagw_model_info(_P(ctx), ct.byref(n), ct.byref(nb), ct.byref(nk)))
+    return n.value, nb.value, nk.value
+
+
+def tdagw_get_model(ctx: int):
+    N, Nb, Nk = tdagw_model_info(ctx)
+    eps = np.empty(Nk * Nb)
+    dx, dy, vx, U = (np.empty(Nk * Nb * Nb, np.complex128) for _ in range(4))
+    _check(lib().tdagw_get_model(_P(ctx), _dptr(eps), _dptr(dx), _dptr(dy), _dptr(vx), _dptr(U)))
+    sh = (Nk, Nb, Nb)
+    return dict(eps=eps.reshape(Nk, Nb), dx=dx.reshape(sh), dy=dy.reshape(sh),
+                vx=vx.reshape(sh), U=U.reshape(sh))
+
+
+def tdagw_get_kernel_entries(ctx: int, rows, cols) -> np.ndarray:
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.empty(rows.size, np.complex128)
+    _check(lib().tdagw_get_kernel_entries(_P(ctx), rows.ctypes.data_as(_I64),
+                                          cols.ctypes.data_as(_I64), rows.size, _dptr(out)))
+    return out
+
+
+def tdagw_compress_svd(ctx: int, rank: int, oversample: int = 64, power_iters: int = 2,
+                       seed: int = 1, precision: int = 0):
+    _check(lib().tdagw_compress_svd(_P(ctx), rank, oversample, power_iters, seed, precision))
+
+
+def tdagw_set_factors(ctx: int, U, S, V, diag=None):
+    U = np.ascontiguousarray(U, np.complex128)
+    V = np.ascontiguousarray(V, np.complex128)
+    S = np.ascontiguousarray(S, np.float64)
+    d = None if diag is None else np.ascontiguousarray(diag, np.complex128)
+    _check(lib().tdagw_set_factors(_P(ctx), U.shape[1], _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
+
+
+def tdagw_get_factors(ctx: int):
+    N = tdagw_model_info(ctx)[0]
+    r = ct.c_int()
+    _check(lib().tdagw_get_factors(_P(ctx), ct.byref(r), None, None, None, None))
+    r = r.value
+    U = np.empty((N, r), np.complex128)
+    V = np.empty((N, r), np.complex128)
+    S = np.empty(r)
+    d = np.empty(N, np.complex128)
+    _check(lib().tdagw_get_factors(_P(ctx), None, _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
+    return U, S, V, d
+
+
+def tdagw_apply(ctx: int, mode: int, x, y):
+    _check(lib().tdagw_apply(_P(ctx), mode, _P(_devptr(x)), _P(_devptr(y))))
+
+
+def make_field(pulse, table=None) -> Field:
+    """Field struct from an object with E0, omega, t0, sigma, T_pulse, dir_x, dir_y, kind."""
+    f = Field(kind=int(pulse.kind), E0=pulse.E0, omega=pulse.omega, t0=pulse.t0,
+              sigma=pulse.sigma, T_pulse=pulse.T_pulse, dir_x=pulse.dir_x, dir_y=pulse.dir_y)
+    if table is not None:
+        f.kind = FIELD_TABLE
+        f.table = _dptr(table)
+    return f
+
+
+def tdagw_propagate(ctx: int, fields, steps, dt: float, mode: int, flags: int = FLAG_RESET):
+    arr = (Field * len(fields))(*fields)
+    st = (ct.c_int * len(steps))(*[int(s) for s in steps])
+    _check(lib().tdagw_propagate(_P(ctx), arr, len(fields), st, float(dt), mode, flags))
+
+
+def tdagw_observables(ctx: int, out=None) -> np.ndarray:
+    rows = ct.c_int64()
+    _check(lib().tdagw_observables(_P(ctx), None, 0, ct.byref(rows), 1))
+    if out is None:
+        out = np.empty((rows.value, 3))
+    _check(lib().tdagw_observables(_P(ctx), _dptr(out), out.shape[0], ct.byref(rows), 1))
+    return out
+
+
+def tdagw_get_state(ctx: int):
+    N = tdagw_model_info(ctx)[0]
+    drho = np.empty(N, np.complex128)
+    carry = np.empty(N, np.complex128)
+    step = ct.c_int64()
+    _check(lib().tdagw_get_state(_P(ctx), _dptr(drho), _dptr(carry), ct.byref(step)))
+    return drho, carry, step.value
+
+
+def tdagw_set_state(ctx: int, drho, carry=None, step: int = 0):
+    drho = np.ascontiguousarray(drho, np.complex128)
+    c = None if carry is None else np.ascontiguousarray(carry, np.complex128)
+    _check(lib().tdagw_set_state(_P(ctx), _dptr(drho), _dptr(c), int(step)))
+
+
+def tdagw_sync(ctx: int):
+    _check(lib().tdagw_sync(_P(ctx)))
+
+
+def tdagw_last_error() -> str:
+    return lib().tdagw_last_error().decode()
+
+
+def tdagw_destroy(ctx: int):
+    lib().tdagw_destroy(_P(ctx))
+
+
+# ---------------------------------------------------------------- convenience -----------
+
+def model_desc(p, dtype: int = C64) -> ModelDesc:
+    """ModelDesc from an object with L, nb_copies, offsets, Delta, t, m, a, r0."""
+    offs = list(p.offsets) + [0.0] * (4 - len(p.offsets))
+    return ModelDesc(L=p.L, nb_copies=p.nb_copies, offsets=(ct.c_double * 4)(*offs[:4]),
+                     Delta=p.Delta, t=p.t, m=p.m, a=p.a, r0=p.r0, dtype=dtype)
+
+
+class Context:
+    """Owns one library context; methods forward to the tdagw_* functions."""
+
+    def __init__(self, params, dtype: int = C64, stream: int | None = None, build: bool = True):
+        self.h = tdagw_create(model_desc(params, dtype), stream)
+        self.dtype = dtype
+        if build:
+            tdagw_build_kernel(self.h)
+        self.N, self.Nb, self.Nk = tdagw_model_info(self.h)
+
+    def close(self):
+        if self.h:
+            tdagw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def propagate(self, pulse, steps: int, dt: float, mode: int = FULL, flags: int = FLAG_RESET,
+                  table=None) -> np.ndarray:
+        tdagw_propagate(self.h, [make_field(pulse, table)], [steps], dt, mode, flags)
+        return tdagw_observables(self.h)

@@ -1,0 +1,206 @@
+// Shared definitions of the TD-aGW CUDA library: complex arithmetic on float2/double2,
+// error handling, device buffers and the context object behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "tdagw.h"
+
+namespace tdagw {
+
+// ------------------------------------------------------------------ errors -----------
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define TDAGW_CUDA(call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            throw ::tdagw::Error(e_ == cudaErrorMemoryAllocation ? TDAGW_ERR_OOM           \
+                                                                 : TDAGW_ERR_CUDA,         \
+                                 std::string(#call) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                  \
+    } while (0)
+
+#define TDAGW_REQUIRE(cond, code, msg)                                                     \
+    do {                                                                                   \
+        if (!(cond)) throw ::tdagw::Error((code), (msg));                                  \
+    } while (0)
+
+inline void check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        throw Error(TDAGW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ complex ----------
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename R> using cplx_t = typename Cplx<R>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) {
+    return mk(a.x * s, a.y * s);
+}
+// acc + a * b (complex fused multiply-add, 4 real FMAs)
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+// acc + conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cfmac(C a, C b, C acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// ------------------------------------------------------------------ buffers ----------
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void ensure(size_t b) {
+        if (b <= bytes && p) return;
+        release();
+        if (b == 0) return;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            throw Error(e == cudaErrorMemoryAllocation ? TDAGW_ERR_OOM : TDAGW_ERR_CUDA,
+                        "cudaMalloc(" + std::to_string(b) + " B): " + cudaGetErrorString(e));
+        }
+        bytes = b;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------ host model -------
+
+using zd = std::complex<double>;
+
+struct HostModel {
+    int L = 0, Nb = 0, Nk = 0, norb = 0;
+    int64_t N = 0;
+    std::vector<double> eps;     // Nk * Nb
+    std::vector<zd> U;           // Nk * norb * Nb (column n = band n)
+    std::vector<zd> dx, dy, vx;  // Nk * Nb * Nb
+    std::vector<double> Wtab;    // L * L, W at grid offset (di, dj) (minimum image), W0 at 0
+    double W0 = 0.0;
+    double occ[4] = {0, 0, 0, 0};
+    int c1 = 0;
+};
+
+void build_host_model(const tdagw_model_desc& d, HostModel& hm);
+
+// ------------------------------------------------------------------ context ----------
+
+struct Ctx {
+    tdagw_model_desc desc{};
+    cudaStream_t stream = nullptr;
+    HostModel hm;
+    bool built = false;
+    int dtype = TDAGW_C64;
+    size_t csz = 8;  // bytes per complex element
+
+    // model on device (context dtype)
+    DevBuf K, diagK, dx, dy, vx, gap, Ud, Wd;
+    // low-rank factors: U (N x r), Vh = V^H (r x N), S (r, real of the dtype)
+    DevBuf U, Vh, S, diagF;
+    int rank = 0;
+    // propagation state (trajectory 0): compensated sum (Ssum + Ccomp), stage input X,
+    // RK4 accumulator, dSigma, low-rank partials and projected vector
+    DevBuf Ssum, Ccomp, X, acc, dS, ypart, ytil;
+    DevBuf Etab, obs, red, counter, stepctr;
+    int64_t step = 0;        // steps completed since the last reset
+    int64_t obs_rows = 0;    // rows recorded by the last propagate
+    int ysplit = 1;          // number of partial sums of V^H x
+
+    // CUDA graph of a chunk of RK4 steps
+    cudaGraphExec_t graph = nullptr;
+    int graph_key_mode = -1, graph_key_steps = -1, graph_key_kahan = -1;
+    const void* graph_key_etab = nullptr;
+    ~Ctx() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+};
+
+// Number of column ranges of the split V^H x product: enough blocks of four rows to fill
+// the GPU twice over, each range at least 1024 columns wide.
+inline int choose_ysplit(int r, int64_t N) {
+    const int64_t rgs = (r + 3) / 4;
+    int64_t sp = (2 * 152 * 8 + rgs - 1) / rgs;
+    const int64_t cap = N / 1024 > 1 ? N / 1024 : 1;
+    sp = sp < cap ? sp : cap;
+    sp = sp > 64 ? 64 : sp;
+    return sp < 1 ? 1 : (int)sp;
+}
+
+// ------------------------------------------------------------------ launchers --------
+
+template <typename R>
+void launch_build_kernel(const Ctx& c, cudaStream_t s);
+template <typename R>
+void launch_gather_entries(const Ctx& c, const int64_t* rows, const int64_t* cols, int64_t n,
+                           double2* out, cudaStream_t s);
+// y[row] (+ diag[row] * xd[row]) = sum_j A[row, j] x[j] for rows [0, nrows); with nsplit > 1
+// the columns are split and out holds nsplit partial vectors (no diag term then).
+template <typename R>
+void launch_gemv(const void* A, int64_t lda, int64_t nrows, int64_t ncols, const void* x,
+                 void* out, int nsplit, const void* diag, const void* xd, cudaStream_t s);
+template <typename R>
+void launch_yreduce(const void* part, int nsplit, int r, const void* S, void* ytil,
+                    cudaStream_t s);
+template <typename R>
+void launch_stage(Ctx& c, int stage, double dt, double dirx, double diry, bool kahan,
+                  cudaStream_t s);
+template <typename R>
+void launch_observables_row(Ctx& c, const void* X, int64_t row, cudaStream_t s);
+void launch_field_table(const tdagw_field& f, double t_start, double dt, int64_t nsamp,
+                        double* out, cudaStream_t s);
+template <typename R>
+void launch_convert_in(const double2* src, void* dst, int64_t n, cudaStream_t s);
+template <typename R>
+void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s);
+
+template <typename R>
+void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed);
+
+}  // namespace tdagw

@@ -1,0 +1,177 @@
+// Device construction of the dense direct kernel (Eq. bse-direct-def for the lattice model),
+// sampled reads of it, precision conversions at the boundary, and the pulse sample table.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace tdagw {
+
+namespace {
+
+constexpr int kBuildThreads = 128;
+
+// One thread per (k, k') pair of grid points: it forms the Nb x Nb overlap
+// O = U_k^+ U_k' in FP64 and writes the Nb^2 x Nb^2 block
+//   K[(k n m), (k' n' m')] = -W(k - k') O[n][n'] conj(O[m][m'])
+// row by row; consecutive threads hold consecutive k', so each row segment of the block
+// (Nb^2 complex) is adjacent to its neighbour's and the stores coalesce.
+template <typename R, int NB>
+__global__ void __launch_bounds__(kBuildThreads)
+build_kernel_kernel(const double2* __restrict__ U, const double* __restrict__ Wtab, int L,
+                    int Nk, cplx_t<R>* __restrict__ K) {
+    using C = cplx_t<R>;
+    constexpr int NB2 = NB * NB;
+    __shared__ double2 Uk[NB * NB];
+    const int k = blockIdx.y;
+    const int kp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x < NB * NB) Uk[threadIdx.x] = U[(size_t)k * NB * NB + threadIdx.x];
+    __syncthreads();
+    if (kp >= Nk) return;
+    double2 Ukp[NB * NB];
+#pragma unroll
+    for (int i = 0; i < NB * NB; ++i) Ukp[i] = U[(size_t)kp * NB * NB + i];
+    // U layout: [k][orbital][band]
+    double2 O[NB][NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+#pragma unroll
+        for (int np = 0; np < NB; ++np) {
+            double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int o = 0; o < NB; ++o) s = cfmac(Uk[o * NB + n], Ukp[o * NB + np], s);
+            O[n][np] = s;
+        }
+    int di = (k / L) - (kp / L), dj = (k % L) - (kp % L);
+    di += di < 0 ? L : 0;
+    dj += dj < 0 ? L : 0;
+    const double w = -Wtab[di * L + dj];
+    const int64_t N = (int64_t)Nk * NB2;
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            C* row = K + ((int64_t)k * NB2 + n * NB + m) * N + (int64_t)kp * NB2;
+#pragma unroll
+            for (int np = 0; np < NB; ++np)
+#pragma unroll
+                for (int mp = 0; mp < NB; ++mp) {
+                    const double2 v = cscale(cmulc(O[n][np], O[m][mp]), w);
+                    row[np * NB + mp] = mk((R)v.x, (R)v.y);
+                }
+        }
+}
+
+template <typename R>
+__global__ void gather_kernel(const cplx_t<R>* __restrict__ K, int64_t N,
+                              const int64_t* __restrict__ rows, const int64_t* __restrict__ cols,
+                              int64_t n, double2* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const cplx_t<R> v = K[rows[i] * N + cols[i]];
+    out[i] = make_double2((double)v.x, (double)v.y);
+}
+
+template <typename R>
+__global__ void convert_in_kernel(const double2* __restrict__ src, cplx_t<R>* __restrict__ dst,
+                                  int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = mk((R)src[i].x, (R)src[i].y);
+}
+
+template <typename R>
+__global__ void convert_out_kernel(const cplx_t<R>* __restrict__ src, double2* __restrict__ dst,
+                                   int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = make_double2((double)src[i].x, (double)src[i].y);
+}
+
+// E(t_start + j dt / 2) for j < nsamp: every RK4 stage time of the run (Algorithm: the
+// stage times of classical RK4 are t_n, t_n + dt/2 (twice) and t_n + dt).
+__global__ void field_table_kernel(int kind, double E0, double omega, double t0, double sigma,
+                                   double Tp, double t_start, double dt, int64_t nsamp,
+                                   double* __restrict__ out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nsamp) return;
+    const double t = t_start + 0.5 * dt * (double)j;
+    double e = 0.0;
+    if (kind == TDAGW_FIELD_GAUSS_COS) {
+        const double u = t - t0;
+        e = E0 * exp(-(u * u) / (2.0 * sigma * sigma)) * cos(omega * t);
+    } else if (kind == TDAGW_FIELD_CONST) {
+        e = E0;
+    } else if (kind == TDAGW_FIELD_SIN2_SIN) {
+        if (t >= 0.0 && t <= Tp) {
+            const double s = sin(3.14159265358979323846 * t / Tp);
+            e = E0 * s * s * sin(omega * t);
+        }
+    }
+    out[j] = e;
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+template <typename R>
+void launch_build_kernel(const Ctx& c, cudaStream_t s) {
+    const HostModel& hm = c.hm;
+    dim3 grid((hm.Nk + kBuildThreads - 1) / kBuildThreads, hm.Nk);
+    auto* K = c.K.as<cplx_t<R>>();
+    if (hm.Nb == 2)
+        build_kernel_kernel<R, 2><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(),
+                                                                 c.Wd.as<double>(), hm.L, hm.Nk, K);
+    else
+        build_kernel_kernel<R, 4><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(),
+                                                                 c.Wd.as<double>(), hm.L, hm.Nk, K);
+    check_launch("build_kernel_kernel");
+}
+
+template <typename R>
+void launch_gather_entries(const Ctx& c, const int64_t* rows, const int64_t* cols, int64_t n,
+                           double2* out, cudaStream_t s) {
+    if (n <= 0) return;
+    gather_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.K.as<cplx_t<R>>(), c.hm.N,
+                                                                  rows, cols, n, out);
+    check_launch("gather_kernel");
+}
+
+template <typename R>
+void launch_convert_in(const double2* src, void* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    convert_in_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(src, static_cast<cplx_t<R>*>(dst), n);
+    check_launch("convert_in_kernel");
+}
+
+template <typename R>
+void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    convert_out_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const cplx_t<R>*>(src),
+                                                            dst, n);
+    check_launch("convert_out_kernel");
+}
+
+void launch_field_table(const tdagw_field& f, double t_start, double dt, int64_t nsamp,
+                        double* out, cudaStream_t s) {
+    field_table_kernel<<<(unsigned)((nsamp + 255) / 256), 256, 0, s>>>(
+        f.kind, f.E0, f.omega, f.t0, f.sigma, f.T_pulse, t_start, dt, nsamp, out);
+    check_launch("field_table_kernel");
+}
+
+#define INST(R)                                                                            \
+    template void launch_build_kernel<R>(const Ctx&, cudaStream_t);                        \
+    template void launch_gather_entries<R>(const Ctx&, const int64_t*, const int64_t*,     \
+                                           int64_t, double2*, cudaStream_t);               \
+    template void launch_convert_in<R>(const double2*, void*, int64_t, cudaStream_t);      \
+    template void launch_convert_out<R>(const void*, double2*, int64_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace tdagw

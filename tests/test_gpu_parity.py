@@ -1,0 +1,328 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Small grids span several GEMV tiles and a ragged tail (N = 400, 576, 1296, 2304); the
+full mos2-size grid (N = 20736) is checked on sampled entries, sampled rows, and on a
+propagation prefix against the oracle's FFT form of K.x (pinned to the dense K on small
+grids).  Tolerances: c128 path 1e-10 (rounding only), c64 path 1e-5 relative L2 on P(t)
+(the FP32 bar of the method), applies 2e-6 relative max error (FP32 GEMV of N terms).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import kernel as ok
+from oracle import lowrank as olr
+from oracle import model as om
+from oracle import propagate as op
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2502_05635_gb300 as tg  # noqa: E402
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ctx(p, dtype):
+    return tg.Context(p, dtype, stream=_stream())
+
+
+def _tensor(x, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    return (t.to(torch.complex64) if dtype == tg.C64 else t).cuda()
+
+
+GRIDS = [(5, 2), (12, 1), (9, 2), (24, 1)]   # N = 400, 576, 1296, 2304
+
+
+@pytest.fixture(scope="module", params=GRIDS, ids=lambda g: f"L{g[0]}nb{2 * g[1]}")
+def grid(request):
+    L, nc = request.param
+    p = wl.small_model(L, nc)
+    mdl = om.Model(p)
+    return p, mdl, ok.dense_kernel(mdl)
+
+
+# ---------------------------------------------------------------- model + kernel -------
+
+def test_model_matches_oracle(grid):
+    p, mdl, _ = grid
+    c = _ctx(p, tg.C128)
+    m = tg.tdagw_get_model(c.h)
+    np.testing.assert_allclose(m["eps"], mdl.eps, atol=1e-14)
+    np.testing.assert_allclose(m["U"], mdl.U, atol=1e-14)
+    for key, ref in (("dx", mdl.dx), ("dy", mdl.dy), ("vx", mdl.vx)):
+        np.testing.assert_allclose(m[key], ref, atol=1e-9, err_msg=key)
+
+
+@pytest.mark.parametrize("dtype", [tg.C64, tg.C128])
+def test_kernel_entries(grid, dtype):
+    p, mdl, K = grid
+    c = _ctx(p, dtype)
+    rng = np.random.default_rng(1)
+    r = rng.integers(0, mdl.N, 4000)
+    cc = rng.integers(0, mdl.N, 4000)
+    r = np.concatenate([r, np.arange(mdl.N)])          # the whole diagonal too
+    cc = np.concatenate([cc, np.arange(mdl.N)])
+    got = tg.tdagw_get_kernel_entries(c.h, r, cc)
+    tol = 1e-15 if dtype == tg.C128 else 2e-7
+    assert np.abs(got - K[r, cc]).max() <= tol * np.abs(K).max()
+
+
+@pytest.mark.parametrize("dtype", [tg.C64, tg.C128])
+def test_apply_full(grid, dtype):
+    p, mdl, K = grid
+    c = _ctx(p, dtype)
+    x = wl.random_state(mdl.N, 9)
+    y = torch.empty_like(_tensor(x, dtype))
+    tg.tdagw_apply(c.h, tg.FULL, _tensor(x, dtype), y)
+    torch.cuda.synchronize()
+    ref = K @ x
+    err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < (1e-13 if dtype == tg.C128 else 2e-6), err
+
+
+@pytest.mark.parametrize("dtype", [tg.C64, tg.C128])
+@pytest.mark.parametrize("rank", [1, 7, 64])
+def test_apply_lowrank(grid, dtype, rank):
+    p, mdl, K = grid
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, rank)
+    c = _ctx(p, dtype)
+    tg.tdagw_set_factors(c.h, U, S, V, d)
+    x = wl.random_state(mdl.N, 4)
+    y = torch.empty_like(_tensor(x, dtype))
+    tg.tdagw_apply(c.h, tg.LOWRANK, _tensor(x, dtype), y)
+    torch.cuda.synchronize()
+    ref = olr.apply_lowrank(d, U, S, V, x)
+    err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < (1e-13 if dtype == tg.C128 else 2e-6), err
+    U2, S2, V2, d2 = tg.tdagw_get_factors(c.h)
+    tol = 1e-15 if dtype == tg.C128 else 1e-7
+    assert np.abs(U2 - U).max() < tol and np.abs(V2 - V).max() < tol
+    assert np.abs(S2 - S).max() < tol * S.max()
+
+
+# ---------------------------------------------------------------- propagation ----------
+
+@pytest.fixture(scope="module")
+def cfg0():
+    w = wl.tiny_nb2_l12()
+    mdl = om.Model(w.model)
+    K = ok.dense_kernel(mdl)
+    s = op.half_step_samples(w.pulses[0], w.dt, w.steps[0])
+    ref, xT = op.rk4(mdl, lambda v: K @ v, s, w.dt, w.steps[0])
+    return w, mdl, K, ref, xT
+
+
+@pytest.mark.parametrize("dtype,tol", [(tg.C128, 1e-10), (tg.C64, 1e-5)])
+def test_propagate_full_cfg0(cfg0, dtype, tol):
+    """The 2000-step, 12 x 12 two-band trajectory: P, J, occupation vs the oracle."""
+    w, mdl, K, ref, xT = cfg0
+    c = _ctx(w.model, dtype)
+    got = c.propagate(w.pulses[0], w.steps[0], w.dt, tg.FULL)
+    assert got.shape == ref.shape
+    for j in range(3):
+        e = op.rel_l2(got[:, j], ref[:, j])
+        assert e < tol, (j, e)
+    drho, _, step = tg.tdagw_get_state(c.h)
+    assert step == w.steps[0]
+    assert np.abs(drho - xT).max() < tol * 10 * np.abs(xT).max()
+
+
+@pytest.mark.parametrize("dtype,tol", [(tg.C128, 1e-10), (tg.C64, 1e-5)])
+def test_propagate_lowrank_cfg0(cfg0, dtype, tol):
+    """Low-rank path with the oracle's exact factors at 5% rank, same factors both sides."""
+    w, mdl, K, _, _ = cfg0
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, 29)
+    s = op.half_step_samples(w.pulses[0], w.dt, w.steps[0])
+    ref, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), s, w.dt, w.steps[0])
+    c = _ctx(w.model, dtype)
+    tg.tdagw_set_factors(c.h, U, S, V, d)
+    got = c.propagate(w.pulses[0], w.steps[0], w.dt, tg.LOWRANK)
+    for j in range(3):
+        assert op.rel_l2(got[:, j], ref[:, j]) < tol
+
+
+def test_graph_and_stagewise_launches_agree(cfg0):
+    w = cfg0[0]
+    c = _ctx(w.model, tg.C64)
+    a = c.propagate(w.pulses[0], 300, w.dt, tg.FULL)
+    b = c.propagate(w.pulses[0], 300, w.dt, tg.FULL, flags=tg.FLAG_RESET | tg.FLAG_NO_GRAPH)
+    assert np.array_equal(a, b)
+
+
+def test_resume_is_bitwise(cfg0):
+    """get_state / set_state between two halves reproduces the uninterrupted run exactly."""
+    w = cfg0[0]
+    c = _ctx(w.model, tg.C64)
+    full = c.propagate(w.pulses[0], 400, w.dt, tg.FULL)
+    first = c.propagate(w.pulses[0], 170, w.dt, tg.FULL)
+    drho, carry, step = tg.tdagw_get_state(c.h)
+    c2 = _ctx(w.model, tg.C64)
+    tg.tdagw_set_state(c2.h, drho, carry, step)
+    second = c2.propagate(w.pulses[0], 230, w.dt, tg.FULL, flags=0)
+    assert np.array_equal(first, full[:171])
+    assert np.array_equal(second, full[170:])
+
+
+def test_kahan_reduces_accumulation_error(cfg0):
+    w, _, _, ref, _ = cfg0
+    c = _ctx(w.model, tg.C64)
+    e_k = op.rel_l2(c.propagate(w.pulses[0], w.steps[0], w.dt, tg.FULL)[:, 0], ref[:, 0])
+    e_p = op.rel_l2(c.propagate(w.pulses[0], w.steps[0], w.dt, tg.FULL,
+                                flags=tg.FLAG_RESET | tg.FLAG_NO_KAHAN)[:, 0], ref[:, 0])
+    assert e_k <= e_p
+
+
+def test_zero_steps_and_zero_field():
+    p = wl.small_model(4, 2)
+    c = _ctx(p, tg.C64)
+    o = c.propagate(wl.Pulse(), 0, 0.2, tg.FULL)
+    assert o.shape == (1, 3) and np.all(o == 0)
+    o = c.propagate(wl.Pulse(E0=0.0), 50, 0.2, tg.FULL)
+    assert np.all(o == 0)
+
+
+def test_single_k_rabi_closed_form():
+    """Nk = 1 under a constant field: the GPU c128 path meets the closed form to O(dt^4)."""
+    import scipy.linalg
+    p = wl.small_model(1, 1)
+    mdl = om.Model(p)
+    c = _ctx(p, tg.C128)
+    E, dt, T = 0.01, 0.1, 400
+    c.propagate(wl.Pulse(E0=E, kind=1), T, dt, tg.FULL)
+    drho, _, _ = tg.tdagw_get_state(c.h)
+    W0 = -ok.dense_kernel(mdl)[0, 0].real
+    rho0 = mdl.rho0()[0]
+    Ut = scipy.linalg.expm(-1j * (np.diag(mdl.eps[0]) + E * mdl.dx[0] + W0 * rho0) * (T * dt))
+    exact = Ut @ rho0 @ Ut.conj().T
+    assert np.abs(rho0 + drho.reshape(2, 2) - exact).max() < 1e-7
+
+
+def test_table_field_matches_analytic(cfg0):
+    w = cfg0[0]
+    c = _ctx(w.model, tg.C64)
+    a = c.propagate(w.pulses[0], 200, w.dt, tg.FULL)
+    tab = op.half_step_samples(w.pulses[0], w.dt, 200)
+    b = c.propagate(w.pulses[0], 200, w.dt, tg.FULL, table=tab)
+    assert op.rel_l2(b[:, 0], a[:, 0]) < 1e-6
+
+
+def test_error_codes_on_device():
+    p = wl.small_model(4, 1)
+    c = _ctx(p, tg.C64)
+    with pytest.raises(tg.TdagwError) as e:
+        c.propagate(wl.Pulse(), 10, 0.2, tg.LOWRANK)
+    assert e.value.code == tg.ERR_NO_FACTORS
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_compress_svd(c.h, 10, 64, 2)     # rank + oversample > N = 64
+    assert e.value.code == tg.ERR_INVALID_ARG
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_get_kernel_entries(c.h, [0], [10 ** 9])
+    assert e.value.code == tg.ERR_INVALID_ARG
+    h = tg.tdagw_create(tg.model_desc(p), _stream())
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_propagate(h, [tg.make_field(wl.Pulse())], [5], 0.2, tg.FULL)
+    assert e.value.code == tg.ERR_NOT_BUILT
+    tg.tdagw_destroy(h)
+
+
+# ---------------------------------------------------------------- randomised SVD -------
+
+@pytest.mark.parametrize("dtype", [tg.C64, tg.C128])
+def test_rsvd_near_optimal(dtype):
+    """GPU randomised SVD (p = 64, q = 2): singular values and truncation error vs LAPACK."""
+    p = wl.small_model(12, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    sv = olr.singular_values(Koff)
+    c = _ctx(p, dtype)
+    r = 29
+    tg.tdagw_compress_svd(c.h, r, 64, 2, 1)
+    U, S, V, d2 = tg.tdagw_get_factors(c.h)
+    np.testing.assert_allclose(S, sv[:r], rtol=1e-5 if dtype == tg.C64 else 1e-9)
+    err = np.linalg.norm(Koff - (U * S) @ V.conj().T)
+    opt = np.sqrt(np.sum(sv[r:] ** 2))
+    assert err <= 1.01 * opt + 1e-6 * np.linalg.norm(Koff)
+    np.testing.assert_allclose(np.abs(U.conj().T @ U), np.eye(r), atol=1e-5 if dtype == tg.C64 else 1e-12)
+
+
+def test_rsvd_propagation_within_truncation_error(cfg0):
+    """err(GPU low-rank vs oracle full) <= 1.1 err(oracle exact-SVD low-rank vs full) + 1e-5."""
+    w, mdl, K, ref, _ = cfg0
+    d, Koff = ok.split_diag_off(K)
+    r = 29
+    U, S, V = olr.truncated_svd(Koff, r)
+    s = op.half_step_samples(w.pulses[0], w.dt, w.steps[0])
+    lr, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), s, w.dt, w.steps[0])
+    e_opt = op.rel_l2(lr[:, 0], ref[:, 0])
+    c = _ctx(w.model, tg.C64)
+    tg.tdagw_compress_svd(c.h, r, 64, 2, 1)
+    got = c.propagate(w.pulses[0], w.steps[0], w.dt, tg.LOWRANK)
+    assert op.rel_l2(got[:, 0], ref[:, 0]) <= 1.1 * e_opt + 1e-5
+
+
+# ---------------------------------------------------------------- full size ------------
+
+@pytest.fixture(scope="module")
+def big():
+    w = wl.mos2size_nb4_l36()
+    mdl = om.Model(w.model)
+    c = _ctx(w.model, tg.C64)
+    return w, mdl, c
+
+
+def test_full_size_kernel_and_apply_rows(big):
+    w, mdl, c = big
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, mdl.N, 24)
+    for r in rows:
+        cols = rng.integers(0, mdl.N, 64)
+        got = tg.tdagw_get_kernel_entries(c.h, np.full(64, r), cols)
+        ref = ok.kernel_row(mdl, int(r))[cols]
+        assert np.abs(got - ref).max() <= 2e-7 * np.abs(ref).max() + 1e-12
+    x = wl.random_state(mdl.N, 2)
+    y = torch.empty(mdl.N, dtype=torch.complex64, device="cuda")
+    tg.tdagw_apply(c.h, tg.FULL, _tensor(x, tg.C64), y)
+    yh = y.cpu().numpy()
+    full = ok.apply_fft(mdl, x)
+    assert np.abs(yh - full).max() < 2e-6 * np.abs(full).max()
+    for r in rows:
+        assert abs(yh[r] - ok.kernel_row(mdl, int(r)) @ x) < 2e-6 * np.abs(full).max()
+
+
+def test_full_size_propagation_prefix(big):
+    """N = 20736, dense 3.4 GB kernel, graph-captured path of the benchmark: 400 steps vs
+    the oracle's FFT form of the same kernel."""
+    w, mdl, c = big
+    T = 400
+    s = op.half_step_samples(w.pulses[0], w.dt, T)
+    ref, _ = op.rk4(mdl, ok.fft_applier(mdl), s, w.dt, T)
+    got = c.propagate(w.pulses[0], T, w.dt, tg.FULL)
+    for j in range(3):
+        assert op.rel_l2(got[:, j], ref[:, j]) < 1e-5, j
+
+
+def test_full_size_lowrank_rsvd(big):
+    """rank 1024 randomised SVD at N = 20736, then low-rank propagation vs the oracle run
+    with the same (exported) factors, 60 steps."""
+    w, mdl, c = big
+    tg.tdagw_compress_svd(c.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    U, S, V, d = tg.tdagw_get_factors(c.h)
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, w.rank, 8)
+    # sampled columns are orthonormal and the factors reproduce K^off on sampled entries
+    assert np.abs(U[:, idx].conj().T @ U[:, idx] - np.eye(8)).max() < 1e-5
+    T = 60
+    s = op.half_step_samples(w.pulses[0], w.dt, T)
+    ref, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), s, w.dt, T)
+    got = c.propagate(w.pulses[0], T, w.dt, tg.LOWRANK)
+    assert op.rel_l2(got[:, 0], ref[:, 0]) < 1e-5
