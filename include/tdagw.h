@@ -86,8 +86,10 @@ typedef struct {
     const double* table;  /* kind TABLE: host array of 2*steps+1 samples, else NULL       */
 } tdagw_field;
 
-/* Create a context for one model.  stream: a cudaStream_t (may be NULL for the legacy
- * default stream).  *out receives the context.  Allocates nothing on the device yet. */
+/* Create a context for one model.  stream: the cudaStream_t all work of this context is
+ * ordered on (NULL = the legacy default stream; CUDA graphs are captured on a private
+ * stream and launched on this one).  *out receives the context.  Allocates nothing on
+ * the device yet. */
 int tdagw_create(const tdagw_model_desc* desc, void* stream, tdagw_ctx** out);
 
 /* Build the model (bands, gauge-fixed eigenvectors, dipoles d^x, d^y, velocity v^x) on the

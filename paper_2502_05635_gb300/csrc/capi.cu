@@ -10,7 +10,6 @@
 
 struct tdagw_ctx {
     tdagw::Ctx c;
-    bool own_stream = false;
 };
 
 namespace tdagw {
@@ -240,15 +239,16 @@ template <typename R> void propagate(Ctx& c, const tdagw_field& f, int T, double
     if (!(flags & TDAGW_FLAG_NO_GRAPH) && T >= 2) {
         const int G = std::min(T, 32);
         cudaGraph_t g = nullptr;
-        TDAGW_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        if (!c.cap) TDAGW_CUDA(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
+        TDAGW_CUDA(cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal));
         try {
-            for (int q = 0; q < G; ++q) one_step<R>(c, mode, dt, dirx, diry, kahan, s);
+            for (int q = 0; q < G; ++q) one_step<R>(c, mode, dt, dirx, diry, kahan, c.cap);
         } catch (...) {
-            cudaStreamEndCapture(s, &g);
+            cudaStreamEndCapture(c.cap, &g);
             if (g) cudaGraphDestroy(g);
             throw;
         }
-        TDAGW_CUDA(cudaStreamEndCapture(s, &g));
+        TDAGW_CUDA(cudaStreamEndCapture(c.cap, &g));
         cudaGraphExec_t ge = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
@@ -334,12 +334,7 @@ int tdagw_create(const tdagw_model_desc* desc, void* stream, tdagw_ctx** out) {
         h->c.desc = *desc;
         h->c.dtype = desc->dtype;
         h->c.csz = desc->dtype == TDAGW_C64 ? 8 : 16;
-        if (stream) {
-            h->c.stream = static_cast<cudaStream_t>(stream);
-        } else {
-            TDAGW_CUDA(cudaStreamCreateWithFlags(&h->c.stream, cudaStreamNonBlocking));
-            h->own_stream = true;
-        }
+        h->c.stream = static_cast<cudaStream_t>(stream);  // NULL: legacy default stream
         *out = h.release();
     });
 }
@@ -513,10 +508,7 @@ const char* tdagw_last_error(void) { return g_err.c_str(); }
 void tdagw_destroy(tdagw_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->c.stream);
-    const bool own = ctx->own_stream;
-    cudaStream_t s = ctx->c.stream;
     delete ctx;
-    if (own) cudaStreamDestroy(s);
 }
 
 }  // extern "C"

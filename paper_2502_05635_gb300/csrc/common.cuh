@@ -153,12 +153,11 @@ struct Ctx {
     int64_t obs_rows = 0;    // rows recorded by the last propagate
     int ysplit = 1;          // number of partial sums of V^H x
 
-    // CUDA graph of a chunk of RK4 steps
-    cudaGraphExec_t graph = nullptr;
-    int graph_key_mode = -1, graph_key_steps = -1, graph_key_kahan = -1;
-    const void* graph_key_etab = nullptr;
+    // stream used only to capture CUDA graphs (the caller's stream may be the legacy
+    // default stream, on which capture is not allowed); graphs are launched on `stream`
+    cudaStream_t cap = nullptr;
     ~Ctx() {
-        if (graph) cudaGraphExecDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
     }
 };
 

@@ -145,6 +145,18 @@ def gaussian_sketch(N: int, cols: int, seed: int = SKETCH_SEED) -> np.ndarray:
     return (rng.standard_normal((N, cols)) + 1j * rng.standard_normal((N, cols))) / np.sqrt(2.0)
 
 
+def random_factors(N: int, r: int, seed: int, s0: float = 0.05, decay: float = 3.0):
+    """Seeded synthetic low-rank factors (U, S, V, diag) of kernel-like magnitude:
+    Gaussian columns of norm ~1, S decaying geometrically from s0 by `decay` e-folds,
+    diag constant.  Inputs for parity runs of the low-rank apply; not a decomposition."""
+    rng = np.random.default_rng(seed)
+    U = (rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))) / np.sqrt(2 * N)
+    V = (rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))) / np.sqrt(2 * N)
+    S = s0 * np.exp(-decay * np.arange(r) / max(r, 1))
+    diag = np.full(N, -0.0134 + 0.0j)
+    return U, S, V, diag
+
+
 def as_dict(w: Workload) -> dict:
     d = asdict(w)
     d["N"] = w.model.N
