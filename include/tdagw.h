@@ -57,7 +57,13 @@ enum {
 enum {
     TDAGW_FLAG_RESET = 1,         /* start from drho = 0 and t = 0 (else continue)          */
     TDAGW_FLAG_NO_GRAPH = 2,      /* launch stage by stage instead of replaying a CUDA graph */
-    TDAGW_FLAG_NO_KAHAN = 4       /* plain (uncompensated) RK4 accumulation                 */
+    TDAGW_FLAG_NO_KAHAN = 4,      /* plain (uncompensated) RK4 accumulation                 */
+    TDAGW_FLAG_STAGEWISE = 8,     /* low-rank c64: stage-wise kernels instead of the
+                                     persistent single-launch kernel                        */
+    TDAGW_FLAG_TEST_TIMEOUT = 16  /* fault-injection hook for tests: the persistent kernel's
+                                     grid barrier waits for one block that does not exist,
+                                     every wait runs out a 20 ms budget and the call ends
+                                     with TDAGW_ERR_TIMEOUT at the next synchronising call   */
 };
 
 typedef struct tdagw_ctx tdagw_ctx;
@@ -154,7 +160,9 @@ int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* ro
 int tdagw_get_state(tdagw_ctx* ctx, double* drho, double* carry, int64_t* step);
 int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int64_t step);
 
-/* Wait for all work queued on the context's stream. */
+/* Wait for all work queued on the context's stream.  Reports TDAGW_ERR_TIMEOUT if a bounded
+ * device-side wait of the last propagation gave up (also reported by tdagw_observables to
+ * host memory and tdagw_get_state). */
 int tdagw_sync(tdagw_ctx* ctx);
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -114,22 +114,22 @@ template <typename R> void set_factors(Ctx& c, int r, const double* U, const dou
     cudaStream_t s = c.stream;
     const int64_t N = c.hm.N;
     const int64_t ldu = r + (r & 1);
-    // U: N x ldu (padded, zero pad column), Vh: r x N with Vh[j][i] = conj(V[i][j])
-    std::vector<double2> hu((size_t)N * ldu, make_double2(0, 0)), hv((size_t)r * N);
+    // U and V: N x ldu row-major (padded, zero pad column)
+    std::vector<double2> hu((size_t)N * ldu, make_double2(0, 0)), hv((size_t)N * ldu, make_double2(0, 0));
     for (int64_t i = 0; i < N; ++i)
         for (int j = 0; j < r; ++j) {
             hu[(size_t)i * ldu + j] = make_double2(U[2 * (i * r + j)], U[2 * (i * r + j) + 1]);
-            hv[(size_t)j * N + i] = make_double2(V[2 * (i * r + j)], -V[2 * (i * r + j) + 1]);
+            hv[(size_t)i * ldu + j] = make_double2(V[2 * (i * r + j)], V[2 * (i * r + j) + 1]);
         }
     DevBuf tmp;
-    tmp.ensure(std::max(hu.size(), hv.size()) * sizeof(double2));
+    tmp.ensure(hu.size() * sizeof(double2));
     c.U.ensure(hu.size() * sizeof(C));
     TDAGW_CUDA(cudaMemcpyAsync(tmp.p, hu.data(), hu.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     launch_convert_in<R>(tmp.as<double2>(), c.U.p, (int64_t)hu.size(), s);
     TDAGW_CUDA(cudaStreamSynchronize(s));
-    c.Vh.ensure(hv.size() * sizeof(C));
+    c.V.ensure(hv.size() * sizeof(C));
     TDAGW_CUDA(cudaMemcpyAsync(tmp.p, hv.data(), hv.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-    launch_convert_in<R>(tmp.as<double2>(), c.Vh.p, (int64_t)hv.size(), s);
+    launch_convert_in<R>(tmp.as<double2>(), c.V.p, (int64_t)hv.size(), s);
     TDAGW_CUDA(cudaStreamSynchronize(s));
     std::vector<R> hs(r);
     for (int j = 0; j < r; ++j) hs[j] = (R)S[j];
@@ -155,26 +155,18 @@ template <typename R> void get_factors(Ctx& c, double* U, double* S, double* V, 
     cudaStream_t s = c.stream;
     const int64_t N = c.hm.N, r = c.rank, ldu = r + (r & 1);
     DevBuf tmp;
-    tmp.ensure((size_t)std::max(N * ldu, r * N) * sizeof(double2));
-    std::vector<double2> h((size_t)std::max(N * ldu, r * N));
-    if (U) {
-        launch_convert_out<R>(c.U.p, tmp.as<double2>(), N * ldu, s);
+    tmp.ensure((size_t)N * ldu * sizeof(double2));
+    std::vector<double2> h((size_t)N * ldu);
+    for (int which = 0; which < 2; ++which) {
+        double* out = which == 0 ? U : V;
+        if (!out) continue;
+        launch_convert_out<R>(which == 0 ? c.U.p : c.V.p, tmp.as<double2>(), N * ldu, s);
         TDAGW_CUDA(cudaMemcpyAsync(h.data(), tmp.p, N * ldu * sizeof(double2), cudaMemcpyDeviceToHost, s));
         TDAGW_CUDA(cudaStreamSynchronize(s));
         for (int64_t i = 0; i < N; ++i)
             for (int64_t j = 0; j < r; ++j) {
-                U[2 * (i * r + j)] = h[i * ldu + j].x;
-                U[2 * (i * r + j) + 1] = h[i * ldu + j].y;
-            }
-    }
-    if (V) {
-        launch_convert_out<R>(c.Vh.p, tmp.as<double2>(), r * N, s);
-        TDAGW_CUDA(cudaMemcpyAsync(h.data(), tmp.p, r * N * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        TDAGW_CUDA(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < N; ++i)
-            for (int64_t j = 0; j < r; ++j) {
-                V[2 * (i * r + j)] = h[j * N + i].x;
-                V[2 * (i * r + j) + 1] = -h[j * N + i].y;
+                out[2 * (i * r + j)] = h[i * ldu + j].x;
+                out[2 * (i * r + j) + 1] = h[i * ldu + j].y;
             }
     }
     if (S) {
@@ -199,7 +191,7 @@ template <typename R> void apply(Ctx& c, int mode, const void* x, void* y, cudaS
     } else {
         const int r = c.rank;
         const int64_t ldu = r + (r & 1);
-        launch_gemv<R>(c.Vh.p, N, r, N, x, c.ypart.p, c.ysplit, nullptr, nullptr, s);
+        launch_vcols<R>(c.V.p, ldu, N, r, x, c.ypart.p, c.ysplit, s);
         launch_yreduce<R>(c.ypart.p, c.ysplit, r, c.S.p, c.ytil.p, s);
         launch_gemv<R>(c.U.p, ldu, N, r, c.ytil.p, y, 1, c.diagF.p, x, s);
     }
@@ -236,7 +228,10 @@ template <typename R> void propagate(Ctx& c, const tdagw_field& f, int T, double
     const bool kahan = !(flags & TDAGW_FLAG_NO_KAHAN);
     const double dirx = f.dir_x, diry = f.dir_y;
     int done = 0;
-    if (!(flags & TDAGW_FLAG_NO_GRAPH) && T >= 2) {
+    if (mode == TDAGW_LOWRANK && !(flags & TDAGW_FLAG_STAGEWISE) && T > 0 &&
+        launch_lr_persistent(c, T, dt, dirx, diry, kahan, (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0, s))
+        done = T;
+    if (!(flags & TDAGW_FLAG_NO_GRAPH) && T - done >= 2) {
         const int G = std::min(T, 32);
         cudaGraph_t g = nullptr;
         if (!c.cap) TDAGW_CUDA(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
@@ -302,6 +297,18 @@ template <typename R> void set_state(Ctx& c, const double* drho, const double* c
     TDAGW_CUDA(cudaMemcpyAsync(t.p, drho, N * sizeof(double2), cudaMemcpyHostToDevice, s));
     launch_convert_in<R>(t.as<double2>(), c.X.p, N, s);
     TDAGW_CUDA(cudaStreamSynchronize(s));
+}
+
+// After a synchronisation: report (and clear) the error word of a persistent launch.
+void check_device_error(Ctx& c) {
+    if (!c.persistent_launched || !c.sync.p) return;
+    int err = 0;
+    TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        TDAGW_CUDA(cudaMemset(c.sync.as<unsigned>() + 2, 0, sizeof(int)));
+        c.persistent_launched = false;
+        throw Error(TDAGW_ERR_TIMEOUT, "a bounded device-side wait of the propagation gave up");
+    }
 }
 
 void check_desc(const tdagw_model_desc* d) {
@@ -474,7 +481,10 @@ int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* ro
         cudaStream_t s = ctx->c.stream;
         TDAGW_CUDA(cudaMemcpyAsync(out, ctx->c.obs.p, n * 3 * sizeof(double),
                                    host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-        if (host) TDAGW_CUDA(cudaStreamSynchronize(s));
+        if (host) {
+            TDAGW_CUDA(cudaStreamSynchronize(s));
+            check_device_error(ctx->c);
+        }
     });
 }
 
@@ -484,6 +494,7 @@ int tdagw_get_state(tdagw_ctx* ctx, double* drho, double* carry, int64_t* step) 
         require_built(ctx->c);
         if (step) *step = ctx->c.step;
         if (drho || carry) DISPATCH(ctx, get_state, ctx->c, drho, carry);
+        check_device_error(ctx->c);
     });
 }
 
@@ -500,6 +511,7 @@ int tdagw_sync(tdagw_ctx* ctx) {
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
         TDAGW_CUDA(cudaStreamSynchronize(ctx->c.stream));
+        check_device_error(ctx->c);
     });
 }
 

@@ -142,8 +142,9 @@ struct Ctx {
 
     // model on device (context dtype)
     DevBuf K, diagK, dx, dy, vx, gap, Ud, Wd;
-    // low-rank factors: U (N x r), Vh = V^H (r x N), S (r, real of the dtype)
-    DevBuf U, Vh, S, diagF;
+    // low-rank factors K^off ~ U diag(S) V^H: U and V stored N x ldu row-major
+    // (ldu = rank rounded up to even, zero pad column), S (rank, real of the dtype)
+    DevBuf U, V, S, diagF;
     int rank = 0;
     // propagation state (trajectory 0): compensated sum (Ssum + Ccomp), stage input X,
     // RK4 accumulator, dSigma, low-rank partials and projected vector
@@ -153,6 +154,9 @@ struct Ctx {
     int64_t obs_rows = 0;    // rows recorded by the last propagate
     int ysplit = 1;          // number of partial sums of V^H x
 
+    // persistent low-rank launch: partial vectors, grid-barrier words and error flag
+    DevBuf pbuf, sync;
+    bool persistent_launched = false;
     // stream used only to capture CUDA graphs (the caller's stream may be the legacy
     // default stream, on which capture is not allowed); graphs are launched on `stream`
     cudaStream_t cap = nullptr;
@@ -161,15 +165,13 @@ struct Ctx {
     }
 };
 
-// Number of column ranges of the split V^H x product: enough blocks of four rows to fill
-// the GPU twice over, each range at least 1024 columns wide.
+// Row blocks of the stage-wise V^H x pass (each yields one partial vector): two per SM,
+// at least 16 rows each.
 inline int choose_ysplit(int r, int64_t N) {
-    const int64_t rgs = (r + 3) / 4;
-    int64_t sp = (2 * 152 * 8 + rgs - 1) / rgs;
-    const int64_t cap = N / 1024 > 1 ? N / 1024 : 1;
-    sp = sp < cap ? sp : cap;
-    sp = sp > 64 ? 64 : sp;
-    return sp < 1 ? 1 : (int)sp;
+    (void)r;
+    int64_t nb = (N + 15) / 16;
+    nb = nb < 304 ? nb : 304;
+    return nb < 1 ? 1 : (int)nb;
 }
 
 // ------------------------------------------------------------------ launchers --------
@@ -184,6 +186,10 @@ void launch_gather_entries(const Ctx& c, const int64_t* rows, const int64_t* col
 template <typename R>
 void launch_gemv(const void* A, int64_t lda, int64_t nrows, int64_t ncols, const void* x,
                  void* out, int nsplit, const void* diag, const void* xd, cudaStream_t s);
+// part[b][c] = sum over row block b of conj(V[i][c]) x_i, V stored N x ldv (rows)
+template <typename R>
+void launch_vcols(const void* V, int64_t ldv, int64_t N, int r, const void* x, void* part,
+                  int nblocks, cudaStream_t s);
 template <typename R>
 void launch_yreduce(const void* part, int nsplit, int r, const void* S, void* ytil,
                     cudaStream_t s);
@@ -198,6 +204,10 @@ template <typename R>
 void launch_convert_in(const double2* src, void* dst, int64_t n, cudaStream_t s);
 template <typename R>
 void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s);
+
+// Persistent single-trajectory low-rank propagation (complex64); false if not applicable.
+bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
+                          bool test_timeout, cudaStream_t s);
 
 template <typename R>
 void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed);

@@ -3,6 +3,7 @@
 // truncated-SVD form of Eq. svd_acc), and the fused per-k commutator + RK4 stage update +
 // observables kernel (Eq. tdagw).
 #include "common.cuh"
+#include "stage.cuh"
 
 namespace tdagw {
 
@@ -29,13 +30,6 @@ __device__ __forceinline__ void ld2_cached(const float2* p, float2& a, float2& b
 __device__ __forceinline__ void ld2_cached(const double2* p, double2& a, double2& b) {
     a = __ldg(p);
     b = __ldg(p + 1);
-}
-
-template <typename C> __device__ __forceinline__ C shfl(C v, int src) {
-    return mk(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-template <typename C> __device__ __forceinline__ C shfl_xor(C v, int m) {
-    return mk(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
 // ---------------------------------------------------------------- GEMV ---------------
@@ -113,6 +107,31 @@ gemv_kernel(const cplx_t<R>* __restrict__ A, int64_t lda, int64_t nrows, int64_t
     }
 }
 
+// y = V^H x with V stored N x ldu row-major: block (b, cb) accumulates
+//   part[b][c] = sum_{i in rows of b} conj(V[i][c]) x_i
+// for its 512 columns c (two per thread), streaming the rows of V (16 B per thread per
+// row, so a warp reads 256 contiguous bytes).
+template <typename R>
+__global__ void __launch_bounds__(256)
+vcols_kernel(const cplx_t<R>* __restrict__ V, int64_t ldv, int64_t N, int r,
+             const cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ part, int64_t rpb) {
+    using C = cplx_t<R>;
+    const int64_t i0 = blockIdx.x * rpb, i1 = min(N, i0 + rpb);
+    const int64_t c = (int64_t)blockIdx.y * 512 + 2 * threadIdx.x;
+    if (c >= ldv) return;
+    C a0 = mk((R)0, (R)0), a1 = a0;
+#pragma unroll 4
+    for (int64_t i = i0; i < i1; ++i) {
+        C v0, v1;
+        ld2_stream(V + i * ldv + c, v0, v1);
+        const C xi = __ldg(x + i);
+        a0 = cfmac(v0, xi, a0);
+        a1 = cfmac(v1, xi, a1);
+    }
+    if (c < r) part[(int64_t)blockIdx.x * r + c] = a0;
+    if (c + 1 < r) part[(int64_t)blockIdx.x * r + c + 1] = a1;
+}
+
 // ytil[j] = S[j] * sum_s part[s][j]: finishes y = S o (V^H x) of Eq. svd_acc.
 template <typename R>
 __global__ void yreduce_kernel(const cplx_t<R>* __restrict__ part, int nsplit, int r,
@@ -125,52 +144,6 @@ __global__ void yreduce_kernel(const cplx_t<R>* __restrict__ part, int nsplit, i
 }
 
 // ---------------------------------------------------------------- stage --------------
-
-template <typename R> struct GapT { using type = double; };
-template <> struct GapT<float> { using type = float2; };  // (hi, lo) split of eps_n - eps_m
-
-__device__ __forceinline__ float2 gap_times(float2 g, float2 x) {
-    // (hi + lo) x with both products rounded separately: the systematic rounding of the
-    // band gap, which would accumulate as a phase error over many steps, is kept to FP64
-    // level while each product has only a random FP32 rounding
-    return make_float2(fmaf(g.x, x.x, g.y * x.x), fmaf(g.x, x.y, g.y * x.y));
-}
-__device__ __forceinline__ double2 gap_times(double g, double2 x) {
-    return make_double2(g * x.x, g * x.y);
-}
-
-// error-free sum a + b = s + e (Knuth TwoSum)
-template <typename R> __device__ __forceinline__ R two_sum(R a, R b, R& e) {
-    const R s = a + b;
-    const R bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-    return s;
-}
-
-template <typename R>
-struct StageParams {
-    using C = cplx_t<R>;
-    const C* X;       // stage input X_s
-    const C* dS;      // K . X_s
-    const C* dx;
-    const C* dy;
-    const C* vx;
-    const typename GapT<R>::type* gap;
-    C* acc;           // k1 + 2 k2 + 2 k3 (+ k4)
-    C* Ssum;          // state drho_n = Ssum + Ccomp
-    C* Ccomp;
-    C* Xnext;         // next stage input
-    const double* Etab;   // E at half-step times of this call
-    int64_t* step;        // steps done in this call (device counter)
-    double* obs;          // (rows, 3)
-    double* red;          // gridDim.x * 3 block partials
-    unsigned* counter;    // arrival counter of the last-block reduction
-    int64_t N;
-    int Nk, c1;
-    R occ[4];
-    R dt, dirx, diry;
-    int stage, kahan;
-};
 
 // Block partial sums of (P_x, J_x, occ_c1) in FP64, then the last block to arrive adds
 // the partials in block order (deterministic) and stores row `row` of obs.
@@ -231,73 +204,13 @@ __device__ void reduce_observables(double v0, double v1, double v2, double* red,
 // by shuffles.
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) stage_kernel(StageParams<R> p) {
-    using C = cplx_t<R>;
-    constexpr int NB2 = NB * NB;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool act = i < p.N;
-    const int lane = threadIdx.x & 31;
-    const int base = lane - (lane % NB2);
-    const int g = lane % NB2, n = g / NB, m = g % NB;
     const int64_t nstep = *p.step;
     const int eoff = p.stage == 0 ? 0 : (p.stage == 3 ? 2 : 1);
     const R E = (R)p.Etab[2 * nstep + eoff];
-    const C zero = mk((R)0, (R)0);
-    const C X = act ? p.X[i] : zero;
-    const C dS = act ? p.dS[i] : zero;
-    const C dxv = act ? p.dx[i] : zero;
-    const C dyv = act ? p.dy[i] : zero;
-    // M = E(t).d + dSigma (off-diagonal parts of H; the band energies enter via the gap)
-    C M = cadd(dS, mk(E * (p.dirx * dxv.x + p.diry * dyv.x), E * (p.dirx * dxv.y + p.diry * dyv.y)));
-    // [M, rho0 + X]_nm = M_nm (f_m - f_n) + sum_l (M_nl X_lm - X_nl M_lm)
-    C comm = cscale(M, p.occ[m] - p.occ[n]);
-#pragma unroll
-    for (int l = 0; l < NB; ++l) {
-        const C Mnl = shfl(M, base + n * NB + l);
-        const C Xlm = shfl(X, base + l * NB + m);
-        const C Xnl = shfl(X, base + n * NB + l);
-        const C Mlm = shfl(M, base + l * NB + m);
-        comm = cfma(Mnl, Xlm, comm);
-        comm = csub(comm, cmul(Xnl, Mlm));
-    }
-    double o0 = 0.0, o1 = 0.0, o2 = 0.0;
-    if (act) {
-        const C h0 = gap_times(p.gap[i], X);  // [diag(eps), rho0 + X]_nm = (eps_n - eps_m) X_nm
-        const C s = cadd(h0, comm);
-        const C kv = mk(s.y, -s.x);  // -i s
-        const C xs = p.Ssum[i], xc = p.Ccomp[i];
-        C Xn;
-        if (p.stage < 3) {
-            const C a = p.stage == 0 ? kv : cadd(p.acc[i], cscale(kv, (R)2));
-            p.acc[i] = a;
-            const R cn = p.stage == 2 ? p.dt : (R)0.5 * p.dt;
-            Xn = cadd(xs, cadd(xc, cscale(kv, cn)));
-        } else {
-            const C a = cadd(p.acc[i], kv);
-            const C inc = cscale(a, p.dt / (R)6);
-            C ns, nc;
-            if (p.kahan) {
-                R ex, ey;
-                ns.x = two_sum(xs.x, inc.x, ex);
-                ns.y = two_sum(xs.y, inc.y, ey);
-                nc = mk(xc.x + ex, xc.y + ey);
-            } else {
-                ns = cadd(xs, inc);
-                nc = xc;
-            }
-            p.Ssum[i] = ns;
-            p.Ccomp[i] = nc;
-            Xn = cadd(ns, nc);
-            // observables of rho0 + Xn: Re(rho_nm conj(d_nm)) summed = Re Tr(rho d)
-            const C rho = (n == m) ? cadd(Xn, mk(p.occ[n], (R)0)) : Xn;
-            const C vxv = p.vx[i];
-            o0 = (double)rho.x * (double)dxv.x + (double)rho.y * (double)dxv.y;
-            o1 = (double)rho.x * (double)vxv.x + (double)rho.y * (double)vxv.y;
-            o2 = (n == m && n == p.c1) ? (double)rho.x : 0.0;
-        }
-        p.Xnext[i] = Xn;
-    }
+    const Obs3 ob = stage_element<R, NB>(p, i, i < p.N, threadIdx.x & 31, p.stage, E);
     if (p.stage == 3)
-        reduce_observables(o0, o1, o2, p.red, p.counter, p.obs + (nstep + 1) * 3,
+        reduce_observables(ob.p, ob.j, ob.o, p.red, p.counter, p.obs + (nstep + 1) * 3,
                            1.0 / (double)p.Nk, p.step, nstep + 1);
 }
 
@@ -337,6 +250,17 @@ void launch_gemv(const void* A, int64_t lda, int64_t nrows, int64_t ncols, const
         static_cast<const C*>(A), lda, nrows, ncols, static_cast<const C*>(x),
         static_cast<C*>(out), nsplit, static_cast<const C*>(diag), static_cast<const C*>(xd));
     check_launch("gemv_kernel");
+}
+
+template <typename R>
+void launch_vcols(const void* V, int64_t ldv, int64_t N, int r, const void* x, void* part,
+                  int nblocks, cudaStream_t s) {
+    using C = cplx_t<R>;
+    const int64_t rpb = (N + nblocks - 1) / nblocks;
+    dim3 grid((unsigned)nblocks, (unsigned)((ldv + 511) / 512));
+    vcols_kernel<R><<<grid, 256, 0, s>>>(static_cast<const C*>(V), ldv, N, r,
+                                          static_cast<const C*>(x), static_cast<C*>(part), rpb);
+    check_launch("vcols_kernel");
 }
 
 template <typename R>
@@ -405,6 +329,8 @@ void launch_observables_row(Ctx& c, const void* X, int64_t row, cudaStream_t s) 
     template void launch_gemv<R>(const void*, int64_t, int64_t, int64_t, const void*, void*, \
                                  int, const void*, const void*, cudaStream_t);             \
     template void launch_yreduce<R>(const void*, int, int, const void*, void*, cudaStream_t); \
+    template void launch_vcols<R>(const void*, int64_t, int64_t, int, const void*, void*, int, \
+                                  cudaStream_t);                                          \
     template void launch_stage<R>(Ctx&, int, double, double, double, bool, cudaStream_t);   \
     template void launch_observables_row<R>(Ctx&, const void*, int64_t, cudaStream_t);
 INST(float)

@@ -1,0 +1,445 @@
+// Persistent low-rank TD-aGW propagation (single trajectory, complex64): one cooperative
+// launch runs all RK4 steps of a call.  Per stage (Eq. svd_acc applied to Eq. sigma-from-k,
+// inside the RK4 update of Eq. tdagw):
+//
+//   V pass   y_c = sum_{i in rows(c)} conj(V_i) x_i          (each CTA: its row range)
+//   grid barrier; y = sum_c y_c, scaled by S (each CTA: a slice of columns)
+//   grid barrier; U pass  dSigma_i = U_i . (S o y) + K^diag_i x_i  (same row range)
+//   grid barrier; commutator, RK4 stage update, observables (each CTA: a range of k)
+//   grid barrier
+//
+// The factors U and V (N x ldu complex64, row-major) are the only large operands.  Each CTA
+// owns one contiguous row range of both, so its operand stream is two contiguous byte
+// ranges per stage.  A producer warp streams them through a shared-memory ring with 1D
+// TMA bulk copies (cp.async.bulk) completing on mbarriers; sixteen consumer warps compute
+// from shared memory.  The producer never depends on data, so it keeps copies in flight
+// across the grid barriers and HBM stays busy while the barriers resolve.
+//
+// Every wait is bounded (a budget in ns of %globaltimer): on expiry the CTA records an
+// error word, raises its abort flag, stops issuing copies, waits for the copies it has in
+// flight and returns; the host reports TDAGW_ERR_TIMEOUT.
+#include <algorithm>
+
+#include "common.cuh"
+#include "stage.cuh"
+
+namespace tdagw {
+
+namespace {
+
+constexpr int kConsumerWarps = 16;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kThreads = kConsumers + 32;
+constexpr int kSlotTarget = 8192;  // bytes per ring slot (whole rows)
+
+struct LRArgs {
+    const float2* U;
+    const float2* V;
+    const float* S;
+    const float2* diag;
+    StageParams<float> sp;
+    float2* dSw;         // dSigma written by the U pass (sp.dS reads it)
+    float2* part;        // gridDim x ldu partial y vectors
+    float2* ytil;        // ldu, S o y
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+    int64_t N;
+    int Nk, r, ldu, T;
+    int rows_per_slot, nslots, slot_bytes, rows_max;
+    int extra_arrivals;  // > 0 only for the timeout test: the barrier can never complete
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of the given parity; false if the budget ran out or abort was raised
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
+                                          unsigned long long budget) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(b, parity)) return true;
+        if ((i & 63) == 0) {
+            if (abort_s && *abort_s) return false;
+            if (gtimer() - t0 > budget) return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier among the consumer threads of all CTAs (sense by generation count).
+// Returns false (and raises abort) if it could not complete within the budget.
+__device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s) {
+    __threadfence();
+    consumer_sync();
+    if (threadIdx.x == 0 && !*abort_s) {
+        const unsigned need = gridDim.x + (unsigned)a.extra_arrivals;
+        const unsigned g = lgen;
+        if (atomicAdd(a.bar_count, 1u) == need - 1) {
+            atomicExch(a.bar_count, 0u);
+            __threadfence();
+            atomicExch(a.bar_gen, g + 1);
+        } else {
+            const uint64_t t0 = gtimer();
+            while (ld_acquire(a.bar_gen) == g) {
+                if (gtimer() - t0 > a.wait_ns || *(volatile int*)a.err) {
+                    atomicExch(a.err, 1);
+                    *abort_s = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        lgen = g + 1;
+    }
+    consumer_sync();
+    return !*abort_s;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t ra = (int64_t)cta * a.N / G, rb = (int64_t)(cta + 1) * a.N / G;
+    const int nrows = (int)(rb - ra);
+    const int rps = a.rows_per_slot, ns = a.nslots, ldu = a.ldu;
+    const int ntiles = (nrows + rps - 1) / rps;
+
+    unsigned char* ring = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
+    uint64_t* empty = full + ns;
+    float2* ys = reinterpret_cast<float2*>(empty + ns);
+    float2* xs = ys + ldu;
+    double* wred = reinterpret_cast<double*>(xs + a.rows_max);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kConsumerWarps);
+
+    if (tid == 0) {
+        for (int s = 0; s < ns; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kConsumerWarps);
+        }
+        *abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        // ------------------------------------------------------------ producer warp
+        if (lane == 0) {
+            uint64_t q = 0;
+            bool ok = true;
+            for (int n = 0; n < a.T && ok; ++n)
+                for (int st = 0; st < 4 && ok; ++st)
+                    for (int pass = 0; pass < 2 && ok; ++pass) {
+                        const float2* base = (pass == 0 ? a.V : a.U) + ra * ldu;
+                        for (int t = 0; t < ntiles; ++t, ++q) {
+                            const int slot = (int)(q % ns);
+                            if (q >= (uint64_t)ns &&
+                                !mbar_wait(empty + slot, (uint32_t)((q / ns - 1) & 1), abort_s, a.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            const int r0 = t * rps;
+                            const int nr = min(rps, nrows - r0);
+                            const uint32_t bytes = (uint32_t)nr * ldu * 8u;
+                            mbar_expect_tx(full + slot, bytes);
+                            bulk_g2s(ring + (size_t)slot * a.slot_bytes, base + (int64_t)r0 * ldu, bytes,
+                                     full + slot);
+                        }
+                    }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                *abort_s = 1;
+            }
+            // every issued copy must land before the CTA may exit
+            for (uint64_t j = q > (uint64_t)ns ? q - ns : 0; j < q; ++j)
+                mbar_wait(full + (j % ns), (uint32_t)((j / ns) & 1), nullptr, a.wait_ns);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ consumer warps
+        const int64_t ka = (int64_t)cta * a.Nk / G, kb = (int64_t)(cta + 1) * a.Nk / G;
+        const int64_t ea = ka * NB * NB, eb = kb * NB * NB;
+        const int jr0 = (int)((int64_t)cta * a.r / G), jr1 = (int)((int64_t)(cta + 1) * a.r / G);
+        unsigned lgen = 0;
+        uint64_t q = 0;
+        bool ok = true;
+        for (int e = tid; e < nrows; e += kConsumers) xs[e] = __ldcg(a.sp.X + ra + e);
+        consumer_sync();
+        for (int n = 0; n < a.T && ok; ++n) {
+            for (int st = 0; st < 4 && ok; ++st) {
+                // ---- V pass: thread owns column pairs tid, tid + 512 (ldu <= 2048)
+                float2 acc[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+                for (int t = 0; t < ntiles; ++t, ++q) {
+                    const int slot = (int)(q % ns);
+                    if (*abort_s || !mbar_wait(full + slot, (uint32_t)((q / ns) & 1), abort_s, a.wait_ns)) {
+                        *abort_s = 1;
+                        break;
+                    }
+                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)slot * a.slot_bytes);
+                    const int r0 = t * rps, nr = min(rps, nrows - r0);
+                    for (int rr = 0; rr < nr; ++rr) {
+                        const float2 xi = xs[r0 + rr];
+                        const float2* row = tile + (size_t)rr * ldu;
+#pragma unroll
+                        for (int m = 0; m < 2; ++m) {
+                            const int p = tid + m * kConsumers;
+                            if (2 * p < ldu) {
+                                const float4 v = *reinterpret_cast<const float4*>(row + 2 * p);
+                                acc[2 * m] = cfmac(make_float2(v.x, v.y), xi, acc[2 * m]);
+                                acc[2 * m + 1] = cfmac(make_float2(v.z, v.w), xi, acc[2 * m + 1]);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + slot);
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int p = tid + m * kConsumers;
+                    if (2 * p < ldu)
+                        *reinterpret_cast<float4*>(a.part + (size_t)cta * ldu + 2 * p) =
+                            make_float4(acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
+                }
+                if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                // ---- y = S o sum_c y_c for this CTA's columns, fixed summation order
+                for (int j = jr0 + warp; j < jr1; j += kConsumerWarps) {
+                    float2 s = make_float2(0.f, 0.f);
+                    for (int c2 = lane; c2 < G; c2 += 32) s = cadd(s, __ldcg(a.part + (size_t)c2 * ldu + j));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s = cadd(s, shfl_xor(s, o));
+                    if (lane == 0) a.ytil[j] = cscale(s, a.S[j]);
+                }
+                if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
+                consumer_sync();
+                // ---- U pass: warp w takes rows w, w + 16, ... of the range
+                for (int t = 0; t < ntiles; ++t, ++q) {
+                    const int slot = (int)(q % ns);
+                    if (*abort_s || !mbar_wait(full + slot, (uint32_t)((q / ns) & 1), abort_s, a.wait_ns)) {
+                        *abort_s = 1;
+                        break;
+                    }
+                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)slot * a.slot_bytes);
+                    const int r0 = t * rps, nr = min(rps, nrows - r0);
+                    for (int rr = 0; rr < nr; ++rr) {
+                        const int row = r0 + rr;
+                        if ((row % kConsumerWarps) != warp) continue;
+                        const float2* urow = tile + (size_t)rr * ldu;
+                        float2 d = make_float2(0.f, 0.f);
+                        for (int p = lane; 2 * p < ldu; p += 32) {
+                            const float4 u = *reinterpret_cast<const float4*>(urow + 2 * p);
+                            const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
+                            d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
+                            d = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
+                        if (lane == 0) {
+                            const int64_t i = ra + row;
+                            a.dSw[i] = cfma(a.diag[i], xs[row], d);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + slot);
+                }
+                if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                // ---- commutator + RK4 stage update for k in [ka, kb)
+                const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
+                const float E = (float)a.sp.Etab[2 * (int64_t)n + eoff];
+                double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+                for (int64_t b = ea; b < eb; b += kConsumers) {
+                    const int64_t i = b + tid;
+                    const Obs3 ob = stage_element<float, NB>(a.sp, i, i < eb, lane, st, E);
+                    o0 += ob.p;
+                    o1 += ob.j;
+                    o2 += ob.o;
+                }
+                if (st == 3) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        o0 += __shfl_xor_sync(0xffffffffu, o0, o);
+                        o1 += __shfl_xor_sync(0xffffffffu, o1, o);
+                        o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+                    }
+                    if (lane == 0) {
+                        wred[3 * warp] = o0;
+                        wred[3 * warp + 1] = o1;
+                        wred[3 * warp + 2] = o2;
+                    }
+                    consumer_sync();
+                    if (tid == 0) {
+                        double s0 = 0, s1 = 0, s2 = 0;
+                        for (int w = 0; w < kConsumerWarps; ++w) {
+                            s0 += wred[3 * w];
+                            s1 += wred[3 * w + 1];
+                            s2 += wred[3 * w + 2];
+                        }
+                        a.sp.red[3 * cta] = s0;
+                        a.sp.red[3 * cta + 1] = s1;
+                        a.sp.red[3 * cta + 2] = s2;
+                    }
+                }
+                if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                if (st == 3 && cta == 0 && tid == 0) {
+                    double s0 = 0, s1 = 0, s2 = 0;
+                    for (int c2 = 0; c2 < G; ++c2) {
+                        s0 += __ldcg(a.sp.red + 3 * c2);
+                        s1 += __ldcg(a.sp.red + 3 * c2 + 1);
+                        s2 += __ldcg(a.sp.red + 3 * c2 + 2);
+                    }
+                    const double inv = 1.0 / (double)a.Nk;
+                    double* row = a.sp.obs + 3 * (int64_t)(n + 1);
+                    row[0] = s0 * inv;
+                    row[1] = s1 * inv;
+                    row[2] = s2 * inv;
+                }
+                for (int e = tid; e < nrows; e += kConsumers) xs[e] = __ldcg(a.sp.X + ra + e);
+                consumer_sync();
+            }
+        }
+        // ok is uniform here: it only changes through grid_sync, which every consumer
+        // thread enters in the same order and which returns the same shared flag to all
+        if (!ok && tid == 0) {
+            atomicExch(a.err, 1);
+            *abort_s = 1;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// Host side: launch geometry, shared-memory ring sizing, cooperative launch.  Returns false
+// when the path does not apply (rank too large, too little shared memory), in which case
+// the caller uses the stage-wise kernels.
+bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
+                          bool test_timeout, cudaStream_t s) {
+    const HostModel& h = c.hm;
+    const int r = c.rank, ldu = r + (r & 1);
+    if (c.dtype != TDAGW_C64 || ldu > 2048 || r < 1) return false;
+    int dev = 0, nsm = 0, smem_max = 0, coop = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return false;
+    const int G = (int)std::min<int64_t>(nsm, h.N);
+    const int rows_max = (int)((h.N + G - 1) / G) + 1;
+    const int row_bytes = ldu * 8;
+    const int rps = std::max(1, kSlotTarget / row_bytes);
+    const int slot_bytes = rps * row_bytes;
+    const size_t extras = (size_t)ldu * 8 + (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
+    const size_t avail = (size_t)smem_max - 1024;
+    if (avail < extras + 4 * (size_t)slot_bytes) return false;
+    const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
+    const size_t smem = (size_t)nslots * slot_bytes + 16 * (size_t)nslots + extras;
+
+    LRArgs a{};
+    a.U = c.U.as<float2>();
+    a.dSw = c.dS.as<float2>();
+    a.V = c.V.as<float2>();
+    a.S = c.S.as<float>();
+    a.diag = c.diagF.as<float2>();
+    StageParams<float>& p = a.sp;
+    p.X = c.X.as<float2>();
+    p.dS = c.dS.as<float2>();
+    p.dx = c.dx.as<float2>();
+    p.dy = c.dy.as<float2>();
+    p.vx = c.vx.as<float2>();
+    p.gap = c.gap.as<float2>();
+    p.acc = c.acc.as<float2>();
+    p.Ssum = c.Ssum.as<float2>();
+    p.Ccomp = c.Ccomp.as<float2>();
+    p.Xnext = c.X.as<float2>();
+    p.Etab = c.Etab.as<double>();
+    p.step = nullptr;
+    p.obs = c.obs.as<double>();
+    c.red.ensure((size_t)std::max<int64_t>(G, (h.N + 255) / 256) * 3 * sizeof(double));
+    p.red = c.red.as<double>();
+    p.counter = nullptr;
+    p.N = h.N;
+    p.Nk = h.Nk;
+    p.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) p.occ[q] = (float)h.occ[q];
+    p.dt = (float)dt;
+    p.dirx = (float)dirx;
+    p.diry = (float)diry;
+    p.stage = 0;
+    p.kahan = kahan ? 1 : 0;
+    c.pbuf.ensure((size_t)G * ldu * sizeof(float2));
+    c.sync.ensure(4 * sizeof(unsigned));
+    TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+    a.part = c.pbuf.as<float2>();
+    a.ytil = c.ytil.as<float2>();
+    a.bar_count = c.sync.as<unsigned>();
+    a.bar_gen = c.sync.as<unsigned>() + 1;
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.N = h.N;
+    a.Nk = h.Nk;
+    a.r = r;
+    a.ldu = ldu;
+    a.T = T;
+    a.rows_per_slot = rps;
+    a.nslots = nslots;
+    a.slot_bytes = slot_bytes;
+    a.rows_max = rows_max;
+    a.extra_arrivals = test_timeout ? 1 : 0;
+    a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
+    void* args[] = {&a};
+    const void* fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2> : (const void*)lr_persistent_kernel<4>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    if (per_sm < 1) return false;
+    TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, smem, s));
+    c.persistent_launched = true;
+    return true;
+}
+
+}  // namespace tdagw

@@ -328,34 +328,21 @@ __global__ void eye_kernel(double2* __restrict__ W, int n) {
     W[e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
 }
 
-// Final factors in the context precision: U (N x ldu, pad column zero) and Vh (r x N) with
-// Vh[j][i] = sign_j conj(U[i][j]); 32 x 32 tiles transposed through shared memory.
+// Final factors in the context precision: U and V (N x ldu, pad column zero) with
+// V[i][j] = sign_j U[i][j] (K^off Hermitian: v_j = sign(lambda_j) u_j).
 template <typename R>
 __global__ void emit_factors_kernel(const double2* __restrict__ Uq, int64_t N, int r, int ldu,
                                     const double* __restrict__ sgn, cplx_t<R>* __restrict__ U,
-                                    cplx_t<R>* __restrict__ Vh) {
-    __shared__ double2 tile[32][33];
-    const int64_t i0 = blockIdx.y * 32;
-    const int j0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    for (int q = ty; q < 32; q += 8) {
-        const int64_t i = i0 + q;
-        const int j = j0 + tx;
-        if (i < N && j < ldu) {
-            const double2 v = j < r ? Uq[i * r + j] : make_double2(0, 0);
-            U[i * ldu + j] = mk((R)v.x, (R)v.y);
-            tile[q][tx] = v;
-        }
-    }
-    __syncthreads();
-    for (int q = ty; q < 32; q += 8) {
-        const int j = j0 + q;
-        const int64_t i = i0 + tx;
-        if (j < r && i < N) {
-            const double2 v = tile[tx][q];
-            const double sg = sgn[j];
-            Vh[(int64_t)j * N + i] = mk((R)(sg * v.x), (R)(-sg * v.y));
-        }
+                                    cplx_t<R>* __restrict__ V) {
+    const int64_t tot = N * ldu;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldu;
+        const int j = (int)(e % ldu);
+        const double2 v = j < r ? Uq[i * r + j] : make_double2(0, 0);
+        const double sg = j < r ? sgn[j] : 1.0;
+        U[e] = mk((R)v.x, (R)v.y);
+        V[e] = mk((R)(sg * v.x), (R)(sg * v.y));
     }
 }
 
@@ -537,10 +524,9 @@ void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t s
     using C = cplx_t<R>;
     const int ldu = rank + (rank & 1);
     c.U.ensure((size_t)N * ldu * sizeof(C));
-    c.Vh.ensure((size_t)rank * N * sizeof(C));
-    dim3 eg((ldu + 31) / 32, (unsigned)((N + 31) / 32));
-    emit_factors_kernel<R><<<eg, dim3(32, 8), 0, w.s>>>(Z.as<double2>(), N, rank, ldu, dG.as<double>(),
-                                                       c.U.as<C>(), c.Vh.as<C>());
+    c.V.ensure((size_t)N * ldu * sizeof(C));
+    emit_factors_kernel<R><<<152 * 8, 256, 0, w.s>>>(Z.as<double2>(), N, rank, ldu, dG.as<double>(),
+                                                    c.U.as<C>(), c.V.as<C>());
     check_launch("emit_factors_kernel");
     c.S.ensure(rank * sizeof(R));
     to_real_kernel<R><<<(rank + 255) / 256, 256, 0, w.s>>>(dS.as<double>(), c.S.as<R>(), rank);

@@ -151,6 +151,48 @@ def test_propagate_lowrank_cfg0(cfg0, dtype, tol):
         assert op.rel_l2(got[:, j], ref[:, j]) < tol
 
 
+@pytest.mark.parametrize("L,nc,rank", [(5, 2, 7), (12, 1, 1), (9, 2, 64), (24, 1, 256)])
+def test_persistent_lowrank_vs_oracle_and_stagewise(L, nc, rank):
+    """Single-launch persistent low-rank kernel (c64) on grids with ragged per-CTA row
+    ranges and odd ranks: vs the oracle with the same factors, and vs the stage-wise
+    kernels (different summation order only)."""
+    p = wl.small_model(L, nc)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, rank)
+    pulse = wl.Pulse(E0=2e-3, omega=0.1, t0=20.0, sigma=8.0)
+    T = 250
+    s = op.half_step_samples(pulse, 0.2, T)
+    ref, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), s, 0.2, T)
+    c = _ctx(p, tg.C64)
+    tg.tdagw_set_factors(c.h, U, S, V, d)
+    a = c.propagate(pulse, T, 0.2, tg.LOWRANK)
+    b = c.propagate(pulse, T, 0.2, tg.LOWRANK, flags=tg.FLAG_RESET | tg.FLAG_STAGEWISE)
+    for j in range(3):
+        assert op.rel_l2(a[:, j], ref[:, j]) < 1e-5, j
+        assert op.rel_l2(a[:, j], b[:, j]) < 1e-6, j
+
+
+def test_persistent_timeout_is_reported_and_context_survives(cfg0):
+    """Fault injection on the host side of a bounded wait: the grid barrier waits for a
+    block that does not exist; every wait gives up after its budget, the call reports
+    TDAGW_ERR_TIMEOUT, and the same context then propagates normally."""
+    w = cfg0[0]
+    c = _ctx(w.model, tg.C64)
+    d, Koff = ok.split_diag_off(cfg0[2])
+    U, S, V = olr.truncated_svd(Koff, 29)
+    tg.tdagw_set_factors(c.h, U, S, V, d)
+    tg.tdagw_propagate(c.h, [tg.make_field(w.pulses[0])], [50], w.dt, tg.LOWRANK,
+                       tg.FLAG_RESET | tg.FLAG_TEST_TIMEOUT)
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_sync(c.h)
+    assert e.value.code == tg.ERR_TIMEOUT
+    good = c.propagate(w.pulses[0], 50, w.dt, tg.LOWRANK)
+    ref = c.propagate(w.pulses[0], 50, w.dt, tg.LOWRANK, flags=tg.FLAG_RESET | tg.FLAG_STAGEWISE)
+    assert op.rel_l2(good[:, 0], ref[:, 0]) < 1e-6
+
+
 def test_graph_and_stagewise_launches_agree(cfg0):
     w = cfg0[0]
     c = _ctx(w.model, tg.C64)
