@@ -30,7 +30,7 @@ namespace {
 constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
-constexpr int kSlotTarget = 8192;  // bytes per ring slot (whole rows)
+constexpr int kSlotTarget = 32768;  // bytes per ring slot (whole rows)
 
 struct LRArgs {
     const float2* U;
@@ -109,11 +109,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Grid-wide barrier among the consumer threads of all CTAs (sense by generation count).
-// Returns false (and raises abort) if it could not complete within the budget.
+// bar.sync orders this CTA's prior stores before thread 0's gpu-scope fence (fences are
+// cumulative), so one fence per CTA publishes them.  Returns false (and raises abort) if
+// the barrier could not complete within the budget.
 __device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s) {
-    __threadfence();
     consumer_sync();
     if (threadIdx.x == 0 && !*abort_s) {
+        __threadfence();
         const unsigned need = gridDim.x + (unsigned)a.extra_arrivals;
         const unsigned g = lgen;
         if (atomicAdd(a.bar_count, 1u) == need - 1) {
@@ -128,7 +130,7 @@ __device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s
                     *abort_s = 1;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -136,6 +138,30 @@ __device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s
     }
     consumer_sync();
     return !*abort_s;
+}
+
+// Position in the shared-memory ring: slot index and the parity of its current use.
+struct RingPos {
+    int slot;
+    uint32_t phase;
+    __device__ __forceinline__ void advance(int by, int ns) {
+        slot += by;
+        while (slot >= ns) {
+            slot -= ns;
+            phase ^= 1u;
+        }
+    }
+};
+
+// One lane waits for the tile, then the warp proceeds (bar.warp.sync orders the lanes'
+// shared-memory reads after lane 0's acquire of the mbarrier phase).
+__device__ __forceinline__ bool warp_wait_full(uint64_t* full, RingPos p, volatile int* abort_s,
+                                               unsigned long long budget, int lane) {
+    int ok = 1;
+    if (lane == 0) ok = (!*abort_s && mbar_wait(full + p.slot, p.phase, abort_s, budget)) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok && lane == 0) *abort_s = 1;
+    return ok != 0;
 }
 
 template <int NB>
@@ -169,25 +195,27 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------------ producer warp
         if (lane == 0) {
-            uint64_t q = 0;
+            RingPos pos{0, 0u};
+            uint64_t issued = 0;
             bool ok = true;
             for (int n = 0; n < a.T && ok; ++n)
                 for (int st = 0; st < 4 && ok; ++st)
                     for (int pass = 0; pass < 2 && ok; ++pass) {
                         const float2* base = (pass == 0 ? a.V : a.U) + ra * ldu;
-                        for (int t = 0; t < ntiles; ++t, ++q) {
-                            const int slot = (int)(q % ns);
-                            if (q >= (uint64_t)ns &&
-                                !mbar_wait(empty + slot, (uint32_t)((q / ns - 1) & 1), abort_s, a.wait_ns)) {
+                        for (int t = 0; t < ntiles; ++t) {
+                            if (issued >= (uint64_t)ns &&
+                                !mbar_wait(empty + pos.slot, pos.phase ^ 1u, abort_s, a.wait_ns)) {
                                 ok = false;
                                 break;
                             }
                             const int r0 = t * rps;
                             const int nr = min(rps, nrows - r0);
                             const uint32_t bytes = (uint32_t)nr * ldu * 8u;
-                            mbar_expect_tx(full + slot, bytes);
-                            bulk_g2s(ring + (size_t)slot * a.slot_bytes, base + (int64_t)r0 * ldu, bytes,
-                                     full + slot);
+                            mbar_expect_tx(full + pos.slot, bytes);
+                            bulk_g2s(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
+                                     bytes, full + pos.slot);
+                            ++issued;
+                            pos.advance(1, ns);
                         }
                     }
             if (!ok) {
@@ -195,8 +223,16 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 *abort_s = 1;
             }
             // every issued copy must land before the CTA may exit
-            for (uint64_t j = q > (uint64_t)ns ? q - ns : 0; j < q; ++j)
-                mbar_wait(full + (j % ns), (uint32_t)((j / ns) & 1), nullptr, a.wait_ns);
+            const int back = issued < (uint64_t)ns ? (int)issued : ns;
+            for (int j = 1; j <= back; ++j) {
+                int s2 = pos.slot - j;
+                uint32_t ph = pos.phase;
+                if (s2 < 0) {
+                    s2 += ns;
+                    ph ^= 1u;
+                }
+                mbar_wait(full + s2, ph, nullptr, a.wait_ns);
+            }
         }
         __syncwarp();
     } else {
@@ -205,23 +241,20 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
         const int64_t ea = ka * NB * NB, eb = kb * NB * NB;
         const int jr0 = (int)((int64_t)cta * a.r / G), jr1 = (int)((int64_t)(cta + 1) * a.r / G);
         unsigned lgen = 0;
-        uint64_t q = 0;
+        RingPos pos{0, 0u};
         bool ok = true;
         for (int e = tid; e < nrows; e += kConsumers) xs[e] = __ldcg(a.sp.X + ra + e);
         consumer_sync();
         for (int n = 0; n < a.T && ok; ++n) {
             for (int st = 0; st < 4 && ok; ++st) {
-                // ---- V pass: thread owns column pairs tid, tid + 512 (ldu <= 2048)
+                // ---- V pass: every warp reads every row; thread owns column pairs
+                //      tid and tid + 512 (ldu <= 2048)
                 float2 acc[4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-                for (int t = 0; t < ntiles; ++t, ++q) {
-                    const int slot = (int)(q % ns);
-                    if (*abort_s || !mbar_wait(full + slot, (uint32_t)((q / ns) & 1), abort_s, a.wait_ns)) {
-                        *abort_s = 1;
-                        break;
-                    }
-                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)slot * a.slot_bytes);
+                for (int t = 0; t < ntiles; ++t) {
+                    if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
+                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
                     const int r0 = t * rps, nr = min(rps, nrows - r0);
                     for (int rr = 0; rr < nr; ++rr) {
                         const float2 xi = xs[r0 + rr];
@@ -237,7 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         }
                     }
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(empty + slot);
+                    if (lane == 0) mbar_arrive(empty + pos.slot);
+                    pos.advance(1, ns);
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
@@ -258,22 +292,20 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
                 consumer_sync();
-                // ---- U pass: warp w takes rows w, w + 16, ... of the range
-                for (int t = 0; t < ntiles; ++t, ++q) {
-                    const int slot = (int)(q % ns);
-                    if (*abort_s || !mbar_wait(full + slot, (uint32_t)((q / ns) & 1), abort_s, a.wait_ns)) {
-                        *abort_s = 1;
-                        break;
-                    }
-                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)slot * a.slot_bytes);
+                // ---- U pass: row q of the range is computed by warp q % 16; every warp
+                //      still observes every tile's phase in order (an mbarrier parity wait
+                //      is only unambiguous for a waiter that saw the slot's previous use)
+                for (int t = 0; t < ntiles; ++t) {
+                    if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
+                    const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
                     const int r0 = t * rps, nr = min(rps, nrows - r0);
                     for (int rr = 0; rr < nr; ++rr) {
                         const int row = r0 + rr;
                         if ((row % kConsumerWarps) != warp) continue;
-                        const float2* urow = tile + (size_t)rr * ldu;
+                        const float2* ur = tile + (size_t)rr * ldu;
                         float2 d = make_float2(0.f, 0.f);
                         for (int p = lane; 2 * p < ldu; p += 32) {
-                            const float4 u = *reinterpret_cast<const float4*>(urow + 2 * p);
+                            const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
                             const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
                             d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
                             d = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d);
@@ -286,7 +318,8 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         }
                     }
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(empty + slot);
+                    if (lane == 0) mbar_arrive(empty + pos.slot);
+                    pos.advance(1, ns);
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 // ---- commutator + RK4 stage update for k in [ka, kb)
@@ -372,7 +405,8 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     const int G = (int)std::min<int64_t>(nsm, h.N);
     const int rows_max = (int)((h.N + G - 1) / G) + 1;
     const int row_bytes = ldu * 8;
-    const int rps = std::max(1, kSlotTarget / row_bytes);
+    int rps = 1;  // rows per slot
+    while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
     const int slot_bytes = rps * row_bytes;
     const size_t extras = (size_t)ldu * 8 + (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
