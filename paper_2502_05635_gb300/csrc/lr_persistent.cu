@@ -2,16 +2,16 @@
 // launch runs all RK4 steps of a call.  Per stage (Eq. svd_acc applied to Eq. sigma-from-k,
 // inside the RK4 update of Eq. tdagw):
 //
-//   V pass   y_c = sum_{i in rows(c)} conj(V_i) x_i          (each CTA: its row range)
+//   V pass   y_c = sum_{i in rows(c)} conj(V_i) x_i          (each CTA: its rows)
 //   grid barrier; y = sum_c y_c, scaled by S (each CTA: a slice of columns)
-//   grid barrier; U pass  dSigma_i = U_i . (S o y) + K^diag_i x_i  (same row range)
-//   grid barrier; commutator, RK4 stage update, observables (each CTA: a range of k)
-//   grid barrier
+//   grid barrier; U pass  dSigma_i = U_i . (S o y) + K^diag_i x_i  (same rows)
+//   commutator, RK4 stage update, observables for the same rows
 //
-// The factors U and V (N x ldu complex64, row-major) are the only large operands.  Each CTA
-// owns one contiguous row range of both, so its operand stream is two contiguous byte
-// ranges per stage.  A producer warp streams them through a shared-memory ring with 1D
-// TMA bulk copies (cp.async.bulk) completing on mbarriers; sixteen consumer warps compute
+// Each CTA owns the pair elements of a contiguous range of k-points, so its commutators use
+// only rows it computed and the next stage's V pass needs only its own rows: two grid
+// barriers per stage.  The factors U and V (N x ldu complex64, row-major) are the only
+// large operands; a CTA's operand stream is two contiguous byte ranges per stage.  A
+// producer warp streams them through a shared-memory ring with 1D TMA bulk copies (cp.async.bulk) completing on mbarriers; sixteen consumer warps compute
 // from shared memory.  The producer never depends on data, so it keeps copies in flight
 // across the grid barriers and HBM stays busy while the barriers resolve.
 //
@@ -32,6 +32,22 @@ constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kSlotTarget = 32768;  // bytes per ring slot (whole rows)
 
+// Optional phase timestamps (build with -DTDAGW_TRACE): thread 0 of every CTA records
+// %globaltimer at ten points of each of the first kTraceStages stages.
+#ifdef TDAGW_TRACE
+constexpr int kTraceStages = 16;
+__device__ unsigned long long g_trace[160 * kTraceStages * 10];
+#define TDAGW_TRACE_POINT(k)                                                                \
+    do {                                                                                    \
+        if (tid == 0 && cta < 160 && n * 4 + st < kTraceStages)                             \
+            g_trace[(cta * kTraceStages + n * 4 + st) * 10 + (k)] = gtimer();               \
+    } while (0)
+#else
+#define TDAGW_TRACE_POINT(k) \
+    do {                     \
+    } while (0)
+#endif
+
 struct LRArgs {
     const float2* U;
     const float2* V;
@@ -41,8 +57,7 @@ struct LRArgs {
     float2* dSw;         // dSigma written by the U pass (sp.dS reads it)
     float2* part;        // gridDim x ldu partial y vectors
     float2* ytil;        // ldu, S o y
-    unsigned* bar_count;
-    unsigned* bar_gen;
+    unsigned long long* bar_count;  // monotonic arrival counter of the grid barrier
     int* err;
     int64_t N;
     int Nk, r, ldu, T;
@@ -102,42 +117,66 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
-// Grid-wide barrier among the consumer threads of all CTAs (sense by generation count).
-// bar.sync orders this CTA's prior stores before thread 0's gpu-scope fence (fences are
-// cumulative), so one fence per CTA publishes them.  Returns false (and raises abort) if
-// the barrier could not complete within the budget.
+// Grid-wide barrier among the consumer threads of all CTAs.  The arrival counter only
+// grows: barrier number g (1, 2, ...) is complete once it reaches g * gridDim.x, so no
+// reset is needed and arrivals are fire-and-forget reductions at L2 (no serialised
+// round trips).  bar.sync orders this CTA's prior stores before thread 0's release
+// (cumulative); the acquire load orders the CTA's later loads after the other CTAs'
+// releases.  Returns false (and raises abort) if the barrier could not complete within
+// the budget.
 __device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s) {
     consumer_sync();
     if (threadIdx.x == 0 && !*abort_s) {
-        __threadfence();
-        const unsigned need = gridDim.x + (unsigned)a.extra_arrivals;
-        const unsigned g = lgen;
-        if (atomicAdd(a.bar_count, 1u) == need - 1) {
-            atomicExch(a.bar_count, 0u);
-            __threadfence();
-            atomicExch(a.bar_gen, g + 1);
-        } else {
+        const unsigned long long target =
+            (unsigned long long)(lgen + 1) * (gridDim.x + (unsigned)a.extra_arrivals);
+        red_release_add64(a.bar_count, 1ull);
+        if (ld_acquire64(a.bar_count) < target) {
             const uint64_t t0 = gtimer();
-            while (ld_acquire(a.bar_gen) == g) {
+            while (ld_acquire64(a.bar_count) < target) {
                 if (gtimer() - t0 > a.wait_ns || *(volatile int*)a.err) {
                     atomicExch(a.err, 1);
                     *abort_s = 1;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(20);
             }
         }
-        __threadfence();
-        lgen = g + 1;
+        lgen += 1;
     }
     consumer_sync();
     return !*abort_s;
+}
+
+// Observables row `row` from the per-CTA partials (one warp; fixed summation order).
+__device__ void reduce_step_obs(const LRArgs& a, int G, int lane, int row) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int c = lane; c < G; c += 32) {
+        s0 += __ldcg(a.sp.red + 3 * c);
+        s1 += __ldcg(a.sp.red + 3 * c + 1);
+        s2 += __ldcg(a.sp.red + 3 * c + 2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        const double inv = 1.0 / (double)a.Nk;
+        double* o = a.sp.obs + 3 * (int64_t)row;
+        o[0] = s0 * inv;
+        o[1] = s1 * inv;
+        o[2] = s2 * inv;
+    }
 }
 
 // Position in the shared-memory ring: slot index and the parity of its current use.
@@ -169,7 +208,11 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int64_t ra = (int64_t)cta * a.N / G, rb = (int64_t)(cta + 1) * a.N / G;
+    // rows of this CTA: all pair elements of the k-points [ka, kb), so the commutator of
+    // every k it owns needs only rows it computed itself (no grid barrier between the
+    // U pass and the next V pass)
+    const int64_t ka = (int64_t)cta * a.Nk / G, kb = (int64_t)(cta + 1) * a.Nk / G;
+    const int64_t ra = ka * NB * NB, rb = kb * NB * NB;
     const int nrows = (int)(rb - ra);
     const int rps = a.rows_per_slot, ns = a.nslots, ldu = a.ldu;
     const int ntiles = (nrows + rps - 1) / rps;
@@ -237,8 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ consumer warps
-        const int64_t ka = (int64_t)cta * a.Nk / G, kb = (int64_t)(cta + 1) * a.Nk / G;
-        const int64_t ea = ka * NB * NB, eb = kb * NB * NB;
+        const int64_t ea = ra, eb = rb;
         const int jr0 = (int)((int64_t)cta * a.r / G), jr1 = (int)((int64_t)(cta + 1) * a.r / G);
         unsigned lgen = 0;
         RingPos pos{0, 0u};
@@ -247,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
         consumer_sync();
         for (int n = 0; n < a.T && ok; ++n) {
             for (int st = 0; st < 4 && ok; ++st) {
+                TDAGW_TRACE_POINT(0);
                 // ---- V pass: every warp reads every row; thread owns column pairs
                 //      tid and tid + 512 (ldu <= 2048)
                 float2 acc[4];
@@ -273,6 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                     if (lane == 0) mbar_arrive(empty + pos.slot);
                     pos.advance(1, ns);
                 }
+                TDAGW_TRACE_POINT(1);
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const int p = tid + m * kConsumers;
@@ -281,6 +325,11 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                             make_float4(acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                TDAGW_TRACE_POINT(2);
+                // observables of the previous step (all CTAs published their partials at its
+                // last stage, before this barrier); the last warp is idle in the y sum below
+                if (st == 0 && n > 0 && cta == 0 && warp == kConsumerWarps - 1)
+                    reduce_step_obs(a, G, lane, n);
                 // ---- y = S o sum_c y_c for this CTA's columns, fixed summation order
                 for (int j = jr0 + warp; j < jr1; j += kConsumerWarps) {
                     float2 s = make_float2(0.f, 0.f);
@@ -290,8 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                     if (lane == 0) a.ytil[j] = cscale(s, a.S[j]);
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                TDAGW_TRACE_POINT(3);
                 for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
                 consumer_sync();
+                TDAGW_TRACE_POINT(4);
                 // ---- U pass: row q of the range is computed by warp q % 16; every warp
                 //      still observes every tile's phase in order (an mbarrier parity wait
                 //      is only unambiguous for a waiter that saw the slot's previous use)
@@ -321,7 +372,9 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                     if (lane == 0) mbar_arrive(empty + pos.slot);
                     pos.advance(1, ns);
                 }
-                if (!(ok = grid_sync(a, lgen, abort_s))) break;
+                TDAGW_TRACE_POINT(5);
+                consumer_sync();  // this CTA's dSigma rows are complete
+                TDAGW_TRACE_POINT(6);
                 // ---- commutator + RK4 stage update for k in [ka, kb)
                 const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
                 const float E = (float)a.sp.Etab[2 * (int64_t)n + eoff];
@@ -358,23 +411,18 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         a.sp.red[3 * cta + 2] = s2;
                     }
                 }
-                if (!(ok = grid_sync(a, lgen, abort_s))) break;
-                if (st == 3 && cta == 0 && tid == 0) {
-                    double s0 = 0, s1 = 0, s2 = 0;
-                    for (int c2 = 0; c2 < G; ++c2) {
-                        s0 += __ldcg(a.sp.red + 3 * c2);
-                        s1 += __ldcg(a.sp.red + 3 * c2 + 1);
-                        s2 += __ldcg(a.sp.red + 3 * c2 + 2);
-                    }
-                    const double inv = 1.0 / (double)a.Nk;
-                    double* row = a.sp.obs + 3 * (int64_t)(n + 1);
-                    row[0] = s0 * inv;
-                    row[1] = s1 * inv;
-                    row[2] = s2 * inv;
-                }
+                TDAGW_TRACE_POINT(7);
+                consumer_sync();
+                TDAGW_TRACE_POINT(8);
                 for (int e = tid; e < nrows; e += kConsumers) xs[e] = __ldcg(a.sp.X + ra + e);
                 consumer_sync();
+                TDAGW_TRACE_POINT(9);
             }
+        }
+        // observables of the last step: every CTA's partial is published by one more barrier
+        if (ok && a.T > 0) {
+            ok = grid_sync(a, lgen, abort_s);
+            if (ok && cta == 0 && warp == 0) reduce_step_obs(a, G, lane, a.T);
         }
         // ok is uniform here: it only changes through grid_sync, which every consumer
         // thread enters in the same order and which returns the same shared flag to all
@@ -387,6 +435,12 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
 }
 
 }  // namespace
+
+#ifdef TDAGW_TRACE
+extern "C" int tdagw_debug_trace(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_trace, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
+}
+#endif
 
 // Host side: launch geometry, shared-memory ring sizing, cooperative launch.  Returns false
 // when the path does not apply (rank too large, too little shared memory), in which case
@@ -402,8 +456,8 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     TDAGW_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     TDAGW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return false;
-    const int G = (int)std::min<int64_t>(nsm, h.N);
-    const int rows_max = (int)((h.N + G - 1) / G) + 1;
+    const int G = (int)std::min<int64_t>(nsm, h.Nk);          // every CTA owns >= 1 k-point
+    const int rows_max = (int)((h.Nk + G - 1) / G) * h.Nb * h.Nb;
     const int row_bytes = ldu * 8;
     int rps = 1;  // rows per slot
     while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
@@ -451,8 +505,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
     a.part = c.pbuf.as<float2>();
     a.ytil = c.ytil.as<float2>();
-    a.bar_count = c.sync.as<unsigned>();
-    a.bar_gen = c.sync.as<unsigned>() + 1;
+    a.bar_count = reinterpret_cast<unsigned long long*>(c.sync.p);
     a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
     a.N = h.N;
     a.Nk = h.Nk;

@@ -219,6 +219,18 @@ __global__ void chol_inv_kernel(const double2* __restrict__ G, int b, double2* _
 
 // ---------------------------------------------------------------- Jacobi -------------
 
+struct __align__(16) Rot4 {
+    double x, y, z, w;  // c, s, cos phi, sin phi
+};
+__device__ __forceinline__ Rot4 make_rot4(double a, double b, double c, double d) {
+    Rot4 r;
+    r.x = a;
+    r.y = b;
+    r.z = c;
+    r.w = d;
+    return r;
+}
+
 // Round-robin ("circle") pairing of n_e (even) indices: round r, pair t.
 __device__ __forceinline__ void rr_pair(int ne, int r, int t, int& p, int& q) {
     const int m = ne - 1;
@@ -232,11 +244,11 @@ __device__ __forceinline__ void rr_pair(int ne, int r, int t, int& p, int& q) {
 // t = s/c the smaller root of t^2 + 2 tau t - 1 = 0, tau = (d - a) / (2 |b|).  This kernel
 // applies G^H to rows p and q (all columns) and stores (c, s, e^{i phi}).
 __global__ void jacobi_rows_kernel(double2* __restrict__ A, int n, int ne, int round,
-                                   double4* __restrict__ rot) {
+                                   Rot4* __restrict__ rot) {
     int p, q;
     rr_pair(ne, round, blockIdx.x, p, q);
     if (q >= n) return;
-    __shared__ double4 sr;
+    __shared__ Rot4 sr;
     if (threadIdx.x == 0) {
         const double a = A[(int64_t)p * n + p].x, d = A[(int64_t)q * n + q].x;
         const double2 b = A[(int64_t)p * n + q];
@@ -250,7 +262,7 @@ __global__ void jacobi_rows_kernel(double2* __restrict__ A, int n, int ne, int r
             ex = b.x / bb;
             ey = b.y / bb;
         }
-        sr = make_double4(c, s, ex, ey);
+        sr = make_rot4(c, s, ex, ey);
         rot[blockIdx.x] = sr;
     }
     __syncthreads();
@@ -268,11 +280,11 @@ __global__ void jacobi_rows_kernel(double2* __restrict__ A, int n, int ne, int r
 
 // Applies G to columns p and q of A and of the eigenvector accumulator W.
 __global__ void jacobi_cols_kernel(double2* __restrict__ A, double2* __restrict__ W, int n, int ne,
-                                   int round, const double4* __restrict__ rot) {
+                                   int round, const Rot4* __restrict__ rot) {
     int p, q;
     rr_pair(ne, round, blockIdx.x, p, q);
     if (q >= n) return;
-    const double4 r = rot[blockIdx.x];
+    const Rot4 r = rot[blockIdx.x];
     const double c = r.x, s = r.y;
     const double2 ec = make_double2(r.z, -r.w);  // e^{-i phi}
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
@@ -438,7 +450,7 @@ void apply_koff(Ws& w, const Ctx& c, const double2* X, double2* Y, int l) {
 int jacobi_eigh(Ws& w, double2* B, double2* W, int n) {
     const int ne = n + (n & 1);
     DevBuf rot, nrm;
-    rot.ensure((size_t)(ne / 2) * sizeof(double4));
+    rot.ensure((size_t)(ne / 2) * sizeof(Rot4));
     nrm.ensure(2 * sizeof(double));
     eye_kernel<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, w.s>>>(W, n);
     check_launch("eye_kernel");
@@ -450,8 +462,8 @@ int jacobi_eigh(Ws& w, double2* B, double2* W, int n) {
         TDAGW_CUDA(cudaStreamSynchronize(w.s));
         if (!(h[0] > 1e-26 * h[1]) || h[1] == 0.0) break;
         for (int r = 0; r < ne - 1; ++r) {
-            jacobi_rows_kernel<<<ne / 2, 256, 0, w.s>>>(B, n, ne, r, rot.as<double4>());
-            jacobi_cols_kernel<<<ne / 2, 256, 0, w.s>>>(B, W, n, ne, r, rot.as<double4>());
+            jacobi_rows_kernel<<<ne / 2, 256, 0, w.s>>>(B, n, ne, r, rot.as<Rot4>());
+            jacobi_cols_kernel<<<ne / 2, 256, 0, w.s>>>(B, W, n, ne, r, rot.as<Rot4>());
         }
         check_launch("jacobi kernels");
     }
