@@ -31,6 +31,7 @@ constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kSlotTarget = 32768;  // bytes per ring slot (whole rows)
+constexpr int kPrefetchTiles = 12;  // L2 prefetch distance beyond the ring, in tiles
 
 // Optional phase timestamps (build with -DTDAGW_TRACE): thread 0 of every CTA records
 // %globaltimer at ten points of each of the first kTraceStages stages.
@@ -113,6 +114,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             saddr(dst)),
         "l"(src), "r"(bytes), "r"(saddr(bar))
         : "memory");
+}
+// hint: pull a future tile into L2 so its later bulk copy is served from L2
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
@@ -241,6 +246,19 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
             RingPos pos{0, 0u};
             uint64_t issued = 0;
             bool ok = true;
+            // L2 prefetch cursor, kPrefetchTiles ahead of the copies in the (periodic)
+            // tile sequence V tiles, U tiles, V tiles, ... of this CTA's rows
+            int pf_pass = 0, pf_t = 0;
+            auto pf_issue = [&]() {
+                const float2* b = (pf_pass == 0 ? a.V : a.U) + ra * ldu;
+                const int r0 = pf_t * rps, nr = min(rps, nrows - r0);
+                bulk_prefetch_l2(b + (int64_t)r0 * ldu, (uint32_t)nr * ldu * 8u);
+                if (++pf_t == ntiles) {
+                    pf_t = 0;
+                    pf_pass ^= 1;
+                }
+            };
+            for (int j = 0; j < kPrefetchTiles; ++j) pf_issue();
             for (int n = 0; n < a.T && ok; ++n)
                 for (int st = 0; st < 4 && ok; ++st)
                     for (int pass = 0; pass < 2 && ok; ++pass) {
@@ -257,6 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                             mbar_expect_tx(full + pos.slot, bytes);
                             bulk_g2s(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
                                      bytes, full + pos.slot);
+                            pf_issue();
                             ++issued;
                             pos.advance(1, ns);
                         }
@@ -354,13 +373,15 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         const int row = r0 + rr;
                         if ((row % kConsumerWarps) != warp) continue;
                         const float2* ur = tile + (size_t)rr * ldu;
-                        float2 d = make_float2(0.f, 0.f);
+                        float2 d = make_float2(0.f, 0.f), d1 = d;
+#pragma unroll 4
                         for (int p = lane; 2 * p < ldu; p += 32) {
                             const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
                             const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
                             d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
-                            d = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d);
+                            d1 = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d1);
                         }
+                        d = cadd(d, d1);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
                         if (lane == 0) {
