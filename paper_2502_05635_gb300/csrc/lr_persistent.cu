@@ -11,7 +11,7 @@
 // only rows it computed and the next stage's V pass needs only its own rows: two grid
 // barriers per stage.  The factors U and V (N x ldu complex64, row-major) are the only
 // large operands; a CTA's operand stream is two contiguous byte ranges per stage.  A
-// producer warp streams them through a shared-memory ring with 1D TMA bulk copies (cp.async.bulk) completing on mbarriers; sixteen consumer warps compute
+// producer warp streams them through a shared-memory ring with 1D TMA bulk copies (cp.async.bulk) completing on mbarriers; eight consumer warps compute
 // from shared memory.  The producer never depends on data, so it keeps copies in flight
 // across the grid barriers and HBM stays busy while the barriers resolve.
 //
@@ -27,11 +27,10 @@ namespace tdagw {
 
 namespace {
 
-constexpr int kConsumerWarps = 16;
+constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kSlotTarget = 32768;  // bytes per ring slot (whole rows)
-constexpr int kPrefetchTiles = 12;  // L2 prefetch distance beyond the ring, in tiles
 
 // Optional phase timestamps (build with -DTDAGW_TRACE): thread 0 of every CTA records
 // %globaltimer at ten points of each of the first kTraceStages stages.
@@ -114,10 +113,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             saddr(dst)),
         "l"(src), "r"(bytes), "r"(saddr(bar))
         : "memory");
-}
-// hint: pull a future tile into L2 so its later bulk copy is served from L2
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
@@ -208,8 +203,10 @@ __device__ __forceinline__ bool warp_wait_full(uint64_t* full, RingPos p, volati
     return ok != 0;
 }
 
-template <int NB>
+// NB: bands; YP: float4 registers per lane holding S o y in the U pass (ldu <= 64 YP).
+template <int NB, int YP>
 __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
+    constexpr int MV = (64 * YP + 2 * kConsumers - 1) / (2 * kConsumers);  // V-pass pairs per thread
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -225,8 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     unsigned char* ring = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
-    float2* ys = reinterpret_cast<float2*>(empty + ns);
-    float2* xs = ys + ldu;
+    float2* xs = reinterpret_cast<float2*>(empty + ns);
     double* wred = reinterpret_cast<double*>(xs + a.rows_max);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kConsumerWarps);
 
@@ -246,19 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
             RingPos pos{0, 0u};
             uint64_t issued = 0;
             bool ok = true;
-            // L2 prefetch cursor, kPrefetchTiles ahead of the copies in the (periodic)
-            // tile sequence V tiles, U tiles, V tiles, ... of this CTA's rows
-            int pf_pass = 0, pf_t = 0;
-            auto pf_issue = [&]() {
-                const float2* b = (pf_pass == 0 ? a.V : a.U) + ra * ldu;
-                const int r0 = pf_t * rps, nr = min(rps, nrows - r0);
-                bulk_prefetch_l2(b + (int64_t)r0 * ldu, (uint32_t)nr * ldu * 8u);
-                if (++pf_t == ntiles) {
-                    pf_t = 0;
-                    pf_pass ^= 1;
-                }
-            };
-            for (int j = 0; j < kPrefetchTiles; ++j) pf_issue();
+
             for (int n = 0; n < a.T && ok; ++n)
                 for (int st = 0; st < 4 && ok; ++st)
                     for (int pass = 0; pass < 2 && ok; ++pass) {
@@ -275,7 +259,6 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                             mbar_expect_tx(full + pos.slot, bytes);
                             bulk_g2s(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
                                      bytes, full + pos.slot);
-                            pf_issue();
                             ++issued;
                             pos.advance(1, ns);
                         }
@@ -310,10 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
             for (int st = 0; st < 4 && ok; ++st) {
                 TDAGW_TRACE_POINT(0);
                 // ---- V pass: every warp reads every row; thread owns column pairs
-                //      tid and tid + 512 (ldu <= 2048)
-                float2 acc[4];
+                //      tid + 256 m
+                float2 acc[2 * MV];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+                for (int m = 0; m < 2 * MV; ++m) acc[m] = make_float2(0.f, 0.f);
                 for (int t = 0; t < ntiles; ++t) {
                     if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                     const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
@@ -322,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         const float2 xi = xs[r0 + rr];
                         const float2* row = tile + (size_t)rr * ldu;
 #pragma unroll
-                        for (int m = 0; m < 2; ++m) {
+                        for (int m = 0; m < MV; ++m) {
                             const int p = tid + m * kConsumers;
                             if (2 * p < ldu) {
                                 const float4 v = *reinterpret_cast<const float4*>(row + 2 * p);
@@ -337,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 TDAGW_TRACE_POINT(1);
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
+                for (int m = 0; m < MV; ++m) {
                     const int p = tid + m * kConsumers;
                     if (2 * p < ldu)
                         *reinterpret_cast<float4*>(a.part + (size_t)cta * ldu + 2 * p) =
@@ -359,10 +342,16 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 TDAGW_TRACE_POINT(3);
-                for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
-                consumer_sync();
+                // S o y in registers: lane holds column pairs lane + 32 m
+                float4 yr[YP];
+#pragma unroll
+                for (int m = 0; m < YP; ++m) {
+                    const int p = lane + 32 * m;
+                    yr[m] = 2 * p < ldu ? __ldcg(reinterpret_cast<const float4*>(a.ytil + 2 * p))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 TDAGW_TRACE_POINT(4);
-                // ---- U pass: row q of the range is computed by warp q % 16; every warp
+                // ---- U pass: row q of the range is computed by warp q % 8; every warp
                 //      still observes every tile's phase in order (an mbarrier parity wait
                 //      is only unambiguous for a waiter that saw the slot's previous use)
                 for (int t = 0; t < ntiles; ++t) {
@@ -374,12 +363,14 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         if ((row % kConsumerWarps) != warp) continue;
                         const float2* ur = tile + (size_t)rr * ldu;
                         float2 d = make_float2(0.f, 0.f), d1 = d;
-#pragma unroll 4
-                        for (int p = lane; 2 * p < ldu; p += 32) {
-                            const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
-                            const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
-                            d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
-                            d1 = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d1);
+#pragma unroll
+                        for (int m = 0; m < YP; ++m) {
+                            const int p = lane + 32 * m;
+                            if (2 * p < ldu) {
+                                const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
+                                d = cfma(make_float2(u.x, u.y), make_float2(yr[m].x, yr[m].y), d);
+                                d1 = cfma(make_float2(u.z, u.w), make_float2(yr[m].z, yr[m].w), d1);
+                            }
                         }
                         d = cadd(d, d1);
 #pragma unroll
@@ -483,7 +474,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     int rps = 1;  // rows per slot
     while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
     const int slot_bytes = rps * row_bytes;
-    const size_t extras = (size_t)ldu * 8 + (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
+    const size_t extras = (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
     if (avail < extras + 4 * (size_t)slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
@@ -540,7 +531,17 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.extra_arrivals = test_timeout ? 1 : 0;
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};
-    const void* fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2> : (const void*)lr_persistent_kernel<4>;
+    const void* fn = nullptr;
+    const int yp = ldu <= 256 ? 4 : ldu <= 512 ? 8 : ldu <= 1024 ? 16 : 32;
+#define TDAGW_PICK(YPV)                                                                    \
+    fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2, YPV> : (const void*)lr_persistent_kernel<4, YPV>
+    switch (yp) {
+        case 4: TDAGW_PICK(4); break;
+        case 8: TDAGW_PICK(8); break;
+        case 16: TDAGW_PICK(16); break;
+        default: TDAGW_PICK(32); break;
+    }
+#undef TDAGW_PICK
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
