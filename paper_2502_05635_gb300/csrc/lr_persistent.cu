@@ -203,10 +203,10 @@ __device__ __forceinline__ bool warp_wait_full(uint64_t* full, RingPos p, volati
     return ok != 0;
 }
 
-// NB: bands; YP: float4 registers per lane holding S o y in the U pass (ldu <= 64 YP).
-template <int NB, int YP>
+// NB: bands; MV: column pairs per consumer thread (ldu <= 2 * 256 * MV).  Thread t owns
+// the column pairs t + 256 m of every row in both passes.
+template <int NB, int MV>
 __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
-    constexpr int MV = (64 * YP + 2 * kConsumers - 1) / (2 * kConsumers);  // V-pass pairs per thread
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
     float2* xs = reinterpret_cast<float2*>(empty + ns);
-    double* wred = reinterpret_cast<double*>(xs + a.rows_max);
+    float2* wpart = xs + a.rows_max;  // U pass: per-warp partial dot products [row][warp]
+    double* wred = reinterpret_cast<double*>(wpart + (size_t)a.rows_max * kConsumerWarps);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kConsumerWarps);
 
     if (tid == 0) {
@@ -342,30 +343,27 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 TDAGW_TRACE_POINT(3);
-                // S o y in registers: lane holds column pairs lane + 32 m
-                float4 yr[YP];
+                // S o y for this thread's column pairs, in registers
+                float4 yr[MV];
 #pragma unroll
-                for (int m = 0; m < YP; ++m) {
-                    const int p = lane + 32 * m;
+                for (int m = 0; m < MV; ++m) {
+                    const int p = tid + m * kConsumers;
                     yr[m] = 2 * p < ldu ? __ldcg(reinterpret_cast<const float4*>(a.ytil + 2 * p))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 TDAGW_TRACE_POINT(4);
-                // ---- U pass: row q of the range is computed by warp q % 8; every warp
-                //      still observes every tile's phase in order (an mbarrier parity wait
-                //      is only unambiguous for a waiter that saw the slot's previous use)
+                // ---- U pass: every warp reads every row (its column pairs) and keeps one
+                //      partial dot product per row; slots are released as fast as in the V pass
                 for (int t = 0; t < ntiles; ++t) {
                     if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                     const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
                     const int r0 = t * rps, nr = min(rps, nrows - r0);
                     for (int rr = 0; rr < nr; ++rr) {
-                        const int row = r0 + rr;
-                        if ((row % kConsumerWarps) != warp) continue;
                         const float2* ur = tile + (size_t)rr * ldu;
                         float2 d = make_float2(0.f, 0.f), d1 = d;
 #pragma unroll
-                        for (int m = 0; m < YP; ++m) {
-                            const int p = lane + 32 * m;
+                        for (int m = 0; m < MV; ++m) {
+                            const int p = tid + m * kConsumers;
                             if (2 * p < ldu) {
                                 const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
                                 d = cfma(make_float2(u.x, u.y), make_float2(yr[m].x, yr[m].y), d);
@@ -375,14 +373,19 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         d = cadd(d, d1);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
-                        if (lane == 0) {
-                            const int64_t i = ra + row;
-                            a.dSw[i] = cfma(a.diag[i], xs[row], d);
-                        }
+                        if (lane == 0) wpart[(size_t)(r0 + rr) * kConsumerWarps + warp] = d;
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty + pos.slot);
                     pos.advance(1, ns);
+                }
+                consumer_sync();
+                // dSigma_i = sum over warps (fixed order) + K^diag_i x_i
+                for (int e = tid; e < nrows; e += kConsumers) {
+                    float2 d = wpart[(size_t)e * kConsumerWarps];
+#pragma unroll
+                    for (int w = 1; w < kConsumerWarps; ++w) d = cadd(d, wpart[(size_t)e * kConsumerWarps + w]);
+                    a.dSw[ra + e] = cfma(a.diag[ra + e], xs[e], d);
                 }
                 TDAGW_TRACE_POINT(5);
                 consumer_sync();  // this CTA's dSigma rows are complete
@@ -474,7 +477,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     int rps = 1;  // rows per slot
     while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
     const int slot_bytes = rps * row_bytes;
-    const size_t extras = (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
+    const size_t extras = (size_t)rows_max * 8 * (1 + kConsumerWarps) + 3 * kConsumerWarps * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
     if (avail < extras + 4 * (size_t)slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
@@ -532,14 +535,14 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};
     const void* fn = nullptr;
-    const int yp = ldu <= 256 ? 4 : ldu <= 512 ? 8 : ldu <= 1024 ? 16 : 32;
-#define TDAGW_PICK(YPV)                                                                    \
-    fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2, YPV> : (const void*)lr_persistent_kernel<4, YPV>
-    switch (yp) {
-        case 4: TDAGW_PICK(4); break;
-        case 8: TDAGW_PICK(8); break;
-        case 16: TDAGW_PICK(16); break;
-        default: TDAGW_PICK(32); break;
+    const int mv = (ldu + 2 * kConsumers - 1) / (2 * kConsumers);
+#define TDAGW_PICK(MVV)                                                                    \
+    fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2, MVV> : (const void*)lr_persistent_kernel<4, MVV>
+    switch (mv) {
+        case 1: TDAGW_PICK(1); break;
+        case 2: TDAGW_PICK(2); break;
+        case 3: TDAGW_PICK(3); break;
+        default: TDAGW_PICK(4); break;
     }
 #undef TDAGW_PICK
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
