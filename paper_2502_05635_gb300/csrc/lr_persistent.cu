@@ -11,7 +11,7 @@
 // only rows it computed and the next stage's V pass needs only its own rows: two grid
 // barriers per stage.  The factors U and V (N x ldu complex64, row-major) are the only
 // large operands; a CTA's operand stream is two contiguous byte ranges per stage.  A
-// producer warp streams them through a shared-memory ring with 1D TMA bulk copies (cp.async.bulk) completing on mbarriers; eight consumer warps compute
+// producer warp streams them through a shared-memory ring with 1D TMA bulk copies (cp.async.bulk) completing on mbarriers; sixteen consumer warps compute
 // from shared memory.  The producer never depends on data, so it keeps copies in flight
 // across the grid barriers and HBM stays busy while the barriers resolve.
 //
@@ -27,7 +27,7 @@ namespace tdagw {
 
 namespace {
 
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kSlotTarget = 32768;  // bytes per ring slot (whole rows)
@@ -203,9 +203,7 @@ __device__ __forceinline__ bool warp_wait_full(uint64_t* full, RingPos p, volati
     return ok != 0;
 }
 
-// NB: bands; MV: column pairs per consumer thread (ldu <= 2 * 256 * MV).  Thread t owns
-// the column pairs t + 256 m of every row in both passes.
-template <int NB, int MV>
+template <int NB>
 __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
@@ -222,9 +220,9 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     unsigned char* ring = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
-    float2* xs = reinterpret_cast<float2*>(empty + ns);
-    float2* wpart = xs + a.rows_max;  // U pass: per-warp partial dot products [row][warp]
-    double* wred = reinterpret_cast<double*>(wpart + (size_t)a.rows_max * kConsumerWarps);
+    float2* ys = reinterpret_cast<float2*>(empty + ns);
+    float2* xs = ys + ldu;
+    double* wred = reinterpret_cast<double*>(xs + a.rows_max);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kConsumerWarps);
 
     if (tid == 0) {
@@ -294,10 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
             for (int st = 0; st < 4 && ok; ++st) {
                 TDAGW_TRACE_POINT(0);
                 // ---- V pass: every warp reads every row; thread owns column pairs
-                //      tid + 256 m
-                float2 acc[2 * MV];
+                //      tid and tid + 512 (ldu <= 2048)
+                float2 acc[4];
 #pragma unroll
-                for (int m = 0; m < 2 * MV; ++m) acc[m] = make_float2(0.f, 0.f);
+                for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
                 for (int t = 0; t < ntiles; ++t) {
                     if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                     const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
@@ -306,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                         const float2 xi = xs[r0 + rr];
                         const float2* row = tile + (size_t)rr * ldu;
 #pragma unroll
-                        for (int m = 0; m < MV; ++m) {
+                        for (int m = 0; m < 2; ++m) {
                             const int p = tid + m * kConsumers;
                             if (2 * p < ldu) {
                                 const float4 v = *reinterpret_cast<const float4*>(row + 2 * p);
@@ -321,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 TDAGW_TRACE_POINT(1);
 #pragma unroll
-                for (int m = 0; m < MV; ++m) {
+                for (int m = 0; m < 2; ++m) {
                     const int p = tid + m * kConsumers;
                     if (2 * p < ldu)
                         *reinterpret_cast<float4*>(a.part + (size_t)cta * ldu + 2 * p) =
@@ -343,49 +341,39 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 TDAGW_TRACE_POINT(3);
-                // S o y for this thread's column pairs, in registers
-                float4 yr[MV];
-#pragma unroll
-                for (int m = 0; m < MV; ++m) {
-                    const int p = tid + m * kConsumers;
-                    yr[m] = 2 * p < ldu ? __ldcg(reinterpret_cast<const float4*>(a.ytil + 2 * p))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
+                consumer_sync();
                 TDAGW_TRACE_POINT(4);
-                // ---- U pass: every warp reads every row (its column pairs) and keeps one
-                //      partial dot product per row; slots are released as fast as in the V pass
+                // ---- U pass: row q of the range is computed by warp q % 16; every warp
+                //      still observes every tile's phase in order (an mbarrier parity wait
+                //      is only unambiguous for a waiter that saw the slot's previous use)
                 for (int t = 0; t < ntiles; ++t) {
                     if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                     const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
                     const int r0 = t * rps, nr = min(rps, nrows - r0);
                     for (int rr = 0; rr < nr; ++rr) {
+                        const int row = r0 + rr;
+                        if ((row % kConsumerWarps) != warp) continue;
                         const float2* ur = tile + (size_t)rr * ldu;
                         float2 d = make_float2(0.f, 0.f), d1 = d;
-#pragma unroll
-                        for (int m = 0; m < MV; ++m) {
-                            const int p = tid + m * kConsumers;
-                            if (2 * p < ldu) {
-                                const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
-                                d = cfma(make_float2(u.x, u.y), make_float2(yr[m].x, yr[m].y), d);
-                                d1 = cfma(make_float2(u.z, u.w), make_float2(yr[m].z, yr[m].w), d1);
-                            }
+#pragma unroll 4
+                        for (int p = lane; 2 * p < ldu; p += 32) {
+                            const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
+                            const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
+                            d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
+                            d1 = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d1);
                         }
                         d = cadd(d, d1);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
-                        if (lane == 0) wpart[(size_t)(r0 + rr) * kConsumerWarps + warp] = d;
+                        if (lane == 0) {
+                            const int64_t i = ra + row;
+                            a.dSw[i] = cfma(a.diag[i], xs[row], d);
+                        }
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty + pos.slot);
                     pos.advance(1, ns);
-                }
-                consumer_sync();
-                // dSigma_i = sum over warps (fixed order) + K^diag_i x_i
-                for (int e = tid; e < nrows; e += kConsumers) {
-                    float2 d = wpart[(size_t)e * kConsumerWarps];
-#pragma unroll
-                    for (int w = 1; w < kConsumerWarps; ++w) d = cadd(d, wpart[(size_t)e * kConsumerWarps + w]);
-                    a.dSw[ra + e] = cfma(a.diag[ra + e], xs[e], d);
                 }
                 TDAGW_TRACE_POINT(5);
                 consumer_sync();  // this CTA's dSigma rows are complete
@@ -477,7 +465,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     int rps = 1;  // rows per slot
     while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
     const int slot_bytes = rps * row_bytes;
-    const size_t extras = (size_t)rows_max * 8 * (1 + kConsumerWarps) + 3 * kConsumerWarps * 8 + 16;
+    const size_t extras = (size_t)ldu * 8 + (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
     if (avail < extras + 4 * (size_t)slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
@@ -534,17 +522,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.extra_arrivals = test_timeout ? 1 : 0;
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};
-    const void* fn = nullptr;
-    const int mv = (ldu + 2 * kConsumers - 1) / (2 * kConsumers);
-#define TDAGW_PICK(MVV)                                                                    \
-    fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2, MVV> : (const void*)lr_persistent_kernel<4, MVV>
-    switch (mv) {
-        case 1: TDAGW_PICK(1); break;
-        case 2: TDAGW_PICK(2); break;
-        case 3: TDAGW_PICK(3); break;
-        default: TDAGW_PICK(4); break;
-    }
-#undef TDAGW_PICK
+    const void* fn = h.Nb == 2 ? (const void*)lr_persistent_kernel<2> : (const void*)lr_persistent_kernel<4>;
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
