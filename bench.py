@@ -112,6 +112,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _profiled_traffic(stages: int):
+    """DRAM bytes of one persistent launch from the committed ncu summary, scaled by the
+    stages the launch runs; None if the kernel sources changed since the capture."""
+    import hashlib
+    import re
+    h = hashlib.sha1()
+    for f in ("lr_persistent.cu", "stage.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2502_05635_gb300", "csrc", f), "rb").read())
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "lr_persistent_kernel_mos2size.md")).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha1:\s*([0-9a-f]+)", txt)
+    per = re.search(r"dram_bytes_per_stage:\s*(\d+)", txt)
+    if not sha or not per or sha.group(1) != h.hexdigest():
+        return None
+    return int(per.group(1)) * stages
+
+
 # ---------------------------------------------------------------- oracle leg --------
 
 def oracle_lowrank_rate(max_seconds: float, max_steps: int):
@@ -269,6 +288,7 @@ def run_ours(a):
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"first {n} RK4 steps of the same trajectory on the FP64 oracle, "
                          f"low-rank apply with seeded rank-{r} factors ({secs:.1f} s)"}
+    traffic = _profiled_traffic(4 * a.steps)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -295,7 +315,7 @@ def run_ours(a):
                      "frac": achieved / hbm, "peak_source": peak_src,
                      "bytes_per_launch": bytes_launch, "ms_per_launch": ms_lr,
                      "bytes_per_stage": bytes_apply,
-                     "traffic": None},
+                     "traffic": traffic},
         "stagewise_apply": {"gbs": achieved_stagewise, "ms": ms_apply},
         "e2e": {"value": ws * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
