@@ -160,6 +160,36 @@ int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* ro
 int tdagw_get_state(tdagw_ctx* ctx, double* drho, double* carry, int64_t* step);
 int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int64_t step);
 
+/* Allocation-free variant of the low-rank contraction (the paper has no counterpart: this
+ * is a deployment convenience).  Computes y = diag o x + U (S o (V^H x)) like
+ * tdagw_apply(TDAGW_LOWRANK), but on arrays the caller owns and without allocating any
+ * device memory.  It is meant for callers that cannot call cudaMalloc on their call path:
+ * code whose device memory belongs to another framework's pool (a direct allocation would
+ * escape that pool's accounting and limits), loops that must not take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, and processes running at a hard memory cap.
+ *
+ *   U, V    device, complex64, N x ld row-major (rows 16-byte aligned: ld even), columns
+ *           [0, rank) used; the factors of K^off ~ U diag(S) V^H.
+ *   S       device, rank floats.
+ *   diag    device, N complex64 (K^diag).
+ *   x, y    device, N complex64 each, 16-byte aligned, not aliasing.
+ *   stream  cudaStream_t the work is queued on (NULL = legacy default stream).
+ *
+ * Intermediate vectors live in one fixed device array of 2.4 MiB ((152 + 1) x 2048
+ * complex64) defined in the library, which every GPU that loads the library holds until
+ * the process exits; rank above 2048 is rejected with TDAGW_ERR_INVALID_ARG.  The first
+ * call on each device looks up that array's device address (cudaGetSymbolAddress, which
+ * may load the library's device code); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; every value a call
+ * reads from it is written by the same call first, so nothing needs clearing.  Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on the array:
+ * serialise them.  Errors: TDAGW_ERR_INVALID_ARG for NULL or misaligned pointers, N < 1,
+ * rank outside [1, 2048], odd ld or ld < rank; TDAGW_ERR_CUDA if the address lookup or a
+ * launch fails. */
+int tdagw_apply_lowrank_noalloc(const void* U, const void* V, int64_t ld, const float* S,
+                                const void* diag, int64_t N, int rank, const void* x, void* y,
+                                void* stream);
+
 /* Wait for all work queued on the context's stream.  Reports TDAGW_ERR_TIMEOUT if a bounded
  * device-side wait of the last propagation gave up (also reported by tdagw_observables to
  * host memory and tdagw_get_state). */

@@ -62,6 +62,7 @@ _SIGS = {
     "tdagw_get_state": [_P, _D, _D, _I64],
     "tdagw_set_state": [_P, _D, _D, ct.c_int64],
     "tdagw_sync": [_P],
+    "tdagw_apply_lowrank_noalloc": [_P, _P, ct.c_int64, _P, _P, ct.c_int64, ct.c_int, _P, _P, _P],
 }
 EXPORTED = sorted(list(_SIGS) + ["tdagw_last_error", "tdagw_destroy"])
 
@@ -211,6 +212,15 @@ def tdagw_set_state(ctx: int, drho, carry=None, step: int = 0):
     drho = np.ascontiguousarray(drho, np.complex128)
     c = None if carry is None else np.ascontiguousarray(carry, np.complex128)
     _check(lib().tdagw_set_state(_P(ctx), _dptr(drho), _dptr(c), int(step)))
+
+
+def tdagw_apply_lowrank_noalloc(U, V, S, diag, x, y, stream: int | None = None):
+    """Allocation-free low-rank contraction on caller-owned CUDA tensors: U, V complex64
+    (N, ld) with ld even, S float32 (rank,), diag/x/y complex64 (N,); rank = len(S)."""
+    N, ld = U.shape
+    _check(lib().tdagw_apply_lowrank_noalloc(
+        _P(_devptr(U)), _P(_devptr(V)), ld, _P(_devptr(S)), _P(_devptr(diag)), N, S.shape[0],
+        _P(_devptr(x)), _P(_devptr(y)), _P(stream or 0)))
 
 
 def tdagw_sync(ctx: int):

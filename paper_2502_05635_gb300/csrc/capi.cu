@@ -15,7 +15,18 @@ struct tdagw_ctx {
 namespace tdagw {
 namespace {
 
-thread_local std::string g_err;
+}  // namespace
+
+// message of the last failing call on this thread (tdagw_last_error)
+std::string& last_error_message() {
+    thread_local std::string msg;
+    return msg;
+}
+
+namespace {
+
+std::string& g_err_ref() { return last_error_message(); }
+#define g_err g_err_ref()
 
 template <class F> int guard(F&& f) {
     try {

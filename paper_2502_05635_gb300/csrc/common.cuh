@@ -36,6 +36,9 @@ struct Error : std::runtime_error {
         if (!(cond)) throw ::tdagw::Error((code), (msg));                                  \
     } while (0)
 
+// message of the last failing call on this thread (returned by tdagw_last_error)
+std::string& last_error_message();
+
 inline void check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
