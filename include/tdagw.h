@@ -140,16 +140,23 @@ int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V
  * on device vectors of N elements in the context dtype. */
 int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
 
-/* Propagate B trajectories (B = 1 here) by classical RK4 (four stages per step, dSigma
- * re-evaluated at every stage, Kahan-compensated state accumulation) for steps[b] steps of
- * dt.  fields: B host structs.  Observables (P_x, J_x, occupation of the first conduction
- * band; Sec. "SVD acceleration") are recorded at every step including t = 0 of this call.
- * Errors: NO_FACTORS for LOWRANK without factors; NOT_BUILT before tdagw_build_kernel. */
+/* Propagate B trajectories by classical RK4 (four stages per step, dSigma re-evaluated at
+ * every stage, Kahan-compensated state accumulation) for steps[b] steps of dt; trajectory b
+ * is driven by fields[b] (B host structs).  Observables (P_x, J_x, occupation of the first
+ * conduction band; Sec. "SVD acceleration") are recorded at every step including t = 0.
+ * B = 1: the single-trajectory path (continues from the current state unless
+ * TDAGW_FLAG_RESET).  B > 1 (complex64 contexts): all trajectories in one persistent
+ * launch, each starting from drho = 0 (TDAGW_FLAG_RESET required); trajectories of
+ * different lengths are sorted so finished ones stop costing work; the state buffers of
+ * the single-trajectory path are not touched.
+ * Errors: NO_FACTORS for LOWRANK without factors; NOT_BUILT before tdagw_build_kernel;
+ * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
 
-/* Copy the observables recorded by the last tdagw_propagate: rows (steps+1) x B x 3 FP64,
- * row-major.  host != 0: out is host memory (synchronises); else device memory.
+/* Copy the observables recorded by the last tdagw_propagate: rows (max steps + 1) x B x 3
+ * FP64, row-major, trajectories in the caller's order; entries after a trajectory's last
+ * step are NaN.  host != 0: out is host memory (synchronises); else device memory.
  * max_rows bounds the rows written; *rows receives the rows available. */
 int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* rows, int host);
 

@@ -190,11 +190,12 @@ def tdagw_propagate(ctx: int, fields, steps, dt: float, mode: int, flags: int = 
     _check(lib().tdagw_propagate(_P(ctx), arr, len(fields), st, float(dt), mode, flags))
 
 
-def tdagw_observables(ctx: int, out=None) -> np.ndarray:
+def tdagw_observables(ctx: int, out=None, B: int = 1) -> np.ndarray:
+    """Observables of the last propagate: (rows, 3) for one trajectory, (rows, B, 3) for B."""
     rows = ct.c_int64()
     _check(lib().tdagw_observables(_P(ctx), None, 0, ct.byref(rows), 1))
     if out is None:
-        out = np.empty((rows.value, 3))
+        out = np.empty((rows.value, 3) if B == 1 else (rows.value, B, 3))
     _check(lib().tdagw_observables(_P(ctx), _dptr(out), out.shape[0], ct.byref(rows), 1))
     return out
 
@@ -269,3 +270,9 @@ class Context:
                   table=None) -> np.ndarray:
         tdagw_propagate(self.h, [make_field(pulse, table)], [steps], dt, mode, flags)
         return tdagw_observables(self.h)
+
+    def propagate_batch(self, pulses, steps, dt: float, mode: int = LOWRANK,
+                        flags: int = FLAG_RESET) -> np.ndarray:
+        """B trajectories in one launch; returns (max steps + 1, B, 3), NaN after the end."""
+        tdagw_propagate(self.h, [make_field(p) for p in pulses], list(steps), dt, mode, flags)
+        return tdagw_observables(self.h, B=len(pulses))

@@ -1,0 +1,629 @@
+// Batched TD-aGW propagation: B trajectories (different pulses and lengths) in one
+// persistent cooperative launch (complex64).  Across trajectories the contraction of Eq.
+// sigma-from-k becomes a matrix product: with the states as columns of X (N x B),
+//   low rank (Eq. svd_acc):  Y = S o (V^H X)  (r x B),   dSigma = K^diag o X + U Y
+//   dense:                   dSigma = K X
+// followed by the per-k commutator and RK4 stage update of Eq. tdagw for every column.
+//
+// Work split: CTA (rg, tg) owns the pair elements of a k-aligned row group rg and the
+// trajectories of group tg; trajectories are sorted by length (longest first), so the
+// active ones at step n are a prefix of length B_act(n) and each group takes an equal
+// share of that prefix -- finished trajectories cost nothing (compaction by sorting).
+// Per low-rank stage:
+//   A  P[rg] = V[rows(rg)]^H X[rows(rg), tg]        (partial over the row group)
+//   -- grid barrier --
+//   C  Y[j, tg] = S_j sum_rg P[rg][j, tg]            (each CTA: a slice of j)
+//   -- grid barrier --
+//   D  dSigma[rows(rg), tg] = U[rows(rg)] Y[:, tg] + K^diag o X
+//   E  commutator + RK4 for k in rg, trajectories in tg (rows this CTA just computed)
+// Dense stages: grid barrier (X complete), dSigma[rows(rg), tg] = K[rows(rg)] X[:, tg], E.
+// The matrix products are register-tiled (4 x 4 complex outputs per thread) FP32 FMAs
+// through shared memory.  Grid barriers are bounded waits (as in the single-trajectory
+// persistent kernel); on expiry the kernel sets an error word and returns.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "stage.cuh"
+
+namespace tdagw {
+
+namespace {
+
+constexpr int kBThreads = 512;
+constexpr int kTileB = 32;      // trajectories per CTA block (max)
+constexpr int kChunk = 16;      // reduction-dimension chunk staged in shared memory
+constexpr int kLdA = 258;       // padded row of the staged A chunk (float2), 16-B aligned
+
+struct BatchArgs {
+    // factors / kernel
+    const float2* U;      // N x ldu
+    const float2* V;      // N x ldu
+    const float* S;       // r
+    const float2* diag;   // N
+    const float2* K;      // N x N (dense mode)
+    // model (per pair element)
+    const float2* dx;
+    const float2* dy;
+    const float2* vx;
+    const float2* gap;
+    // batched state, N x Bp row-major (column b = trajectory b in sorted order)
+    float2* X;
+    float2* Ssum;
+    float2* Ccomp;
+    float2* acc;
+    float2* dS;
+    // low-rank intermediates
+    float2* P;            // Rg x r x Bp
+    float2* Y;            // r x Bp
+    // per trajectory (sorted order)
+    const double* Etab;   // B x ldE
+    const float2* dir;    // B (dir_x, dir_y)
+    const int* act;       // T_max: active trajectories during step n
+    double* red;          // Rg x Bp x 3 observables partials
+    double* obs;          // (T_max + 1) x B x 3 (sorted order)
+    unsigned long long* bar;
+    int* err;
+    int64_t N, ldE;
+    int Nk, Nb, r, ldu, Bp, B, Tmax, Rg, Tg, mode, kahan, c1;
+    float occ[4];
+    float dt;
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ uint64_t gtimer_b() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_rel(unsigned long long* p) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+
+// grid barrier with a monotonic arrival counter (see lr_persistent.cu); all threads call
+__device__ bool bgrid_sync(const BatchArgs& a, unsigned& gen, int* abort_s) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !*abort_s) {
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        red_rel(a.bar);
+        const uint64_t t0 = gtimer_b();
+        while (ld_acq(a.bar) < target) {
+            if (gtimer_b() - t0 > a.wait_ns || *(volatile int*)a.err) {
+                atomicExch(a.err, 1);
+                *abort_s = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+        gen += 1;
+    }
+    __syncthreads();
+    return !*(volatile int*)abort_s;
+}
+
+// trajectories [b0, b1) of group tg among the B_act active ones
+__device__ __forceinline__ void group_range(int Bact, int Tg, int tg, int& b0, int& b1) {
+    b0 = (int)((int64_t)tg * Bact / Tg);
+    b1 = (int)((int64_t)(tg + 1) * Bact / Tg);
+}
+
+// C[m][b] (+)= sum_q opA(q, m) Bm[q][b] for m in [0, M), b in [0, nb) (nb <= 32),
+// q in [0, Q).  opA(q, m) = conj(A[q lda + m]) (TRANS: A is Q x M, rows q) or
+// A[m lda + q] (NN: A is M x Q, rows m).  Bm rows q at Bm + q ldb.  Output accumulated in
+// registers: thread (ty, tx) owns rows m = 4 ty + {0..3} (+ 256 per pass) and columns
+// b = 4 tx + {0..3}; 64 x 8 threads cover 256 x 32 outputs per pass.
+template <bool TRANS>
+__device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int M, int Q,
+                           const float2* __restrict__ Bm, int64_t ldb, int nb,
+                           float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
+                           const float2* __restrict__ diag, const float2* __restrict__ xd,
+                           float2* sA, float2* sB) {
+    const int tid = threadIdx.x;
+    const int tx = tid % 8, ty = tid / 8;  // 8 column groups of 4, 64 row groups of 4
+    for (int m0 = 0; m0 < M; m0 += 256) {
+        float2 c[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) c[u][v] = make_float2(0.f, 0.f);
+        const int mrows = min(256, M - m0);
+        for (int q0 = 0; q0 < Q; q0 += kChunk) {
+            const int qn = min(kChunk, Q - q0);
+            // stage A chunk as sA[q][m] (kChunk x 256, padded rows) and B chunk as
+            // sB[q][b] (kChunk x 32); global reads run along contiguous memory
+            for (int e = tid; e < kChunk * 256; e += kBThreads) {
+                int q, m;
+                if (TRANS) {  // A rows are q: consecutive threads read consecutive m
+                    q = e / 256;
+                    m = e % 256;
+                } else {      // A rows are m: consecutive threads read consecutive q
+                    m = e / kChunk;
+                    q = e % kChunk;
+                }
+                float2 v = make_float2(0.f, 0.f);
+                if (q < qn && m < mrows) {
+                    if (TRANS) {
+                        v = __ldcg(A + (int64_t)(q0 + q) * lda + m0 + m);
+                        v.y = -v.y;
+                    } else {
+                        v = __ldcg(A + (int64_t)(m0 + m) * lda + q0 + q);
+                    }
+                }
+                sA[q * kLdA + m] = v;
+            }
+            for (int e = tid; e < kChunk * kTileB; e += kBThreads) {
+                const int q = e / kTileB, b = e % kTileB;
+                sB[e] = (q < qn && b < nb) ? __ldcg(Bm + (int64_t)(q0 + q) * ldb + b) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int q = 0; q < kChunk; ++q) {
+                const float4 a01 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty);
+                const float4 a23 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty + 2);
+                const float4 b01 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx);
+                const float4 b23 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx + 2);
+                const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                                      make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+                const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                                      make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) c[u][v] = cfma(av[u], bv[v], c[u][v]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = m0 + 4 * ty + u;
+            if (m >= M) continue;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int b = 4 * tx + v;
+                if (b >= nb) continue;
+                float2 r = c[u][v];
+                if (accumulate_diag) r = cfma(diag[m], __ldcg(xd + (int64_t)m * ldb + b), r);
+                out[(int64_t)m * ldo + b] = r;
+            }
+        }
+    }
+}
+
+// Commutator + RK4 stage update of one (k, trajectory) block, all NB^2 elements in
+// registers (the same arithmetic as stage_element, Eq. tdagw).  Returns the observables.
+template <int NB>
+__device__ Obs3 stage_kb(const BatchArgs& a, int k, int b, int st, float E, float2 dr) {
+    constexpr int NB2 = NB * NB;
+    const int64_t Bp = a.Bp;
+    float2 X[NB2], M[NB2];
+#pragma unroll
+    for (int g = 0; g < NB2; ++g) {
+        const int64_t i = (int64_t)k * NB2 + g;
+        X[g] = __ldcg(a.X + i * Bp + b);
+        const float2 d1 = a.dx[i], d2 = a.dy[i];
+        const float2 ds = __ldcg(a.dS + i * Bp + b);
+        M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
+    }
+    Obs3 ob{0.0, 0.0, 0.0};
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            const int g = n * NB + m;
+            const int64_t i = (int64_t)k * NB2 + g;
+            float2 comm = cscale(M[g], a.occ[m] - a.occ[n]);
+#pragma unroll
+            for (int l = 0; l < NB; ++l) {
+                comm = cfma(M[n * NB + l], X[l * NB + m], comm);
+                comm = csub(comm, cmul(X[n * NB + l], M[l * NB + m]));
+            }
+            const float2 h0 = gap_times(a.gap[i], X[g]);
+            const float2 s = cadd(h0, comm);
+            const float2 kv = make_float2(s.y, -s.x);
+            const int64_t e = i * Bp + b;
+            const float2 xs = __ldcg(a.Ssum + e), xc = __ldcg(a.Ccomp + e);
+            float2 Xn;
+            if (st < 3) {
+                const float2 ac = st == 0 ? kv : cadd(__ldcg(a.acc + e), cscale(kv, 2.f));
+                a.acc[e] = ac;
+                const float cn = st == 2 ? a.dt : 0.5f * a.dt;
+                Xn = cadd(xs, cadd(xc, cscale(kv, cn)));
+            } else {
+                const float2 ac = cadd(__ldcg(a.acc + e), kv);
+                const float2 inc = cscale(ac, a.dt / 6.f);
+                float2 ns, nc;
+                if (a.kahan) {
+                    float ex, ey;
+                    ns.x = two_sum(xs.x, inc.x, ex);
+                    ns.y = two_sum(xs.y, inc.y, ey);
+                    nc = make_float2(xc.x + ex, xc.y + ey);
+                } else {
+                    ns = cadd(xs, inc);
+                    nc = xc;
+                }
+                a.Ssum[e] = ns;
+                a.Ccomp[e] = nc;
+                Xn = cadd(ns, nc);
+                const float2 rho = (n == m) ? make_float2(Xn.x + a.occ[n], Xn.y) : Xn;
+                const float2 d1 = a.dx[i], v1 = a.vx[i];
+                ob.p += (double)rho.x * (double)d1.x + (double)rho.y * (double)d1.y;
+                ob.j += (double)rho.x * (double)v1.x + (double)rho.y * (double)v1.y;
+                if (n == m && n == a.c1) ob.o += (double)rho.x;
+            }
+            a.X[e] = Xn;
+        }
+    return ob;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    float2* sA = sm;                       // kChunk x kLdA
+    float2* sB = sA + kChunk * kLdA;       // kChunk x 32
+    double* sred = reinterpret_cast<double*>(sB + kChunk * kTileB);  // 16 x kTileB x 3
+    __shared__ int abort_s;
+    const int tid = threadIdx.x;
+    const int rg = blockIdx.x % a.Rg, tg = blockIdx.x / a.Rg;
+    const int ka = (int)((int64_t)rg * a.Nk / a.Rg), kb = (int)((int64_t)(rg + 1) * a.Nk / a.Rg);
+    const int NB2 = NB * NB;
+    const int64_t ra = (int64_t)ka * NB2;
+    const int nrows = (kb - ka) * NB2;
+    const int jr0 = (int)((int64_t)rg * a.r / a.Rg), jr1 = (int)((int64_t)(rg + 1) * a.r / a.Rg);
+    if (tid == 0) abort_s = 0;
+    __syncthreads();
+    unsigned gen = 0;
+    bool ok = true;
+    int prev_act = -1;
+    for (int n = 0; n < a.Tmax && ok; ++n) {
+        const int Bact = a.act[n];
+        int b0, b1;
+        group_range(Bact, a.Tg, tg, b0, b1);
+        const int nb = b1 - b0;
+        for (int st = 0; st < 4 && ok; ++st) {
+            const bool need_x_barrier = (a.mode == TDAGW_FULL) ? !(n == 0 && st == 0)
+                                                               : (st == 0 && Bact != prev_act && n > 0);
+            if (need_x_barrier && !(ok = bgrid_sync(a, gen, &abort_s))) break;
+            if (st == 0 && n > 0 && rg == 0 && a.mode == TDAGW_FULL) {
+                // observables of step n-1 for this group's trajectories at that step
+                int p0, p1;
+                group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+                for (int b = p0 + tid; b < p1; b += kBThreads) {
+                    double s0 = 0, s1 = 0, s2 = 0;
+                    for (int g2 = 0; g2 < a.Rg; ++g2) {
+                        s0 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3);
+                        s1 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 1);
+                        s2 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 2);
+                    }
+                    double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+                    o[0] = s0 / a.Nk;
+                    o[1] = s1 / a.Nk;
+                    o[2] = s2 / a.Nk;
+                }
+            }
+            if (a.mode == TDAGW_LOWRANK) {
+                // A: partial V^H X over this row group
+                if (nb > 0)
+                    block_gemm<true>(a.V + ra * a.ldu, a.ldu, a.r, nrows, a.X + ra * a.Bp + b0, a.Bp, nb,
+                                     a.P + (int64_t)rg * a.r * a.Bp + b0, a.Bp, false, nullptr, nullptr,
+                                     sA, sB);
+                if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
+                if (st == 0 && n > 0 && rg == 0) {
+                    int p0, p1;
+                    group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+                    for (int b = p0 + tid; b < p1; b += kBThreads) {
+                        double s0 = 0, s1 = 0, s2 = 0;
+                        for (int g2 = 0; g2 < a.Rg; ++g2) {
+                            s0 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3);
+                            s1 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 1);
+                            s2 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 2);
+                        }
+                        double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+                        o[0] = s0 / a.Nk;
+                        o[1] = s1 / a.Nk;
+                        o[2] = s2 / a.Nk;
+                    }
+                }
+                // C: Y[j][b] = S_j sum over row groups, j in this CTA's slice
+                for (int e = tid; e < (jr1 - jr0) * nb; e += kBThreads) {
+                    const int j = jr0 + e / nb, b = b0 + e % nb;
+                    float2 s = make_float2(0.f, 0.f);
+                    for (int g2 = 0; g2 < a.Rg; ++g2)
+                        s = cadd(s, __ldcg(a.P + ((int64_t)g2 * a.r + j) * a.Bp + b));
+                    a.Y[(int64_t)j * a.Bp + b] = cscale(s, a.S[j]);
+                }
+                if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
+                // D: dSigma = U Y + diag o X for this row group
+                if (nb > 0)
+                    block_gemm<false>(a.U + ra * a.ldu, a.ldu, nrows, a.r, a.Y + b0, a.Bp, nb,
+                                      a.dS + ra * a.Bp + b0, a.Bp, true, a.diag + ra, a.X + ra * a.Bp + b0,
+                                      sA, sB);
+            } else {
+                if (nb > 0)
+                    block_gemm<false>(a.K + ra * a.N, a.N, nrows, (int)a.N, a.X + b0, a.Bp, nb,
+                                      a.dS + ra * a.Bp + b0, a.Bp, false, nullptr, nullptr, sA, sB);
+                // every CTA has read all rows of X before any CTA rewrites its rows
+                if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
+            }
+            __syncthreads();
+            // E: commutator + RK4 for (k in [ka, kb), b in [b0, b1))
+            const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
+            {
+                const int bl = tid % kTileB, kg = tid / kTileB;  // 16 k-groups x 32 trajectories
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                if (bl < nb) {
+                    const int b = b0 + bl;
+                    const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                    const float2 dr = a.dir[b];
+                    for (int k = ka + kg; k < kb; k += kBThreads / kTileB) {
+                        const Obs3 ob = stage_kb<NB>(a, k, b, st, E, dr);
+                        s0 += ob.p;
+                        s1 += ob.j;
+                        s2 += ob.o;
+                    }
+                }
+                if (st == 3) {
+                    sred[(kg * kTileB + bl) * 3] = s0;
+                    sred[(kg * kTileB + bl) * 3 + 1] = s1;
+                    sred[(kg * kTileB + bl) * 3 + 2] = s2;
+                }
+            }
+            __syncthreads();
+            if (st == 3)
+                for (int bl = tid; bl < nb; bl += kBThreads) {
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    for (int kg = 0; kg < kBThreads / kTileB; ++kg) {
+                        s0 += sred[(kg * kTileB + bl) * 3];
+                        s1 += sred[(kg * kTileB + bl) * 3 + 1];
+                        s2 += sred[(kg * kTileB + bl) * 3 + 2];
+                    }
+                    double* rr = a.red + ((int64_t)rg * a.Bp + b0 + bl) * 3;
+                    rr[0] = s0;
+                    rr[1] = s1;
+                    rr[2] = s2;
+                }
+            __syncthreads();
+        }
+        prev_act = Bact;
+    }
+    // observables of the last step
+    if (ok && a.Tmax > 0 && bgrid_sync(a, gen, &abort_s) && rg == 0) {
+        const int n = a.Tmax;
+        int p0, p1;
+        group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+        for (int b = p0 + tid; b < p1; b += kBThreads) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int g2 = 0; g2 < a.Rg; ++g2) {
+                s0 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3);
+                s1 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 1);
+                s2 += __ldcg(a.red + ((int64_t)g2 * a.Bp + b) * 3 + 2);
+            }
+            double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+            o[0] = s0 / a.Nk;
+            o[1] = s1 / a.Nk;
+            o[2] = s2 / a.Nk;
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace tdagw
+
+namespace tdagw {
+
+namespace {
+
+__global__ void replicate_rows_kernel(const double* __restrict__ row, double* __restrict__ obs, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) {
+        obs[3 * b] = row[0];
+        obs[3 * b + 1] = row[1];
+        obs[3 * b + 2] = row[2];
+    }
+}
+
+// obs_out[n][perm[b]] = obs_sorted[n][b]
+__global__ void unpermute_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                 const int* __restrict__ perm, int B, int64_t rows) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * B) return;
+    const int64_t n = e / B;
+    const int b = (int)(e % B);
+    for (int q = 0; q < 3; ++q) dst[(n * B + perm[b]) * 3 + q] = src[e * 3 + q];
+}
+
+struct BatchPlan {
+    int Rg = 0, Tg = 0;
+};
+
+}  // namespace
+
+// Host driver of the batched path (complex64 contexts).  Trajectories are sorted by length
+// (longest first); the block shape (row groups x trajectory groups) is picked by timing a
+// few steps of each candidate (cached per context for this mode, batch size and rank).
+void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
+                       int mode, int flags) {
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "batched propagation needs a complex64 context");
+    TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
+                  "batched propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
+    const HostModel& h = c.hm;
+    cudaStream_t s = c.stream;
+    const int64_t N = h.N;
+    std::vector<int> perm(B);
+    for (int b = 0; b < B; ++b) perm[b] = b;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return steps[x] > steps[y]; });
+    const int Tmax = steps[perm[0]];
+    const int Bp = (B + 3) / 4 * 4;
+    const int64_t ldE = 2 * (int64_t)Tmax + 1;
+    std::vector<int> act(std::max(Tmax, 1), 0);
+    for (int n = 0; n < Tmax; ++n) {
+        int cnt = 0;
+        for (int b = 0; b < B; ++b) cnt += steps[b] > n ? 1 : 0;
+        act[n] = cnt;
+    }
+    // per-trajectory inputs in sorted order
+    c.bEtab.ensure((size_t)B * ldE * sizeof(double));
+    TDAGW_CUDA(cudaMemsetAsync(c.bEtab.p, 0, (size_t)B * ldE * sizeof(double), s));
+    std::vector<float2> dir(B);
+    for (int q = 0; q < B; ++q) {
+        const tdagw_field& f = fields[perm[q]];
+        const int64_t ns = 2 * (int64_t)steps[perm[q]] + 1;
+        double* dst = c.bEtab.as<double>() + (int64_t)q * ldE;
+        if (f.kind == TDAGW_FIELD_TABLE)
+            TDAGW_CUDA(cudaMemcpyAsync(dst, f.table, ns * sizeof(double), cudaMemcpyHostToDevice, s));
+        else
+            launch_field_table(f, 0.0, dt, ns, dst, s);
+        dir[q] = make_float2((float)f.dir_x, (float)f.dir_y);
+    }
+    c.bdir.ensure(B * sizeof(float2));
+    TDAGW_CUDA(cudaMemcpyAsync(c.bdir.p, dir.data(), B * sizeof(float2), cudaMemcpyHostToDevice, s));
+    c.bact.ensure(act.size() * sizeof(int));
+    TDAGW_CUDA(cudaMemcpyAsync(c.bact.p, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    c.bperm.ensure(B * sizeof(int));
+    TDAGW_CUDA(cudaMemcpyAsync(c.bperm.p, perm.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    // state
+    const size_t sbytes = (size_t)N * Bp * sizeof(float2);
+    for (DevBuf* b : {&c.bX, &c.bS, &c.bC, &c.bA, &c.bdS}) b->ensure(sbytes);
+    const int r = mode == TDAGW_LOWRANK ? c.rank : 0;
+    const int ldu = r + (r & 1);
+    // observables: row 0 is the equilibrium value for every trajectory
+    const int64_t rows = Tmax + 1;
+    c.bobs.ensure((size_t)rows * B * 3 * sizeof(double));
+    TDAGW_CUDA(cudaMemsetAsync(c.bobs.p, 0xFF, (size_t)rows * B * 3 * sizeof(double), s));  // NaN
+    c.obs.ensure((size_t)std::max<int64_t>(rows * B, 1) * 3 * sizeof(double));
+    TDAGW_CUDA(cudaMemsetAsync(c.X.p, 0, N * sizeof(float2), s));
+    launch_observables_row<float>(c, c.X.p, 0, s);
+    replicate_rows_kernel<<<(B + 127) / 128, 128, 0, s>>>(c.obs.as<double>(), c.bobs.as<double>(), B);
+    check_launch("replicate_rows_kernel");
+
+    int dev = 0, nsm = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = (size_t)kChunk * kLdA * sizeof(float2) + (size_t)kChunk * kTileB * sizeof(float2) +
+                        (size_t)(kBThreads / kTileB) * kTileB * 3 * sizeof(double);
+    const void* fn = h.Nb == 2 ? (const void*)batched_kernel<2> : (const void*)batched_kernel<4>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBThreads, smem));
+    TDAGW_REQUIRE(per_sm >= 1, TDAGW_ERR_UNSUPPORTED, "batched kernel does not fit on this device");
+    const int max_ctas = nsm * per_sm;
+
+    BatchArgs a{};
+    a.U = c.U.as<float2>();
+    a.V = c.V.as<float2>();
+    a.S = c.S.as<float>();
+    a.diag = c.diagF.as<float2>();
+    a.K = c.K.as<float2>();
+    a.dx = c.dx.as<float2>();
+    a.dy = c.dy.as<float2>();
+    a.vx = c.vx.as<float2>();
+    a.gap = c.gap.as<float2>();
+    a.X = c.bX.as<float2>();
+    a.Ssum = c.bS.as<float2>();
+    a.Ccomp = c.bC.as<float2>();
+    a.acc = c.bA.as<float2>();
+    a.dS = c.bdS.as<float2>();
+    a.Etab = c.bEtab.as<double>();
+    a.dir = c.bdir.as<float2>();
+    a.act = c.bact.as<int>();
+    a.obs = c.bobs.as<double>();
+    a.N = N;
+    a.ldE = ldE;
+    a.Nk = h.Nk;
+    a.Nb = h.Nb;
+    a.r = r;
+    a.ldu = ldu;
+    a.Bp = Bp;
+    a.B = B;
+    a.mode = mode;
+    a.kahan = (flags & TDAGW_FLAG_NO_KAHAN) ? 0 : 1;
+    a.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) a.occ[q] = (float)h.occ[q];
+    a.dt = (float)dt;
+    a.wait_ns = 2000000000ull;
+    c.sync.ensure(4 * sizeof(unsigned));
+    a.bar = reinterpret_cast<unsigned long long*>(c.sync.p);
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+
+    auto run = [&](const BatchPlan& pl, int T) {
+        a.Rg = pl.Rg;
+        a.Tg = pl.Tg;
+        a.Tmax = T;
+        c.bP.ensure((size_t)std::max(1, pl.Rg * std::max(r, 1)) * Bp * sizeof(float2));
+        c.bY.ensure((size_t)std::max(r, 1) * Bp * sizeof(float2));
+        c.bred.ensure((size_t)pl.Rg * Bp * 3 * sizeof(double));
+        a.P = c.bP.as<float2>();
+        a.Y = c.bY.as<float2>();
+        a.red = c.bred.as<double>();
+        for (DevBuf* b : {&c.bX, &c.bS, &c.bC}) TDAGW_CUDA(cudaMemsetAsync(b->p, 0, sbytes, s));
+        TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+        void* args[] = {&a};
+        TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(pl.Rg * pl.Tg), dim3(kBThreads), args, smem, s));
+        c.persistent_launched = true;
+    };
+
+    const int key = (mode << 28) ^ (B << 12) ^ r;
+    BatchPlan plan;
+    auto it = c.batch_plans.find(key);
+    if (it != c.batch_plans.end()) {
+        plan.Rg = it->second.first;
+        plan.Tg = it->second.second;
+    } else {
+        // candidates: at most 32 trajectories per block (the register tile), CTAs <= SMs
+        std::vector<BatchPlan> cands;
+        const int tg_min = (B + kTileB - 1) / kTileB;
+        for (int tg = tg_min; tg <= std::min(B, 8 * tg_min); tg *= 2) {
+            const int rg = std::min(h.Nk, max_ctas / tg);
+            if (rg >= 1) cands.push_back({rg, tg});
+        }
+        TDAGW_REQUIRE(!cands.empty(), TDAGW_ERR_UNSUPPORTED, "too many trajectories for one launch");
+        if (cands.size() == 1 || Tmax < 8) {
+            plan = cands[0];
+        } else {
+            cudaEvent_t e0, e1;
+            TDAGW_CUDA(cudaEventCreate(&e0));
+            TDAGW_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (const BatchPlan& pl : cands) {
+                run(pl, 2);  // warm
+                TDAGW_CUDA(cudaEventRecord(e0, s));
+                run(pl, 6);
+                TDAGW_CUDA(cudaEventRecord(e1, s));
+                TDAGW_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                TDAGW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    plan = pl;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            int err = 0;
+            TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
+            TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the batched kernel");
+            // the tuning runs overwrote the observables: restore the first row
+            TDAGW_CUDA(cudaMemsetAsync(c.bobs.p, 0xFF, (size_t)rows * B * 3 * sizeof(double), s));
+            replicate_rows_kernel<<<(B + 127) / 128, 128, 0, s>>>(c.obs.as<double>(), c.bobs.as<double>(), B);
+            check_launch("replicate_rows_kernel");
+        }
+        c.batch_plans[key] = {plan.Rg, plan.Tg};
+    }
+    run(plan, Tmax);
+    c.last_plan_rg = plan.Rg;
+    c.last_plan_tg = plan.Tg;
+    // observables in the caller's trajectory order
+    c.obs.ensure((size_t)rows * B * 3 * sizeof(double));
+    unpermute_kernel<<<(unsigned)((rows * B + 255) / 256), 256, 0, s>>>(c.bobs.as<double>(), c.obs.as<double>(),
+                                                                       c.bperm.as<int>(), B, rows);
+    check_launch("unpermute_kernel");
+    c.obs_rows = rows;
+    c.obs_B = B;
+}
+
+}  // namespace tdagw

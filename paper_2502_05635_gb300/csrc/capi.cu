@@ -464,21 +464,32 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
     return guard([&] {
         TDAGW_REQUIRE(ctx && fields && steps, TDAGW_ERR_INVALID_ARG, "NULL argument");
         require_built(ctx->c);
-        TDAGW_REQUIRE(B == 1, TDAGW_ERR_UNSUPPORTED, "this entry point propagates one trajectory");
-        TDAGW_REQUIRE(steps[0] >= 0 && steps[0] <= (1 << 26), TDAGW_ERR_INVALID_ARG, "bad step count");
+        TDAGW_REQUIRE(B >= 1 && B <= 65536, TDAGW_ERR_INVALID_ARG, "B must be in [1, 65536]");
+        for (int b = 0; b < B; ++b)
+            TDAGW_REQUIRE(steps[b] >= 0 && steps[b] <= (1 << 26), TDAGW_ERR_INVALID_ARG, "bad step count");
         TDAGW_REQUIRE(dt > 0 && dt < 1e6, TDAGW_ERR_INVALID_ARG, "bad dt");
         TDAGW_REQUIRE(mode == TDAGW_FULL || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG, "bad mode");
         TDAGW_REQUIRE(mode == TDAGW_FULL || ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS,
                       "low-rank mode needs factors (tdagw_compress_svd or tdagw_set_factors)");
-        const tdagw_field& f = fields[0];
-        TDAGW_REQUIRE(f.kind >= 0 && f.kind <= 3, TDAGW_ERR_INVALID_ARG, "bad field kind");
-        TDAGW_REQUIRE(f.kind != TDAGW_FIELD_TABLE || f.table, TDAGW_ERR_INVALID_ARG,
-                      "table field without samples");
-        TDAGW_REQUIRE(f.kind != TDAGW_FIELD_GAUSS_COS || f.sigma > 0, TDAGW_ERR_INVALID_ARG,
-                      "sigma must be positive");
-        TDAGW_REQUIRE(f.kind != TDAGW_FIELD_SIN2_SIN || f.T_pulse > 0, TDAGW_ERR_INVALID_ARG,
-                      "T_pulse must be positive");
-        DISPATCH(ctx, propagate, ctx->c, f, steps[0], dt, mode, flags);
+        for (int b = 0; b < B; ++b) {
+            const tdagw_field& f = fields[b];
+            TDAGW_REQUIRE(f.kind >= 0 && f.kind <= 3, TDAGW_ERR_INVALID_ARG, "bad field kind");
+            TDAGW_REQUIRE(f.kind != TDAGW_FIELD_TABLE || f.table, TDAGW_ERR_INVALID_ARG,
+                          "table field without samples");
+            TDAGW_REQUIRE(f.kind != TDAGW_FIELD_GAUSS_COS || f.sigma > 0, TDAGW_ERR_INVALID_ARG,
+                          "sigma must be positive");
+            TDAGW_REQUIRE(f.kind != TDAGW_FIELD_SIN2_SIN || f.T_pulse > 0, TDAGW_ERR_INVALID_ARG,
+                          "T_pulse must be positive");
+        }
+        if (B == 1) {
+            DISPATCH(ctx, propagate, ctx->c, fields[0], steps[0], dt, mode, flags);
+            ctx->c.obs_B = 1;
+        } else {
+            int tmax = 0;
+            for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);
+            TDAGW_REQUIRE(tmax > 0, TDAGW_ERR_INVALID_ARG, "at least one trajectory needs steps");
+            propagate_batched(ctx->c, fields, B, steps, dt, mode, flags);
+        }
     });
 }
 
@@ -490,7 +501,7 @@ int tdagw_observables(tdagw_ctx* ctx, double* out, int64_t max_rows, int64_t* ro
         const int64_t n = std::min<int64_t>(max_rows, ctx->c.obs_rows);
         if (n <= 0) return;
         cudaStream_t s = ctx->c.stream;
-        TDAGW_CUDA(cudaMemcpyAsync(out, ctx->c.obs.p, n * 3 * sizeof(double),
+        TDAGW_CUDA(cudaMemcpyAsync(out, ctx->c.obs.p, n * ctx->c.obs_B * 3 * sizeof(double),
                                    host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
         if (host) {
             TDAGW_CUDA(cudaStreamSynchronize(s));

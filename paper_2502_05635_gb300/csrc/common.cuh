@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <complex>
+#include <map>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -160,6 +161,11 @@ struct Ctx {
     // persistent low-rank launch: partial vectors, grid-barrier words and error flag
     DevBuf pbuf, sync;
     bool persistent_launched = false;
+    // batched propagation: states N x Bp, intermediates, per-trajectory tables
+    DevBuf bX, bS, bC, bA, bdS, bP, bY, bred, bobs, bEtab, bdir, bact, bperm;
+    std::map<int, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
+    int last_plan_rg = 0, last_plan_tg = 0;
+    int obs_B = 1;           // trajectories in the recorded observables
     // stream used only to capture CUDA graphs (the caller's stream may be the legacy
     // default stream, on which capture is not allowed); graphs are launched on `stream`
     cudaStream_t cap = nullptr;
@@ -207,6 +213,10 @@ template <typename R>
 void launch_convert_in(const double2* src, void* dst, int64_t n, cudaStream_t s);
 template <typename R>
 void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s);
+
+// Batched propagation of B trajectories (complex64, from drho = 0).
+void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
+                       int mode, int flags);
 
 // Persistent single-trajectory low-rank propagation (complex64); false if not applicable.
 bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
