@@ -45,6 +45,7 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--full-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -172,6 +173,36 @@ def run_reference(a):
                                        f"low-rank apply with seeded rank-1024 factors ({secs:.1f} s)"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(tg, torch, stream, sh):
+    """Field sweep: 256 trajectories of uneven length (500-4000 steps) in one launch,
+    two-band 24 x 24 model (N = 2304), rank 256; low-rank vs dense kernel."""
+    w = wl.sweep_nb2_l24()
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    fields = [tg.make_field(p) for p in w.pulses]
+    total = int(sum(w.steps))
+    out = {"workload": "sweep_nb2_l24", "N": w.model.N, "B": w.B, "rank": w.rank,
+           "traj_steps": total, "max_steps": int(max(w.steps))}
+    for name, mode in (("lowrank", tg.LOWRANK), ("full", tg.FULL)):
+        # first call tunes the block shape (cached per context, mode and batch size)
+        tg.tdagw_propagate(ctx.h, fields, [min(16, s) for s in w.steps], w.dt, mode, tg.FLAG_RESET)
+        tg.tdagw_sync(ctx.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        tg.tdagw_propagate(ctx.h, fields, list(w.steps), w.dt, mode, tg.FLAG_RESET)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tg.tdagw_sync(ctx.h)
+        flops = total * 4 * (2 * 8 * w.model.N * w.rank if mode == tg.LOWRANK else 8 * w.model.N ** 2)
+        out[name] = {"value": total / (ms * 1e-3), "unit": "traj*steps/s", "ms": ms,
+                     "algorithmic_tflops": flops / (ms * 1e-3) / 1e12}
+    out["speedup_lowrank_vs_full"] = out["lowrank"]["value"] / out["full"]["value"]
+    ctx.close()
+    return out
 
 
 # ---------------------------------------------------------------- our arm -----------
@@ -325,6 +356,8 @@ def run_ours(a):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if not a.no_batched:
+        line["batched_sweep"] = bench_batched(tg, torch, stream, sh)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
