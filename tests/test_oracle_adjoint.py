@@ -1,0 +1,101 @@
+"""Pins of the oracle's discrete adjoint: vector-Jacobian identity, objective derivative,
+and central finite differences of the FP64 forward (field samples and pulse parameters).
+No GPU."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import adjoint as oa
+from oracle import kernel as ok
+from oracle import lowrank as olr
+from oracle import model as om
+from oracle import propagate as op
+
+
+@pytest.fixture(scope="module")
+def setup():
+    p = wl.small_model(4, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    return mdl, K
+
+
+def _inner(a, b):
+    return float(np.real(np.vdot(a, b)))
+
+
+def test_vjp_dot_product_identity(setup):
+    mdl, K = setup
+    rng = np.random.default_rng(0)
+    X = wl.random_state(mdl.N, 1, 0.05)
+    g = wl.random_state(mdl.N, 2, 1.0)
+    dX = wl.random_state(mdl.N, 3, 1.0)
+    E, direction = 0.003, (0.6, 0.8)
+    f = lambda x, e: op.rhs(mdl, lambda v: K @ v, e * direction[0], e * direction[1], x)
+    eps = 1e-6
+    jdx = (f(X + eps * dX, E) - f(X - eps * dX, E)) / (2 * eps)
+    jde = (f(X, E + eps) - f(X, E - eps)) / (2 * eps)
+    xbar, ebar = oa.vjp(mdl, lambda v: K @ v, lambda v: K.conj().T @ v, E, direction, X, g)
+    assert abs(_inner(g, jdx) - _inner(xbar, dX)) < 1e-8 * abs(_inner(g, jdx))
+    assert abs(_inner(g, jde) - ebar) < 1e-8 * abs(ebar)
+
+
+def test_objective_derivative():
+    rng = np.random.default_rng(4)
+    P = rng.standard_normal(101)
+    J, dJ = oa.spectral_objective(P, 0.2, 0.1)
+    for n in (0, 17, 100):
+        e = np.zeros_like(P)
+        e[n] = 1e-6
+        fd = (oa.spectral_objective(P + e, 0.2, 0.1)[0] - oa.spectral_objective(P - e, 0.2, 0.1)[0]) / 2e-6
+        assert abs(fd - dJ[n]) < 1e-7 * max(1.0, abs(fd))
+
+
+def _J_of_samples(mdl, apply, samples, dt, T, direction, w0):
+    obs, _ = op.rk4(mdl, apply, samples, dt, T, direction=direction)
+    return oa.spectral_objective(obs[:, 0], dt, w0)[0]
+
+
+@pytest.mark.parametrize("lowrank", [False, True])
+def test_adjoint_field_samples_vs_finite_differences(setup, lowrank):
+    mdl, K = setup
+    if lowrank:
+        d, Koff = ok.split_diag_off(K)
+        U, S, V = olr.truncated_svd(Koff, 9)
+        apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
+        applyH = lambda v: np.conj(d) * v + V @ (S * (U.conj().T @ v))
+    else:
+        apply, applyH = (lambda v: K @ v), (lambda v: K.conj().T @ v)
+    pulse = wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0, dir_x=0.8, dir_y=0.6)
+    dt, T = 0.2, 60
+    direction = (pulse.dir_x, pulse.dir_y)
+    samples = op.half_step_samples(pulse, dt, T)
+    obs, _ = op.rk4(mdl, apply, samples, dt, T, direction=direction)
+    _, dJdP = oa.spectral_objective(obs[:, 0], dt, pulse.omega)
+    gE = oa.adjoint(mdl, apply, applyH, samples, dt, T, direction, dJdP)
+    for j in (0, 1, 31, 60, 61, 119, 120):
+        hj = 1e-6 * max(1e-3, abs(samples[j]))
+        sp, sm = samples.copy(), samples.copy()
+        sp[j] += hj
+        sm[j] -= hj
+        fd = (_J_of_samples(mdl, apply, sp, dt, T, direction, pulse.omega)
+              - _J_of_samples(mdl, apply, sm, dt, T, direction, pulse.omega)) / (2 * hj)
+        assert abs(fd - gE[j]) <= 1e-5 * np.abs(gE).max(), (j, fd, gE[j])
+
+
+def test_adjoint_pulse_parameters_vs_finite_differences(setup):
+    mdl, K = setup
+    apply, applyH = (lambda v: K @ v), (lambda v: K.conj().T @ v)
+    pulse = wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0)
+    dt, T = 0.2, 60
+    J, gp, _ = oa.objective_and_gradients(mdl, apply, applyH, pulse, dt, T)
+    import dataclasses
+    for i, name in enumerate(("E0", "omega", "t0", "sigma")):
+        v = getattr(pulse, name)
+        h = 1e-6 * abs(v)
+        Jp = _J_of_samples(mdl, apply, op.half_step_samples(dataclasses.replace(pulse, **{name: v + h}), dt, T),
+                           dt, T, (1.0, 0.0), pulse.omega)
+        Jm = _J_of_samples(mdl, apply, op.half_step_samples(dataclasses.replace(pulse, **{name: v - h}), dt, T),
+                           dt, T, (1.0, 0.0), pulse.omega)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - gp[i]) <= 1e-5 * abs(gp[i]) + 1e-12 * abs(J), (name, fd, gp[i])
