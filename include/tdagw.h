@@ -60,10 +60,12 @@ enum {
     TDAGW_FLAG_NO_KAHAN = 4,      /* plain (uncompensated) RK4 accumulation                 */
     TDAGW_FLAG_STAGEWISE = 8,     /* low-rank c64: stage-wise kernels instead of the
                                      persistent single-launch kernel                        */
-    TDAGW_FLAG_TEST_TIMEOUT = 16  /* fault-injection hook for tests: the persistent kernel's
+    TDAGW_FLAG_TEST_TIMEOUT = 16, /* fault-injection hook for tests: the persistent kernel's
                                      grid barrier waits for one block that does not exist,
                                      every wait runs out a 20 ms budget and the call ends
                                      with TDAGW_ERR_TIMEOUT at the next synchronising call   */
+    TDAGW_FLAG_CHECKPOINT = 32    /* keep checkpoints for tdagw_adjoint (runs the batched
+                                     path, also for B = 1; needs TDAGW_FLAG_RESET)           */
 };
 
 typedef struct tdagw_ctx tdagw_ctx;
@@ -153,6 +155,18 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
+
+/* Gradients through the last tdagw_propagate (run with TDAGW_FLAG_CHECKPOINT) by the exact
+ * discrete adjoint of its RK4 steps.  The objective is any function of the recorded
+ * observables; the caller passes its derivatives dJdobs (host, (max steps + 1) x B x 3,
+ * the layout of tdagw_observables; entries after a trajectory's end are ignored).
+ * Outputs (host, may be NULL): dJdE ((2 max steps + 1) x B): dJ/dE_j for the field sample
+ * E(j dt/2) of each trajectory (the amplitude along its direction); dJdparams (B x 4):
+ * dJ/d(E0, omega, t0, sigma) for TDAGW_FIELD_GAUSS_COS pulses (zeros otherwise).  The
+ * backward sweep recomputes the forward run segment by segment from checkpoints taken
+ * every ceil(sqrt(steps)) steps.  Synchronises.  Errors: INVALID_ARG without a
+ * checkpointed run; UNSUPPORTED on complex128 contexts; TIMEOUT if a bounded wait gave up. */
+int tdagw_adjoint(tdagw_ctx* ctx, const double* dJdobs, double* dJdE, double* dJdparams);
 
 /* Copy the observables recorded by the last tdagw_propagate: rows (max steps + 1) x B x 3
  * FP64, row-major, trajectories in the caller's order; entries after a trajectory's last

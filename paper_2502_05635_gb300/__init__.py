@@ -21,7 +21,8 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_BUILT, ERR_NO_FACTORS, ERR_TIMEO
 C64, C128 = 0, 1
 FULL, LOWRANK = 0, 1
 FIELD_GAUSS_COS, FIELD_CONST, FIELD_SIN2_SIN, FIELD_TABLE = 0, 1, 2, 3
-FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN, FLAG_STAGEWISE, FLAG_TEST_TIMEOUT = 1, 2, 4, 8, 16
+FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN, FLAG_STAGEWISE, FLAG_TEST_TIMEOUT, FLAG_CHECKPOINT = \
+    1, 2, 4, 8, 16, 32
 
 
 class TdagwError(RuntimeError):
@@ -63,6 +64,7 @@ _SIGS = {
     "tdagw_set_state": [_P, _D, _D, ct.c_int64],
     "tdagw_sync": [_P],
     "tdagw_apply_lowrank_noalloc": [_P, _P, ct.c_int64, _P, _P, ct.c_int64, ct.c_int, _P, _P, _P],
+    "tdagw_adjoint": [_P, _D, _D, _D],
 }
 EXPORTED = sorted(list(_SIGS) + ["tdagw_last_error", "tdagw_destroy"])
 
@@ -224,6 +226,16 @@ def tdagw_apply_lowrank_noalloc(U, V, S, diag, x, y, stream: int | None = None):
         _P(_devptr(x)), _P(_devptr(y)), _P(stream or 0)))
 
 
+def tdagw_adjoint(ctx: int, dJdobs, steps_max: int, B: int):
+    """Gradients through the last checkpointed propagate: returns (dJ/dE_j of shape
+    (2 steps_max + 1, B), dJ/d(E0, omega, t0, sigma) of shape (B, 4))."""
+    d = np.ascontiguousarray(dJdobs, np.float64).reshape(steps_max + 1, B, 3)
+    gE = np.empty((2 * steps_max + 1, B))
+    gp = np.empty((B, 4))
+    _check(lib().tdagw_adjoint(_P(ctx), _dptr(d), _dptr(gE), _dptr(gp)))
+    return gE, gp
+
+
 def tdagw_sync(ctx: int):
     _check(lib().tdagw_sync(_P(ctx)))
 
@@ -243,6 +255,38 @@ def model_desc(p, dtype: int = C64) -> ModelDesc:
     offs = list(p.offsets) + [0.0] * (4 - len(p.offsets))
     return ModelDesc(L=p.L, nb_copies=p.nb_copies, offsets=(ct.c_double * 4)(*offs[:4]),
                      Delta=p.Delta, t=p.t, m=p.m, a=p.a, r0=p.r0, dtype=dtype)
+
+
+def propagate_autograd(context: "Context", params, pulses, steps, dt: float, mode: int = 1):
+    """P_x(t) of B trajectories as a differentiable function of their Gaussian * cos pulse
+    parameters params (B x 4 torch float64: E0, omega, t0, sigma).  Forward: one batched
+    checkpointed propagation; backward: the library's discrete adjoint.  Returns a
+    (max steps + 1, B) float64 tensor (NaN after each trajectory's end)."""
+    import dataclasses
+
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, p):
+            pv = p.detach().cpu().numpy()
+            ps = [dataclasses.replace(pl, E0=float(v[0]), omega=float(v[1]), t0=float(v[2]),
+                                      sigma=float(v[3]), kind=FIELD_GAUSS_COS)
+                  for pl, v in zip(pulses, pv)]
+            tdagw_propagate(context.h, [make_field(q) for q in ps], list(steps), dt, mode,
+                            FLAG_RESET | FLAG_CHECKPOINT)
+            obs = tdagw_observables(context.h, B=len(ps))
+            return torch.from_numpy(obs[:, :, 0].copy())
+
+        @staticmethod
+        def backward(fctx, gP):
+            g = gP.detach().cpu().numpy()
+            d = np.zeros(g.shape + (3,))
+            d[:, :, 0] = np.nan_to_num(g)
+            _, gp = tdagw_adjoint(context.h, d, g.shape[0] - 1, g.shape[1])
+            return torch.from_numpy(gp)
+
+    return _Fn.apply(params)
 
 
 class Context:

@@ -21,178 +21,17 @@
 // through shared memory.  Grid barriers are bounded waits (as in the single-trajectory
 // persistent kernel); on expiry the kernel sets an error word and returns.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <vector>
 
-#include "common.cuh"
-#include "stage.cuh"
+#include "batched_common.cuh"
 
 namespace tdagw {
 
+using namespace batched;
+
 namespace {
-
-constexpr int kBThreads = 512;
-constexpr int kTileB = 32;      // trajectories per CTA block (max)
-constexpr int kChunk = 16;      // reduction-dimension chunk staged in shared memory
-constexpr int kLdA = 258;       // padded row of the staged A chunk (float2), 16-B aligned
-
-struct BatchArgs {
-    // factors / kernel
-    const float2* U;      // N x ldu
-    const float2* V;      // N x ldu
-    const float* S;       // r
-    const float2* diag;   // N
-    const float2* K;      // N x N (dense mode)
-    // model (per pair element)
-    const float2* dx;
-    const float2* dy;
-    const float2* vx;
-    const float2* gap;
-    // batched state, N x Bp row-major (column b = trajectory b in sorted order)
-    float2* X;
-    float2* Ssum;
-    float2* Ccomp;
-    float2* acc;
-    float2* dS;
-    // low-rank intermediates
-    float2* P;            // Rg x r x Bp
-    float2* Y;            // r x Bp
-    // per trajectory (sorted order)
-    const double* Etab;   // B x ldE
-    const float2* dir;    // B (dir_x, dir_y)
-    const int* act;       // T_max: active trajectories during step n
-    double* red;          // Rg x Bp x 3 observables partials
-    double* obs;          // (T_max + 1) x B x 3 (sorted order)
-    unsigned long long* bar;
-    int* err;
-    int64_t N, ldE;
-    int Nk, Nb, r, ldu, Bp, B, Tmax, Rg, Tg, mode, kahan, c1;
-    float occ[4];
-    float dt;
-    unsigned long long wait_ns;
-};
-
-__device__ __forceinline__ uint64_t gtimer_b() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_rel(unsigned long long* p) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
-}
-
-// grid barrier with a monotonic arrival counter (see lr_persistent.cu); all threads call
-__device__ bool bgrid_sync(const BatchArgs& a, unsigned& gen, int* abort_s) {
-    __syncthreads();
-    if (threadIdx.x == 0 && !*abort_s) {
-        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
-        red_rel(a.bar);
-        const uint64_t t0 = gtimer_b();
-        while (ld_acq(a.bar) < target) {
-            if (gtimer_b() - t0 > a.wait_ns || *(volatile int*)a.err) {
-                atomicExch(a.err, 1);
-                *abort_s = 1;
-                break;
-            }
-            __nanosleep(32);
-        }
-        gen += 1;
-    }
-    __syncthreads();
-    return !*(volatile int*)abort_s;
-}
-
-// trajectories [b0, b1) of group tg among the B_act active ones
-__device__ __forceinline__ void group_range(int Bact, int Tg, int tg, int& b0, int& b1) {
-    b0 = (int)((int64_t)tg * Bact / Tg);
-    b1 = (int)((int64_t)(tg + 1) * Bact / Tg);
-}
-
-// C[m][b] (+)= sum_q opA(q, m) Bm[q][b] for m in [0, M), b in [0, nb) (nb <= 32),
-// q in [0, Q).  opA(q, m) = conj(A[q lda + m]) (TRANS: A is Q x M, rows q) or
-// A[m lda + q] (NN: A is M x Q, rows m).  Bm rows q at Bm + q ldb.  Output accumulated in
-// registers: thread (ty, tx) owns rows m = 4 ty + {0..3} (+ 256 per pass) and columns
-// b = 4 tx + {0..3}; 64 x 8 threads cover 256 x 32 outputs per pass.
-template <bool TRANS>
-__device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int M, int Q,
-                           const float2* __restrict__ Bm, int64_t ldb, int nb,
-                           float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
-                           const float2* __restrict__ diag, const float2* __restrict__ xd,
-                           float2* sA, float2* sB) {
-    const int tid = threadIdx.x;
-    const int tx = tid % 8, ty = tid / 8;  // 8 column groups of 4, 64 row groups of 4
-    for (int m0 = 0; m0 < M; m0 += 256) {
-        float2 c[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) c[u][v] = make_float2(0.f, 0.f);
-        const int mrows = min(256, M - m0);
-        for (int q0 = 0; q0 < Q; q0 += kChunk) {
-            const int qn = min(kChunk, Q - q0);
-            // stage A chunk as sA[q][m] (kChunk x 256, padded rows) and B chunk as
-            // sB[q][b] (kChunk x 32); global reads run along contiguous memory
-            for (int e = tid; e < kChunk * 256; e += kBThreads) {
-                int q, m;
-                if (TRANS) {  // A rows are q: consecutive threads read consecutive m
-                    q = e / 256;
-                    m = e % 256;
-                } else {      // A rows are m: consecutive threads read consecutive q
-                    m = e / kChunk;
-                    q = e % kChunk;
-                }
-                float2 v = make_float2(0.f, 0.f);
-                if (q < qn && m < mrows) {
-                    if (TRANS) {
-                        v = __ldcg(A + (int64_t)(q0 + q) * lda + m0 + m);
-                        v.y = -v.y;
-                    } else {
-                        v = __ldcg(A + (int64_t)(m0 + m) * lda + q0 + q);
-                    }
-                }
-                sA[q * kLdA + m] = v;
-            }
-            for (int e = tid; e < kChunk * kTileB; e += kBThreads) {
-                const int q = e / kTileB, b = e % kTileB;
-                sB[e] = (q < qn && b < nb) ? __ldcg(Bm + (int64_t)(q0 + q) * ldb + b) : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int q = 0; q < kChunk; ++q) {
-                const float4 a01 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty);
-                const float4 a23 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty + 2);
-                const float4 b01 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx);
-                const float4 b23 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx + 2);
-                const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
-                                      make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
-                const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
-                                      make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) c[u][v] = cfma(av[u], bv[v], c[u][v]);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int m = m0 + 4 * ty + u;
-            if (m >= M) continue;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int b = 4 * tx + v;
-                if (b >= nb) continue;
-                float2 r = c[u][v];
-                if (accumulate_diag) r = cfma(diag[m], __ldcg(xd + (int64_t)m * ldb + b), r);
-                out[(int64_t)m * ldo + b] = r;
-            }
-        }
-    }
-}
 
 // Commutator + RK4 stage update of one (k, trajectory) block, all NB^2 elements in
 // registers (the same arithmetic as stage_element, Eq. tdagw).  Returns the observables.
@@ -280,10 +119,19 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
     bool ok = true;
     int prev_act = -1;
     for (int n = 0; n < a.Tmax && ok; ++n) {
-        const int Bact = a.act[n];
+        const int Bact = a.act[a.n0 + n];
         int b0, b1;
         group_range(Bact, a.Tg, tg, b0, b1);
         const int nb = b1 - b0;
+        if (a.ckS && (a.n0 + n) % a.ck_period == 0) {
+            // checkpoint of the compensated state at the start of step n0 + n (own block)
+            const int64_t slot = (int64_t)((a.n0 + n) / a.ck_period) * a.N * a.Bp;
+            for (int e = threadIdx.x; e < nrows * nb; e += kBThreads) {
+                const int64_t off = (ra + e / nb) * a.Bp + b0 + e % nb;
+                a.ckS[slot + off] = __ldcg(a.Ssum + off);
+                a.ckC[slot + off] = __ldcg(a.Ccomp + off);
+            }
+        }
         for (int st = 0; st < 4 && ok; ++st) {
             const bool need_x_barrier = (a.mode == TDAGW_FULL) ? !(n == 0 && st == 0)
                                                                : (st == 0 && Bact != prev_act && n > 0);
@@ -291,7 +139,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
             if (st == 0 && n > 0 && rg == 0 && a.mode == TDAGW_FULL) {
                 // observables of step n-1 for this group's trajectories at that step
                 int p0, p1;
-                group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+                group_range(a.act[a.n0 + n - 1], a.Tg, tg, p0, p1);
                 for (int b = p0 + tid; b < p1; b += kBThreads) {
                     double s0 = 0, s1 = 0, s2 = 0;
                     for (int g2 = 0; g2 < a.Rg; ++g2) {
@@ -314,7 +162,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                 if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
                 if (st == 0 && n > 0 && rg == 0) {
                     int p0, p1;
-                    group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+                    group_range(a.act[a.n0 + n - 1], a.Tg, tg, p0, p1);
                     for (int b = p0 + tid; b < p1; b += kBThreads) {
                         double s0 = 0, s1 = 0, s2 = 0;
                         for (int g2 = 0; g2 < a.Rg; ++g2) {
@@ -350,6 +198,15 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                 if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
             }
             __syncthreads();
+            if (a.recX) {
+                // stage input and dSigma of this stage, for the adjoint's backward sweep
+                const int64_t slot = (int64_t)(n * 4 + st) * a.N * a.Bp;
+                for (int e = threadIdx.x; e < nrows * nb; e += kBThreads) {
+                    const int64_t off = (ra + e / nb) * a.Bp + b0 + e % nb;
+                    a.recX[slot + off] = __ldcg(a.X + off);
+                    a.recDS[slot + off] = __ldcg(a.dS + off);
+                }
+            }
             // E: commutator + RK4 for (k in [ka, kb), b in [b0, b1))
             const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
             {
@@ -357,7 +214,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                 double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                 if (bl < nb) {
                     const int b = b0 + bl;
-                    const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                    const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
                     const float2 dr = a.dir[b];
                     for (int k = ka + kg; k < kb; k += kBThreads / kTileB) {
                         const Obs3 ob = stage_kb<NB>(a, k, b, st, E, dr);
@@ -394,7 +251,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
     if (ok && a.Tmax > 0 && bgrid_sync(a, gen, &abort_s) && rg == 0) {
         const int n = a.Tmax;
         int p0, p1;
-        group_range(a.act[n - 1], a.Tg, tg, p0, p1);
+        group_range(a.act[a.n0 + n - 1], a.Tg, tg, p0, p1);
         for (int b = p0 + tid; b < p1; b += kBThreads) {
             double s0 = 0, s1 = 0, s2 = 0;
             for (int g2 = 0; g2 < a.Rg; ++g2) {
@@ -614,7 +471,38 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         }
         c.batch_plans[key] = {plan.Rg, plan.Tg};
     }
+    const bool ckpt = (flags & TDAGW_FLAG_CHECKPOINT) != 0;
+    c.adj.valid = false;
+    if (ckpt) {
+        // compensated state every ceil(sqrt(Tmax)) steps for the adjoint's recomputes
+        const int period = std::max(1, (int)std::ceil(std::sqrt((double)Tmax)));
+        const int nck = (Tmax + period - 1) / period;
+        c.ckS.ensure((size_t)nck * sbytes);
+        c.ckC.ensure((size_t)nck * sbytes);
+        a.ckS = c.ckS.as<float2>();
+        a.ckC = c.ckC.as<float2>();
+        a.ck_period = period;
+    }
     run(plan, Tmax);
+    if (ckpt) {
+        AdjointState& st = c.adj;
+        st.valid = true;
+        st.B = B;
+        st.Bp = Bp;
+        st.Tmax = Tmax;
+        st.period = a.ck_period;
+        st.Rg = plan.Rg;
+        st.Tg = plan.Tg;
+        st.mode = mode;
+        st.dt = dt;
+        st.perm = perm;
+        st.steps.assign(steps, steps + B);
+        st.fields.assign(fields, fields + B);
+        for (tdagw_field& f : st.fields) f.table = nullptr;
+        st.fwd_args.resize(sizeof(BatchArgs));
+        std::memcpy(st.fwd_args.data(), &a, sizeof(BatchArgs));
+        st.fwd_fn = fn;
+    }
     c.last_plan_rg = plan.Rg;
     c.last_plan_tg = plan.Tg;
     // observables in the caller's trajectory order

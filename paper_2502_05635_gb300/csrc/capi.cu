@@ -481,15 +481,25 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
             TDAGW_REQUIRE(f.kind != TDAGW_FIELD_SIN2_SIN || f.T_pulse > 0, TDAGW_ERR_INVALID_ARG,
                           "T_pulse must be positive");
         }
-        if (B == 1) {
+        if (B == 1 && !(flags & TDAGW_FLAG_CHECKPOINT)) {
             DISPATCH(ctx, propagate, ctx->c, fields[0], steps[0], dt, mode, flags);
             ctx->c.obs_B = 1;
+            ctx->c.adj.valid = false;
         } else {
             int tmax = 0;
             for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);
             TDAGW_REQUIRE(tmax > 0, TDAGW_ERR_INVALID_ARG, "at least one trajectory needs steps");
             propagate_batched(ctx->c, fields, B, steps, dt, mode, flags);
         }
+    });
+}
+
+int tdagw_adjoint(tdagw_ctx* ctx, const double* dJdobs, double* dJdE, double* dJdparams) {
+    return guard([&] {
+        TDAGW_REQUIRE(ctx && dJdobs, TDAGW_ERR_INVALID_ARG, "NULL argument");
+        require_built(ctx->c);
+        TDAGW_REQUIRE(ctx->c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "the adjoint needs a complex64 context");
+        adjoint_batched(ctx->c, dJdobs, dJdE, dJdparams);
     });
 }
 

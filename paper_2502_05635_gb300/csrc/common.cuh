@@ -136,6 +136,18 @@ void build_host_model(const tdagw_model_desc& d, HostModel& hm);
 
 // ------------------------------------------------------------------ context ----------
 
+// What the adjoint needs from the last checkpointed batched propagation.
+struct AdjointState {
+    bool valid = false;
+    int B = 0, Bp = 0, Tmax = 0, period = 1, Rg = 0, Tg = 0, mode = 0;
+    double dt = 0.0;
+    std::vector<int> perm, steps;          // sorted -> caller order; caller-order lengths
+    std::vector<tdagw_field> fields;       // caller order
+    std::vector<unsigned char> fwd_args;   // argument block of the forward kernel launch
+    const void* fwd_fn = nullptr;          // the forward kernel (for segment recomputes)
+};
+
+
 struct Ctx {
     tdagw_model_desc desc{};
     cudaStream_t stream = nullptr;
@@ -166,6 +178,9 @@ struct Ctx {
     std::map<int, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
     int last_plan_rg = 0, last_plan_tg = 0;
     int obs_B = 1;           // trajectories in the recorded observables
+    // checkpoints (compensated state every `period` steps) and adjoint work buffers
+    DevBuf ckS, ckC, aLam, aMu, aMusum, aC1, aMm, aKhm, aRecX, aRecDS;
+    AdjointState adj;
     // stream used only to capture CUDA graphs (the caller's stream may be the legacy
     // default stream, on which capture is not allowed); graphs are launched on `stream`
     cudaStream_t cap = nullptr;
@@ -217,6 +232,9 @@ void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s
 // Batched propagation of B trajectories (complex64, from drho = 0).
 void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
                        int mode, int flags);
+
+// Backward sweep of the last checkpointed batched propagation (host arrays).
+void adjoint_batched(Ctx& c, const double* dJdobs, double* dJdE, double* dJdparams);
 
 // Persistent single-trajectory low-rank propagation (complex64); false if not applicable.
 bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
