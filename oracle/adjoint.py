@@ -22,7 +22,7 @@ X3 = x + h/2 k2, X4 = x + h k3 and lam = dJ/dx':
     gk3 = h/3 lam + h mu4;       mu3 = VJP(X3, gk3)
     gk2 = h/3 lam + h/2 mu3;     mu2 = VJP(X2, gk2)
     gk1 = h/6 lam + h/2 mu2;     mu1 = VJP(X1, gk1)
-    dJ/dx = lam + mu1 + mu2 + mu3 + mu4 (+ the direct term of P_n)
+    dJ/dx = lam + mu1 + mu2 + mu3 + mu4 (+ the direct terms of the observables at step n)
 and dJ/dE at the stage samples is the Ebar of each stage (the two middle stages share
 the sample at t_n + dt/2).
 """
@@ -83,12 +83,29 @@ def forward_states(model, apply_K, samples, dt, T, direction):
     return obs, states
 
 
-def adjoint(model, apply_K, apply_KH, samples, dt, T, direction, dJdP):
-    """dJ/dE_j for the half-step field samples j = 0..2T, given dJ/dP_n (n = 0..T)."""
+def observable_gradients(model):
+    """Gradients of (P_x, J_x, occ_c1) with respect to the state X in the real inner product
+    <a, b> = Re sum conj(a_i) b_i.  Each observable is Re sum_k sum_nm X_nm O_mn / Nk with O
+    Hermitian (d^x, v^x, the projector on c1), so its gradient is O_nm / Nk."""
+    occ = np.zeros((model.Nk, model.Nb, model.Nb), dtype=np.complex128)
+    occ[:, model.c1, model.c1] = 1.0
+    return [o.reshape(-1) / model.Nk for o in (model.dx, model.vx, occ)]
+
+
+def adjoint(model, apply_K, apply_KH, samples, dt, T, direction, dJdP, dJdJ=None, dJdocc=None):
+    """dJ/dE_j for the half-step field samples j = 0..2T, given the derivatives of the
+    objective with respect to the observables P_x, J_x and occ_c1 at steps n = 0..T (the
+    last two optional, zero by default)."""
     _, states = forward_states(model, apply_K, samples, dt, T, direction)
-    dvec = model.dx.reshape(-1) / model.Nk               # dP_x / dx (real inner product)
+    gP, gJ, go = observable_gradients(model)
+    dJdJ = np.zeros(T + 1) if dJdJ is None else np.asarray(dJdJ)
+    dJdocc = np.zeros(T + 1) if dJdocc is None else np.asarray(dJdocc)
+
+    def direct(n):
+        return dJdP[n] * gP + dJdJ[n] * gJ + dJdocc[n] * go
+
     h = dt
-    lam = dJdP[T] * dvec
+    lam = direct(T)
     gE = np.zeros(2 * T + 1)
 
     def f(j, X):
@@ -114,7 +131,7 @@ def adjoint(model, apply_K, apply_KH, samples, dt, T, direction, dJdP):
         gE[2 * n] += e1
         gE[2 * n + 1] += e2 + e3
         gE[2 * n + 2] += e4
-        lam = lam + mu1 + mu2 + mu3 + mu4 + dJdP[n] * dvec
+        lam = lam + mu1 + mu2 + mu3 + mu4 + direct(n)
     return gE
 
 

@@ -99,3 +99,47 @@ def test_adjoint_pulse_parameters_vs_finite_differences(setup):
                            dt, T, (1.0, 0.0), pulse.omega)
         fd = (Jp - Jm) / (2 * h)
         assert abs(fd - gp[i]) <= 1e-5 * abs(gp[i]) + 1e-12 * abs(J), (name, fd, gp[i])
+
+
+def test_adjoint_all_observables_vs_finite_differences(setup):
+    """Objective weighting P, J and the c1 occupation: the direct terms of J and occ."""
+    mdl, K = setup
+    apply, applyH = (lambda v: K @ v), (lambda v: K.conj().T @ v)
+    pulse = wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0, dir_x=0.6, dir_y=0.8)
+    dt, T = 0.2, 40
+    direction = (pulse.dir_x, pulse.dir_y)
+    samples = op.half_step_samples(pulse, dt, T)
+    rng = np.random.default_rng(11)
+    W = rng.standard_normal((T + 1, 3))
+    W[:, 2] *= 50.0                                     # occupations are small; weight them up
+
+    def J_of(s):
+        obs, _ = op.rk4(mdl, apply, s, dt, T, direction=direction)
+        return float(np.sum(W * obs ** 2))
+
+    obs, _ = op.rk4(mdl, apply, samples, dt, T, direction=direction)
+    G = 2 * W * obs
+    gE = oa.adjoint(mdl, apply, applyH, samples, dt, T, direction, G[:, 0], G[:, 1], G[:, 2])
+    for j in (0, 7, 40, 41, 79, 80):
+        hj = 1e-6 * max(1e-3, abs(samples[j]))
+        sp, sm = samples.copy(), samples.copy()
+        sp[j] += hj
+        sm[j] -= hj
+        fd = (J_of(sp) - J_of(sm)) / (2 * hj)
+        assert abs(fd - gE[j]) <= 1e-5 * np.abs(gE).max(), (j, fd, gE[j])
+    # each observable's direct term matters: dropping one changes the gradient
+    for z in range(3):
+        Gz = G.copy()
+        Gz[:, z] = 0
+        gz = oa.adjoint(mdl, apply, applyH, samples, dt, T, direction, Gz[:, 0], Gz[:, 1], Gz[:, 2])
+        assert np.abs(gz - gE).max() > 1e-3 * np.abs(gE).max()
+
+
+def test_observable_gradients_match_observables(setup):
+    """<grad O, X> reproduces the observable's linear part for a random state."""
+    mdl, _ = setup
+    X = wl.random_state(mdl.N, 5, 0.1)
+    base = op.observables(mdl, np.zeros(mdl.N, dtype=np.complex128))
+    got = op.observables(mdl, X) - base
+    for g, v in zip(oa.observable_gradients(mdl), got):
+        assert abs(_inner(g, X) - v) < 1e-13
