@@ -64,8 +64,12 @@ enum {
                                      grid barrier waits for one block that does not exist,
                                      every wait runs out a 20 ms budget and the call ends
                                      with TDAGW_ERR_TIMEOUT at the next synchronising call   */
-    TDAGW_FLAG_CHECKPOINT = 32    /* keep checkpoints for tdagw_adjoint (runs the batched
+    TDAGW_FLAG_CHECKPOINT = 32,   /* keep checkpoints for tdagw_adjoint (runs the batched
                                      path, also for B = 1; needs TDAGW_FLAG_RESET)           */
+    TDAGW_FLAG_SPLIT_F16 = 64     /* low-rank c64 (any B, needs TDAGW_FLAG_RESET): factors as
+                                     split FP16 pairs (hi + lo) on the tensor cores with FP32
+                                     accumulation (three products per term); not combinable
+                                     with TDAGW_FLAG_CHECKPOINT                              */
 };
 
 typedef struct tdagw_ctx tdagw_ctx;
@@ -124,8 +128,10 @@ int tdagw_get_kernel_entries(tdagw_ctx* ctx, const int64_t* rows, const int64_t*
  * (Halko-Martinsson-Tropp range finder with `oversample` extra columns and `power_iters`
  * power iterations, Gaussian test matrix from `seed`; FP64 orthogonalisation and core
  * eigen-solve on the device, K^off being Hermitian).  Replaces any factors present.
- * precision: 0 = factors stored in the context dtype.  Errors: INVALID_ARG if
- * rank + oversample > N. */
+ * precision: 0 = factors stored in the context dtype; 1 = in addition, the split-FP16
+ * tiled copy used by TDAGW_FLAG_SPLIT_F16 is made now (otherwise on first use after the
+ * factors change; complex64 contexts only).  Errors: INVALID_ARG if rank + oversample > N
+ * or precision is not 0 or 1; UNSUPPORTED for precision 1 on a complex128 context. */
 int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
                        uint64_t seed, int precision);
 
@@ -151,8 +157,13 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * launch, each starting from drho = 0 (TDAGW_FLAG_RESET required); trajectories of
  * different lengths are sorted so finished ones stop costing work; the state buffers of
  * the single-trajectory path are not touched.
+ * With TDAGW_FLAG_SPLIT_F16 (LOWRANK, complex64, any B) the two products of Eq. svd_acc run
+ * on the tensor cores with the factors split into FP16 hi + lo pairs and FP32
+ * accumulation; P(t) then agrees with the FP32 path to about 1e-6 relative.
  * Errors: NO_FACTORS for LOWRANK without factors; NOT_BUILT before tdagw_build_kernel;
- * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET. */
+ * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
+ * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT; INVALID_ARG for TDAGW_FLAG_SPLIT_F16
+ * with FULL. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
 

@@ -21,8 +21,8 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_BUILT, ERR_NO_FACTORS, ERR_TIMEO
 C64, C128 = 0, 1
 FULL, LOWRANK = 0, 1
 FIELD_GAUSS_COS, FIELD_CONST, FIELD_SIN2_SIN, FIELD_TABLE = 0, 1, 2, 3
-FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN, FLAG_STAGEWISE, FLAG_TEST_TIMEOUT, FLAG_CHECKPOINT = \
-    1, 2, 4, 8, 16, 32
+FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN, FLAG_STAGEWISE, FLAG_TEST_TIMEOUT, FLAG_CHECKPOINT, \
+    FLAG_SPLIT_F16 = 1, 2, 4, 8, 16, 32, 64
 
 
 class TdagwError(RuntimeError):

@@ -303,21 +303,20 @@ struct BatchPlan {
 // Host driver of the batched path (complex64 contexts).  Trajectories are sorted by length
 // (longest first); the block shape (row groups x trajectory groups) is picked by timing a
 // few steps of each candidate (cached per context for this mode, batch size and rank).
-void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
-                       int mode, int flags) {
-    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "batched propagation needs a complex64 context");
-    TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
-                  "batched propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
+BatchSetup prepare_batch(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt) {
     const HostModel& h = c.hm;
     cudaStream_t s = c.stream;
     const int64_t N = h.N;
-    std::vector<int> perm(B);
+    BatchSetup bs;
+    std::vector<int>& perm = bs.perm;
+    perm.resize(B);
     for (int b = 0; b < B; ++b) perm[b] = b;
     std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return steps[x] > steps[y]; });
     const int Tmax = steps[perm[0]];
     const int Bp = (B + 3) / 4 * 4;
     const int64_t ldE = 2 * (int64_t)Tmax + 1;
-    std::vector<int> act(std::max(Tmax, 1), 0);
+    std::vector<int>& act = bs.act;
+    act.assign(std::max(Tmax, 1), 0);
     for (int n = 0; n < Tmax; ++n) {
         int cnt = 0;
         for (int b = 0; b < B; ++b) cnt += steps[b] > n ? 1 : 0;
@@ -346,8 +345,6 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     // state
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
     for (DevBuf* b : {&c.bX, &c.bS, &c.bC, &c.bA, &c.bdS}) b->ensure(sbytes);
-    const int r = mode == TDAGW_LOWRANK ? c.rank : 0;
-    const int ldu = r + (r & 1);
     // observables: row 0 is the equilibrium value for every trajectory
     const int64_t rows = Tmax + 1;
     c.bobs.ensure((size_t)rows * B * 3 * sizeof(double));
@@ -357,6 +354,45 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     launch_observables_row<float>(c, c.X.p, 0, s);
     replicate_rows_kernel<<<(B + 127) / 128, 128, 0, s>>>(c.obs.as<double>(), c.bobs.as<double>(), B);
     check_launch("replicate_rows_kernel");
+    bs.Tmax = Tmax;
+    bs.Bp = Bp;
+    bs.ldE = ldE;
+    bs.rows = rows;
+    return bs;
+}
+
+void reset_batch_observables(Ctx& c, const BatchSetup& bs, int B) {
+    TDAGW_CUDA(cudaMemsetAsync(c.bobs.p, 0xFF, (size_t)bs.rows * B * 3 * sizeof(double), c.stream));
+    replicate_rows_kernel<<<(B + 127) / 128, 128, 0, c.stream>>>(c.obs.as<double>(), c.bobs.as<double>(), B);
+    check_launch("replicate_rows_kernel");
+}
+
+void finish_batch(Ctx& c, const BatchSetup& bs, int B) {
+    const int64_t rows = bs.rows;
+    c.obs.ensure((size_t)rows * B * 3 * sizeof(double));
+    unpermute_kernel<<<(unsigned)((rows * B + 255) / 256), 256, 0, c.stream>>>(
+        c.bobs.as<double>(), c.obs.as<double>(), c.bperm.as<int>(), B, rows);
+    check_launch("unpermute_kernel");
+    c.obs_rows = rows;
+    c.obs_B = B;
+}
+
+void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
+                       int mode, int flags) {
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "batched propagation needs a complex64 context");
+    TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
+                  "batched propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
+    const HostModel& h = c.hm;
+    cudaStream_t s = c.stream;
+    const int64_t N = h.N;
+    const BatchSetup bs = prepare_batch(c, fields, B, steps, dt);
+    const std::vector<int>& perm = bs.perm;
+    const int Tmax = bs.Tmax;
+    const int Bp = bs.Bp;
+    const int64_t ldE = bs.ldE;
+    const size_t sbytes = (size_t)N * Bp * sizeof(float2);
+    const int r = mode == TDAGW_LOWRANK ? c.rank : 0;
+    const int ldu = r + (r & 1);
 
     int dev = 0, nsm = 0;
     TDAGW_CUDA(cudaGetDevice(&dev));
@@ -465,9 +501,7 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
             TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
             TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the batched kernel");
             // the tuning runs overwrote the observables: restore the first row
-            TDAGW_CUDA(cudaMemsetAsync(c.bobs.p, 0xFF, (size_t)rows * B * 3 * sizeof(double), s));
-            replicate_rows_kernel<<<(B + 127) / 128, 128, 0, s>>>(c.obs.as<double>(), c.bobs.as<double>(), B);
-            check_launch("replicate_rows_kernel");
+            reset_batch_observables(c, bs, B);
         }
         c.batch_plans[key] = {plan.Rg, plan.Tg};
     }
@@ -506,12 +540,7 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     c.last_plan_rg = plan.Rg;
     c.last_plan_tg = plan.Tg;
     // observables in the caller's trajectory order
-    c.obs.ensure((size_t)rows * B * 3 * sizeof(double));
-    unpermute_kernel<<<(unsigned)((rows * B + 255) / 256), 256, 0, s>>>(c.bobs.as<double>(), c.obs.as<double>(),
-                                                                       c.bperm.as<int>(), B, rows);
-    check_launch("unpermute_kernel");
-    c.obs_rows = rows;
-    c.obs_B = B;
+    finish_batch(c, bs, B);
 }
 
 }  // namespace tdagw

@@ -1,0 +1,905 @@
+// Batched low-rank TD-aGW propagation on the fifth-generation tensor cores, with the
+// truncated-SVD factors of Eq. svd_acc stored as split FP16 pairs (hi + lo, 8 bytes per
+// complex element like complex64).
+//
+// Per RK4 stage the two products of the low-rank contraction,
+//   Y = V^H X  (r x B)   and   dSigma = K^diag o X + U (S o Y)  (N x B),
+// run as real tcgen05 kind::f16 MMAs with FP32 accumulation in tensor memory.  Complex
+// arithmetic: the factor (the large, streamed operand) is read as an interleaved real
+// matrix (re, im per complex column) and the small operand is expanded to 2 x 2 real
+// blocks, so one real product yields real and imaginary parts in adjacent accumulator
+// columns.  Split FP16: with a = s (a_hi + a_lo), each product is accumulated as
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs; the dropped a_lo b_lo is 2^-22 relative).
+// Power-of-two scales keep the FP16 values in range: 2^(13 - e) with 2^e above the largest
+// magnitude, for U and V (measured once when the tiles are made) and, per trajectory, for
+// X (the exact maximum of the stage input) and for S o Y (bound
+// max|S| max_j ||v_j|| sqrt(2N) max|X|).
+//
+// Work of one stage (one cooperative launch for the whole propagation, one CTA per SM):
+//   A  partials of V^H X over K-ranges of rows: CTA items (trajectory group, group of up
+//      to four 128-row tiles of V^H, K-range).  The V^H tiles (pre-tiled 16 KB blocks in
+//      the MMA's shared-memory layout) stream through a ring by bulk copies; the
+//      expanded split X block is built in shared memory by the worker warps.
+//   -- grid barrier --
+//   B  Y = S o sum of partials (fixed order), expanded and split into the B-operand tiles
+//      of the second product.
+//   -- grid barrier --
+//   C  items (128-row tile of U, trajectory group): U tiles and Y tiles stream through
+//      the ring; the accumulator (128 rows x 2 columns per trajectory) is staged through
+//      shared memory and the commutator + RK4 epilogue (Eq. tdagw) runs per (k, b) block.
+//   -- grid barrier --
+// Thread 0 issues all bulk copies and MMAs (both asynchronous); eight worker warps build
+// operands and run the epilogues.  Every wait is bounded; on expiry the kernel records an
+// error, waits (bounded) for its own copies and MMAs, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "batched_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace tdagw {
+
+namespace {
+
+using namespace batched;
+
+constexpr int kWorkers = 256;
+constexpr int kTcThreads = kWorkers + 32;    // warp 0: copies and MMAs; warps 1-8: workers
+constexpr int kRing = 8;                     // ring slots of one tile each
+constexpr uint32_t kTile = 16384;            // 128 rows x 32 real columns, hi (8 KB) + lo (8 KB)
+constexpr uint32_t kHalf = 8192;
+constexpr int kKc = 32;                      // real reduction columns per tile (16 complex)
+constexpr int kGroup = 64;                   // trajectories per group: MMA N = 2 x 64 max
+constexpr int kDsLd = 65;                    // padded row (float2) of the staged dSigma tile
+constexpr uint32_t kLbo = 128, kSbo = (kKc / 8) * 128;
+constexpr uint32_t kXbuf = 128 * kDsLd * 8;  // >= two built B tiles (32 KB)
+constexpr int kTmemCols = 512;
+
+struct TcArgs {
+    const unsigned char* tU;  // Nt x nchU tiles of U (rows) x 2r (real columns)
+    const unsigned char* tV;  // Mt x nchV tiles of V^T (rows j) x 2 Np (real columns)
+    unsigned char* tY;        // Gmax x nchU tiles: expanded split S o Y (rows 2b + c)
+    float2* P;                // KS x rp x Bp raw partials of V^H X
+    unsigned* xmax;           // 3 x Bp: max(|Re|, |Im|) of the stage input (float bits)
+    const float* S;
+    const float2* diag;
+    const float2* dx;
+    const float2* dy;
+    const float2* vx;
+    const float2* gap;
+    float2* X;
+    float2* Ssum;
+    float2* Ccomp;
+    float2* acc;
+    const double* Etab;
+    const float2* dir;
+    const int* act;
+    double* red;  // Nt x Bp x 3
+    double* obs;  // (Tmax + 1) x B x 3
+    unsigned long long* bar;
+    int* err;
+    int64_t N, ldE;
+    int Nk, r, rp, Nt, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;
+    float occ[4];
+    float dt;
+    float su, sv;   // power-of-two scales of the U and V tiles
+    float ybound;   // max|S| max_j ||v_j|| sqrt(2N): |(S o Y)_jb| <= ybound max|X_b|
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity; false on expiry or abort
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
+                                        unsigned long long budget) {
+    if (mb_try(b, parity)) return true;
+    const uint64_t t0 = gtime();
+    for (uint32_t i = 1;; ++i) {
+        if (mb_try(b, parity)) return true;
+        if ((i & 63) == 0) {
+            if (abort_s && *abort_s) return false;
+            if (gtime() - t0 > budget) return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void workers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
+}
+
+// 2^(13 - e) for bound < 2^e (1 for a zero bound)
+__device__ __forceinline__ float pow2_scale(float bound) {
+    if (!(bound > 0.f)) return 1.f;
+    int e;
+    frexpf(bound, &e);
+    e = max(e, -100);
+    return ldexpf(1.f, 13 - e);
+}
+__device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+}
+
+// grid barrier over the monotonic arrival counter (all threads call)
+__device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !*abort_s) {
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        red_rel(a.bar);
+        const uint64_t t0 = gtime();
+        while (ld_acq(a.bar) < target) {
+            if (gtime() - t0 > a.wait_ns || *(volatile int*)a.err) {
+                atomicExch(a.err, 1);
+                *abort_s = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+        gen += 1;
+    }
+    __syncthreads();
+    return !*(volatile int*)abort_s;
+}
+
+// Thread 0's copy/MMA pipeline over the ring.  Tiles of an item are numbered 0..nt-1 in
+// consumption order (tpc tiles per chunk); tile i lands in ring slot (pos0 + i) % kRing.
+struct Ring {
+    uint64_t* full;
+    uint64_t* empty;
+    unsigned char* buf;
+    uint32_t pos0;       // ring position of the item's first tile
+    int issued, waited;  // tiles issued / tiles whose arrival thread 0 has seen
+};
+
+template <typename Src>
+__device__ __forceinline__ bool ring_issue(Ring& R, const Src& src, volatile int* abort_s,
+                                           unsigned long long budget) {
+    const uint32_t pos = R.pos0 + (uint32_t)R.issued;
+    const uint32_t slot = pos % kRing, use = pos / kRing;
+    if (!mb_wait(R.empty + slot, (use & 1u) ^ 1u, abort_s, budget)) return false;
+    mb_expect_tx(R.full + slot, kTile);
+    bulk_load(R.buf + slot * kTile, src(R.issued), kTile, R.full + slot);
+    ++R.issued;
+    return true;
+}
+__device__ __forceinline__ bool ring_arrived(Ring& R, int i, volatile int* abort_s, unsigned long long budget) {
+    const uint32_t pos = R.pos0 + (uint32_t)i;
+    const bool ok = mb_wait(R.full + pos % kRing, (pos / kRing) & 1u, abort_s, budget);
+    if (ok) R.waited = max(R.waited, i + 1);
+    return ok;
+}
+__device__ __forceinline__ uint32_t ring_slot_addr(const Ring& R, int i) {
+    return tc::smem_u32(R.buf + ((R.pos0 + (uint32_t)i) % kRing) * kTile);
+}
+// after an abort: wait (bounded, ignoring the abort flag) for every issued copy
+__device__ void ring_drain(Ring& R, unsigned long long budget) {
+    for (int i = R.waited; i < R.issued; ++i) {
+        const uint32_t pos = R.pos0 + (uint32_t)i;
+        mb_wait(R.full + pos % kRing, (pos / kRing) & 1u, nullptr, budget);
+    }
+    R.waited = R.issued;
+}
+
+// the three split products of one 128 x N x 32 tile pair (two K = 16 steps each)
+__device__ __forceinline__ void mma_tile(uint32_t d, uint32_t a_addr, uint32_t b_addr, uint32_t idesc, bool first) {
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ah = tc::sdesc(a_addr + ks * 256, kLbo, kSbo);
+        const uint64_t al = tc::sdesc(a_addr + kHalf + ks * 256, kLbo, kSbo);
+        const uint64_t bh = tc::sdesc(b_addr + ks * 256, kLbo, kSbo);
+        const uint64_t bl = tc::sdesc(b_addr + kHalf + ks * 256, kLbo, kSbo);
+        tc::mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+        tc::mma_f16(d, ah, bl, idesc, 1u);
+        tc::mma_f16(d, al, bh, idesc, 1u);
+    }
+}
+
+// Commutator + RK4 stage update of one (k, trajectory) block (Eq. tdagw; the arithmetic of
+// the FP32 batched path), with the low-rank part of dSigma read from shared memory (row g
+// of the block at dsl[g * kDsLd]) and K^diag o X added here.  xm: running max(|Re|, |Im|)
+// of the values written to X (the next stage input).
+template <int NB>
+__device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
+                            const float2* dsl, float& xm) {
+    constexpr int NB2 = NB * NB;
+    const int64_t Bp = a.Bp;
+    float2 X[NB2], M[NB2];
+#pragma unroll
+    for (int g = 0; g < NB2; ++g) {
+        const int64_t i = (int64_t)k * NB2 + g;
+        X[g] = __ldcg(a.X + i * Bp + b);
+        const float2 d1 = a.dx[i], d2 = a.dy[i];
+        const float2 ds = cfma(a.diag[i], X[g], dsl[g * kDsLd]);
+        M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
+    }
+    Obs3 ob{0.0, 0.0, 0.0};
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            const int g = n * NB + m;
+            const int64_t i = (int64_t)k * NB2 + g;
+            float2 comm = cscale(M[g], a.occ[m] - a.occ[n]);
+#pragma unroll
+            for (int l = 0; l < NB; ++l) {
+                comm = cfma(M[n * NB + l], X[l * NB + m], comm);
+                comm = csub(comm, cmul(X[n * NB + l], M[l * NB + m]));
+            }
+            const float2 h0 = gap_times(a.gap[i], X[g]);
+            const float2 s = cadd(h0, comm);
+            const float2 kv = make_float2(s.y, -s.x);
+            const int64_t e = i * Bp + b;
+            const float2 xs = __ldcg(a.Ssum + e), xc = __ldcg(a.Ccomp + e);
+            float2 Xn;
+            if (st < 3) {
+                const float2 ac = st == 0 ? kv : cadd(__ldcg(a.acc + e), cscale(kv, 2.f));
+                a.acc[e] = ac;
+                const float cn = st == 2 ? a.dt : 0.5f * a.dt;
+                Xn = cadd(xs, cadd(xc, cscale(kv, cn)));
+            } else {
+                const float2 ac = cadd(__ldcg(a.acc + e), kv);
+                const float2 inc = cscale(ac, a.dt / 6.f);
+                float2 ns, nc;
+                if (a.kahan) {
+                    float ex, ey;
+                    ns.x = two_sum(xs.x, inc.x, ex);
+                    ns.y = two_sum(xs.y, inc.y, ey);
+                    nc = make_float2(xc.x + ex, xc.y + ey);
+                } else {
+                    ns = cadd(xs, inc);
+                    nc = xc;
+                }
+                a.Ssum[e] = ns;
+                a.Ccomp[e] = nc;
+                Xn = cadd(ns, nc);
+                const float2 rho = (n == m) ? make_float2(Xn.x + a.occ[n], Xn.y) : Xn;
+                const float2 d1 = a.dx[i], v1 = a.vx[i];
+                ob.p += (double)rho.x * (double)d1.x + (double)rho.y * (double)d1.y;
+                ob.j += (double)rho.x * (double)v1.x + (double)rho.y * (double)v1.y;
+                if (n == m && n == a.c1) ob.o += (double)rho.x;
+            }
+            a.X[e] = Xn;
+            xm = fmaxf(xm, fmaxf(fabsf(Xn.x), fabsf(Xn.y)));
+        }
+    return ob;
+}
+
+struct Groups {
+    int G, MGn, KS;
+};
+__device__ __forceinline__ Groups stage_groups(const TcArgs& a, int Bact) {
+    Groups q;
+    q.G = (Bact + kGroup - 1) / kGroup;
+    q.MGn = (a.Mt + 3) / 4;
+    q.KS = max(1, min((int)gridDim.x / max(1, q.G * q.MGn), a.nchV));
+    return q;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* ring_buf = smem;
+    unsigned char* xbuf = ring_buf + kRing * kTile;
+    float2* sDS = reinterpret_cast<float2*>(xbuf);
+    double* sred = reinterpret_cast<double*>(xbuf + kXbuf);
+    float* ssc = reinterpret_cast<float*>(sred + kWorkers * 3);
+    unsigned* smx = reinterpret_cast<unsigned*>(ssc + kGroup);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smx + kGroup);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kRing;
+    uint64_t* bfull = bars + 2 * kRing;
+    uint64_t* bempty = bfull + 2;
+    uint64_t* done = bempty + 2;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_s;
+
+    const int tid = threadIdx.x;
+    const int warp = tid / 32, lane = tid % 32;
+    const int wt = tid - 32;  // worker index (warps 1-8)
+    const bool worker = warp >= 1;
+    constexpr int NB2 = NB * NB;
+    const unsigned long long budget = a.wait_ns;
+    volatile int* vabort = &abort_s;
+
+    if (tid == 0) {
+        abort_s = 0;
+        for (int s = 0; s < kRing; ++s) {
+            mb_init(full + s, 1);
+            mb_init(empty + s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mb_init(bfull + s, kWorkers);
+            mb_init(bempty + s, 1);
+        }
+        mb_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_base;
+
+    Ring R{full, empty, ring_buf, 0u, 0, 0};
+    uint32_t bcnt = 0;  // uses of the two built-B buffers so far
+    uint32_t dcnt = 0;  // completions of `done` so far
+    unsigned gen = 0;
+    bool ok = true;
+
+    // thread 0 after an abort: no copy or MMA of this CTA may remain in flight
+    auto quiesce = [&]() {
+        ring_drain(R, budget);
+        tc::mma_commit(done);
+        mb_wait(done, dcnt & 1u, nullptr, budget);
+        ++dcnt;
+    };
+    auto fail = [&]() {
+        atomicExch(a.err, 1);
+        abort_s = 1;
+    };
+
+    for (int n = 0; n < a.Tmax && ok; ++n) {
+        const int Bact = a.act[n];
+        const Groups q = stage_groups(a, Bact);
+        for (int st = 0; st < 4 && ok; ++st) {
+            const int gs = 4 * n + st;
+            const unsigned* xin = a.xmax + (gs % 3) * a.Bp;
+            unsigned* xout = a.xmax + ((gs + 1) % 3) * a.Bp;
+            if (blockIdx.x == 0)
+                for (int b = tid; b < a.Bp; b += kTcThreads) xout[b] = 0u;
+
+            // ---------------- A: partials of V^H X ----------------
+            const int nA = q.G * q.MGn * q.KS;
+            for (int item = blockIdx.x; item < nA && ok; item += gridDim.x) {
+                const int g = item % q.G, mg = (item / q.G) % q.MGn, ks = item / (q.G * q.MGn);
+                int b0, b1;
+                group_range(Bact, q.G, g, b0, b1);
+                const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                const int m0 = 4 * mg, mc = min(4, a.Mt - m0);
+                const int c0 = (int)((int64_t)ks * a.nchV / q.KS), c1 = (int)((int64_t)(ks + 1) * a.nchV / q.KS);
+                const int nch = c1 - c0;
+                if (worker && wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
+                if (worker) workers_sync();
+                if (tid == 0) {
+                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
+                    const int nt = nch * mc;
+                    auto src = [&](int i) {
+                        const int c = c0 + i / mc, m = m0 + i % mc;
+                        return a.tV + ((int64_t)m * a.nchV + c) * kTile;
+                    };
+                    R.issued = R.waited = 0;
+                    for (int cc = 0; cc < nch && ok; ++cc) {
+                        while (ok && R.issued < (cc + 1) * mc) ok = ring_issue(R, src, vabort, budget);
+                        for (int i = cc * mc; ok && i < (cc + 1) * mc; ++i) ok = ring_arrived(R, i, vabort, budget);
+                        const uint32_t bu = bcnt + cc;
+                        if (ok) ok = mb_wait(bfull + (bu & 1), (bu >> 1) & 1u, vabort, budget);
+                        if (!ok) break;
+                        tc::fence_after_sync();
+                        const uint32_t baddr = tc::smem_u32(xbuf + (bu & 1) * kTile);
+                        for (int ml = 0; ml < mc; ++ml)
+                            mma_tile(tm + ml * 128, ring_slot_addr(R, cc * mc + ml), baddr, idesc, cc == 0);
+                        for (int ml = 0; ml < mc; ++ml)
+                            tc::mma_commit(empty + (R.pos0 + cc * mc + ml) % kRing);
+                        tc::mma_commit(bempty + (bu & 1));
+                        while (ok && R.issued < nt && R.issued - kRing < cc * mc)
+                            ok = ring_issue(R, src, vabort, budget);
+                    }
+                    if (ok) {
+                        tc::mma_commit(done);
+                    } else {
+                        fail();
+                        quiesce();
+                        --dcnt;  // the item's completion below is the quiesce commit
+                    }
+                    R.pos0 += (uint32_t)R.issued;
+                } else if (worker) {
+                    // build the expanded split X block of each chunk (16 rows x nbp trajectories)
+                    for (int cc = 0; cc < nch; ++cc) {
+                        const uint32_t bu = bcnt + cc;
+                        if (!mb_wait(bempty + (bu & 1), ((bu >> 1) & 1u) ^ 1u, vabort, budget)) {
+                            fail();
+                            break;
+                        }
+                        unsigned char* tile = xbuf + (bu & 1) * kTile;
+                        const int64_t i0 = (int64_t)(c0 + cc) * 16;
+                        for (int e = wt; e < 16 * kGroup; e += kWorkers) {
+                            const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
+                            if (bl >= nbp) continue;
+                            const int64_t i = i0 + il;
+                            float2 x = make_float2(0.f, 0.f);
+                            if (bl < nbg && i < a.N) x = __ldcg(a.X + i * a.Bp + b0 + bl);
+                            const float sx = ssc[bl];
+                            __half rh, rl, ih, il2;
+                            split16(x.x * sx, rh, rl);
+                            split16(x.y * sx, ih, il2);
+                            const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * il, kKc);
+                            const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * il, kKc);
+                            *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, ih);
+                            *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, __hneg(rh));
+                            *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, il2);
+                            *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il2, __hneg(rl));
+                        }
+                        tc::fence_proxy_async();
+                        mb_arrive(bfull + (bu & 1));
+                    }
+                }
+                bcnt += nch;
+                // accumulators -> raw partials P[ks][j][b]
+                if (worker) {
+                    const bool got = mb_wait(done, dcnt & 1u, vabort, budget);
+                    tc::fence_after_sync();
+                    if (got && !*vabort) {
+                        const int quarter = warp & 3, half = (warp - 1) >> 2;
+                        const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
+                        for (int ml = 0; ml < mc; ++ml) {
+                            const int j = (m0 + ml) * 128 + 32 * quarter + lane;
+                            float2* prow = a.P + ((int64_t)ks * a.rp + j) * a.Bp + b0;
+                            for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
+                                float v[16];
+                                tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ml * 128 + 16 * u, v);
+#pragma unroll
+                                for (int p = 0; p < 8; ++p) {
+                                    const int bl = 8 * u + p;
+                                    if (bl < nbg) prow[bl] = make_float2(v[2 * p], v[2 * p + 1]);
+                                }
+                            }
+                        }
+                    } else if (!got) {
+                        fail();
+                    }
+                }
+                ++dcnt;
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (*vabort) ok = false;
+            }
+            if (ok) ok = tc_grid_sync(a, gen, &abort_s);
+            if (!ok) break;
+
+            // ---------------- B: Y = S o sum of partials -> split expanded tiles ----------------
+            {
+                const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
+                for (int g = 0; g < q.G; ++g) {
+                    int b0, b1;
+                    group_range(Bact, q.G, g, b0, b1);
+                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                    for (int64_t e = gt; e < (int64_t)a.rp * nbp; e += total) {
+                        const int j = (int)(e / nbp), bl = (int)(e % nbp);
+                        float2 v = make_float2(0.f, 0.f);
+                        if (bl < nbg && j < a.r) {
+                            const int b = b0 + bl;
+                            float2 s = make_float2(0.f, 0.f);
+                            for (int k2 = 0; k2 < q.KS; ++k2) s = cadd(s, __ldcg(a.P + ((int64_t)k2 * a.rp + j) * a.Bp + b));
+                            const float mx = __uint_as_float(__ldcg(xin + b));
+                            const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
+                            v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
+                        }
+                        __half rh, rl, ih, il;
+                        split16(v.x, rh, rl);
+                        split16(v.y, ih, il);
+                        unsigned char* tile = a.tY + ((int64_t)g * a.nchU + j / 16) * kTile;
+                        const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * (j % 16), kKc);
+                        const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * (j % 16), kKc);
+                        *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, __hneg(ih));
+                        *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, rh);
+                        *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, __hneg(il));
+                        *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il, rl);
+                    }
+                }
+                if (st == 0 && n > 0) {
+                    // observables of step n (written by the last stage of step n - 1)
+                    for (int64_t b = gt; b < a.act[n - 1]; b += total) {
+                        double s0 = 0, s1 = 0, s2 = 0;
+                        for (int t = 0; t < a.Nt; ++t) {
+                            const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
+                            s0 += __ldcg(rr);
+                            s1 += __ldcg(rr + 1);
+                            s2 += __ldcg(rr + 2);
+                        }
+                        double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+                        o[0] = s0 / a.Nk;
+                        o[1] = s1 / a.Nk;
+                        o[2] = s2 / a.Nk;
+                    }
+                }
+            }
+            // the tiles were written through the generic proxy and are read by bulk copies
+            asm volatile("fence.proxy.async;" ::: "memory");
+            if (!(ok = tc_grid_sync(a, gen, &abort_s))) break;
+
+            // ---------------- C: dSigma = U (S o Y) + K^diag o X, commutator, RK4 ----------------
+            const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
+            const int nC = a.Nt * q.G;
+            for (int item = blockIdx.x; item < nC && ok; item += gridDim.x) {
+                const int t = item % a.Nt, g = item / a.Nt;
+                int b0, b1;
+                group_range(Bact, q.G, g, b0, b1);
+                const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                if (worker && wt < kGroup) {
+                    if (wt < nbg) {
+                        const float mx = __uint_as_float(__ldcg(xin + b0 + wt));
+                        ssc[wt] = 1.f / (a.su * pow2_scale(a.ybound * mx));
+                    }
+                    smx[wt] = 0u;
+                }
+                if (tid == 0) {
+                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
+                    const int nt = 2 * a.nchU;
+                    auto src = [&](int i) {
+                        const int c = i >> 1;
+                        return (i & 1) ? a.tY + ((int64_t)g * a.nchU + c) * kTile
+                                       : a.tU + ((int64_t)t * a.nchU + c) * kTile;
+                    };
+                    R.issued = R.waited = 0;
+                    for (int cc = 0; cc < a.nchU && ok; ++cc) {
+                        while (ok && R.issued < 2 * (cc + 1)) ok = ring_issue(R, src, vabort, budget);
+                        if (ok) ok = ring_arrived(R, 2 * cc, vabort, budget);
+                        if (ok) ok = ring_arrived(R, 2 * cc + 1, vabort, budget);
+                        if (!ok) break;
+                        tc::fence_after_sync();
+                        mma_tile(tm, ring_slot_addr(R, 2 * cc), ring_slot_addr(R, 2 * cc + 1), idesc, cc == 0);
+                        tc::mma_commit(empty + (R.pos0 + 2 * cc) % kRing);
+                        tc::mma_commit(empty + (R.pos0 + 2 * cc + 1) % kRing);
+                        while (ok && R.issued < nt && R.issued - kRing < 2 * cc) ok = ring_issue(R, src, vabort, budget);
+                    }
+                    if (ok) {
+                        tc::mma_commit(done);
+                    } else {
+                        fail();
+                        quiesce();
+                        --dcnt;
+                    }
+                    R.pos0 += (uint32_t)R.issued;
+                }
+                // thread 0 has issued (or, after an abort, drained) everything: one decision
+                // for the whole CTA, taken after this barrier (the workers' named barriers
+                // below are reached by all of them or by none)
+                __syncthreads();
+                const bool go = !*vabort;
+                if (go && worker) {
+                    const bool got = mb_wait(done, dcnt & 1u, vabort, budget);
+                    tc::fence_after_sync();
+                    if (!got) fail();
+                    if (got) {
+                        // accumulator (raw U (S o Y)) -> sDS[row][bl], unscaled
+                        const int quarter = warp & 3, half = (warp - 1) >> 2;
+                        const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
+                        const int row = 32 * quarter + lane;
+                        for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
+                            float v[16];
+                            tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + 16 * u, v);
+#pragma unroll
+                            for (int p = 0; p < 8; ++p) {
+                                const int bl = 8 * u + p;
+                                if (bl < nbg) sDS[row * kDsLd + bl] = make_float2(v[2 * p] * ssc[bl], v[2 * p + 1] * ssc[bl]);
+                            }
+                        }
+                    }
+                    workers_sync();
+                    // commutator + RK4 for the tile's k-blocks and the group's trajectories
+                    const int kt = min(128 / NB2, a.Nk - t * (128 / NB2));
+                    const int kgroups = kWorkers / nbg;
+                    const int bl = wt % nbg, kg = wt / nbg;
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    float xm = 0.f;
+                    if (kg < kgroups) {
+                        const int b = b0 + bl;
+                        const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                        const float2 dr = a.dir[b];
+                        for (int kl = kg; kl < kt; kl += kgroups) {
+                            const Obs3 ob = stage_kb_tc<NB>(a, t * (128 / NB2) + kl, b, st, E, dr,
+                                                            sDS + kl * NB2 * kDsLd + bl, xm);
+                            s0 += ob.p;
+                            s1 += ob.j;
+                            s2 += ob.o;
+                        }
+                        atomicMax(smx + bl, __float_as_uint(xm));
+                        if (st == 3) {
+                            sred[(kg * nbg + bl) * 3] = s0;
+                            sred[(kg * nbg + bl) * 3 + 1] = s1;
+                            sred[(kg * nbg + bl) * 3 + 2] = s2;
+                        }
+                    }
+                    workers_sync();
+                    if (wt < nbg) {
+                        atomicMax(xout + b0 + wt, smx[wt]);
+                        if (st == 3) {
+                            double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+                            for (int k2 = 0; k2 < kgroups; ++k2) {
+                                r0 += sred[(k2 * nbg + wt) * 3];
+                                r1 += sred[(k2 * nbg + wt) * 3 + 1];
+                                r2 += sred[(k2 * nbg + wt) * 3 + 2];
+                            }
+                            double* rr = a.red + ((int64_t)t * a.Bp + b0 + wt) * 3;
+                            rr[0] = r0;
+                            rr[1] = r1;
+                            rr[2] = r2;
+                        }
+                    }
+                }
+                ++dcnt;
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (*vabort) ok = false;
+            }
+            if (ok) ok = tc_grid_sync(a, gen, &abort_s);
+        }
+    }
+    // observables of the last step
+    if (ok && a.Tmax > 0) {
+        const int n = a.Tmax;
+        const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
+        for (int64_t b = gt; b < a.act[n - 1]; b += total) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int t = 0; t < a.Nt; ++t) {
+                const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
+                s0 += __ldcg(rr);
+                s1 += __ldcg(rr + 1);
+                s2 += __ldcg(rr + 2);
+            }
+            double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+            o[0] = s0 / a.Nk;
+            o[1] = s1 / a.Nk;
+            o[2] = s2 / a.Nk;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tm, kTmemCols);
+    }
+}
+
+// Per column j: max(|Re|, |Im|) of U and of V, and ||v_j||^2.
+__global__ void factor_stats_kernel(const float2* __restrict__ U, const float2* __restrict__ V, int64_t N,
+                                    int r, int ldu, float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= r) return;
+    float mu = 0.f, mv = 0.f;
+    double nv = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        const float2 u = U[i * ldu + j], v = V[i * ldu + j];
+        mu = fmaxf(mu, fmaxf(fabsf(u.x), fabsf(u.y)));
+        mv = fmaxf(mv, fmaxf(fabsf(v.x), fabsf(v.y)));
+        nv += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    out[j] = mu;
+    out[r + j] = mv;
+    out[2 * r + j] = (float)nv;
+}
+
+// Split-FP16 tiles of U: tile (t, c) holds rows 128 t .. +127 and complex columns
+// 16 c .. +15 as 32 real columns (re, im), scaled by `scale`; zero outside N x r.
+__global__ void pack_u_kernel(const float2* __restrict__ U, int64_t N, int r, int ldu, int rp, int nchU,
+                              float scale, unsigned char* __restrict__ out, int64_t total) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t i = e / rp;
+    const int j = (int)(e % rp);
+    float2 v = make_float2(0.f, 0.f);
+    if (i < N && j < r) v = U[i * ldu + j];
+    __half rh, rl, ih, il;
+    split16(v.x * scale, rh, rl);
+    split16(v.y * scale, ih, il);
+    unsigned char* tile = out + ((i / 128) * nchU + j / 16) * (int64_t)kTile;
+    const uint32_t o = tc::kmajor_offset((uint32_t)(i % 128), 2 * (j % 16), kKc);
+    *reinterpret_cast<__half2*>(tile + o) = __halves2half2(rh, ih);
+    *reinterpret_cast<__half2*>(tile + kHalf + o) = __halves2half2(rl, il);
+}
+
+// Split-FP16 tiles of V^T: tile (m, c) holds rows j = 128 m .. +127 (columns of V) and
+// rows i = 16 c .. +15 of V as 32 real columns (re, im), scaled by `scale`.
+__global__ void pack_v_kernel(const float2* __restrict__ V, int64_t N, int r, int ldu, int rp, int nchV,
+                              float scale, unsigned char* __restrict__ out, int64_t total) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t i = e / rp;
+    const int j = (int)(e % rp);
+    float2 v = make_float2(0.f, 0.f);
+    if (i < N && j < r) v = V[i * ldu + j];
+    __half rh, rl, ih, il;
+    split16(v.x * scale, rh, rl);
+    split16(v.y * scale, ih, il);
+    unsigned char* tile = out + ((int64_t)(j / 128) * nchV + i / 16) * (int64_t)kTile;
+    const uint32_t o = tc::kmajor_offset((uint32_t)(j % 128), (uint32_t)(2 * (i % 16)), kKc);
+    *reinterpret_cast<__half2*>(tile + o) = __halves2half2(rh, ih);
+    *reinterpret_cast<__half2*>(tile + kHalf + o) = __halves2half2(rl, il);
+}
+
+struct TcDims {
+    int Nt, Np, rp, Mt, nchU, nchV;
+};
+TcDims tc_dims(int64_t N, int r) {
+    TcDims d;
+    d.Nt = (int)((N + 127) / 128);
+    d.Np = d.Nt * 128;
+    d.rp = (r + 127) / 128 * 128;
+    d.Mt = d.rp / 128;
+    d.nchU = 2 * d.rp / kKc;
+    d.nchV = 2 * d.Np / kKc;
+    return d;
+}
+
+size_t tc_smem_bytes() {
+    return (size_t)kRing * kTile + kXbuf + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
+           kGroup * sizeof(unsigned) + (2 * kRing + 5) * sizeof(uint64_t);
+}
+
+}  // namespace
+
+void pack_factors_tc(Ctx& c) {
+    if (c.tc_valid) return;
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "split-FP16 factors need a complex64 context");
+    TDAGW_REQUIRE(c.rank > 0, TDAGW_ERR_NO_FACTORS, "no low-rank factors installed");
+    cudaStream_t s = c.stream;
+    const int64_t N = c.hm.N;
+    const int r = c.rank, ldu = r + (r & 1);
+    const TcDims d = tc_dims(N, r);
+    const int64_t total = (int64_t)d.Np * d.rp;
+    c.tcU.ensure((size_t)d.Nt * d.nchU * kTile);
+    c.tcV.ensure((size_t)d.Mt * d.nchV * kTile);
+    // magnitudes of the factors: power-of-two tile scales and the bound of S o Y
+    DevBuf stats;
+    stats.ensure((size_t)3 * r * sizeof(float));
+    factor_stats_kernel<<<(r + 127) / 128, 128, 0, s>>>(c.U.as<float2>(), c.V.as<float2>(), N, r, ldu,
+                                                       stats.as<float>());
+    check_launch("factor_stats_kernel");
+    std::vector<float> st(3 * (size_t)r), S(r);
+    TDAGW_CUDA(cudaMemcpyAsync(st.data(), stats.p, st.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    TDAGW_CUDA(cudaMemcpyAsync(S.data(), c.S.p, r * sizeof(float), cudaMemcpyDeviceToHost, s));
+    TDAGW_CUDA(cudaStreamSynchronize(s));
+    float mu = 0.f, mv = 0.f, nv = 0.f, smax = 0.f;
+    for (int j = 0; j < r; ++j) {
+        mu = std::max(mu, st[j]);
+        mv = std::max(mv, st[r + j]);
+        nv = std::max(nv, st[2 * r + j]);
+        smax = std::max(smax, std::fabs(S[j]));
+    }
+    TDAGW_REQUIRE(std::isfinite(mu) && std::isfinite(mv) && std::isfinite(nv) && std::isfinite(smax),
+                  TDAGW_ERR_INVALID_ARG, "factors are not finite");
+    auto p2 = [](float bound) {
+        if (!(bound > 0.f)) return 1.f;
+        int e = 0;
+        std::frexp(bound, &e);
+        return std::ldexp(1.f, 13 - std::max(e, -100));
+    };
+    c.tc_su = p2(mu);
+    c.tc_sv = p2(mv);
+    c.tc_ybound = smax * std::sqrt(nv) * (float)std::sqrt(2.0 * (double)N);
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    pack_u_kernel<<<blocks, 256, 0, s>>>(c.U.as<float2>(), N, r, ldu, d.rp, d.nchU, c.tc_su,
+                                         c.tcU.as<unsigned char>(), total);
+    check_launch("pack_u_kernel");
+    pack_v_kernel<<<blocks, 256, 0, s>>>(c.V.as<float2>(), N, r, ldu, d.rp, d.nchV, c.tc_sv,
+                                         c.tcV.as<unsigned char>(), total);
+    check_launch("pack_v_kernel");
+    TDAGW_CUDA(cudaStreamSynchronize(s));
+    c.tc_valid = true;
+}
+
+void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt, int flags) {
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "split-FP16 propagation needs a complex64 context");
+    TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
+                  "split-FP16 propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
+    TDAGW_REQUIRE(!(flags & TDAGW_FLAG_CHECKPOINT), TDAGW_ERR_UNSUPPORTED,
+                  "checkpoints for the adjoint are kept by the FP32 path only");
+    pack_factors_tc(c);
+    const HostModel& h = c.hm;
+    cudaStream_t s = c.stream;
+    const int64_t N = h.N;
+    const int r = c.rank;
+    const TcDims d = tc_dims(N, r);
+    const BatchSetup bs = prepare_batch(c, fields, B, steps, dt);
+    const int Bp = bs.Bp;
+
+    int dev = 0, nsm = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = tc_smem_bytes();
+    const void* fn = h.Nb == 2 ? (const void*)batched_tc_kernel<2> : (const void*)batched_tc_kernel<4>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
+    TDAGW_REQUIRE(per_sm == 1, TDAGW_ERR_UNSUPPORTED, "tensor-core batched kernel needs exactly one CTA per SM");
+    const int nctas = nsm;
+
+    // largest split of the V^H X reduction over the run (one trajectory group)
+    const int MGn = (d.Mt + 3) / 4;
+    const int KSmax = std::max(1, std::min(nctas / MGn, d.nchV));
+    const int Gmax = (B + kGroup - 1) / kGroup;
+    c.tcP.ensure((size_t)KSmax * d.rp * Bp * sizeof(float2));
+    c.tcY.ensure((size_t)Gmax * d.nchU * kTile);
+    c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
+    c.tcRed.ensure((size_t)d.Nt * Bp * 3 * sizeof(double));
+    const size_t sbytes = (size_t)N * Bp * sizeof(float2);
+    for (DevBuf* b : {&c.bX, &c.bS, &c.bC}) TDAGW_CUDA(cudaMemsetAsync(b->p, 0, sbytes, s));
+    TDAGW_CUDA(cudaMemsetAsync(c.tcMax.p, 0, 3 * Bp * sizeof(unsigned), s));
+    c.sync.ensure(4 * sizeof(unsigned));
+    TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+
+    TcArgs a{};
+    a.tU = c.tcU.as<unsigned char>();
+    a.tV = c.tcV.as<unsigned char>();
+    a.tY = c.tcY.as<unsigned char>();
+    a.P = c.tcP.as<float2>();
+    a.xmax = c.tcMax.as<unsigned>();
+    a.S = c.S.as<float>();
+    a.diag = c.diagF.as<float2>();
+    a.dx = c.dx.as<float2>();
+    a.dy = c.dy.as<float2>();
+    a.vx = c.vx.as<float2>();
+    a.gap = c.gap.as<float2>();
+    a.X = c.bX.as<float2>();
+    a.Ssum = c.bS.as<float2>();
+    a.Ccomp = c.bC.as<float2>();
+    a.acc = c.bA.as<float2>();
+    a.Etab = c.bEtab.as<double>();
+    a.dir = c.bdir.as<float2>();
+    a.act = c.bact.as<int>();
+    a.red = c.tcRed.as<double>();
+    a.obs = c.bobs.as<double>();
+    a.bar = reinterpret_cast<unsigned long long*>(c.sync.p);
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.N = N;
+    a.ldE = bs.ldE;
+    a.Nk = h.Nk;
+    a.r = r;
+    a.rp = d.rp;
+    a.Nt = d.Nt;
+    a.Mt = d.Mt;
+    a.nchU = d.nchU;
+    a.nchV = d.nchV;
+    a.Bp = Bp;
+    a.B = B;
+    a.Tmax = bs.Tmax;
+    a.kahan = (flags & TDAGW_FLAG_NO_KAHAN) ? 0 : 1;
+    a.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) a.occ[q] = (float)h.occ[q];
+    a.dt = (float)dt;
+    a.su = c.tc_su;
+    a.sv = c.tc_sv;
+    a.ybound = c.tc_ybound;
+    a.wait_ns = 2000000000ull;
+    void* args[] = {&a};
+    TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(kTcThreads), args, smem, s));
+    c.persistent_launched = true;
+    c.adj.valid = false;
+    finish_batch(c, bs, B);
+}
+
+}  // namespace tdagw

@@ -421,8 +421,12 @@ int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters
         TDAGW_REQUIRE(rank >= 1 && oversample >= 0 && power_iters >= 0 &&
                           (int64_t)rank + oversample <= ctx->c.hm.N,
                       TDAGW_ERR_INVALID_ARG, "need 1 <= rank and rank + oversample <= N");
-        TDAGW_REQUIRE(precision == 0, TDAGW_ERR_UNSUPPORTED, "precision must be 0");
+        TDAGW_REQUIRE(precision == 0 || precision == 1, TDAGW_ERR_INVALID_ARG, "precision must be 0 or 1");
+        TDAGW_REQUIRE(precision == 0 || ctx->c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED,
+                      "split-FP16 factors need a complex64 context");
+        ctx->c.tc_valid = false;
         DISPATCH(ctx, rsvd_compress, ctx->c, rank, oversample, power_iters, seed);
+        if (precision == 1) pack_factors_tc(ctx->c);
     });
 }
 
@@ -432,6 +436,7 @@ int tdagw_set_factors(tdagw_ctx* ctx, int rank, const double* U, const double* S
         TDAGW_REQUIRE(ctx && U && S && V, TDAGW_ERR_INVALID_ARG, "NULL argument");
         require_built(ctx->c);
         TDAGW_REQUIRE(rank >= 1 && rank <= ctx->c.hm.N, TDAGW_ERR_INVALID_ARG, "rank out of range");
+        ctx->c.tc_valid = false;
         DISPATCH(ctx, set_factors, ctx->c, rank, U, S, V, diag);
     });
 }
@@ -481,7 +486,14 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
             TDAGW_REQUIRE(f.kind != TDAGW_FIELD_SIN2_SIN || f.T_pulse > 0, TDAGW_ERR_INVALID_ARG,
                           "T_pulse must be positive");
         }
-        if (B == 1 && !(flags & TDAGW_FLAG_CHECKPOINT)) {
+        TDAGW_REQUIRE(!(flags & TDAGW_FLAG_SPLIT_F16) || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG,
+                      "TDAGW_FLAG_SPLIT_F16 applies to the low-rank kernel");
+        if (flags & TDAGW_FLAG_SPLIT_F16) {
+            int tmax = 0;
+            for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);
+            TDAGW_REQUIRE(tmax > 0, TDAGW_ERR_INVALID_ARG, "at least one trajectory needs steps");
+            propagate_batched_tc(ctx->c, fields, B, steps, dt, flags);
+        } else if (B == 1 && !(flags & TDAGW_FLAG_CHECKPOINT)) {
             DISPATCH(ctx, propagate, ctx->c, fields[0], steps[0], dt, mode, flags);
             ctx->c.obs_B = 1;
             ctx->c.adj.valid = false;

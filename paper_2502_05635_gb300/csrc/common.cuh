@@ -178,6 +178,11 @@ struct Ctx {
     std::map<int, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
     int last_plan_rg = 0, last_plan_tg = 0;
     int obs_B = 1;           // trajectories in the recorded observables
+    // split-FP16 tiled factors for the tensor-core batched path, its intermediates, and
+    // whether the tiles match the installed factors
+    DevBuf tcU, tcV, tcY, tcP, tcMax, tcRed;
+    bool tc_valid = false;
+    float tc_su = 1.f, tc_sv = 1.f, tc_ybound = 0.f;
     // checkpoints (compensated state every `period` steps) and adjoint work buffers
     DevBuf ckS, ckC, aLam, aMu, aMusum, aC1, aMm, aKhm, aRecX, aRecDS;
     AdjointState adj;
@@ -232,6 +237,24 @@ void launch_convert_out(const void* src, double2* dst, int64_t n, cudaStream_t s
 // Batched propagation of B trajectories (complex64, from drho = 0).
 void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
                        int mode, int flags);
+// The same for the low-rank kernel with split-FP16 factors on the tensor cores.
+void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt,
+                          int flags);
+// Split-FP16 tiled copies of the installed factors (made once per set of factors).
+void pack_factors_tc(Ctx& c);
+
+// Host-side preparation shared by the batched drivers: trajectories sorted by length
+// (longest first), active counts per step, per-trajectory field tables and directions,
+// state buffers, and row 0 of the observables for every trajectory.
+struct BatchSetup {
+    std::vector<int> perm, act;
+    int Tmax = 0, Bp = 0;
+    int64_t ldE = 0, rows = 0;
+};
+BatchSetup prepare_batch(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt);
+void reset_batch_observables(Ctx& c, const BatchSetup& bs, int B);
+// observables in the caller's trajectory order
+void finish_batch(Ctx& c, const BatchSetup& bs, int B);
 
 // Backward sweep of the last checkpointed batched propagation (host arrays).
 void adjoint_batched(Ctx& c, const double* dJdobs, double* dJdE, double* dJdparams);

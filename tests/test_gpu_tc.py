@@ -1,0 +1,151 @@
+"""Split-FP16 tensor-core batched propagation (TDAGW_FLAG_SPLIT_F16) vs the FP64 oracle and
+vs the FP32 batched path, with the same factors on every side.
+
+The split-FP16 products carry about 22 significant bits (FP32 accumulation), so P(t) must
+match the oracle to the split-FP16 bound 1e-4 (relative L2 over the run) and in practice
+sits at the FP32 level.  Cases: ragged row tiles (N not a multiple of 128), several
+trajectory groups (B > 64), ranks spanning one to several 128-row tiles of V^H (and more
+than four, i.e. two tile groups), both band counts, field strengths over two decades in one
+batch, lengths ending at different steps.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import kernel as ok
+from oracle import lowrank as olr
+from oracle import model as om
+from oracle import propagate as op
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2502_05635_gb300 as tg  # noqa: E402
+
+SPLIT = tg.FLAG_RESET | tg.FLAG_SPLIT_F16
+
+
+def _pulses(B, seed, lo=-4.0, hi=-2.0):
+    rng = np.random.default_rng(seed)
+    return [wl.Pulse(E0=float(10 ** rng.uniform(lo, hi)), omega=float(rng.uniform(0.06, 0.16)),
+                     t0=float(rng.uniform(5, 20)), sigma=float(rng.uniform(3, 10)),
+                     dir_x=float(np.cos(th)), dir_y=float(np.sin(th)))
+            for th in rng.uniform(0, np.pi, B)]
+
+
+def _oracle(mdl, apply, pulse, T, dt=0.2):
+    s = op.half_step_samples(pulse, dt, T)
+    ref, _ = op.rk4(mdl, apply, s, dt, T, direction=(pulse.dir_x, pulse.dir_y))
+    return ref
+
+
+def _ctx(p, U, S, V, d):
+    ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    return ctx
+
+
+@pytest.mark.parametrize("L,nc,rank", [(4, 1, 9), (12, 1, 29), (6, 2, 200)])
+def test_split_f16_vs_oracle(L, nc, rank):
+    p = wl.small_model(L, nc)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, rank)
+    ctx = _ctx(p, U, S, V, d)
+    steps = [120, 37, 120, 80, 5]
+    pulses = _pulses(len(steps), 3)
+    got = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
+    for b, (q, T) in enumerate(zip(pulses, steps)):
+        ref = _oracle(mdl, apply, q, T)
+        for j in range(3):
+            e = op.rel_l2(got[:T + 1, b, j], ref[:, j])
+            assert e < 1e-4, (b, j, e)
+        assert np.all(np.isnan(got[T + 1:, b]))
+
+
+def test_split_f16_single_trajectory():
+    p = wl.small_model(12, 1)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, 64, seed=5)
+    ctx = _ctx(p, U, S, V, d)
+    q = wl.Pulse(E0=0.01, omega=0.12, t0=10.0, sigma=5.0)
+    got = ctx.propagate_batch([q], [150], 0.2, tg.LOWRANK, SPLIT)
+    ref = _oracle(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), q, 150)
+    assert op.rel_l2(got[:, 0], ref[:, 0]) < 1e-4
+
+
+@pytest.mark.parametrize("rank", [64, 520])
+def test_split_f16_many_groups_vs_fp32(rank):
+    """B = 150 (three trajectory groups), field strengths 1e-4..1e-2; rank 520 uses five
+    128-row tiles of V^H (two tile groups)."""
+    p = wl.small_model(12, 1)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, rank, seed=6)
+    ctx = _ctx(p, U, S, V, d)
+    rng = np.random.default_rng(10)
+    steps = [int(x) for x in rng.integers(5, 40, 150)]
+    pulses = _pulses(150, 4)
+    got = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    fp32 = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK)
+    for b, T in enumerate(steps):
+        e = op.rel_l2(got[:T + 1, b, 0], fp32[:T + 1, b, 0])
+        assert e < 1e-4, (b, e)
+        assert np.all(np.isnan(got[T + 1:, b]))
+    for b in (0, 77, 149):
+        ref = _oracle(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), pulses[b], steps[b])
+        assert op.rel_l2(got[:steps[b] + 1, b, 0], ref[:, 0]) < 1e-4, b
+
+
+def test_split_f16_after_compress_precision1():
+    p = wl.small_model(12, 1)
+    ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_compress_svd(ctx.h, 48, 32, 2, 1, precision=1)
+    pulses = _pulses(6, 5)
+    steps = [60, 50, 40, 30, 20, 10]
+    got = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    fp32 = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK)
+    for b, T in enumerate(steps):
+        assert op.rel_l2(got[:T + 1, b, 0], fp32[:T + 1, b, 0]) < 1e-4, b
+
+
+def test_split_f16_refreshes_after_new_factors():
+    """The tiled copy follows tdagw_set_factors."""
+    p = wl.small_model(4, 1)
+    mdl = om.Model(p)
+    ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    q = wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0)
+    for seed in (7, 8):
+        U, S, V, d = wl.random_factors(mdl.N, 12, seed=seed)
+        tg.tdagw_set_factors(ctx.h, U, S, V, d)
+        got = ctx.propagate_batch([q, q], [40, 40], 0.2, tg.LOWRANK, SPLIT)
+        ref = _oracle(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), q, 40)
+        assert op.rel_l2(got[:, 1, 0], ref[:, 0]) < 1e-4
+
+
+def test_split_f16_errors():
+    p = wl.small_model(4, 1)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, 8, seed=1)
+    ctx = _ctx(p, U, S, V, d)
+    q = wl.Pulse()
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_propagate(ctx.h, [tg.make_field(q)], [5], 0.2, tg.LOWRANK, SPLIT | tg.FLAG_CHECKPOINT)
+    assert e.value.code == tg.ERR_UNSUPPORTED
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_propagate(ctx.h, [tg.make_field(q)], [5], 0.2, tg.FULL, SPLIT)
+    assert e.value.code == tg.ERR_INVALID_ARG
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_propagate(ctx.h, [tg.make_field(q)], [5], 0.2, tg.LOWRANK, tg.FLAG_SPLIT_F16)
+    assert e.value.code == tg.ERR_UNSUPPORTED
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_compress_svd(ctx.h, 8, 8, 1, 1, precision=2)
+    assert e.value.code == tg.ERR_INVALID_ARG
+    c128 = tg.Context(p, tg.C128, stream=torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_compress_svd(c128.h, 8, 8, 1, 1, precision=1)
+    assert e.value.code == tg.ERR_UNSUPPORTED
