@@ -16,25 +16,29 @@
 // max|S| max_j ||v_j|| sqrt(2N) max|X|).
 //
 // Work of one stage (one cooperative launch for the whole propagation, one CTA per SM):
-//   A  partials of V^H X over K-ranges of rows: CTA items (trajectory group, group of up
-//      to four 128-row tiles of V^H, K-range).  The V^H tiles (pre-tiled 16 KB blocks in
-//      the MMA's shared-memory layout) stream through a ring by bulk copies; the
-//      expanded split X block is built in shared memory by the worker warps.
+//   A  partials of V^H X over K-ranges of rows: CTA items (trajectory group, pair of
+//      128-row tiles of V^H, K-range).  The V^H tiles (pre-tiled 16 KB blocks in the MMA's
+//      shared-memory layout) stream through a ring by bulk copies; the expanded split X
+//      block is built in shared memory by the worker warps.
 //   -- grid barrier --
 //   B  Y = S o sum of partials (fixed order), expanded and split into the B-operand tiles
 //      of the second product.
 //   -- grid barrier --
-//   C  items (128-row tile of U, trajectory group): U tiles and Y tiles stream through
-//      the ring; the accumulator (128 rows x 2 columns per trajectory) is staged through
-//      shared memory and the commutator + RK4 epilogue (Eq. tdagw) runs per (k, b) block.
+//   C  items (one or two 128-row tiles of U, trajectory group): U tiles and the Y tiles
+//      they share stream through the ring; each accumulator (128 rows x 2 columns per
+//      trajectory) is staged through shared memory in two halves and the commutator + RK4
+//      epilogue (Eq. tdagw) runs per (k, b) block.
 //   -- grid barrier --
-// Thread 0 issues all bulk copies and MMAs (both asynchronous); eight worker warps build
-// operands and run the epilogues.  Every wait is bounded; on expiry the kernel records an
-// error, waits (bounded) for its own copies and MMAs, frees its tensor memory and returns.
+// Roles: warp 0 streams tiles into the ring (running ahead across items), warp 1 issues
+// the MMAs into one of two tensor-memory accumulators, warps 2-9 build operands and drain
+// the other accumulator (epilogue of item i overlaps the MMAs of item i + 1).  Every wait
+// is bounded; on expiry the kernel records an error, lets its own copies and MMAs finish
+// (bounded waits), frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "batched_common.cuh"
@@ -47,16 +51,22 @@ namespace {
 using namespace batched;
 
 constexpr int kWorkers = 256;
-constexpr int kTcThreads = kWorkers + 32;    // warp 0: copies and MMAs; warps 1-8: workers
-constexpr int kRing = 8;                     // ring slots of one tile each
-constexpr uint32_t kTile = 16384;            // 128 rows x 32 real columns, hi (8 KB) + lo (8 KB)
+constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
+constexpr int kRing = 11;                  // ring slots of one tile each
+constexpr uint32_t kTile = 16384;          // 128 rows x 32 real columns, hi (8 KB) + lo (8 KB)
 constexpr uint32_t kHalf = 8192;
-constexpr int kKc = 32;                      // real reduction columns per tile (16 complex)
-constexpr int kGroup = 64;                   // trajectories per group: MMA N = 2 x 64 max
-constexpr int kDsLd = 65;                    // padded row (float2) of the staged dSigma tile
+constexpr int kKc = 32;                    // real reduction columns per tile (16 complex)
+constexpr int kGroup = 64;                 // trajectories per group: MMA N = 2 x 64 max
 constexpr uint32_t kLbo = 128, kSbo = (kKc / 8) * 128;
-constexpr uint32_t kXbuf = 128 * kDsLd * 8;  // >= two built B tiles (32 KB)
+constexpr uint32_t kXbuf = 2 * kTile;      // B blocks (phase A) / staged half tile (phase C)
+constexpr int kAccCols = 256;              // columns of one accumulator buffer (two buffers)
 constexpr int kTmemCols = 512;
+
+// staged half tile: 64 rows x 64 trajectories of float2, columns XOR-swizzled by row so
+// that both the row-wise writes and the trajectory-wise reads avoid bank conflicts
+__device__ __forceinline__ int ds_index(int row, int bl) {
+    return row * 64 + (bl ^ (row & 31));
+}
 
 struct TcArgs {
     const unsigned char* tU;  // Nt x nchU tiles of U (rows) x 2r (real columns)
@@ -77,12 +87,12 @@ struct TcArgs {
     const double* Etab;
     const float2* dir;
     const int* act;
-    double* red;  // Nt x Bp x 3
+    double* red;  // Ntp x Bp x 3 (per phase C row-tile item)
     double* obs;  // (Tmax + 1) x B x 3
     unsigned long long* bar;
     int* err;
     int64_t N, ldE;
-    int Nk, r, rp, Nt, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;
+    int Nk, r, rp, Nt, Ntp, tpi, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;  // tpi: U row tiles per phase C item
     float occ[4];
     float dt;
     float su, sv;   // power-of-two scales of the U and V tiles
@@ -95,6 +105,27 @@ __device__ __forceinline__ uint64_t gtime() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// Optional phase timestamps (build with -DTDAGW_TRACE): one thread per CTA and role records
+// %globaltimer at the phase boundaries of stages kTraceFirst .. kTraceFirst + kTraceStages - 1
+// (points 0-6: stage start, end of A items, after barrier 1, end of B, after barrier 2, end
+// of C items, after barrier 3; 7: MMA thread done with C items; 8: producer done with C
+// tiles).
+#ifdef TDAGW_TRACE
+constexpr int kTraceFirst = 40, kTraceStages = 16;
+__device__ unsigned long long g_trace_tc[160 * kTraceStages * 9];
+#define TC_TRACE(who, k)                                                                         \
+    do {                                                                                         \
+        const int ts_ = 4 * n + st - kTraceFirst;                                                \
+        if ((who) && blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                         \
+            g_trace_tc[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] = gtime();                   \
+    } while (0)
+#else
+#define TC_TRACE(who, k) \
+    do {                 \
+    } while (0)
+#endif
+
 __device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(b)), "r"(n) : "memory");
 }
@@ -104,6 +135,18 @@ __device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes) {
 }
 __device__ __forceinline__ void mb_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
+}
+// non-blocking test (copy and MMA threads poll) and potentially blocking test (workers:
+// the hardware may suspend the thread until the phase completes)
+__device__ __forceinline__ bool mb_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 __device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
     uint32_t ok;
@@ -116,12 +159,13 @@ __device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
     return ok != 0;
 }
 // bounded wait for the phase of the given parity; false on expiry or abort
+template <bool POLL>
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
                                         unsigned long long budget) {
-    if (mb_try(b, parity)) return true;
+    if (POLL ? mb_test(b, parity) : mb_try(b, parity)) return true;
     const uint64_t t0 = gtime();
     for (uint32_t i = 1;; ++i) {
-        if (mb_try(b, parity)) return true;
+        if (POLL ? mb_test(b, parity) : mb_try(b, parity)) return true;
         if ((i & 63) == 0) {
             if (abort_s && *abort_s) return false;
             if (gtime() - t0 > budget) return false;
@@ -173,45 +217,6 @@ __device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
     return !*(volatile int*)abort_s;
 }
 
-// Thread 0's copy/MMA pipeline over the ring.  Tiles of an item are numbered 0..nt-1 in
-// consumption order (tpc tiles per chunk); tile i lands in ring slot (pos0 + i) % kRing.
-struct Ring {
-    uint64_t* full;
-    uint64_t* empty;
-    unsigned char* buf;
-    uint32_t pos0;       // ring position of the item's first tile
-    int issued, waited;  // tiles issued / tiles whose arrival thread 0 has seen
-};
-
-template <typename Src>
-__device__ __forceinline__ bool ring_issue(Ring& R, const Src& src, volatile int* abort_s,
-                                           unsigned long long budget) {
-    const uint32_t pos = R.pos0 + (uint32_t)R.issued;
-    const uint32_t slot = pos % kRing, use = pos / kRing;
-    if (!mb_wait(R.empty + slot, (use & 1u) ^ 1u, abort_s, budget)) return false;
-    mb_expect_tx(R.full + slot, kTile);
-    bulk_load(R.buf + slot * kTile, src(R.issued), kTile, R.full + slot);
-    ++R.issued;
-    return true;
-}
-__device__ __forceinline__ bool ring_arrived(Ring& R, int i, volatile int* abort_s, unsigned long long budget) {
-    const uint32_t pos = R.pos0 + (uint32_t)i;
-    const bool ok = mb_wait(R.full + pos % kRing, (pos / kRing) & 1u, abort_s, budget);
-    if (ok) R.waited = max(R.waited, i + 1);
-    return ok;
-}
-__device__ __forceinline__ uint32_t ring_slot_addr(const Ring& R, int i) {
-    return tc::smem_u32(R.buf + ((R.pos0 + (uint32_t)i) % kRing) * kTile);
-}
-// after an abort: wait (bounded, ignoring the abort flag) for every issued copy
-__device__ void ring_drain(Ring& R, unsigned long long budget) {
-    for (int i = R.waited; i < R.issued; ++i) {
-        const uint32_t pos = R.pos0 + (uint32_t)i;
-        mb_wait(R.full + pos % kRing, (pos / kRing) & 1u, nullptr, budget);
-    }
-    R.waited = R.issued;
-}
-
 // the three split products of one 128 x N x 32 tile pair (two K = 16 steps each)
 __device__ __forceinline__ void mma_tile(uint32_t d, uint32_t a_addr, uint32_t b_addr, uint32_t idesc, bool first) {
 #pragma unroll
@@ -227,12 +232,12 @@ __device__ __forceinline__ void mma_tile(uint32_t d, uint32_t a_addr, uint32_t b
 }
 
 // Commutator + RK4 stage update of one (k, trajectory) block (Eq. tdagw; the arithmetic of
-// the FP32 batched path), with the low-rank part of dSigma read from shared memory (row g
-// of the block at dsl[g * kDsLd]) and K^diag o X added here.  xm: running max(|Re|, |Im|)
-// of the values written to X (the next stage input).
+// the FP32 batched path), with the low-rank part of dSigma read from the staged half tile
+// (block rows row0 .. row0 + NB^2 - 1, trajectory column bl) and K^diag o X added here.
+// xm: running max(|Re|, |Im|) of the values written to X (the next stage input).
 template <int NB>
 __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
-                            const float2* dsl, float& xm) {
+                            const float2* sDS, int row0, int bl, float& xm) {
     constexpr int NB2 = NB * NB;
     const int64_t Bp = a.Bp;
     float2 X[NB2], M[NB2];
@@ -241,15 +246,29 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
         const int64_t i = (int64_t)k * NB2 + g;
         X[g] = __ldcg(a.X + i * Bp + b);
         const float2 d1 = a.dx[i], d2 = a.dy[i];
-        const float2 ds = cfma(a.diag[i], X[g], dsl[g * kDsLd]);
+        const float2 ds = cfma(a.diag[i], X[g], sDS[ds_index(row0 + g, bl)]);
         M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
     }
     Obs3 ob{0.0, 0.0, 0.0};
+    // state loads of RB rows at a time, issued before any store of those rows (all rows
+    // for two bands, one row for four: register budget)
+    constexpr int RB = NB == 2 ? 2 : 1;
 #pragma unroll
-    for (int n = 0; n < NB; ++n)
+    for (int n0 = 0; n0 < NB; n0 += RB) {
+        float2 XS[RB * NB], XC[RB * NB], AC[RB * NB];
+#pragma unroll
+        for (int q = 0; q < RB * NB; ++q) {
+            const int64_t e = ((int64_t)k * NB2 + n0 * NB + q) * Bp + b;
+            XS[q] = __ldcg(a.Ssum + e);
+            XC[q] = __ldcg(a.Ccomp + e);
+            AC[q] = st > 0 ? __ldcg(a.acc + e) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+    for (int n = n0; n < n0 + RB; ++n)
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
             const int g = n * NB + m;
+            const int q = (n - n0) * NB + m;
             const int64_t i = (int64_t)k * NB2 + g;
             float2 comm = cscale(M[g], a.occ[m] - a.occ[n]);
 #pragma unroll
@@ -261,15 +280,15 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
             const float2 s = cadd(h0, comm);
             const float2 kv = make_float2(s.y, -s.x);
             const int64_t e = i * Bp + b;
-            const float2 xs = __ldcg(a.Ssum + e), xc = __ldcg(a.Ccomp + e);
+            const float2 xs = XS[q], xc = XC[q];
             float2 Xn;
             if (st < 3) {
-                const float2 ac = st == 0 ? kv : cadd(__ldcg(a.acc + e), cscale(kv, 2.f));
+                const float2 ac = st == 0 ? kv : cadd(AC[q], cscale(kv, 2.f));
                 a.acc[e] = ac;
                 const float cn = st == 2 ? a.dt : 0.5f * a.dt;
                 Xn = cadd(xs, cadd(xc, cscale(kv, cn)));
             } else {
-                const float2 ac = cadd(__ldcg(a.acc + e), kv);
+                const float2 ac = cadd(AC[q], kv);
                 const float2 inc = cscale(ac, a.dt / 6.f);
                 float2 ns, nc;
                 if (a.kahan) {
@@ -293,42 +312,69 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
             a.X[e] = Xn;
             xm = fmaxf(xm, fmaxf(fabsf(Xn.x), fabsf(Xn.y)));
         }
+    }
     return ob;
 }
 
+// Trajectory groups: at most kGroup trajectories each, and enough groups for about one
+// item of the U product per CTA (row tiles x groups <= CTAs) while groups keep >= 8.
+__host__ __device__ __forceinline__ int group_count(int Bact, int Nt, int nctas) {
+    const int g_min = (Bact + kGroup - 1) / kGroup;
+    const int g_fill = min(max(1, nctas / Nt), (Bact + 7) / 8);
+    return max(g_min, g_fill);
+}
 struct Groups {
-    int G, MGn, KS;
+    int G, MGn, KS;  // phase A: trajectory groups, pairs of V^H tiles, K-ranges
+    int GC;          // phase C (and B): trajectory groups
 };
 __device__ __forceinline__ Groups stage_groups(const TcArgs& a, int Bact) {
     Groups q;
-    q.G = (Bact + kGroup - 1) / kGroup;
-    q.MGn = (a.Mt + 3) / 4;
+    q.G = group_count(Bact, a.Nt, (int)gridDim.x);
+    q.GC = group_count(Bact, a.Ntp, (int)gridDim.x);
+    q.MGn = (a.Mt + 1) / 2;
     q.KS = max(1, min((int)gridDim.x / max(1, q.G * q.MGn), a.nchV));
     return q;
+}
+// phase A item -> (trajectory group, first V^H tile, tile count, chunk range)
+struct ItemA {
+    int g, m0, mc, ks, c0, c1;
+};
+__device__ __forceinline__ ItemA item_a(const TcArgs& a, const Groups& q, int item) {
+    ItemA it;
+    it.g = item % q.G;
+    const int mg = (item / q.G) % q.MGn;
+    it.ks = item / (q.G * q.MGn);
+    it.m0 = 2 * mg;
+    it.mc = min(2, a.Mt - it.m0);
+    it.c0 = (int)((int64_t)it.ks * a.nchV / q.KS);
+    it.c1 = (int)((int64_t)(it.ks + 1) * a.nchV / q.KS);
+    return it;
 }
 
 template <int NB>
 __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* ring_buf = smem;
-    unsigned char* xbuf = ring_buf + kRing * kTile;
+    unsigned char* ring = smem;
+    unsigned char* xbuf = ring + kRing * kTile;
     float2* sDS = reinterpret_cast<float2*>(xbuf);
     double* sred = reinterpret_cast<double*>(xbuf + kXbuf);
     float* ssc = reinterpret_cast<float*>(sred + kWorkers * 3);
     unsigned* smx = reinterpret_cast<unsigned*>(ssc + kGroup);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smx + kGroup);
     uint64_t* full = bars;
-    uint64_t* empty = bars + kRing;
-    uint64_t* bfull = bars + 2 * kRing;
+    uint64_t* empty = full + kRing;
+    uint64_t* bfull = empty + kRing;
     uint64_t* bempty = bfull + 2;
-    uint64_t* done = bempty + 2;
+    uint64_t* accf = bempty + 2;  // accumulator written (MMA -> workers)
+    uint64_t* acce = accf + 2;    // accumulator drained (workers -> MMA)
+    uint64_t* fin = acce + 2;     // last MMAs complete (teardown)
     __shared__ uint32_t tmem_base;
     __shared__ int abort_s;
 
     const int tid = threadIdx.x;
-    const int warp = tid / 32, lane = tid % 32;
-    const int wt = tid - 32;  // worker index (warps 1-8)
-    const bool worker = warp >= 1;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool producer = tid == 0, mma = tid == 32, worker = warp >= 2;
+    const int wt = tid - 64;  // worker index
     constexpr int NB2 = NB * NB;
     const unsigned long long budget = a.wait_ns;
     volatile int* vabort = &abort_s;
@@ -342,32 +388,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         for (int s = 0; s < 2; ++s) {
             mb_init(bfull + s, kWorkers);
             mb_init(bempty + s, 1);
+            mb_init(accf + s, 1);
+            mb_init(acce + s, kWorkers);
         }
-        mb_init(done, 1);
+        mb_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = tmem_base;
 
-    Ring R{full, empty, ring_buf, 0u, 0, 0};
-    uint32_t bcnt = 0;  // uses of the two built-B buffers so far
-    uint32_t dcnt = 0;  // completions of `done` so far
+    uint32_t ppos = 0;  // producer: tiles issued so far (ring position)
+    uint32_t mpos = 0;  // MMA thread: tiles consumed so far
+    uint32_t bu = 0;    // uses of the two built-B buffers (MMA thread and workers)
+    uint32_t acnt = 0;  // uses of the two accumulators (MMA thread and workers)
     unsigned gen = 0;
     bool ok = true;
-
-    // thread 0 after an abort: no copy or MMA of this CTA may remain in flight
-    auto quiesce = [&]() {
-        ring_drain(R, budget);
-        tc::mma_commit(done);
-        mb_wait(done, dcnt & 1u, nullptr, budget);
-        ++dcnt;
-    };
     auto fail = [&]() {
         atomicExch(a.err, 1);
         abort_s = 1;
+    };
+    // producer: one tile into the next ring slot
+    auto issue = [&](const unsigned char* src) {
+        if (*vabort) return;
+        const uint32_t slot = ppos % kRing, use = ppos / kRing;
+        if (!mb_wait<true>(empty + slot, (use & 1u) ^ 1u, vabort, budget)) {
+            fail();
+            return;
+        }
+        mb_expect_tx(full + slot, kTile);
+        bulk_load(ring + slot * kTile, src, kTile, full + slot);
+        ++ppos;
+    };
+    // MMA thread: wait for the next tile; returns its shared-memory address (0 on failure)
+    auto next_tile = [&]() -> uint32_t {
+        const uint32_t slot = mpos % kRing, use = mpos / kRing;
+        if (*vabort || !mb_wait<true>(full + slot, use & 1u, vabort, budget)) {
+            fail();
+            return 0u;
+        }
+        ++mpos;
+        return tc::smem_u32(ring + slot * kTile);
+    };
+    auto release_tile = [&](uint32_t back) {  // slot of the tile consumed `back` tiles ago
+        tc::mma_commit(empty + (mpos - back) % kRing);
     };
 
     for (int n = 0; n < a.Tmax && ok; ++n) {
@@ -377,98 +443,113 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             const int gs = 4 * n + st;
             const unsigned* xin = a.xmax + (gs % 3) * a.Bp;
             unsigned* xout = a.xmax + ((gs + 1) % 3) * a.Bp;
-            if (blockIdx.x == 0)
-                for (int b = tid; b < a.Bp; b += kTcThreads) xout[b] = 0u;
+            TC_TRACE(producer, 0);
+            if (blockIdx.x == 0 && worker)
+                for (int b = wt; b < a.Bp; b += kWorkers) xout[b] = 0u;
 
             // ---------------- A: partials of V^H X ----------------
             const int nA = q.G * q.MGn * q.KS;
-            for (int item = blockIdx.x; item < nA && ok; item += gridDim.x) {
-                const int g = item % q.G, mg = (item / q.G) % q.MGn, ks = item / (q.G * q.MGn);
-                int b0, b1;
-                group_range(Bact, q.G, g, b0, b1);
-                const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
-                const int m0 = 4 * mg, mc = min(4, a.Mt - m0);
-                const int c0 = (int)((int64_t)ks * a.nchV / q.KS), c1 = (int)((int64_t)(ks + 1) * a.nchV / q.KS);
-                const int nch = c1 - c0;
-                if (worker && wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
-                if (worker) workers_sync();
-                if (tid == 0) {
+            if (producer) {
+                for (int item = blockIdx.x; item < nA; item += gridDim.x) {
+                    const ItemA it = item_a(a, q, item);
+                    for (int c = it.c0; c < it.c1; ++c)
+                        for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile);
+                }
+            } else if (mma) {
+                for (int item = blockIdx.x; item < nA; item += gridDim.x) {
+                    const ItemA it = item_a(a, q, item);
+                    int b0, b1;
+                    group_range(Bact, q.G, it.g, b0, b1);
+                    const int nbp = (b1 - b0 + 7) & ~7;
+                    const uint32_t ab = acnt & 1u;
+                    if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
-                    const int nt = nch * mc;
-                    auto src = [&](int i) {
-                        const int c = c0 + i / mc, m = m0 + i % mc;
-                        return a.tV + ((int64_t)m * a.nchV + c) * kTile;
-                    };
-                    R.issued = R.waited = 0;
-                    for (int cc = 0; cc < nch && ok; ++cc) {
-                        while (ok && R.issued < (cc + 1) * mc) ok = ring_issue(R, src, vabort, budget);
-                        for (int i = cc * mc; ok && i < (cc + 1) * mc; ++i) ok = ring_arrived(R, i, vabort, budget);
-                        const uint32_t bu = bcnt + cc;
-                        if (ok) ok = mb_wait(bfull + (bu & 1), (bu >> 1) & 1u, vabort, budget);
-                        if (!ok) break;
-                        tc::fence_after_sync();
-                        const uint32_t baddr = tc::smem_u32(xbuf + (bu & 1) * kTile);
-                        for (int ml = 0; ml < mc; ++ml)
-                            mma_tile(tm + ml * 128, ring_slot_addr(R, cc * mc + ml), baddr, idesc, cc == 0);
-                        for (int ml = 0; ml < mc; ++ml)
-                            tc::mma_commit(empty + (R.pos0 + cc * mc + ml) % kRing);
-                        tc::mma_commit(bempty + (bu & 1));
-                        while (ok && R.issued < nt && R.issued - kRing < cc * mc)
-                            ok = ring_issue(R, src, vabort, budget);
-                    }
-                    if (ok) {
-                        tc::mma_commit(done);
-                    } else {
-                        fail();
-                        quiesce();
-                        --dcnt;  // the item's completion below is the quiesce commit
-                    }
-                    R.pos0 += (uint32_t)R.issued;
-                } else if (worker) {
-                    // build the expanded split X block of each chunk (16 rows x nbp trajectories)
-                    for (int cc = 0; cc < nch; ++cc) {
-                        const uint32_t bu = bcnt + cc;
-                        if (!mb_wait(bempty + (bu & 1), ((bu >> 1) & 1u) ^ 1u, vabort, budget)) {
+                    for (int c = it.c0; c < it.c1 && !*vabort; ++c) {
+                        uint32_t ta[2] = {0u, 0u};
+                        for (int ml = 0; ml < it.mc; ++ml) ta[ml] = next_tile();
+                        if (*vabort || !mb_wait<true>(bfull + (bu & 1u), (bu >> 1) & 1u, vabort, budget)) {
                             fail();
                             break;
                         }
-                        unsigned char* tile = xbuf + (bu & 1) * kTile;
-                        const int64_t i0 = (int64_t)(c0 + cc) * 16;
-                        for (int e = wt; e < 16 * kGroup; e += kWorkers) {
+                        tc::fence_after_sync();
+                        const uint32_t baddr = tc::smem_u32(xbuf + (bu & 1u) * kTile);
+                        for (int ml = 0; ml < it.mc; ++ml)
+                            mma_tile(tm + ab * kAccCols + ml * 128, ta[ml], baddr, idesc, c == it.c0);
+                        for (int ml = 0; ml < it.mc; ++ml) release_tile(it.mc - ml);
+                        tc::mma_commit(bempty + (bu & 1u));
+                        ++bu;
+                    }
+                    tc::mma_commit(accf + ab);
+                    ++acnt;
+                }
+            } else if (worker) {
+                for (int item = blockIdx.x; item < nA; item += gridDim.x) {
+                    const ItemA it = item_a(a, q, item);
+                    int b0, b1;
+                    group_range(Bact, q.G, it.g, b0, b1);
+                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                    workers_sync();  // the previous item's readers of ssc are done
+                    if (wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
+                    workers_sync();
+                    // expanded split X block of each chunk (16 rows x nbp trajectories); each
+                    // worker owns elements e = wt + 256 u, u < 4, and loads the next chunk's
+                    // values before building the current one
+                    constexpr int kPer = 16 * kGroup / kWorkers;
+                    float2 cur[kPer], nxt[kPer];
+                    auto load_chunk = [&](int c, float2 (&xv)[kPer]) {
+#pragma unroll
+                        for (int u = 0; u < kPer; ++u) {
+                            const int e = wt + kWorkers * u;
                             const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
-                            if (bl >= nbp) continue;
-                            const int64_t i = i0 + il;
-                            float2 x = make_float2(0.f, 0.f);
-                            if (bl < nbg && i < a.N) x = __ldcg(a.X + i * a.Bp + b0 + bl);
-                            const float sx = ssc[bl];
-                            __half rh, rl, ih, il2;
-                            split16(x.x * sx, rh, rl);
-                            split16(x.y * sx, ih, il2);
-                            const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * il, kKc);
-                            const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * il, kKc);
-                            *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, ih);
-                            *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, __hneg(rh));
-                            *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, il2);
-                            *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il2, __hneg(rl));
+                            const int64_t i = (int64_t)c * 16 + il;
+                            xv[u] = (bl < nbg && i < a.N) ? __ldcg(a.X + i * a.Bp + b0 + bl) : make_float2(0.f, 0.f);
+                        }
+                    };
+                    if (it.c0 < it.c1) load_chunk(it.c0, cur);
+                    for (int c = it.c0; c < it.c1; ++c) {
+                        if (c + 1 < it.c1) load_chunk(c + 1, nxt);
+                        const uint32_t bs = bu & 1u;
+                        if (!*vabort && !mb_wait<false>(bempty + bs, ((bu >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                        if (!*vabort) {
+                            unsigned char* tile = xbuf + bs * kTile;
+#pragma unroll
+                            for (int u = 0; u < kPer; ++u) {
+                                const int e = wt + kWorkers * u;
+                                const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
+                                if (bl >= nbp) continue;
+                                const float2 x = cur[u];
+                                const float sx = ssc[bl];
+                                __half rh, rl, ih, il2;
+                                split16(x.x * sx, rh, rl);
+                                split16(x.y * sx, ih, il2);
+                                const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * il, kKc);
+                                const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * il, kKc);
+                                *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, ih);
+                                *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, __hneg(rh));
+                                *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, il2);
+                                *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il2, __hneg(rl));
+                            }
                         }
                         tc::fence_proxy_async();
-                        mb_arrive(bfull + (bu & 1));
+                        mb_arrive(bfull + bs);
+                        ++bu;
+#pragma unroll
+                        for (int u = 0; u < kPer; ++u) cur[u] = nxt[u];
                     }
-                }
-                bcnt += nch;
-                // accumulators -> raw partials P[ks][j][b]
-                if (worker) {
-                    const bool got = mb_wait(done, dcnt & 1u, vabort, budget);
+                    // accumulators -> raw partials P[ks][j][b]
+                    const uint32_t ab = acnt & 1u;
+                    if (!*vabort && !mb_wait<false>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
                     tc::fence_after_sync();
-                    if (got && !*vabort) {
-                        const int quarter = warp & 3, half = (warp - 1) >> 2;
+                    if (!*vabort) {
+                        const int quarter = warp & 3, half = (warp - 2) >> 2;
                         const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
-                        for (int ml = 0; ml < mc; ++ml) {
-                            const int j = (m0 + ml) * 128 + 32 * quarter + lane;
-                            float2* prow = a.P + ((int64_t)ks * a.rp + j) * a.Bp + b0;
+                        for (int ml = 0; ml < it.mc; ++ml) {
+                            const int j = (it.m0 + ml) * 128 + 32 * quarter + lane;
+                            float2* prow = a.P + ((int64_t)it.ks * a.rp + j) * a.Bp + b0;
                             for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
                                 float v[16];
-                                tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ml * 128 + 16 * u, v);
+                                tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + ml * 128 + 16 * u, v);
 #pragma unroll
                                 for (int p = 0; p < 8; ++p) {
                                     const int bl = 8 * u + p;
@@ -476,54 +557,77 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 }
                             }
                         }
-                    } else if (!got) {
-                        fail();
                     }
+                    tc::fence_before_sync();
+                    mb_arrive(acce + ab);
+                    ++acnt;
                 }
-                ++dcnt;
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (*vabort) ok = false;
             }
-            if (ok) ok = tc_grid_sync(a, gen, &abort_s);
-            if (!ok) break;
+            TC_TRACE(producer, 1);
+            if (!(ok = tc_grid_sync(a, gen, &abort_s))) break;
+            TC_TRACE(producer, 2);
 
             // ---------------- B: Y = S o sum of partials -> split expanded tiles ----------------
             {
                 const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
-                for (int g = 0; g < q.G; ++g) {
+                // elements (g, j, bl) of all groups, flattened
+                int64_t tot_el = 0;
+                for (int g = 0; g < q.GC; ++g) {
                     int b0, b1;
-                    group_range(Bact, q.G, g, b0, b1);
-                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
-                    for (int64_t e = gt; e < (int64_t)a.rp * nbp; e += total) {
-                        const int j = (int)(e / nbp), bl = (int)(e % nbp);
-                        float2 v = make_float2(0.f, 0.f);
-                        if (bl < nbg && j < a.r) {
-                            const int b = b0 + bl;
-                            float2 s = make_float2(0.f, 0.f);
-                            for (int k2 = 0; k2 < q.KS; ++k2) s = cadd(s, __ldcg(a.P + ((int64_t)k2 * a.rp + j) * a.Bp + b));
-                            const float mx = __uint_as_float(__ldcg(xin + b));
-                            const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
-                            v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
-                        }
-                        __half rh, rl, ih, il;
-                        split16(v.x, rh, rl);
-                        split16(v.y, ih, il);
-                        unsigned char* tile = a.tY + ((int64_t)g * a.nchU + j / 16) * kTile;
-                        const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * (j % 16), kKc);
-                        const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * (j % 16), kKc);
-                        *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, __hneg(ih));
-                        *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, rh);
-                        *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, __hneg(il));
-                        *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il, rl);
+                    group_range(Bact, q.GC, g, b0, b1);
+                    tot_el += (int64_t)a.rp * ((b1 - b0 + 7) & ~7);
+                }
+                for (int64_t e = gt; e < tot_el; e += total) {
+                    int g = 0, b0 = 0, b1 = 0, nbp = 0;
+                    int64_t rem = e;
+                    for (;; ++g) {
+                        group_range(Bact, q.GC, g, b0, b1);
+                        nbp = (b1 - b0 + 7) & ~7;
+                        const int64_t sz = (int64_t)a.rp * nbp;
+                        if (rem < sz || g == q.GC - 1) break;
+                        rem -= sz;
                     }
+                    const int nbg = b1 - b0;
+                    const int j = (int)(rem / nbp), bl = (int)(rem % nbp);
+                    float2 v = make_float2(0.f, 0.f);
+                    if (bl < nbg && j < a.r) {
+                        const int b = b0 + bl;
+                        // eight independent partial sums (loads in flight), fixed order
+                        const float2* pp = a.P + (int64_t)j * a.Bp + b;
+                        const int64_t pstride = (int64_t)a.rp * a.Bp;
+                        float2 s8[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
+                        int k2 = 0;
+                        for (; k2 + 8 <= q.KS; k2 += 8) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                        const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
+                                              cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
+                        const float mx = __uint_as_float(__ldcg(xin + b));
+                        const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
+                        v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
+                    }
+                    __half rh, rl, ih, il;
+                    split16(v.x, rh, rl);
+                    split16(v.y, ih, il);
+                    unsigned char* tile = a.tY + ((int64_t)g * a.nchU + j / 16) * kTile;
+                    const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * (j % 16), kKc);
+                    const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * (j % 16), kKc);
+                    *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, __hneg(ih));
+                    *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, rh);
+                    *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, __hneg(il));
+                    *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il, rl);
                 }
                 if (st == 0 && n > 0) {
                     // observables of step n (written by the last stage of step n - 1)
                     for (int64_t b = gt; b < a.act[n - 1]; b += total) {
                         double s0 = 0, s1 = 0, s2 = 0;
-                        for (int t = 0; t < a.Nt; ++t) {
+                        for (int t = 0; t < a.Ntp; ++t) {
                             const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                             s0 += __ldcg(rr);
                             s1 += __ldcg(rr + 1);
@@ -538,94 +642,111 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             }
             // the tiles were written through the generic proxy and are read by bulk copies
             asm volatile("fence.proxy.async;" ::: "memory");
+            TC_TRACE(producer, 3);
             if (!(ok = tc_grid_sync(a, gen, &abort_s))) break;
+            TC_TRACE(producer, 4);
 
             // ---------------- C: dSigma = U (S o Y) + K^diag o X, commutator, RK4 ----------------
             const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
-            const int nC = a.Nt * q.G;
-            for (int item = blockIdx.x; item < nC && ok; item += gridDim.x) {
-                const int t = item % a.Nt, g = item / a.Nt;
-                int b0, b1;
-                group_range(Bact, q.G, g, b0, b1);
-                const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
-                if (worker && wt < kGroup) {
-                    if (wt < nbg) {
-                        const float mx = __uint_as_float(__ldcg(xin + b0 + wt));
-                        ssc[wt] = 1.f / (a.su * pow2_scale(a.ybound * mx));
+            const int nC = a.Ntp * q.GC;
+            if (producer) {
+                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                    const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
+                    const int tcnt = min(a.tpi, a.Nt - t0);
+                    for (int c = 0; c < a.nchU; ++c) {
+                        for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile);
+                        issue(a.tY + ((int64_t)g * a.nchU + c) * kTile);
                     }
-                    smx[wt] = 0u;
                 }
-                if (tid == 0) {
-                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
-                    const int nt = 2 * a.nchU;
-                    auto src = [&](int i) {
-                        const int c = i >> 1;
-                        return (i & 1) ? a.tY + ((int64_t)g * a.nchU + c) * kTile
-                                       : a.tU + ((int64_t)t * a.nchU + c) * kTile;
-                    };
-                    R.issued = R.waited = 0;
-                    for (int cc = 0; cc < a.nchU && ok; ++cc) {
-                        while (ok && R.issued < 2 * (cc + 1)) ok = ring_issue(R, src, vabort, budget);
-                        if (ok) ok = ring_arrived(R, 2 * cc, vabort, budget);
-                        if (ok) ok = ring_arrived(R, 2 * cc + 1, vabort, budget);
-                        if (!ok) break;
-                        tc::fence_after_sync();
-                        mma_tile(tm, ring_slot_addr(R, 2 * cc), ring_slot_addr(R, 2 * cc + 1), idesc, cc == 0);
-                        tc::mma_commit(empty + (R.pos0 + 2 * cc) % kRing);
-                        tc::mma_commit(empty + (R.pos0 + 2 * cc + 1) % kRing);
-                        while (ok && R.issued < nt && R.issued - kRing < 2 * cc) ok = ring_issue(R, src, vabort, budget);
-                    }
-                    if (ok) {
-                        tc::mma_commit(done);
-                    } else {
-                        fail();
-                        quiesce();
-                        --dcnt;
-                    }
-                    R.pos0 += (uint32_t)R.issued;
-                }
-                // thread 0 has issued (or, after an abort, drained) everything: one decision
-                // for the whole CTA, taken after this barrier (the workers' named barriers
-                // below are reached by all of them or by none)
-                __syncthreads();
-                const bool go = !*vabort;
-                if (go && worker) {
-                    const bool got = mb_wait(done, dcnt & 1u, vabort, budget);
+                TC_TRACE(true, 8);
+            } else if (mma) {
+                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                    const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
+                    const int tcnt = min(a.tpi, a.Nt - t0);
+                    int b0, b1;
+                    group_range(Bact, q.GC, g, b0, b1);
+                    const int nbp = (b1 - b0 + 7) & ~7;
+                    const uint32_t ab = acnt & 1u;
+                    if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
                     tc::fence_after_sync();
-                    if (!got) fail();
-                    if (got) {
-                        // accumulator (raw U (S o Y)) -> sDS[row][bl], unscaled
-                        const int quarter = warp & 3, half = (warp - 1) >> 2;
-                        const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
-                        const int row = 32 * quarter + lane;
-                        for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
-                            float v[16];
-                            tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + 16 * u, v);
-#pragma unroll
-                            for (int p = 0; p < 8; ++p) {
-                                const int bl = 8 * u + p;
-                                if (bl < nbg) sDS[row * kDsLd + bl] = make_float2(v[2 * p] * ssc[bl], v[2 * p + 1] * ssc[bl]);
-                            }
+                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
+                    for (int c = 0; c < a.nchU && !*vabort; ++c) {
+                        uint32_t tu[2] = {0u, 0u};
+                        for (int u = 0; u < tcnt; ++u) tu[u] = next_tile();
+                        const uint32_t ty = next_tile();
+                        if (*vabort) break;
+                        tc::fence_after_sync();
+                        for (int u = 0; u < tcnt; ++u) mma_tile(tm + ab * kAccCols + u * 128, tu[u], ty, idesc, c == 0);
+                        for (int u = 0; u <= tcnt; ++u) release_tile(tcnt + 1 - u);
+                    }
+                    tc::mma_commit(accf + ab);
+                    ++acnt;
+                }
+                TC_TRACE(true, 7);
+            } else if (worker) {
+                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                    const int tp = item % a.Ntp, t0 = a.tpi * tp, g = item / a.Ntp;
+                    const int tcnt = min(a.tpi, a.Nt - t0);
+                    int b0, b1;
+                    group_range(Bact, q.GC, g, b0, b1);
+                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                    workers_sync();  // the previous item's readers of ssc, smx, sred are done
+                    if (wt < kGroup) {
+                        if (wt < nbg) {
+                            const float mx = __uint_as_float(__ldcg(xin + b0 + wt));
+                            ssc[wt] = 1.f / (a.su * pow2_scale(a.ybound * mx));
                         }
+                        smx[wt] = 0u;
                     }
                     workers_sync();
-                    // commutator + RK4 for the tile's k-blocks and the group's trajectories
-                    const int kt = min(128 / NB2, a.Nk - t * (128 / NB2));
+                    const uint32_t ab = acnt & 1u;
+                    if (!*vabort && !mb_wait<false>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    tc::fence_after_sync();
+                    const int quarter = warp & 3, half = (warp - 2) >> 2;
+                    const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
                     const int kgroups = kWorkers / nbg;
                     const int bl = wt % nbg, kg = wt / nbg;
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                     float xm = 0.f;
-                    if (kg < kgroups) {
-                        const int b = b0 + bl;
-                        const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
-                        const float2 dr = a.dir[b];
-                        for (int kl = kg; kl < kt; kl += kgroups) {
-                            const Obs3 ob = stage_kb_tc<NB>(a, t * (128 / NB2) + kl, b, st, E, dr,
-                                                            sDS + kl * NB2 * kDsLd + bl, xm);
-                            s0 += ob.p;
-                            s1 += ob.j;
-                            s2 += ob.o;
+                    for (int u2 = 0; u2 < a.tpi; ++u2) {
+                        const int t = t0 + u2;
+                        for (int ph = 0; ph < 2; ++ph) {
+                            // accumulator rows 64 ph .. +63 (lane quarters 2 ph, 2 ph + 1) -> staged half
+                            if (u2 < tcnt && (quarter >> 1) == ph && !*vabort) {
+                                const int row = 32 * (quarter & 1) + lane;
+                                for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
+                                    float v[16];
+                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + u2 * 128 + 16 * u, v);
+#pragma unroll
+                                    for (int p = 0; p < 8; ++p) {
+                                        const int b2 = 8 * u + p;
+                                        if (b2 < nbg)
+                                            sDS[ds_index(row, b2)] = make_float2(v[2 * p] * ssc[b2], v[2 * p + 1] * ssc[b2]);
+                                    }
+                                }
+                            }
+                            workers_sync();
+                            // commutator + RK4 for the k-blocks of these 64 rows
+                            const int kbase = (t * 128 + 64 * ph) / NB2;
+                            const int kt = u2 < tcnt ? min(64 / NB2, a.Nk - kbase) : 0;
+                            if (kg < kgroups && !*vabort) {
+                                const int b = b0 + bl;
+                                const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                                const float2 dr = a.dir[b];
+                                for (int kl = kg; kl < kt; kl += kgroups) {
+                                    const Obs3 ob = stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm);
+                                    s0 += ob.p;
+                                    s1 += ob.j;
+                                    s2 += ob.o;
+                                }
+                            }
+                            workers_sync();  // the staged half is consumed before it is rewritten
                         }
+                    }
+                    tc::fence_before_sync();
+                    mb_arrive(acce + ab);
+                    ++acnt;
+                    if (kg < kgroups) {
                         atomicMax(smx + bl, __float_as_uint(xm));
                         if (st == 3) {
                             sred[(kg * nbg + bl) * 3] = s0;
@@ -634,7 +755,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         }
                     }
                     workers_sync();
-                    if (wt < nbg) {
+                    if (wt < nbg && !*vabort) {
                         atomicMax(xout + b0 + wt, smx[wt]);
                         if (st == 3) {
                             double r0 = 0.0, r1 = 0.0, r2 = 0.0;
@@ -643,20 +764,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 r1 += sred[(k2 * nbg + wt) * 3 + 1];
                                 r2 += sred[(k2 * nbg + wt) * 3 + 2];
                             }
-                            double* rr = a.red + ((int64_t)t * a.Bp + b0 + wt) * 3;
+                            double* rr = a.red + ((int64_t)tp * a.Bp + b0 + wt) * 3;
                             rr[0] = r0;
                             rr[1] = r1;
                             rr[2] = r2;
                         }
                     }
                 }
-                ++dcnt;
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (*vabort) ok = false;
             }
-            if (ok) ok = tc_grid_sync(a, gen, &abort_s);
+            TC_TRACE(producer, 5);
+            ok = tc_grid_sync(a, gen, &abort_s);
+            TC_TRACE(producer, 6);
         }
     }
     // observables of the last step
@@ -665,7 +783,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
         for (int64_t b = gt; b < a.act[n - 1]; b += total) {
             double s0 = 0, s1 = 0, s2 = 0;
-            for (int t = 0; t < a.Nt; ++t) {
+            for (int t = 0; t < a.Ntp; ++t) {
                 const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                 s0 += __ldcg(rr);
                 s1 += __ldcg(rr + 1);
@@ -677,9 +795,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             o[2] = s2 / a.Nk;
         }
     }
+    // teardown: no copy and no MMA of this CTA may remain in flight (after an abort some
+    // issued tiles may never have been consumed)
+    if (producer) {
+        const uint32_t first = ppos > (uint32_t)kRing ? ppos - kRing : 0u;
+        for (uint32_t p = first; p < ppos; ++p) mb_wait<true>(full + p % kRing, (p / kRing) & 1u, nullptr, budget);
+    }
+    if (mma) {
+        tc::mma_commit(fin);
+        mb_wait<true>(fin, 0u, nullptr, budget);
+    }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tm, kTmemCols);
     }
@@ -757,10 +885,16 @@ TcDims tc_dims(int64_t N, int r) {
 
 size_t tc_smem_bytes() {
     return (size_t)kRing * kTile + kXbuf + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
-           kGroup * sizeof(unsigned) + (2 * kRing + 5) * sizeof(uint64_t);
+           kGroup * sizeof(unsigned) + (2 * kRing + 9) * sizeof(uint64_t);
 }
 
 }  // namespace
+
+#ifdef TDAGW_TRACE
+extern "C" int tdagw_debug_trace_tc(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_trace_tc, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
+}
+#endif
 
 void pack_factors_tc(Ctx& c) {
     if (c.tc_valid) return;
@@ -841,11 +975,19 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     // largest split of the V^H X reduction over the run (one trajectory group)
     const int MGn = (d.Mt + 3) / 4;
     const int KSmax = std::max(1, std::min(nctas / MGn, d.nchV));
-    const int Gmax = (B + kGroup - 1) / kGroup;
+    // two U row tiles per phase C item (sharing the S o Y tiles) only when each CTA has
+    // several items: the epilogue of a CTA's last item is not overlapped by MMAs
+    int tpi = d.Nt >= 4 * nctas ? 2 : 1;
+    if (const char* e = std::getenv("TDAGW_TC_TILES_PER_ITEM")) {  // tuning override (1 or 2)
+        const int v = std::atoi(e);
+        if (v == 1 || v == 2) tpi = v;
+    }
+    const int Ntp = (d.Nt + tpi - 1) / tpi;
+    const int Gmax = group_count(B, Ntp, nctas);
     c.tcP.ensure((size_t)KSmax * d.rp * Bp * sizeof(float2));
     c.tcY.ensure((size_t)Gmax * d.nchU * kTile);
     c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
-    c.tcRed.ensure((size_t)d.Nt * Bp * 3 * sizeof(double));
+    c.tcRed.ensure((size_t)Ntp * Bp * 3 * sizeof(double));
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
     for (DevBuf* b : {&c.bX, &c.bS, &c.bC}) TDAGW_CUDA(cudaMemsetAsync(b->p, 0, sbytes, s));
     TDAGW_CUDA(cudaMemsetAsync(c.tcMax.p, 0, 3 * Bp * sizeof(unsigned), s));
@@ -881,6 +1023,8 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.r = r;
     a.rp = d.rp;
     a.Nt = d.Nt;
+    a.Ntp = Ntp;
+    a.tpi = tpi;
     a.Mt = d.Mt;
     a.nchU = d.nchU;
     a.nchV = d.nchV;

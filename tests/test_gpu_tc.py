@@ -149,3 +149,22 @@ def test_split_f16_errors():
     with pytest.raises(tg.TdagwError) as e:
         tg.tdagw_compress_svd(c128.h, 8, 8, 1, 1, precision=1)
     assert e.value.code == tg.ERR_UNSUPPORTED
+
+
+def test_split_f16_two_row_tiles_per_item(monkeypatch):
+    """The phase of U (S o Y) with two row tiles sharing each S o Y tile (used for large N)
+    gives the same observables as one tile per item."""
+    p = wl.small_model(12, 2)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, 96, seed=9)
+    ctx = _ctx(p, U, S, V, d)
+    pulses = _pulses(20, 6)
+    steps = [int(x) for x in np.random.default_rng(3).integers(5, 30, 20)]
+    monkeypatch.setenv("TDAGW_TC_TILES_PER_ITEM", "1")
+    one = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    monkeypatch.setenv("TDAGW_TC_TILES_PER_ITEM", "2")
+    two = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    for b, T in enumerate(steps):
+        assert op.rel_l2(two[:T + 1, b, 0], one[:T + 1, b, 0]) < 1e-6, b
+    ref = _oracle(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), pulses[0], steps[0])
+    assert op.rel_l2(two[:steps[0] + 1, 0, 0], ref[:, 0]) < 1e-4
