@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--full-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid"], default=None,
+                    help="run one secondary leg alone and print its JSON (profiling runs)")
+    ap.add_argument("--leg-steps", type=int, default=None, help="step count of the --leg run")
     return ap.parse_args()
 
 
@@ -175,37 +178,165 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def bench_batched(tg, torch, stream, sh):
+def _time_propagate(tg, torch, stream, ctx, fields, steps, dt, mode, flags):
+    """Device time (ms) of one batched propagate after a short warm-up run."""
+    tg.tdagw_propagate(ctx.h, fields, [min(8, s) for s in steps], dt, mode, flags)
+    tg.tdagw_sync(ctx.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    tg.tdagw_propagate(ctx.h, fields, list(steps), dt, mode, flags)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tg.tdagw_sync(ctx.h)
+    return e0.elapsed_time(e1)
+
+
+def _rel_errs(a, b, steps):
+    errs = []
+    for j, T in enumerate(steps):
+        x, y = a[:T + 1, j, 0], b[:T + 1, j, 0]
+        errs.append(float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)))
+    return {"max": max(errs), "median": float(np.median(errs))}
+
+
+def bench_batched(tg, torch, stream, sh, tflops_peak):
     """Field sweep: 256 trajectories of uneven length (500-4000 steps) in one launch,
-    two-band 24 x 24 model (N = 2304), rank 256; low-rank vs dense kernel."""
+    two-band 24 x 24 model (N = 2304), rank 256: low-rank FP32 (SIMT), low-rank split-FP16
+    on the tensor cores, and the dense kernel."""
     w = wl.sweep_nb2_l24()
     ctx = tg.Context(w.model, tg.C64, stream=sh)
-    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED, precision=1)
     fields = [tg.make_field(p) for p in w.pulses]
     total = int(sum(w.steps))
     out = {"workload": "sweep_nb2_l24", "N": w.model.N, "B": w.B, "rank": w.rank,
            "traj_steps": total, "max_steps": int(max(w.steps))}
-    for name, mode in (("lowrank", tg.LOWRANK), ("full", tg.FULL)):
-        # first call tunes the block shape (cached per context, mode and batch size)
-        tg.tdagw_propagate(ctx.h, fields, [min(16, s) for s in w.steps], w.dt, mode, tg.FLAG_RESET)
-        tg.tdagw_sync(ctx.h)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        tg.tdagw_propagate(ctx.h, fields, list(w.steps), w.dt, mode, tg.FLAG_RESET)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        tg.tdagw_sync(ctx.h)
+    obs = {}
+    legs = (("lowrank", tg.LOWRANK, tg.FLAG_RESET),
+            ("lowrank_split_f16", tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16),
+            ("full", tg.FULL, tg.FLAG_RESET))
+    for name, mode, flags in legs:
+        ms = _time_propagate(tg, torch, stream, ctx, fields, w.steps, w.dt, mode, flags)
+        obs[name] = tg.tdagw_observables(ctx.h, B=w.B)
         flops = total * 4 * (2 * 8 * w.model.N * w.rank if mode == tg.LOWRANK else 8 * w.model.N ** 2)
         out[name] = {"value": total / (ms * 1e-3), "unit": "traj*steps/s", "ms": ms,
                      "algorithmic_tflops": flops / (ms * 1e-3) / 1e12}
+    sp = out["lowrank_split_f16"]
+    # tensor-pipe fractions of the split-FP16 leg: algorithmic complex FLOPs, and the
+    # executed FP16 MMA FLOPs (three split products per term)
+    sp["tensor_frac_algorithmic"] = sp["algorithmic_tflops"] / tflops_peak
+    sp["tensor_frac_executed"] = 3 * sp["algorithmic_tflops"] / tflops_peak
     out["speedup_lowrank_vs_full"] = out["lowrank"]["value"] / out["full"]["value"]
+    out["speedup_split_f16_vs_full"] = sp["value"] / out["full"]["value"]
+    out["p_rel_err_split_f16_vs_fp32_lowrank"] = _rel_errs(obs["lowrank_split_f16"], obs["lowrank"], w.steps)
     ctx.close()
     return out
 
 
+def bench_precision(tg, torch, stream, sh, hbm, split_steps=300, fp32_steps=30, full_steps=6):
+    """Precision-study size: four-band 48 x 48 model (N = 36864), rank 2048, B = 64 equal
+    lengths.  Seeded synthetic factors of that shape (the throughput does not depend on
+    their values; the randomised SVD at this size takes about 26 s and is left out)."""
+    w = wl.prec_nb4_l48()
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    U, S, V, d = wl.random_factors(w.model.N, w.rank, seed=3)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    del U, V
+    fields = [tg.make_field(p) for p in w.pulses]
+    N, r, B = w.model.N, w.rank, w.B
+    out = {"workload": "prec_nb4_l48", "N": N, "B": B, "rank": r, "factors": "seeded synthetic"}
+    obs = {}
+    legs = (("lowrank_split_f16", tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16, split_steps),
+            ("lowrank", tg.LOWRANK, tg.FLAG_RESET, fp32_steps),
+            ("full", tg.FULL, tg.FLAG_RESET, full_steps))
+    for name, mode, flags, T in legs:
+        ms = _time_propagate(tg, torch, stream, ctx, fields, [T] * B, w.dt, mode, flags)
+        obs[name] = tg.tdagw_observables(ctx.h, B=B)
+        per_stage = 2 * N * r * 8 if mode == tg.LOWRANK else N * N * 8
+        gbs = 4 * T * per_stage / (ms * 1e-3) / 1e9
+        out[name] = {"value": T * B / (ms * 1e-3), "unit": "traj*steps/s", "steps": T, "ms": ms,
+                     "factor_gbs": gbs, "hbm_frac": gbs / hbm}
+    out["speedup_split_f16_vs_full"] = out["lowrank_split_f16"]["value"] / out["full"]["value"]
+    out["speedup_split_f16_vs_fp32_lowrank"] = out["lowrank_split_f16"]["value"] / out["lowrank"]["value"]
+    # the FP32 run is a prefix of the same trajectories
+    tg.tdagw_propagate(ctx.h, fields, [fp32_steps] * B, w.dt, tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    split_prefix = tg.tdagw_observables(ctx.h, B=B)
+    out["p_rel_err_split_f16_vs_fp32"] = _rel_errs(split_prefix, obs["lowrank"], [fp32_steps] * B)
+    ctx.close()
+    return out
+
+
+def bench_adjoint(tg, torch, stream, sh, T=1000):
+    """Differentiation size: two-band 36 x 36 model (N = 5184), rank 512, B = 32 equal
+    lengths: the checkpointed forward and the discrete adjoint (objective 1/2 sum P_x^2)."""
+    w = wl.adj_nb2_l36()
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    fields = [tg.make_field(p) for p in w.pulses]
+    B = w.B
+    ms_fwd = _time_propagate(tg, torch, stream, ctx, fields, [T] * B, w.dt, tg.LOWRANK,
+                             tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
+    P = tg.tdagw_observables(ctx.h, B=B)
+    d = np.zeros((T + 1, B, 3))
+    d[:, :, 0] = P[:, :, 0]
+    t0 = time.perf_counter()
+    gE, gp = tg.tdagw_adjoint(ctx.h, d, T, B)
+    s_adj = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "adj_nb2_l36", "N": w.model.N, "B": B, "rank": w.rank, "steps": T,
+            "forward_checkpointed": {"value": T * B / (ms_fwd * 1e-3), "unit": "traj*steps/s", "ms": ms_fwd},
+            "adjoint": {"value": T * B / s_adj, "unit": "traj*steps/s", "ms": s_adj * 1e3},
+            "forward_plus_adjoint": {"value": T * B / (ms_fwd * 1e-3 + s_adj), "unit": "traj*steps/s"},
+            "gradients_finite": bool(np.all(np.isfinite(gE)) and np.all(np.isfinite(gp)))}
+
+
+def bench_tc_mid(tg, torch, stream, sh, hbm, steps=20):
+    """Split-FP16 batched propagation at the four-band 36 x 36 size (N = 20736), rank 1024,
+    B = 64 (seeded synthetic factors, 340 MB, larger than L2): the profiling case of the
+    tensor-core kernel (a few GB on the device)."""
+    w = wl.mos2size_nb4_l36()
+    pulses, _ = wl.draw_pulses(64)
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    U, S, V, d = wl.random_factors(w.model.N, w.rank, seed=3)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    fields = [tg.make_field(p) for p in pulses]
+    ms = _time_propagate(tg, torch, stream, ctx, fields, [steps] * 64, w.dt, tg.LOWRANK,
+                         tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    gbs = 4 * steps * 2 * w.model.N * w.rank * 8 / (ms * 1e-3) / 1e9
+    ctx.close()
+    return {"workload": "mos2size_nb4_l36 x 64", "N": w.model.N, "B": 64, "rank": w.rank, "steps": steps,
+            "value": steps * 64 / (ms * 1e-3), "unit": "traj*steps/s", "ms": ms, "factor_gbs": gbs,
+            "hbm_frac": gbs / hbm}
+
+
 # ---------------------------------------------------------------- our arm -----------
+
+def run_leg(a):
+    import torch
+
+    import paper_2502_05635_gb300 as tg
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    tflops = peaks.get("bf16_tflops_sustained") or 1700.0
+    n = a.leg_steps
+    if a.leg == "sweep":
+        out = bench_batched(tg, torch, stream, sh, tflops)
+    elif a.leg == "precision":
+        out = bench_precision(tg, torch, stream, sh, hbm, *( (n, n, n) if n else ()))
+    elif a.leg == "adjoint":
+        out = bench_adjoint(tg, torch, stream, sh, n or 1000)
+    else:
+        out = bench_tc_mid(tg, torch, stream, sh, hbm, n or 20)
+    print(json.dumps({"leg": a.leg, **out}), flush=True)
+
 
 def run_ours(a):
     import torch
@@ -328,6 +459,9 @@ def run_ours(a):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
+    # FP16 and BF16 MMAs run at the same rate: the dense-bf16 figure, sustained (the
+    # batched kernels run inside seconds-long launches)
+    tflops = peaks.get("bf16_tflops_sustained") or 1700.0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_lr / a.steps, "higher_is_better": True,
@@ -357,7 +491,9 @@ def run_ours(a):
     if cpu:
         line["cpu_baseline"] = cpu
     if not a.no_batched:
-        line["batched_sweep"] = bench_batched(tg, torch, stream, sh)
+        line["batched_sweep"] = bench_batched(tg, torch, stream, sh, tflops)
+        line["precision_study"] = bench_precision(tg, torch, stream, sh, hbm)
+        line["adjoint"] = bench_adjoint(tg, torch, stream, sh)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -369,5 +505,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.leg:
+        run_leg(a)
     else:
         run_ours(a)
