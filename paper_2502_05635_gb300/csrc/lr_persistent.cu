@@ -62,6 +62,7 @@ struct LRArgs {
     int64_t N;
     int Nk, r, ldu, T;
     int rows_per_slot, nslots, slot_bytes, rows_max;
+    int u_parts, u_part_w;  // U pass: column parts per row (power of 2) and their width
     int extra_arrivals;  // > 0 only for the timeout test: the barrier can never complete
     unsigned long long wait_ns;
 };
@@ -220,8 +221,9 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
     unsigned char* ring = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
-    float2* ys = reinterpret_cast<float2*>(empty + ns);
-    float2* xs = ys + ldu;
+    // partial U-pass dot products: rows_max x u_parts (at least ldu entries of room)
+    float2* upart = reinterpret_cast<float2*>(empty + ns);
+    float2* xs = upart + max(ldu, a.rows_max * a.u_parts);
     double* wred = reinterpret_cast<double*>(xs + a.rows_max);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kConsumerWarps);
 
@@ -341,41 +343,57 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 if (!(ok = grid_sync(a, lgen, abort_s))) break;
                 TDAGW_TRACE_POINT(3);
-                for (int e = tid; e < ldu; e += kConsumers) ys[e] = __ldcg(a.ytil + e);
-                consumer_sync();
+                // ---- U pass: the rows of a tile are split over all consumer warps by
+                //      column parts (warp = (row in tile) x parts + part), so a tile is
+                //      released as soon as the 16 short partial dot products are done;
+                //      each warp keeps its slice of S o y in registers.  Every warp still
+                //      observes every tile's phase in order (an mbarrier parity wait is
+                //      only unambiguous for a waiter that saw the slot's previous use).
+                const int cp = a.u_parts, pw = a.u_part_w;
+                const int myq = warp % cp, myr = warp / cp, rstride = kConsumerWarps / cp;
+                const int c0 = myq * pw, c1 = min(ldu, c0 + pw);
+                float4 yv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int col = c0 + 2 * (lane + 32 * k);
+                    yv[k] = col < c1 ? __ldcg(reinterpret_cast<const float4*>(a.ytil + col))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 TDAGW_TRACE_POINT(4);
-                // ---- U pass: row q of the range is computed by warp q % 16; every warp
-                //      still observes every tile's phase in order (an mbarrier parity wait
-                //      is only unambiguous for a waiter that saw the slot's previous use)
                 for (int t = 0; t < ntiles; ++t) {
                     if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                     const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
                     const int r0 = t * rps, nr = min(rps, nrows - r0);
-                    for (int rr = 0; rr < nr; ++rr) {
-                        const int row = r0 + rr;
-                        if ((row % kConsumerWarps) != warp) continue;
+                    for (int rr = myr; rr < nr; rr += rstride) {
                         const float2* ur = tile + (size_t)rr * ldu;
                         float2 d = make_float2(0.f, 0.f), d1 = d;
-#pragma unroll 4
-                        for (int p = lane; 2 * p < ldu; p += 32) {
-                            const float4 u = *reinterpret_cast<const float4*>(ur + 2 * p);
-                            const float4 y = *reinterpret_cast<const float4*>(ys + 2 * p);
-                            d = cfma(make_float2(u.x, u.y), make_float2(y.x, y.y), d);
-                            d1 = cfma(make_float2(u.z, u.w), make_float2(y.z, y.w), d1);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int col = c0 + 2 * (lane + 32 * k);
+                            if (col < c1) {
+                                const float4 u = *reinterpret_cast<const float4*>(ur + col);
+                                d = cfma(make_float2(u.x, u.y), make_float2(yv[k].x, yv[k].y), d);
+                                d1 = cfma(make_float2(u.z, u.w), make_float2(yv[k].z, yv[k].w), d1);
+                            }
                         }
                         d = cadd(d, d1);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
-                        if (lane == 0) {
-                            const int64_t i = ra + row;
-                            a.dSw[i] = cfma(a.diag[i], xs[row], d);
-                        }
+                        if (lane == 0) upart[(r0 + rr) * cp + myq] = d;
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty + pos.slot);
                     pos.advance(1, ns);
                 }
                 TDAGW_TRACE_POINT(5);
+                consumer_sync();  // all partial dot products of this CTA's rows are in
+                // dSigma = sum of the parts (fixed order) + K^diag o x
+                for (int row = tid; row < nrows; row += kConsumers) {
+                    float2 sum = upart[row * cp];
+                    for (int q = 1; q < cp; ++q) sum = cadd(sum, upart[row * cp + q]);
+                    const int64_t i = ra + row;
+                    a.dSw[i] = cfma(a.diag[i], xs[row], sum);
+                }
                 consumer_sync();  // this CTA's dSigma rows are complete
                 TDAGW_TRACE_POINT(6);
                 // ---- commutator + RK4 stage update for k in [ka, kb)
@@ -465,7 +483,11 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     int rps = 1;  // rows per slot
     while (rps < 64 && 2 * rps * row_bytes <= kSlotTarget) rps *= 2;
     const int slot_bytes = rps * row_bytes;
-    const size_t extras = (size_t)ldu * 8 + (size_t)rows_max * 8 + 3 * kConsumerWarps * 8 + 16;
+    // U pass: rows per slot x column parts = 16 consumer warps (parts of even width)
+    const int u_parts = rps >= kConsumerWarps ? 1 : kConsumerWarps / rps;
+    const int u_part_w = ((ldu + u_parts - 1) / u_parts + 1) / 2 * 2;
+    const size_t extras = (size_t)std::max(ldu, rows_max * u_parts) * 8 + (size_t)rows_max * 8 +
+                          3 * kConsumerWarps * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
     if (avail < extras + 4 * (size_t)slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
@@ -519,6 +541,8 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.nslots = nslots;
     a.slot_bytes = slot_bytes;
     a.rows_max = rows_max;
+    a.u_parts = u_parts;
+    a.u_part_w = u_part_w;
     a.extra_arrivals = test_timeout ? 1 : 0;
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};
