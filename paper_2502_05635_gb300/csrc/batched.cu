@@ -326,16 +326,20 @@ BatchSetup prepare_batch(Ctx& c, const tdagw_field* fields, int B, const int* st
     c.bEtab.ensure((size_t)B * ldE * sizeof(double));
     TDAGW_CUDA(cudaMemsetAsync(c.bEtab.p, 0, (size_t)B * ldE * sizeof(double), s));
     std::vector<float2> dir(B);
+    std::vector<FieldParams> fp(B);
     for (int q = 0; q < B; ++q) {
         const tdagw_field& f = fields[perm[q]];
         const int64_t ns = 2 * (int64_t)steps[perm[q]] + 1;
-        double* dst = c.bEtab.as<double>() + (int64_t)q * ldE;
         if (f.kind == TDAGW_FIELD_TABLE)
-            TDAGW_CUDA(cudaMemcpyAsync(dst, f.table, ns * sizeof(double), cudaMemcpyHostToDevice, s));
-        else
-            launch_field_table(f, 0.0, dt, ns, dst, s);
+            TDAGW_CUDA(cudaMemcpyAsync(c.bEtab.as<double>() + (int64_t)q * ldE, f.table, ns * sizeof(double),
+                                       cudaMemcpyHostToDevice, s));
+        fp[q] = FieldParams{f.E0, f.omega, f.t0, f.sigma, f.T_pulse, f.kind, ns};
         dir[q] = make_float2((float)f.dir_x, (float)f.dir_y);
     }
+    // analytic tables of all trajectories in one launch
+    c.bfield.ensure(B * sizeof(FieldParams));
+    TDAGW_CUDA(cudaMemcpyAsync(c.bfield.p, fp.data(), B * sizeof(FieldParams), cudaMemcpyHostToDevice, s));
+    launch_field_tables(c.bfield.as<FieldParams>(), B, ldE, ldE, dt, c.bEtab.as<double>(), s);
     c.bdir.ensure(B * sizeof(float2));
     TDAGW_CUDA(cudaMemcpyAsync(c.bdir.p, dir.data(), B * sizeof(float2), cudaMemcpyHostToDevice, s));
     c.bact.ensure(act.size() * sizeof(int));

@@ -174,7 +174,7 @@ struct Ctx {
     DevBuf pbuf, sync;
     bool persistent_launched = false;
     // batched propagation: states N x Bp, intermediates, per-trajectory tables
-    DevBuf bX, bS, bC, bA, bdS, bP, bY, bred, bobs, bEtab, bdir, bact, bperm;
+    DevBuf bX, bS, bC, bA, bdS, bP, bY, bred, bobs, bEtab, bdir, bact, bperm, bfield;
     std::map<int, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
     int last_plan_rg = 0, last_plan_tg = 0;
     int obs_B = 1;           // trajectories in the recorded observables
@@ -229,6 +229,14 @@ template <typename R>
 void launch_observables_row(Ctx& c, const void* X, int64_t row, cudaStream_t s);
 void launch_field_table(const tdagw_field& f, double t_start, double dt, int64_t nsamp,
                         double* out, cudaStream_t s);
+// analytic pulse parameters of one trajectory for the batched field tables
+struct FieldParams {
+    double E0, omega, t0, sigma, Tp;
+    int kind;
+    int64_t nsamp;
+};
+void launch_field_tables(const FieldParams* p_dev, int B, int64_t max_nsamp, int64_t ldE, double dt,
+                         double* out, cudaStream_t s);
 template <typename R>
 void launch_convert_in(const double2* src, void* dst, int64_t n, cudaStream_t s);
 template <typename R>

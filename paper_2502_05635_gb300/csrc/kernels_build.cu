@@ -1,5 +1,6 @@
 // Device construction of the dense direct kernel (Eq. bse-direct-def for the lattice model),
 // sampled reads of it, precision conversions at the boundary, and the pulse sample table.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -89,12 +90,8 @@ __global__ void convert_out_kernel(const cplx_t<R>* __restrict__ src, double2* _
 
 // E(t_start + j dt / 2) for j < nsamp: every RK4 stage time of the run (Algorithm: the
 // stage times of classical RK4 are t_n, t_n + dt/2 (twice) and t_n + dt).
-__global__ void field_table_kernel(int kind, double E0, double omega, double t0, double sigma,
-                                   double Tp, double t_start, double dt, int64_t nsamp,
-                                   double* __restrict__ out) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= nsamp) return;
-    const double t = t_start + 0.5 * dt * (double)j;
+__device__ double field_value(int kind, double E0, double omega, double t0, double sigma, double Tp,
+                              double t) {
     double e = 0.0;
     if (kind == TDAGW_FIELD_GAUSS_COS) {
         const double u = t - t0;
@@ -107,7 +104,28 @@ __global__ void field_table_kernel(int kind, double E0, double omega, double t0,
             e = E0 * s * s * sin(omega * t);
         }
     }
-    out[j] = e;
+    return e;
+}
+
+__global__ void field_table_kernel(int kind, double E0, double omega, double t0, double sigma,
+                                   double Tp, double t_start, double dt, int64_t nsamp,
+                                   double* __restrict__ out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nsamp) return;
+    out[j] = field_value(kind, E0, omega, t0, sigma, Tp, t_start + 0.5 * dt * (double)j);
+}
+
+// all analytic tables of a batch in one launch: row q of out (stride ldE) holds the
+// half-step samples of trajectory q (table-kind rows are left to the caller)
+__global__ void field_tables_kernel(const FieldParams* __restrict__ p, int B, int64_t ldE, double dt,
+                                    double* __restrict__ out) {
+    for (int q = blockIdx.y; q < B; q += gridDim.y) {
+        const FieldParams f = p[q];
+        if (f.kind == TDAGW_FIELD_TABLE) continue;
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < f.nsamp;
+             j += (int64_t)gridDim.x * blockDim.x)
+            out[(int64_t)q * ldE + j] = field_value(f.kind, f.E0, f.omega, f.t0, f.sigma, f.Tp, 0.5 * dt * (double)j);
+    }
 }
 
 inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
@@ -162,6 +180,14 @@ void launch_field_table(const tdagw_field& f, double t_start, double dt, int64_t
     field_table_kernel<<<(unsigned)((nsamp + 255) / 256), 256, 0, s>>>(
         f.kind, f.E0, f.omega, f.t0, f.sigma, f.T_pulse, t_start, dt, nsamp, out);
     check_launch("field_table_kernel");
+}
+
+void launch_field_tables(const FieldParams* p_dev, int B, int64_t max_nsamp, int64_t ldE, double dt,
+                         double* out, cudaStream_t s) {
+    const unsigned gx = (unsigned)std::min<int64_t>(64, (max_nsamp + 255) / 256);
+    const unsigned gy = (unsigned)std::min(B, 4096);
+    field_tables_kernel<<<dim3(std::max(1u, gx), std::max(1u, gy)), 256, 0, s>>>(p_dev, B, ldE, dt, out);
+    check_launch("field_tables_kernel");
 }
 
 #define INST(R)                                                                            \
