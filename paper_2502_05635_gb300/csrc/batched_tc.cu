@@ -52,13 +52,17 @@ using namespace batched;
 
 constexpr int kWorkers = 256;
 constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
-constexpr int kRing = 11;                  // ring slots of one tile each
+constexpr int kRing = 9;                   // ring slots of one tile each
+constexpr int kBBuf = 4;                   // built B blocks in flight (phase A)
+constexpr int kCmb = 16;                   // chunk-completion barriers (ring); every wait on
+                                           // one targets a chunk < kCmb chunks behind the
+                                           // MMA thread's next chunk, so parities cannot alias
 constexpr uint32_t kTile = 16384;          // 128 rows x 32 real columns, hi (8 KB) + lo (8 KB)
 constexpr uint32_t kHalf = 8192;
 constexpr int kKc = 32;                    // real reduction columns per tile (16 complex)
 constexpr int kGroup = 64;                 // trajectories per group: MMA N = 2 x 64 max
 constexpr uint32_t kLbo = 128, kSbo = (kKc / 8) * 128;
-constexpr uint32_t kXbuf = 2 * kTile;      // B blocks (phase A) / staged half tile (phase C)
+constexpr uint32_t kXbuf = kBBuf * kTile;  // B blocks (phase A) / staged half tile (phase C)
 constexpr int kAccCols = 256;              // columns of one accumulator buffer (two buffers)
 constexpr int kTmemCols = 512;
 
@@ -120,9 +124,22 @@ __device__ unsigned long long g_trace_tc[160 * kTraceStages * 9];
         if ((who) && blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                         \
             g_trace_tc[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] = gtime();                   \
     } while (0)
+// per-chunk timestamps of phase A in CTA 0, stage kTraceFirst + 1, first item:
+// [chunk][0] MMA thread has the chunk's tiles and B block, [1] its MMAs are issued,
+// [2] worker 0 may overwrite the B buffer, [3] worker 0 has built the block;
+// [63][0..3]: worker 0 accumulator ready, readout done, MMA thread item done, -
+__device__ unsigned long long g_trace_a[64 * 4];
+#define TC_TRACE_A(who, cc, k)                                                                   \
+    do {                                                                                         \
+        if ((who) && blockIdx.x == 0 && 4 * n + st == kTraceFirst + 1 && item == (int)blockIdx.x && (cc) < 64) \
+            g_trace_a[(cc) * 4 + (k)] = gtime();                                                 \
+    } while (0)
 #else
 #define TC_TRACE(who, k) \
     do {                 \
+    } while (0)
+#define TC_TRACE_A(who, cc, k) \
+    do {                       \
     } while (0)
 #endif
 
@@ -362,10 +379,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     unsigned* smx = reinterpret_cast<unsigned*>(ssc + kGroup);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smx + kGroup);
     uint64_t* full = bars;
-    uint64_t* empty = full + kRing;
-    uint64_t* bfull = empty + kRing;
-    uint64_t* bempty = bfull + 2;
-    uint64_t* accf = bempty + 2;  // accumulator written (MMA -> workers)
+    uint64_t* cmb = full + kRing;     // MMAs of chunk q complete (one commit per chunk)
+    uint64_t* bfull = cmb + kCmb;
+    uint64_t* accf = bfull + kBBuf;   // accumulator written (MMA -> workers)
     uint64_t* acce = accf + 2;    // accumulator drained (workers -> MMA)
     uint64_t* fin = acce + 2;     // last MMAs complete (teardown)
     __shared__ uint32_t tmem_base;
@@ -381,13 +397,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 
     if (tid == 0) {
         abort_s = 0;
-        for (int s = 0; s < kRing; ++s) {
-            mb_init(full + s, 1);
-            mb_init(empty + s, 1);
-        }
+        for (int s = 0; s < kRing; ++s) mb_init(full + s, 1);
+        for (int s = 0; s < kCmb; ++s) mb_init(cmb + s, 1);
+        for (int s = 0; s < kBBuf; ++s) mb_init(bfull + s, kWorkers);
         for (int s = 0; s < 2; ++s) {
-            mb_init(bfull + s, kWorkers);
-            mb_init(bempty + s, 1);
             mb_init(accf + s, 1);
             mb_init(acce + s, kWorkers);
         }
@@ -402,22 +415,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 
     uint32_t ppos = 0;  // producer: tiles issued so far (ring position)
     uint32_t mpos = 0;  // MMA thread: tiles consumed so far
-    uint32_t bu = 0;    // uses of the two built-B buffers (MMA thread and workers)
+    uint32_t bu = 0;    // uses of the built-B buffers (MMA thread and workers)
     uint32_t acnt = 0;  // uses of the two accumulators (MMA thread and workers)
+    int gch = 0;        // chunks so far (all roles count the same sequence)
+    int slot_ch[kRing]; // producer: chunk that last used each ring slot
+    int buf_ch[kBBuf];  // workers: chunk that last used each B buffer
+    for (int q = 0; q < kRing; ++q) slot_ch[q] = -1;
+    for (int q = 0; q < kBBuf; ++q) buf_ch[q] = -1;
     unsigned gen = 0;
     bool ok = true;
     auto fail = [&]() {
         atomicExch(a.err, 1);
         abort_s = 1;
     };
-    // producer: one tile into the next ring slot
+    // wait until the MMAs of chunk q are complete (q < 0: nothing to wait for; a chunk
+    // kCmb or more behind is complete: an accumulator wait or a grid barrier came between)
+    auto chunk_done = [&](int q, bool poll) -> bool {
+        if (q < 0 || gch - q >= kCmb) return true;
+        return poll ? mb_wait<true>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget)
+                    : mb_wait<false>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
+    };
+    // producer: one tile of chunk gch into the next ring slot
     auto issue = [&](const unsigned char* src) {
         if (*vabort) return;
-        const uint32_t slot = ppos % kRing, use = ppos / kRing;
-        if (!mb_wait<true>(empty + slot, (use & 1u) ^ 1u, vabort, budget)) {
+        const uint32_t slot = ppos % kRing;
+        if (!chunk_done(slot_ch[slot], true)) {
             fail();
             return;
         }
+        slot_ch[slot] = gch;
         mb_expect_tx(full + slot, kTile);
         bulk_load(ring + slot * kTile, src, kTile, full + slot);
         ++ppos;
@@ -432,8 +458,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         ++mpos;
         return tc::smem_u32(ring + slot * kTile);
     };
-    auto release_tile = [&](uint32_t back) {  // slot of the tile consumed `back` tiles ago
-        tc::mma_commit(empty + (mpos - back) % kRing);
+    auto end_chunk = [&]() {  // MMA thread: the chunk's MMAs are issued
+        tc::mma_commit(cmb + gch % kCmb);
     };
 
     for (int n = 0; n < a.Tmax && ok; ++n) {
@@ -452,7 +478,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             if (producer) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
-                    for (int c = it.c0; c < it.c1; ++c)
+                    for (int c = it.c0; c < it.c1; ++c, ++gch)
                         for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile);
                 }
             } else if (mma) {
@@ -468,19 +494,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     for (int c = it.c0; c < it.c1 && !*vabort; ++c) {
                         uint32_t ta[2] = {0u, 0u};
                         for (int ml = 0; ml < it.mc; ++ml) ta[ml] = next_tile();
-                        if (*vabort || !mb_wait<true>(bfull + (bu & 1u), (bu >> 1) & 1u, vabort, budget)) {
+                        if (*vabort || !mb_wait<true>(bfull + bu % kBBuf, (bu / kBBuf) & 1u, vabort, budget)) {
                             fail();
                             break;
                         }
+                        TC_TRACE_A(true, c - it.c0, 0);
                         tc::fence_after_sync();
-                        const uint32_t baddr = tc::smem_u32(xbuf + (bu & 1u) * kTile);
+                        const uint32_t baddr = tc::smem_u32(xbuf + (bu % kBBuf) * kTile);
                         for (int ml = 0; ml < it.mc; ++ml)
                             mma_tile(tm + ab * kAccCols + ml * 128, ta[ml], baddr, idesc, c == it.c0);
-                        for (int ml = 0; ml < it.mc; ++ml) release_tile(it.mc - ml);
-                        tc::mma_commit(bempty + (bu & 1u));
+                        TC_TRACE_A(true, c - it.c0, 1);
+                        end_chunk();
+                        ++gch;
                         ++bu;
                     }
                     tc::mma_commit(accf + ab);
+                    TC_TRACE_A(true, 63, 2);
                     ++acnt;
                 }
             } else if (worker) {
@@ -493,10 +522,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     if (wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
                     workers_sync();
                     // expanded split X block of each chunk (16 rows x nbp trajectories); each
-                    // worker owns elements e = wt + 256 u, u < 4, and loads the next chunk's
-                    // values before building the current one
+                    // worker owns elements e = wt + 256 u, u < 4, and loads the values of the
+                    // chunk after next before building the current one
                     constexpr int kPer = 16 * kGroup / kWorkers;
-                    float2 cur[kPer], nxt[kPer];
                     auto load_chunk = [&](int c, float2 (&xv)[kPer]) {
 #pragma unroll
                         for (int u = 0; u < kPer; ++u) {
@@ -506,11 +534,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             xv[u] = (bl < nbg && i < a.N) ? __ldcg(a.X + i * a.Bp + b0 + bl) : make_float2(0.f, 0.f);
                         }
                     };
-                    if (it.c0 < it.c1) load_chunk(it.c0, cur);
-                    for (int c = it.c0; c < it.c1; ++c) {
-                        if (c + 1 < it.c1) load_chunk(c + 1, nxt);
-                        const uint32_t bs = bu & 1u;
-                        if (!*vabort && !mb_wait<false>(bempty + bs, ((bu >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    auto build_chunk = [&](int c, const float2 (&xv)[kPer]) {
+                        const uint32_t bs = bu % kBBuf;
+                        if (!*vabort && !chunk_done(buf_ch[bs], false)) fail();
+                        buf_ch[bs] = gch;
+                        TC_TRACE_A(wt == 0, c - it.c0, 2);
                         if (!*vabort) {
                             unsigned char* tile = xbuf + bs * kTile;
 #pragma unroll
@@ -518,7 +546,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 const int e = wt + kWorkers * u;
                                 const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
                                 if (bl >= nbp) continue;
-                                const float2 x = cur[u];
+                                const float2 x = xv[u];
                                 const float sx = ssc[bl];
                                 __half rh, rl, ih, il2;
                                 split16(x.x * sx, rh, rl);
@@ -533,33 +561,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         }
                         tc::fence_proxy_async();
                         mb_arrive(bfull + bs);
+                        TC_TRACE_A(wt == 0, c - it.c0, 3);
                         ++bu;
-#pragma unroll
-                        for (int u = 0; u < kPer; ++u) cur[u] = nxt[u];
+                        ++gch;
+                    };
+                    // expanded split X block of each chunk (16 rows x nbp trajectories); each
+                    // worker owns elements e = wt + 256 u, u < 4; its loads run two chunks
+                    // ahead of the build (three rotating register sets, no copies)
+                    float2 xa[kPer], xb[kPer], xc[kPer];
+                    if (it.c0 < it.c1) load_chunk(it.c0, xa);
+                    if (it.c0 + 1 < it.c1) load_chunk(it.c0 + 1, xb);
+                    for (int c = it.c0; c < it.c1; c += 3) {
+                        if (c + 2 < it.c1) load_chunk(c + 2, xc);
+                        build_chunk(c, xa);
+                        if (c + 1 >= it.c1) break;
+                        if (c + 3 < it.c1) load_chunk(c + 3, xa);
+                        build_chunk(c + 1, xb);
+                        if (c + 2 >= it.c1) break;
+                        if (c + 4 < it.c1) load_chunk(c + 4, xb);
+                        build_chunk(c + 2, xc);
                     }
-                    // accumulators -> raw partials P[ks][j][b]
+                    // accumulators -> raw partials P[ks][j][b], one 128-row tile at a time
+                    // staged in the (now idle) B buffers so that the global writes run
+                    // along trajectories (coalesced)
                     const uint32_t ab = acnt & 1u;
                     if (!*vabort && !mb_wait<false>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    TC_TRACE_A(wt == 0, 63, 0);
                     tc::fence_after_sync();
-                    if (!*vabort) {
-                        const int quarter = warp & 3, half = (warp - 2) >> 2;
-                        const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
-                        for (int ml = 0; ml < it.mc; ++ml) {
-                            const int j = (it.m0 + ml) * 128 + 32 * quarter + lane;
-                            float2* prow = a.P + ((int64_t)it.ks * a.rp + j) * a.Bp + b0;
+                    float2* stg = reinterpret_cast<float2*>(xbuf);  // 128 x 64 float2 (64 KB)
+                    const int quarter = warp & 3, half = (warp - 2) >> 2;
+                    const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
+                    for (int ml = 0; ml < it.mc; ++ml) {
+                        TC_TRACE_A(wt == 0, 62, ml);
+                        workers_sync();  // B buffers no longer read (all MMAs of the item are done)
+                        if (!*vabort) {
+                            const int row = 32 * quarter + lane;
                             for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
                                 float v[16];
                                 tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + ml * 128 + 16 * u, v);
 #pragma unroll
-                                for (int p = 0; p < 8; ++p) {
-                                    const int bl = 8 * u + p;
-                                    if (bl < nbg) prow[bl] = make_float2(v[2 * p], v[2 * p + 1]);
-                                }
+                                for (int p = 0; p < 8; ++p)
+                                    stg[row * 64 + ((8 * u + p) ^ (row & 31))] = make_float2(v[2 * p], v[2 * p + 1]);
+                            }
+                        }
+                        workers_sync();
+                        if (!*vabort) {
+                            float2* pbase = a.P + ((int64_t)it.ks * a.rp + (it.m0 + ml) * 128) * a.Bp + b0;
+                            for (int e = wt; e < 128 * nbg; e += kWorkers) {
+                                const int row = e / nbg, bl = e % nbg;
+                                pbase[(int64_t)row * a.Bp + bl] = stg[row * 64 + (bl ^ (row & 31))];
                             }
                         }
                     }
+                    workers_sync();  // staging reads done before the next item's B blocks
                     tc::fence_before_sync();
                     mb_arrive(acce + ab);
+                    TC_TRACE_A(wt == 0, 63, 1);
                     ++acnt;
                 }
             }
@@ -653,7 +710,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 for (int item = blockIdx.x; item < nC; item += gridDim.x) {
                     const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
                     const int tcnt = min(a.tpi, a.Nt - t0);
-                    for (int c = 0; c < a.nchU; ++c) {
+                    for (int c = 0; c < a.nchU; ++c, ++gch) {
                         for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile);
                         issue(a.tY + ((int64_t)g * a.nchU + c) * kTile);
                     }
@@ -677,7 +734,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         if (*vabort) break;
                         tc::fence_after_sync();
                         for (int u = 0; u < tcnt; ++u) mma_tile(tm + ab * kAccCols + u * 128, tu[u], ty, idesc, c == 0);
-                        for (int u = 0; u <= tcnt; ++u) release_tile(tcnt + 1 - u);
+                        end_chunk();
+                        ++gch;
                     }
                     tc::mma_commit(accf + ab);
                     ++acnt;
@@ -687,6 +745,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 for (int item = blockIdx.x; item < nC; item += gridDim.x) {
                     const int tp = item % a.Ntp, t0 = a.tpi * tp, g = item / a.Ntp;
                     const int tcnt = min(a.tpi, a.Nt - t0);
+                    gch += a.nchU;  // the item's chunks (counted like the copy and MMA threads)
                     int b0, b1;
                     group_range(Bact, q.GC, g, b0, b1);
                     const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
@@ -885,7 +944,7 @@ TcDims tc_dims(int64_t N, int r) {
 
 size_t tc_smem_bytes() {
     return (size_t)kRing * kTile + kXbuf + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
-           kGroup * sizeof(unsigned) + (2 * kRing + 9) * sizeof(uint64_t);
+           kGroup * sizeof(unsigned) + (kRing + kCmb + kBBuf + 5) * sizeof(uint64_t);
 }
 
 }  // namespace
@@ -893,6 +952,9 @@ size_t tc_smem_bytes() {
 #ifdef TDAGW_TRACE
 extern "C" int tdagw_debug_trace_tc(unsigned long long* out, int n) {
     return cudaMemcpyFromSymbol(out, g_trace_tc, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
+}
+extern "C" int tdagw_debug_trace_tc_a(unsigned long long* out) {
+    return cudaMemcpyFromSymbol(out, g_trace_a, sizeof(unsigned long long) * 64 * 4) == cudaSuccess ? 0 : -3;
 }
 #endif
 
