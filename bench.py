@@ -59,6 +59,21 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest per-rank value of a timing (one all-reduce); x itself on one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of ws independent replicas timed over the slowest rank."""
+    return ws * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------- clocks ------------
 
 class ClockSampler:
@@ -373,12 +388,7 @@ def run_ours(a):
         tg.tdagw_propagate(ctx.h, field, [nsteps], dt, mode, tg.FLAG_RESET)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist if ws > 1 else None, dev)
 
     # low-rank path: the headline
     with ClockSampler(local) as clk:
@@ -433,16 +443,12 @@ def run_ours(a):
     tg.tdagw_set_state(ctx.h, x0, None, 0)
     tg.tdagw_propagate(ctx.h, field, [a.steps], dt, tg.LOWRANK, 0)
     tg.tdagw_observables(ctx.h, out)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist if ws > 1 else None, dev)
     h2d = (x0.nbytes + 72) / a.steps
     d2h = out.nbytes / a.steps
 
-    value = ws * a.steps / (ms_lr * 1e-3)
-    full_value = ws * nf / (ms_full * 1e-3)
+    value = replica_rate(ws, a.steps, ms_lr * 1e-3)
+    full_value = replica_rate(ws, nf, ms_full * 1e-3)
     launches = 3                    # field table, first observables row, persistent kernel
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -482,7 +488,7 @@ def run_ours(a):
                      "bytes_per_stage": bytes_apply,
                      "traffic": traffic},
         "stagewise_apply": {"gbs": achieved_stagewise, "ms": ms_apply},
-        "e2e": {"value": ws * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replica_rate(ws, a.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
