@@ -52,8 +52,16 @@ using namespace batched;
 
 constexpr int kWorkers = 256;
 constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
-constexpr int kRing = 9;                   // ring slots of one tile each
-constexpr int kBBuf = 4;                   // built B blocks in flight (phase A)
+// ring depth and built-B buffers (build-time tuning parameters; smem: (ring + buffers) x 16 KB)
+#ifndef TDAGW_TC_RING
+#define TDAGW_TC_RING 11
+#endif
+#ifndef TDAGW_TC_BBUF
+#define TDAGW_TC_BBUF 2
+#endif
+constexpr int kRing = TDAGW_TC_RING;       // ring slots of one tile each
+constexpr int kBBuf = TDAGW_TC_BBUF;       // built B blocks in flight (phase A)
+static_assert(kRing + kBBuf <= 13, "ring and B buffers must fit in shared memory");
 constexpr int kCmb = 16;                   // chunk-completion barriers (ring); every wait on
                                            // one targets a chunk < kCmb chunks behind the
                                            // MMA thread's next chunk, so parities cannot alias
@@ -134,12 +142,29 @@ __device__ unsigned long long g_trace_a[64 * 4];
         if ((who) && blockIdx.x == 0 && 4 * n + st == kTraceFirst + 1 && item == (int)blockIdx.x && (cc) < 64) \
             g_trace_a[(cc) * 4 + (k)] = gtime();                                                 \
     } while (0)
+// wait/issue time accumulators per CTA and traced stage: [0] MMA thread waiting for tiles,
+// [1] for B blocks, [2] for a free accumulator, [3] issuing MMAs and commits, [4] copy
+// thread waiting for a free slot, [5] issuing copies
+__device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
+#define TC_W_BEGIN(id) const uint64_t tw_##id = gtime()
+#define TC_W_END(id, k)                                                                          \
+    do {                                                                                         \
+        const int ts_ = 4 * n + st - kTraceFirst;                                                \
+        if (blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                                  \
+            g_trace_w[(blockIdx.x * kTraceStages + ts_) * 6 + (k)] += gtime() - tw_##id;         \
+    } while (0)
 #else
 #define TC_TRACE(who, k) \
     do {                 \
     } while (0)
 #define TC_TRACE_A(who, cc, k) \
     do {                       \
+    } while (0)
+#define TC_W_BEGIN(id) \
+    do {               \
+    } while (0)
+#define TC_W_END(id, k) \
+    do {                \
     } while (0)
 #endif
 
@@ -175,6 +200,9 @@ __device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+#ifndef TDAGW_TC_WORKER_POLL
+#define TDAGW_TC_WORKER_POLL 0  // 1: worker warps poll (test_wait) instead of try_wait
+#endif
 // bounded wait for the phase of the given parity; false on expiry or abort
 template <bool POLL>
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
@@ -433,7 +461,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     auto chunk_done = [&](int q, bool poll) -> bool {
         if (q < 0 || gch - q >= kCmb) return true;
         return poll ? mb_wait<true>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget)
-                    : mb_wait<false>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
+                    : mb_wait<TDAGW_TC_WORKER_POLL != 0>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
     };
     // producer: one tile of chunk gch into the next ring slot
     auto issue = [&](const unsigned char* src) {
@@ -478,8 +506,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             if (producer) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
-                    for (int c = it.c0; c < it.c1; ++c, ++gch)
+                    for (int c = it.c0; c < it.c1; ++c, ++gch) {
+                        TC_W_BEGIN(p0);
                         for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile);
+                        TC_W_END(p0, 4);
+                    }
                 }
             } else if (mma) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
@@ -488,23 +519,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     group_range(Bact, q.G, it.g, b0, b1);
                     const int nbp = (b1 - b0 + 7) & ~7;
                     const uint32_t ab = acnt & 1u;
+                    TC_W_BEGIN(a0);
                     if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    TC_W_END(a0, 2);
                     tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
                     for (int c = it.c0; c < it.c1 && !*vabort; ++c) {
                         uint32_t ta[2] = {0u, 0u};
+                        TC_W_BEGIN(t0);
                         for (int ml = 0; ml < it.mc; ++ml) ta[ml] = next_tile();
+                        TC_W_END(t0, 0);
+                        TC_W_BEGIN(b0);
                         if (*vabort || !mb_wait<true>(bfull + bu % kBBuf, (bu / kBBuf) & 1u, vabort, budget)) {
                             fail();
                             break;
                         }
+                        TC_W_END(b0, 1);
                         TC_TRACE_A(true, c - it.c0, 0);
                         tc::fence_after_sync();
                         const uint32_t baddr = tc::smem_u32(xbuf + (bu % kBBuf) * kTile);
+                        TC_W_BEGIN(m0);
                         for (int ml = 0; ml < it.mc; ++ml)
                             mma_tile(tm + ab * kAccCols + ml * 128, ta[ml], baddr, idesc, c == it.c0);
                         TC_TRACE_A(true, c - it.c0, 1);
                         end_chunk();
+                        TC_W_END(m0, 3);
                         ++gch;
                         ++bu;
                     }
@@ -581,35 +620,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         if (c + 4 < it.c1) load_chunk(c + 4, xb);
                         build_chunk(c + 2, xc);
                     }
-                    // accumulators -> raw partials P[ks][j][b], one 128-row tile at a time
-                    // staged in the (now idle) B buffers so that the global writes run
-                    // along trajectories (coalesced)
+                    // accumulators -> raw partials P[ks][j][b], 64 rows at a time staged in
+                    // the (now idle) B buffers so that the global writes run along
+                    // trajectories (coalesced)
                     const uint32_t ab = acnt & 1u;
-                    if (!*vabort && !mb_wait<false>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
                     TC_TRACE_A(wt == 0, 63, 0);
                     tc::fence_after_sync();
-                    float2* stg = reinterpret_cast<float2*>(xbuf);  // 128 x 64 float2 (64 KB)
+                    float2* stg = reinterpret_cast<float2*>(xbuf);  // 64 rows x 64 float2 (32 KB)
                     const int quarter = warp & 3, half = (warp - 2) >> 2;
                     const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
                     for (int ml = 0; ml < it.mc; ++ml) {
                         TC_TRACE_A(wt == 0, 62, ml);
-                        workers_sync();  // B buffers no longer read (all MMAs of the item are done)
-                        if (!*vabort) {
-                            const int row = 32 * quarter + lane;
-                            for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
-                                float v[16];
-                                tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + ml * 128 + 16 * u, v);
+                        for (int ph = 0; ph < 2; ++ph) {
+                            workers_sync();  // B buffers / the previous half no longer read
+                            if ((quarter >> 1) == ph && !*vabort) {
+                                const int row = 32 * (quarter & 1) + lane;
+                                for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
+                                    float v[16];
+                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + ml * 128 + 16 * u, v);
 #pragma unroll
-                                for (int p = 0; p < 8; ++p)
-                                    stg[row * 64 + ((8 * u + p) ^ (row & 31))] = make_float2(v[2 * p], v[2 * p + 1]);
+                                    for (int p = 0; p < 8; ++p)
+                                        stg[ds_index(row, 8 * u + p)] = make_float2(v[2 * p], v[2 * p + 1]);
+                                }
                             }
-                        }
-                        workers_sync();
-                        if (!*vabort) {
-                            float2* pbase = a.P + ((int64_t)it.ks * a.rp + (it.m0 + ml) * 128) * a.Bp + b0;
-                            for (int e = wt; e < 128 * nbg; e += kWorkers) {
-                                const int row = e / nbg, bl = e % nbg;
-                                pbase[(int64_t)row * a.Bp + bl] = stg[row * 64 + (bl ^ (row & 31))];
+                            workers_sync();
+                            if (!*vabort) {
+                                float2* pbase = a.P + ((int64_t)it.ks * a.rp + (it.m0 + ml) * 128 + 64 * ph) * a.Bp + b0;
+                                for (int e = wt; e < 64 * nbg; e += kWorkers) {
+                                    const int row = e / nbg, bl = e % nbg;
+                                    pbase[(int64_t)row * a.Bp + bl] = stg[ds_index(row, bl)];
+                                }
                             }
                         }
                     }
@@ -711,8 +752,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
                     const int tcnt = min(a.tpi, a.Nt - t0);
                     for (int c = 0; c < a.nchU; ++c, ++gch) {
+                        TC_W_BEGIN(p1);
                         for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile);
                         issue(a.tY + ((int64_t)g * a.nchU + c) * kTile);
+                        TC_W_END(p1, 4);
                     }
                 }
                 TC_TRACE(true, 8);
@@ -724,17 +767,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     group_range(Bact, q.GC, g, b0, b1);
                     const int nbp = (b1 - b0 + 7) & ~7;
                     const uint32_t ab = acnt & 1u;
+                    TC_W_BEGIN(a0);
                     if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    TC_W_END(a0, 2);
                     tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
                     for (int c = 0; c < a.nchU && !*vabort; ++c) {
                         uint32_t tu[2] = {0u, 0u};
+                        TC_W_BEGIN(t1);
                         for (int u = 0; u < tcnt; ++u) tu[u] = next_tile();
                         const uint32_t ty = next_tile();
+                        TC_W_END(t1, 0);
                         if (*vabort) break;
                         tc::fence_after_sync();
+                        TC_W_BEGIN(m1);
                         for (int u = 0; u < tcnt; ++u) mma_tile(tm + ab * kAccCols + u * 128, tu[u], ty, idesc, c == 0);
                         end_chunk();
+                        TC_W_END(m1, 3);
                         ++gch;
                     }
                     tc::mma_commit(accf + ab);
@@ -759,7 +808,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     }
                     workers_sync();
                     const uint32_t ab = acnt & 1u;
-                    if (!*vabort && !mb_wait<false>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
                     tc::fence_after_sync();
                     const int quarter = warp & 3, half = (warp - 2) >> 2;
                     const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
@@ -952,6 +1001,9 @@ size_t tc_smem_bytes() {
 #ifdef TDAGW_TRACE
 extern "C" int tdagw_debug_trace_tc(unsigned long long* out, int n) {
     return cudaMemcpyFromSymbol(out, g_trace_tc, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
+}
+extern "C" int tdagw_debug_trace_tc_w(unsigned long long* out) {
+    return cudaMemcpyFromSymbol(out, g_trace_w, sizeof(unsigned long long) * 160 * kTraceStages * 6) == cudaSuccess ? 0 : -3;
 }
 extern "C" int tdagw_debug_trace_tc_a(unsigned long long* out) {
     return cudaMemcpyFromSymbol(out, g_trace_a, sizeof(unsigned long long) * 64 * 4) == cudaSuccess ? 0 : -3;
