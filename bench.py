@@ -137,8 +137,12 @@ def _profiled_traffic(stages: int):
     import hashlib
     import re
     h = hashlib.sha1()
-    for f in ("lr_persistent.cu", "stage.cuh", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2502_05635_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2502_05635_gb300", "csrc")
+    for f in ("lr_persistent.cu", "stage.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    # the device helpers of the common header (everything before its host-side sections)
+    common = open(os.path.join(csrc, "common.cuh"), "rb").read()
+    h.update(common.split(b"// " + b"-" * 66 + b" host model")[0])
     try:
         txt = open(os.path.join(ROOT, "profiles", "lr_persistent_kernel_mos2size.md")).read()
     except OSError:

@@ -371,6 +371,72 @@ void reset_batch_observables(Ctx& c, const BatchSetup& bs, int B) {
     check_launch("replicate_rows_kernel");
 }
 
+void launch_batched(Ctx& c, const void* fn, dim3 grid, dim3 block, size_t smem, const void* args,
+                    size_t args_size, const std::vector<ResetOp>& resets, bool use_graph) {
+    cudaStream_t s = c.stream;
+    void* kargs[] = {const_cast<void*>(args)};
+    auto direct = [&](cudaStream_t st) {
+        for (const ResetOp& r : resets) TDAGW_CUDA(cudaMemsetAsync(r.p, 0, r.bytes, st));
+        TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, kargs, smem, st));
+    };
+    if (!use_graph || c.batch_graphs_off) {
+        direct(s);
+        return;
+    }
+    // key: kernel, geometry, shared memory, the argument bytes and the reset list
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        key.insert(key.end(), b, b + n);
+    };
+    put(&fn, sizeof(fn));
+    put(&grid, sizeof(grid));
+    put(&block, sizeof(block));
+    put(&smem, sizeof(smem));
+    put(args, args_size);
+    for (const ResetOp& r : resets) put(&r, sizeof(r));
+    for (size_t i = 0; i < c.batch_graphs.size(); ++i)
+        if (c.batch_graphs[i].key == key) {
+            TDAGW_CUDA(cudaGraphLaunch(c.batch_graphs[i].exec, s));
+            return;
+        }
+    if (!c.cap) TDAGW_CUDA(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    bool ok = cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        for (const ResetOp& r : resets) ok = ok && cudaMemsetAsync(r.p, 0, r.bytes, c.cap) == cudaSuccess;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeCooperative;
+        attr.val.cooperative = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c.cap;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        ok = ok && cudaLaunchKernelExC(&cfg, fn, kargs) == cudaSuccess;
+        const bool ended = cudaStreamEndCapture(c.cap, &g) == cudaSuccess;
+        ok = ok && ended && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+    }
+    if (!ok) {
+        // capture of a cooperative launch unavailable: direct launches from now on
+        cudaGetLastError();
+        if (ge) cudaGraphExecDestroy(ge);
+        c.batch_graphs_off = true;
+        direct(s);
+        return;
+    }
+    if (c.batch_graphs.size() >= 8) {
+        cudaGraphExecDestroy(c.batch_graphs.front().exec);
+        c.batch_graphs.erase(c.batch_graphs.begin());
+    }
+    c.batch_graphs.push_back({key, ge});
+    TDAGW_CUDA(cudaGraphLaunch(ge, s));
+}
+
 void finish_batch(Ctx& c, const BatchSetup& bs, int B) {
     const int64_t rows = bs.rows;
     c.obs.ensure((size_t)rows * B * 3 * sizeof(double));
@@ -457,10 +523,9 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         a.P = c.bP.as<float2>();
         a.Y = c.bY.as<float2>();
         a.red = c.bred.as<double>();
-        for (DevBuf* b : {&c.bX, &c.bS, &c.bC}) TDAGW_CUDA(cudaMemsetAsync(b->p, 0, sbytes, s));
-        TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
-        void* args[] = {&a};
-        TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(pl.Rg * pl.Tg), dim3(kBThreads), args, smem, s));
+        launch_batched(c, fn, dim3(pl.Rg * pl.Tg), dim3(kBThreads), smem, &a, sizeof(a),
+                       {{c.bX.p, sbytes}, {c.bS.p, sbytes}, {c.bC.p, sbytes}, {c.sync.p, 4 * sizeof(unsigned)}},
+                       !(flags & TDAGW_FLAG_NO_GRAPH));
         c.persistent_launched = true;
     };
 

@@ -1103,10 +1103,7 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
     c.tcRed.ensure((size_t)Ntp * Bp * 3 * sizeof(double));
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
-    for (DevBuf* b : {&c.bX, &c.bS, &c.bC}) TDAGW_CUDA(cudaMemsetAsync(b->p, 0, sbytes, s));
-    TDAGW_CUDA(cudaMemsetAsync(c.tcMax.p, 0, 3 * Bp * sizeof(unsigned), s));
     c.sync.ensure(4 * sizeof(unsigned));
-    TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
 
     TcArgs a{};
     a.tU = c.tcU.as<unsigned char>();
@@ -1153,8 +1150,13 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.sv = c.tc_sv;
     a.ybound = c.tc_ybound;
     a.wait_ns = 2000000000ull;
-    void* args[] = {&a};
-    TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(kTcThreads), args, smem, s));
+    launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
+                   {{c.bX.p, sbytes},
+                    {c.bS.p, sbytes},
+                    {c.bC.p, sbytes},
+                    {c.tcMax.p, 3 * Bp * sizeof(unsigned)},
+                    {c.sync.p, 4 * sizeof(unsigned)}},
+                   !(flags & TDAGW_FLAG_NO_GRAPH));
     c.persistent_launched = true;
     c.adj.valid = false;
     finish_batch(c, bs, B);

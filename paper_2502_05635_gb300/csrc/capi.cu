@@ -568,3 +568,10 @@ void tdagw_destroy(tdagw_ctx* ctx) {
 }
 
 }  // extern "C"
+
+#ifdef TDAGW_TRACE
+// traced builds only: CUDA graphs cached for batched launches (-1: capture unavailable)
+extern "C" int tdagw_debug_batch_graphs(tdagw_ctx* ctx) {
+    return ctx->c.batch_graphs_off ? -1 : (int)ctx->c.batch_graphs.size();
+}
+#endif

@@ -189,7 +189,17 @@ struct Ctx {
     // stream used only to capture CUDA graphs (the caller's stream may be the legacy
     // default stream, on which capture is not allowed); graphs are launched on `stream`
     cudaStream_t cap = nullptr;
+    // CUDA graphs of the batched launches (state resets + the persistent kernel), keyed by
+    // the exact launch parameters and argument bytes; a few most recent kept
+    struct BatchGraph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<BatchGraph> batch_graphs;
+    bool batch_graphs_off = false;  // capture failed once on this device: launch directly
     ~Ctx() {
+        for (BatchGraph& g : batch_graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
         if (cap) cudaStreamDestroy(cap);
     }
 };
@@ -250,6 +260,16 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
                           int flags);
 // Split-FP16 tiled copies of the installed factors (made once per set of factors).
 void pack_factors_tc(Ctx& c);
+
+// One persistent cooperative launch of a batched kernel (argument block `args` of
+// `args_size` bytes, a single by-value struct) after zeroing `resets` (pointer, bytes); with
+// use_graph the sequence is replayed from a CUDA graph cached on the context.
+struct ResetOp {
+    void* p;
+    size_t bytes;
+};
+void launch_batched(Ctx& c, const void* fn, dim3 grid, dim3 block, size_t smem, const void* args,
+                    size_t args_size, const std::vector<ResetOp>& resets, bool use_graph);
 
 // Host-side preparation shared by the batched drivers: trajectories sorted by length
 // (longest first), active counts per step, per-trajectory field tables and directions,

@@ -101,3 +101,22 @@ def test_batched_rejects_continue_without_reset():
     with pytest.raises(tg.TdagwError) as e:
         tg.tdagw_propagate(ctx.h, [tg.make_field(wl.Pulse())] * 2, [5, 5], 0.2, tg.FULL, 0)
     assert e.value.code == tg.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("flags", [0, tg.FLAG_SPLIT_F16])
+def test_graph_replay_matches_direct_launch(flags):
+    """Batched launches replayed from the context's cached CUDA graph give the same bits as
+    direct launches (TDAGW_FLAG_NO_GRAPH), on first capture and on replay."""
+    p = wl.small_model(12, 1)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, 40, seed=2)
+    ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    steps = [30, 12, 25]
+    pulses = _pulses(3, 8)
+    base = tg.FLAG_RESET | flags
+    direct = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, base | tg.FLAG_NO_GRAPH)
+    first = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, base)
+    again = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, base)
+    np.testing.assert_array_equal(np.nan_to_num(first, nan=7.0), np.nan_to_num(direct, nan=7.0))
+    np.testing.assert_array_equal(np.nan_to_num(again, nan=7.0), np.nan_to_num(direct, nan=7.0))
