@@ -168,3 +168,28 @@ def test_split_f16_two_row_tiles_per_item(monkeypatch):
         assert op.rel_l2(two[:T + 1, b, 0], one[:T + 1, b, 0]) < 1e-6, b
     ref = _oracle(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), pulses[0], steps[0])
     assert op.rel_l2(two[:steps[0] + 1, 0, 0], ref[:, 0]) < 1e-4
+
+
+def test_precision_study_size_vs_oracle():
+    """The precision-study size (four-band 48 x 48, N = 36864, rank 2048, B = 64): split-FP16
+    and FP32 batched runs of 64 early pulses (uneven lengths) against the FP64 oracle on two
+    trajectories, with the same seeded factors on every side."""
+    w = wl.prec_nb4_l48()
+    mdl = om.Model(w.model)
+    U, S, V, d = wl.random_factors(mdl.N, w.rank, seed=3)
+    ctx = _ctx(w.model, U, S, V, d)
+    rng = np.random.default_rng(21)
+    pulses = [wl.Pulse(E0=float(10 ** rng.uniform(-4, -2)), omega=float(rng.uniform(0.06, 0.16)),
+                       t0=float(rng.uniform(0.5, 1.0)), sigma=float(rng.uniform(0.4, 0.8)),
+                       dir_x=float(np.cos(th)), dir_y=float(np.sin(th)))
+              for th in rng.uniform(0, np.pi, 64)]
+    steps = [6] * 32 + [4] * 32
+    split = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, SPLIT)
+    fp32 = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK)
+    for b, T in enumerate(steps):
+        assert op.rel_l2(split[:T + 1, b, 0], fp32[:T + 1, b, 0]) < 1e-4, b
+    apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
+    for b in (0, 63):
+        ref = _oracle(mdl, apply, pulses[b], steps[b])
+        assert op.rel_l2(fp32[:steps[b] + 1, b, 0], ref[:, 0]) < 1e-5, b
+        assert op.rel_l2(split[:steps[b] + 1, b, 0], ref[:, 0]) < 1e-4, b
