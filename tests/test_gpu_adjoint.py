@@ -133,3 +133,37 @@ def test_adjoint_all_observables(mode):
     for b, (T, gE) in enumerate(zip(steps, refs)):
         e = np.linalg.norm(gE_gpu[:2 * T + 1, b] - gE) / np.linalg.norm(gE)
         assert e < 1e-4, (b, e)
+
+
+def test_adjoint_full_size_vs_oracle():
+    """The differentiation workload's size (two-band 36 x 36, N = 5184, rank 512, B = 32) with
+    pulses that act inside a 60-step window: field-sample and pulse-parameter gradients of
+    two trajectories against the FP64 oracle adjoint (seeded factors on both sides)."""
+    w = wl.adj_nb2_l36()
+    mdl = om.Model(w.model)
+    U, S, V, d = wl.random_factors(mdl.N, w.rank, seed=29)
+    ctx = tg.Context(w.model, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    rng = np.random.default_rng(31)
+    pulses = [wl.Pulse(E0=float(10 ** rng.uniform(-3.5, -2.5)), omega=float(rng.uniform(0.06, 0.16)),
+                       t0=float(rng.uniform(4, 8)), sigma=float(rng.uniform(2, 3)))
+              for _ in range(w.B)]
+    T, dt = 60, w.dt
+    tg.tdagw_propagate(ctx.h, [tg.make_field(q) for q in pulses], [T] * w.B, dt, tg.LOWRANK,
+                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
+    apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
+    applyH = lambda v: np.conj(d) * v + V @ (S * (U.conj().T @ v))
+    dJ = np.zeros((T + 1, w.B, 3))
+    refs = {}
+    for b in (0, w.B - 1):
+        q = pulses[b]
+        s = op.half_step_samples(q, dt, T)
+        obs, _ = op.rk4(mdl, apply, s, dt, T)
+        _, dJdP = oa.spectral_objective(obs[:, 0], dt, q.omega)
+        dJ[:, b, 0] = dJdP
+        gE = oa.adjoint(mdl, apply, applyH, s, dt, T, (1.0, 0.0), dJdP)
+        refs[b] = (gE, oa.pulse_param_jacobian(q, dt, T).T @ gE)
+    gE_gpu, gp_gpu = tg.tdagw_adjoint(ctx.h, dJ, T, w.B)
+    for b, (gE, gp) in refs.items():
+        assert op.rel_l2(gE_gpu[:, b], gE) < 1e-4, b
+        np.testing.assert_allclose(gp_gpu[b], gp, rtol=1e-4, atol=1e-4 * np.abs(gp).max())

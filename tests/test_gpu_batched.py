@@ -120,3 +120,26 @@ def test_graph_replay_matches_direct_launch(flags):
     again = ctx.propagate_batch(pulses, steps, 0.2, tg.LOWRANK, base)
     np.testing.assert_array_equal(np.nan_to_num(first, nan=7.0), np.nan_to_num(direct, nan=7.0))
     np.testing.assert_array_equal(np.nan_to_num(again, nan=7.0), np.nan_to_num(direct, nan=7.0))
+
+
+def test_sweep_full_size_sampled_vs_oracle():
+    """The field-sweep workload at full size in the benchmark's launch configuration (N =
+    2304, rank 256, 256 trajectories of 500-4000 steps, one launch), FP32 and split-FP16,
+    seeded factors on both sides: the three shortest trajectories over their whole length
+    against the FP64 oracle, and the NaN padding after every trajectory's end."""
+    w = wl.sweep_nb2_l24()
+    mdl = om.Model(w.model)
+    U, S, V, d = wl.random_factors(mdl.N, w.rank, seed=23)
+    ctx = tg.Context(w.model, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    fp32 = ctx.propagate_batch(w.pulses, w.steps, w.dt, tg.LOWRANK)
+    split = ctx.propagate_batch(w.pulses, w.steps, w.dt, tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
+    for b in np.argsort(w.steps)[:3]:
+        T, q = int(w.steps[b]), w.pulses[b]
+        s = op.half_step_samples(q, w.dt, T)
+        ref, _ = op.rk4(mdl, apply, s, w.dt, T, direction=(q.dir_x, q.dir_y))
+        assert op.rel_l2(fp32[:T + 1, b, 0], ref[:, 0]) < 1e-5, b
+        assert op.rel_l2(split[:T + 1, b, 0], ref[:, 0]) < 1e-4, b
+    for b, T in enumerate(w.steps):
+        assert np.all(np.isnan(fp32[T + 1:, b])) and np.all(np.isnan(split[T + 1:, b]))
