@@ -224,6 +224,24 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
         : "memory");
 }
+#ifndef TDAGW_TC_EVICT_FIRST
+#define TDAGW_TC_EVICT_FIRST 1  // factor tiles are streamed with an L2 evict-first policy
+#endif
+// bulk copy with an L2 cache policy (factor tiles: read once per stage, should not displace
+// the reused state, partials and S o Y tiles)
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ void workers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
 }
@@ -463,8 +481,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         return poll ? mb_wait<true>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget)
                     : mb_wait<TDAGW_TC_WORKER_POLL != 0>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
     };
-    // producer: one tile of chunk gch into the next ring slot
-    auto issue = [&](const unsigned char* src) {
+    const uint64_t ef_policy = TDAGW_TC_EVICT_FIRST ? evict_first_policy() : 0ull;
+    // producer: one tile of chunk gch into the next ring slot (factor tiles may carry an
+    // evict-first L2 policy)
+    auto issue = [&](const unsigned char* src, bool factor) {
         if (*vabort) return;
         const uint32_t slot = ppos % kRing;
         if (!chunk_done(slot_ch[slot], true)) {
@@ -473,7 +493,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         }
         slot_ch[slot] = gch;
         mb_expect_tx(full + slot, kTile);
-        bulk_load(ring + slot * kTile, src, kTile, full + slot);
+        if (TDAGW_TC_EVICT_FIRST && factor)
+            bulk_load_hint(ring + slot * kTile, src, kTile, full + slot, ef_policy);
+        else
+            bulk_load(ring + slot * kTile, src, kTile, full + slot);
         ++ppos;
     };
     // MMA thread: wait for the next tile; returns its shared-memory address (0 on failure)
@@ -508,7 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     const ItemA it = item_a(a, q, item);
                     for (int c = it.c0; c < it.c1; ++c, ++gch) {
                         TC_W_BEGIN(p0);
-                        for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile);
+                        for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile, true);
                         TC_W_END(p0, 4);
                     }
                 }
@@ -753,8 +776,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     const int tcnt = min(a.tpi, a.Nt - t0);
                     for (int c = 0; c < a.nchU; ++c, ++gch) {
                         TC_W_BEGIN(p1);
-                        for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile);
-                        issue(a.tY + ((int64_t)g * a.nchU + c) * kTile);
+                        for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile, true);
+                        issue(a.tY + ((int64_t)g * a.nchU + c) * kTile, false);
                         TC_W_END(p1, 4);
                     }
                 }

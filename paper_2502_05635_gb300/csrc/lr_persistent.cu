@@ -108,6 +108,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
         }
     }
 }
+#ifndef TDAGW_LR_EVICT_FIRST
+#define TDAGW_LR_EVICT_FIRST 1  // factor rows streamed with an L2 evict-first policy (read once per stage)
+#endif
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(bar)), "l"(policy)
+        : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -243,6 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
             RingPos pos{0, 0u};
             uint64_t issued = 0;
             bool ok = true;
+            uint64_t policy = 0;
+            if (TDAGW_LR_EVICT_FIRST) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
 
             for (int n = 0; n < a.T && ok; ++n)
                 for (int st = 0; st < 4 && ok; ++st)
@@ -258,8 +271,12 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                             const int nr = min(rps, nrows - r0);
                             const uint32_t bytes = (uint32_t)nr * ldu * 8u;
                             mbar_expect_tx(full + pos.slot, bytes);
-                            bulk_g2s(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
-                                     bytes, full + pos.slot);
+                            if (TDAGW_LR_EVICT_FIRST)
+                                bulk_g2s_hint(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
+                                              bytes, full + pos.slot, policy);
+                            else
+                                bulk_g2s(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ldu,
+                                         bytes, full + pos.slot);
                             ++issued;
                             pos.advance(1, ns);
                         }
