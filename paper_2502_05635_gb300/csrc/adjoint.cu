@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBThreads, 1) adjoint_kernel(AdjArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     float2* sA = sm;
     float2* sB = sA + kChunk * kLdA;
-    double* sred = reinterpret_cast<double*>(sB + kChunk * kTileB);
+    double* sred = reinterpret_cast<double*>(sA + kGemmSmem);
     __shared__ int abort_s;
     const BatchArgs& m = a.b;
     const int tid = threadIdx.x;
@@ -329,7 +329,7 @@ void adjoint_batched(Ctx& c, const double* dJdobs, double* dJdE, double* dJdpara
     aa.dJ = ddj.as<double>();
     aa.red2 = red2.as<double>();
     aa.gE = gE.as<double>();
-    const size_t smem = (size_t)kChunk * kLdA * sizeof(float2) + (size_t)kChunk * kTileB * sizeof(float2) +
+    const size_t smem = (size_t)kGemmSmem * sizeof(float2) +
                         (size_t)(kBThreads / kTileB) * kTileB * 3 * sizeof(double);
     const void* ffn = st.fwd_fn;
     const void* bfn = h.Nb == 2 ? (const void*)adjoint_kernel<2> : (const void*)adjoint_kernel<4>;

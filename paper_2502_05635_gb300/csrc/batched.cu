@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     float2* sA = sm;                       // kChunk x kLdA
     float2* sB = sA + kChunk * kLdA;       // kChunk x 32
-    double* sred = reinterpret_cast<double*>(sB + kChunk * kTileB);  // 16 x kTileB x 3
+    double* sred = reinterpret_cast<double*>(sA + kGemmSmem);  // 16 x kTileB x 3
     __shared__ int abort_s;
     const int tid = threadIdx.x;
     const int rg = blockIdx.x % a.Rg, tg = blockIdx.x / a.Rg;
@@ -467,7 +467,7 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     int dev = 0, nsm = 0;
     TDAGW_CUDA(cudaGetDevice(&dev));
     TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = (size_t)kChunk * kLdA * sizeof(float2) + (size_t)kChunk * kTileB * sizeof(float2) +
+    const size_t smem = (size_t)kGemmSmem * sizeof(float2) +
                         (size_t)(kBThreads / kTileB) * kTileB * 3 * sizeof(double);
     const void* fn = h.Nb == 2 ? (const void*)batched_kernel<2> : (const void*)batched_kernel<4>;
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -12,7 +12,11 @@ namespace batched {
 constexpr int kBThreads = 512;
 constexpr int kTileB = 32;      // trajectories per CTA block (max)
 constexpr int kChunk = 16;      // reduction-dimension chunk staged in shared memory
-constexpr int kLdA = 258;       // padded row of the staged A chunk (float2), 16-B aligned
+constexpr int kLdA = 272;       // staged A chunk row (float2): 256 columns + room for the
+                                // padded per-slice layouts of a split reduction
+constexpr int kKSplitMax = 4;   // reduction-dimension split of block_gemm for small M
+// shared memory of block_gemm (float2): staged A chunk, then one B chunk per slice
+constexpr int kGemmSmem = kChunk * kLdA + kKSplitMax * kChunk * kTileB;
 
 struct BatchArgs {
     // factors / kernel
@@ -101,59 +105,73 @@ __device__ __forceinline__ void group_range(int Bact, int Tg, int tg, int& b0, i
 
 // C[m][b] (+)= sum_q opA(q, m) Bm[q][b] for m in [0, M), b in [0, nb) (nb <= 32),
 // q in [0, Q).  opA(q, m) = conj(A[q lda + m]) (TRANS: A is Q x M, rows q) or
-// A[m lda + q] (NN: A is M x Q, rows m).  Bm rows q at Bm + q ldb.  Output accumulated in
-// registers: thread (ty, tx) owns rows m = 4 ty + {0..3} (+ 256 per pass) and columns
-// b = 4 tx + {0..3}; 64 x 8 threads cover 256 x 32 outputs per pass.
-template <bool TRANS>
-static __device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int M, int Q,
+// A[m lda + q] (NN: A is M x Q, rows m).  Bm rows q at Bm + q ldb.  Outputs accumulate in
+// registers, 4 x 4 complex per thread (8 column groups x row groups).  For small M (a
+// CTA's few rows) the reduction dimension is split over ks = 2 or 4 thread slices, each
+// covering 256 / ks rows with its own staged chunk; the slices' partial tiles are added in
+// fixed slice order through the (then idle) staging memory, so results are deterministic.
+// sA: kChunk x kLdA float2 followed by sB: kKSplitMax x kChunk x kTileB float2 (contiguous).
+template <bool TRANS, int LKS>
+static __device__ void block_gemm_split(const float2* __restrict__ A, int64_t lda, int M, int Q,
                            const float2* __restrict__ Bm, int64_t ldb, int nb,
                            float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
                            const float2* __restrict__ diag, const float2* __restrict__ xd,
                            float2* sA, float2* sB) {
     const int tid = threadIdx.x;
-    const int tx = tid % 8, ty = tid / 8;  // 8 column groups of 4, 64 row groups of 4
-    for (int m0 = 0; m0 < M; m0 += 256) {
+    constexpr int lks = LKS;                   // log2 of the split (compile time: constant
+    constexpr int ks = 1 << lks;               // shared-memory offsets in the inner loop)
+    constexpr int lmt = 8 - lks;               // log2 of the rows per pass
+    constexpr int Mt = 1 << lmt;
+    constexpr int ng = kBThreads >> lks;       // threads per slice
+    const int slice = tid / ng, tl = tid % ng;
+    const int tx = tl % 8, ty = tl / 8;        // 8 column groups of 4, 64 / ks row groups of 4
+    constexpr int lds = Mt + 2;                // staged row of one slice (even: float4 reads)
+    float2* sAs = sA + slice * kChunk * lds;
+    float2* sBs = sB + slice * kChunk * kTileB;
+    for (int m0 = 0; m0 < M; m0 += Mt) {
         float2 c[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) c[u][v] = make_float2(0.f, 0.f);
-        const int mrows = min(256, M - m0);
-        for (int q0 = 0; q0 < Q; q0 += kChunk) {
-            const int qn = min(kChunk, Q - q0);
-            // stage A chunk as sA[q][m] (kChunk x 256, padded rows) and B chunk as
-            // sB[q][b] (kChunk x 32); global reads run along contiguous memory
+        const int mrows = min(Mt, M - m0);
+        for (int q0 = 0; q0 < Q; q0 += ks * kChunk) {
+            // stage ks chunks (slice s: q in [q0 + s kChunk, q0 + (s + 1) kChunk)); global
+            // reads run along contiguous memory
             for (int e = tid; e < kChunk * 256; e += kBThreads) {
+                const int s = e >> (lmt + 4), e2 = e & ((kChunk << lmt) - 1);
                 int q, m;
                 if (TRANS) {  // A rows are q: consecutive threads read consecutive m
-                    q = e / 256;
-                    m = e % 256;
+                    q = e2 >> lmt;
+                    m = e2 & (Mt - 1);
                 } else {      // A rows are m: consecutive threads read consecutive q
-                    m = e / kChunk;
-                    q = e % kChunk;
+                    m = e2 >> 4;
+                    q = e2 & (kChunk - 1);
                 }
+                const int qg = q0 + s * kChunk + q;
                 float2 v = make_float2(0.f, 0.f);
-                if (q < qn && m < mrows) {
+                if (qg < Q && m < mrows) {
                     if (TRANS) {
-                        v = __ldcg(A + (int64_t)(q0 + q) * lda + m0 + m);
+                        v = __ldcg(A + (int64_t)qg * lda + m0 + m);
                         v.y = -v.y;
                     } else {
-                        v = __ldcg(A + (int64_t)(m0 + m) * lda + q0 + q);
+                        v = __ldcg(A + (int64_t)(m0 + m) * lda + qg);
                     }
                 }
-                sA[q * kLdA + m] = v;
+                sA[(s * kChunk + q) * lds + m] = v;
             }
-            for (int e = tid; e < kChunk * kTileB; e += kBThreads) {
-                const int q = e / kTileB, b = e % kTileB;
-                sB[e] = (q < qn && b < nb) ? __ldcg(Bm + (int64_t)(q0 + q) * ldb + b) : make_float2(0.f, 0.f);
+            for (int e = tid; e < (kChunk * kTileB << lks); e += kBThreads) {
+                const int s = e / (kChunk * kTileB), q = (e / kTileB) % kChunk, b = e % kTileB;
+                const int qg = q0 + s * kChunk + q;
+                sB[e] = (qg < Q && b < nb) ? __ldcg(Bm + (int64_t)qg * ldb + b) : make_float2(0.f, 0.f);
             }
             __syncthreads();
 #pragma unroll 4
             for (int q = 0; q < kChunk; ++q) {
-                const float4 a01 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty);
-                const float4 a23 = *reinterpret_cast<const float4*>(sA + q * kLdA + 4 * ty + 2);
-                const float4 b01 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx);
-                const float4 b23 = *reinterpret_cast<const float4*>(sB + q * kTileB + 4 * tx + 2);
+                const float4 a01 = *reinterpret_cast<const float4*>(sAs + q * lds + 4 * ty);
+                const float4 a23 = *reinterpret_cast<const float4*>(sAs + q * lds + 4 * ty + 2);
+                const float4 b01 = *reinterpret_cast<const float4*>(sBs + q * kTileB + 4 * tx);
+                const float4 b23 = *reinterpret_cast<const float4*>(sBs + q * kTileB + 4 * tx + 2);
                 const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
                                       make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
                 const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
@@ -165,20 +183,55 @@ static __device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int
             }
             __syncthreads();
         }
+        if (ks > 1) {
+            // partial tiles of slices 1..ks-1 -> staging memory; slice 0 adds them in order
+            float2* red = sA;
+            if (slice > 0)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int m = m0 + 4 * ty + u;
-            if (m >= M) continue;
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int b = 4 * tx + v;
-                if (b >= nb) continue;
-                float2 r = c[u][v];
-                if (accumulate_diag) r = cfma(diag[m], __ldcg(xd + (int64_t)m * ldb + b), r);
-                out[(int64_t)m * ldo + b] = r;
-            }
+                    for (int v = 0; v < 4; ++v)
+                        red[((slice - 1) * Mt + 4 * ty + u) * kTileB + 4 * tx + v] = c[u][v];
+            __syncthreads();
+            if (slice == 0)
+                for (int s = 1; s < ks; ++s)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            c[u][v] = cadd(c[u][v], red[((s - 1) * Mt + 4 * ty + u) * kTileB + 4 * tx + v]);
         }
+        if (slice == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int m = m0 + 4 * ty + u;
+                if (4 * ty + u >= mrows) continue;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int b = 4 * tx + v;
+                    if (b >= nb) continue;
+                    float2 r = c[u][v];
+                    if (accumulate_diag) r = cfma(diag[m], __ldcg(xd + (int64_t)m * ldb + b), r);
+                    out[(int64_t)m * ldo + b] = r;
+                }
+            }
+        if (ks > 1) __syncthreads();  // staging memory is reused by the next pass
     }
+}
+
+template <bool TRANS>
+static __device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int M, int Q,
+                           const float2* __restrict__ Bm, int64_t ldb, int nb,
+                           float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
+                           const float2* __restrict__ diag, const float2* __restrict__ xd,
+                           float2* sA, float2* sB) {
+    static_assert(kKSplitMax == 4, "split variants below");
+    if (4 * M <= 256)
+        block_gemm_split<TRANS, 2>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
+    else if (2 * M <= 256)
+        block_gemm_split<TRANS, 1>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
+    else
+        block_gemm_split<TRANS, 0>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
 }
 
 
