@@ -62,6 +62,13 @@ constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warp
 constexpr int kRing = TDAGW_TC_RING;       // ring slots of one tile each
 constexpr int kBBuf = TDAGW_TC_BBUF;       // built B blocks in flight (phase A)
 static_assert(kRing + kBBuf <= 13, "ring and B buffers must fit in shared memory");
+#ifndef TDAGW_TC_ATILES
+#define TDAGW_TC_ATILES 4
+#endif
+// 128-row V^H tiles per phase A item (2: one accumulator buffer; 4: both buffers, i.e. two
+// accumulator uses per item)
+constexpr int kAMc = TDAGW_TC_ATILES;
+static_assert(kAMc == 2 || kAMc == 4, "phase A items hold 2 or 4 V^H tiles");
 constexpr int kCmb = 16;                   // chunk-completion barriers (ring); every wait on
                                            // one targets a chunk < kCmb chunks behind the
                                            // MMA thread's next chunk, so parities cannot alias
@@ -387,14 +394,14 @@ __host__ __device__ __forceinline__ int group_count(int Bact, int Nt, int nctas)
     return max(g_min, g_fill);
 }
 struct Groups {
-    int G, MGn, KS;  // phase A: trajectory groups, pairs of V^H tiles, K-ranges
+    int G, MGn, KS;  // phase A: trajectory groups, groups of kAMc V^H tiles, K-ranges
     int GC;          // phase C (and B): trajectory groups
 };
 __device__ __forceinline__ Groups stage_groups(const TcArgs& a, int Bact) {
     Groups q;
     q.G = group_count(Bact, a.Nt, (int)gridDim.x);
     q.GC = group_count(Bact, a.Ntp, (int)gridDim.x);
-    q.MGn = (a.Mt + 1) / 2;
+    q.MGn = (a.Mt + kAMc - 1) / kAMc;
     q.KS = max(1, min((int)gridDim.x / max(1, q.G * q.MGn), a.nchV));
     return q;
 }
@@ -407,8 +414,8 @@ __device__ __forceinline__ ItemA item_a(const TcArgs& a, const Groups& q, int it
     it.g = item % q.G;
     const int mg = (item / q.G) % q.MGn;
     it.ks = item / (q.G * q.MGn);
-    it.m0 = 2 * mg;
-    it.mc = min(2, a.Mt - it.m0);
+    it.m0 = kAMc * mg;
+    it.mc = min(kAMc, a.Mt - it.m0);
     it.c0 = (int)((int64_t)it.ks * a.nchV / q.KS);
     it.c1 = (int)((int64_t)(it.ks + 1) * a.nchV / q.KS);
     return it;
@@ -541,14 +548,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     int b0, b1;
                     group_range(Bact, q.G, it.g, b0, b1);
                     const int nbp = (b1 - b0 + 7) & ~7;
-                    const uint32_t ab = acnt & 1u;
+                    const int nuse = (it.mc + 1) / 2;  // accumulator uses (two tiles each)
                     TC_W_BEGIN(a0);
-                    if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    for (int u = 0; u < nuse; ++u) {
+                        const uint32_t k = acnt + u;
+                        if (*vabort || !mb_wait<true>(acce + (k & 1u), ((k >> 1) & 1u) ^ 1u, vabort, budget)) fail();
+                    }
                     TC_W_END(a0, 2);
                     tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
                     for (int c = it.c0; c < it.c1 && !*vabort; ++c) {
-                        uint32_t ta[2] = {0u, 0u};
+                        uint32_t ta[kAMc] = {};
                         TC_W_BEGIN(t0);
                         for (int ml = 0; ml < it.mc; ++ml) ta[ml] = next_tile();
                         TC_W_END(t0, 0);
@@ -563,16 +573,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         const uint32_t baddr = tc::smem_u32(xbuf + (bu % kBBuf) * kTile);
                         TC_W_BEGIN(m0);
                         for (int ml = 0; ml < it.mc; ++ml)
-                            mma_tile(tm + ab * kAccCols + ml * 128, ta[ml], baddr, idesc, c == it.c0);
+                            mma_tile(tm + ((acnt + ml / 2) & 1u) * kAccCols + (ml % 2) * 128, ta[ml], baddr, idesc,
+                                     c == it.c0);
                         TC_TRACE_A(true, c - it.c0, 1);
                         end_chunk();
                         TC_W_END(m0, 3);
                         ++gch;
                         ++bu;
                     }
-                    tc::mma_commit(accf + ab);
+                    for (int u = 0; u < nuse; ++u) tc::mma_commit(accf + ((acnt + u) & 1u));
                     TC_TRACE_A(true, 63, 2);
-                    ++acnt;
+                    acnt += nuse;
                 }
             } else if (worker) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
@@ -646,8 +657,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     // accumulators -> raw partials P[ks][j][b], 64 rows at a time staged in
                     // the (now idle) B buffers so that the global writes run along
                     // trajectories (coalesced)
-                    const uint32_t ab = acnt & 1u;
-                    if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    const int nuse = (it.mc + 1) / 2;
+                    for (int u = 0; u < nuse; ++u) {
+                        const uint32_t k = acnt + u;
+                        if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + (k & 1u), (k >> 1) & 1u, vabort, budget))
+                            fail();
+                    }
                     TC_TRACE_A(wt == 0, 63, 0);
                     tc::fence_after_sync();
                     float2* stg = reinterpret_cast<float2*>(xbuf);  // 64 rows x 64 float2 (32 KB)
@@ -661,7 +676,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 const int row = 32 * (quarter & 1) + lane;
                                 for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
                                     float v[16];
-                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + ml * 128 + 16 * u, v);
+                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ((acnt + ml / 2) & 1u) * kAccCols +
+                                                      (ml % 2) * 128 + 16 * u,
+                                                  v);
 #pragma unroll
                                     for (int p = 0; p < 8; ++p)
                                         stg[ds_index(row, 8 * u + p)] = make_float2(v[2 * p], v[2 * p + 1]);
@@ -679,9 +696,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     }
                     workers_sync();  // staging reads done before the next item's B blocks
                     tc::fence_before_sync();
-                    mb_arrive(acce + ab);
+                    for (int u = 0; u < nuse; ++u) mb_arrive(acce + ((acnt + u) & 1u));
                     TC_TRACE_A(wt == 0, 63, 1);
-                    ++acnt;
+                    acnt += nuse;
                 }
             }
             TC_TRACE(producer, 1);
