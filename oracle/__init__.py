@@ -15,5 +15,6 @@ function.  Modules:
   kernel     screened interaction W(q), its q=0 cell average, the dense direct kernel,
              the K^diag / K^off split, and an FFT form of K.x (an identity of this kernel)
   lowrank    truncated SVD of K^off, the low-rank apply, R^2 and Eckart-Young error
+  channel    channel-wise truncated SVD (dense diagonal channels) and its apply
   propagate  pulses, the TD-aGW right-hand side, classical RK4, observables
 """

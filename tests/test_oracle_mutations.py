@@ -89,3 +89,35 @@ def test_wrong_W0_breaks_quadrature_pin():
     # slip: average over the disc of radius h instead of the square
     disc = (2 * np.pi / (A * p.r0)) * 2 * np.pi * np.log1p(p.r0 * h) / (np.pi * h * h)
     assert abs(disc - brute) / brute > 1e-3
+
+
+def test_swapped_channel_breaks_full_rank_reconstruction(monkeypatch):
+    """Slip: the channel block read with p and q exchanged (rows of pair q, columns of pair
+    p).  The full-rank channel-wise kernel then differs from K."""
+    from oracle import channel as oc
+    m = om.Model(wl.small_model(4, 1))
+    K = ok.dense_kernel(m)
+    P = m.Nb * m.Nb
+    monkeypatch.setattr(oc, "channel_block", lambda A, Nb, p, q: A[q::P, p::P].copy())
+    D, U, S, V = oc.channel_svd(K, m.Nb, m.Nk)
+    assert np.abs(oc.assemble(D, U, S, V) - K).max() > 1e-6 * np.abs(K).max()
+
+
+def test_unconjugated_v_breaks_channel_apply_pin():
+    """Slip: V^T instead of V^H in the channel apply; the dense kernel of the same factors
+    disagrees with it."""
+    from oracle import channel as oc
+    m = om.Model(wl.small_model(4, 1))
+    K = ok.dense_kernel(m)
+    D, U, S, V = oc.channel_svd(K, m.Nb, 6)
+    x = wl.random_state(m.N, 4)
+    P, Nk = m.Nb * m.Nb, m.Nk
+    xs = x.reshape(Nk, P)
+    bad = np.zeros((Nk, P), complex)
+    for p in range(P):
+        bad[:, p] = D[p] @ xs[:, p]
+        for q in range(P):
+            if q != p:
+                bad[:, p] += U[p, q] @ (S[p, q] * (V[p, q].T @ xs[:, q]))
+    good = oc.assemble(D, U, S, V) @ x
+    assert np.abs(bad.reshape(-1) - good).max() > 1e-6 * np.abs(good).max()
