@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--full-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid"], default=None,
+    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid", "channel"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=None, help="step count of the --leg run")
     return ap.parse_args()
@@ -328,6 +328,40 @@ def bench_tc_mid(tg, torch, stream, sh, hbm, steps=20):
             "hbm_frac": gbs / hbm}
 
 
+def bench_channel(tg, torch, stream, sh, hbm, steps=1000, cmp_steps=200):
+    """Channel-wise kernel at the mos2 size (four-band 36 x 36, N = 20736): dense diagonal
+    channels and off-diagonal channels truncated to rank 65 by the GPU's randomised channel
+    SVDs, single trajectory, one persistent launch; P(t) against the dense kernel on the
+    same GPU over a prefix."""
+    w = wl.mos2size_channel()
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    t0 = time.perf_counter()
+    tg.tdagw_compress_channels(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    tg.tdagw_sync(ctx.h)
+    setup = time.perf_counter() - t0
+    ranks = tg.tdagw_get_channel_factors(ctx.h, arrays=False)
+    N, Nb, Nk = ctx.N, ctx.Nb, ctx.Nk
+    P = Nb * Nb
+    # bytes streamed per stage: U and V of every channel, the dense diagonal channels
+    per_stage = 8 * (2 * Nk * int(ranks.sum()) + P * Nk * Nk)
+    field = [tg.make_field(w.pulses[0])]
+    ms = _time_propagate(tg, torch, stream, ctx, field, [steps], w.dt, tg.CHANNEL, tg.FLAG_RESET)
+    gbs = 4 * steps * per_stage / (ms * 1e-3) / 1e9
+    tg.tdagw_propagate(ctx.h, field, [cmp_steps], w.dt, tg.CHANNEL, tg.FLAG_RESET)
+    ch = tg.tdagw_observables(ctx.h)
+    tg.tdagw_propagate(ctx.h, field, [cmp_steps], w.dt, tg.FULL, tg.FLAG_RESET)
+    full = tg.tdagw_observables(ctx.h)
+    ctx.close()
+    return {"workload": "mos2size_nb4_l36_channel", "N": N, "rank_off_channels": w.rank,
+            "nonzero_off_channels": int((ranks > 0).sum()), "steps": steps,
+            "value": steps / (ms * 1e-3), "unit": "steps*traj/s", "ms": ms,
+            "bytes_per_stage": per_stage,
+            "roofline": {"bound": "hbm", "kernel": "ch_persistent_kernel", "achieved": gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": gbs / hbm},
+            "p_rel_err_vs_full_gpu": float(np.linalg.norm(ch[:, 0] - full[:, 0]) / np.linalg.norm(full[:, 0])),
+            "steps_compared": cmp_steps, "setup_s": setup}
+
+
 # ---------------------------------------------------------------- our arm -----------
 
 def run_leg(a):
@@ -352,6 +386,8 @@ def run_leg(a):
         out = bench_precision(tg, torch, stream, sh, hbm, *( (n, n, n) if n else ()))
     elif a.leg == "adjoint":
         out = bench_adjoint(tg, torch, stream, sh, n or 1000)
+    elif a.leg == "channel":
+        out = bench_channel(tg, torch, stream, sh, hbm, n or 1000)
     else:
         out = bench_tc_mid(tg, torch, stream, sh, hbm, n or 20)
     print(json.dumps({"leg": a.leg, **out}), flush=True)
@@ -504,6 +540,7 @@ def run_ours(a):
         line["batched_sweep"] = bench_batched(tg, torch, stream, sh, tflops)
         line["precision_study"] = bench_precision(tg, torch, stream, sh, hbm)
         line["adjoint"] = bench_adjoint(tg, torch, stream, sh)
+        line["channel_wise"] = bench_channel(tg, torch, stream, sh, hbm)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -46,7 +46,7 @@ enum {
 };
 
 enum { TDAGW_C64 = 0, TDAGW_C128 = 1 };
-enum { TDAGW_FULL = 0, TDAGW_LOWRANK = 1 };
+enum { TDAGW_FULL = 0, TDAGW_LOWRANK = 1, TDAGW_CHANNEL = 2 };
 enum {
     TDAGW_FIELD_GAUSS_COS = 0,    /* E0 exp(-(t-t0)^2 / (2 sigma^2)) cos(omega t)          */
     TDAGW_FIELD_CONST = 1,        /* E0                                                     */
@@ -58,8 +58,8 @@ enum {
     TDAGW_FLAG_RESET = 1,         /* start from drho = 0 and t = 0 (else continue)          */
     TDAGW_FLAG_NO_GRAPH = 2,      /* launch stage by stage instead of replaying a CUDA graph */
     TDAGW_FLAG_NO_KAHAN = 4,      /* plain (uncompensated) RK4 accumulation                 */
-    TDAGW_FLAG_STAGEWISE = 8,     /* low-rank c64: stage-wise kernels instead of the
-                                     persistent single-launch kernel                        */
+    TDAGW_FLAG_STAGEWISE = 8,     /* low-rank or channel-wise c64: stage-wise kernels
+                                     instead of the persistent single-launch kernel         */
     TDAGW_FLAG_TEST_TIMEOUT = 16, /* fault-injection hook for tests: the persistent kernel's
                                      grid barrier waits for one block that does not exist,
                                      every wait runs out a 20 ms budget and the call ends
@@ -144,8 +144,48 @@ int tdagw_set_factors(tdagw_ctx* ctx, int rank, const double* U, const double* S
  * *rank receives the rank; any array pointer may be NULL. */
 int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V, double* diag);
 
-/* One kernel application y = K x (mode FULL) or y = K^diag x + U (S (V^H x)) (LOWRANK)
- * on device vectors of N elements in the context dtype. */
+/* Channel-wise compression (Sec. "SVD analysis of electron-hole kernel", Eq.
+ * svd-channel-wise).  With pair indices p = n1 Nb + n2 and q = n3 Nb + n4 (P = Nb^2 pairs),
+ * channel p -> q is the Nk x Nk block K^pq[k, k'] = K[k P + p, k' P + q].  Diagonal channels
+ * (p = q, close to full rank) are kept exact as dense blocks; every off-diagonal channel holds
+ * its own truncated SVD K^pq ~ U^pq diag(S^pq) (V^pq)^H of rank z_pq (0 <= z_pq <= Nk).
+ * Mode TDAGW_CHANNEL of tdagw_apply / tdagw_propagate applies
+ *   dSigma[k P + p] = sum_k' K^pp[k, k'] x[k' P + p] + sum_{q != p} U^pq (S^pq o ((V^pq)^H x_q)),
+ * x_q[k'] = x[k' P + q].  Channel factors are independent of the low-rank factors above.
+ *
+ * tdagw_compress_channels: randomised SVD of every off-diagonal channel p < q of the built
+ * kernel (Gaussian range finder with `oversample` extra columns, at most Nk in all, and
+ * `power_iters` power iterations, test matrices from `seed`; FP64 orthogonalisation; the
+ * core from the eigen-decomposition of B B^H, B = Q^H K^pq), keeping of the `rank` largest
+ * singular values those above rel_tol times the channel's largest (a vanishing channel gets
+ * rank 0); channel q -> p is the conjugate transpose of p -> q (K is Hermitian).  Diagonal
+ * channels are copied from the kernel.  Replaces any channel factors present.  Errors:
+ * INVALID_ARG for rank outside [0, Nk], oversample < 0, power_iters < 0 or rel_tol < 0;
+ * NOT_BUILT before tdagw_build_kernel. */
+int tdagw_compress_channels(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
+                            uint64_t seed, double rel_tol);
+
+/* Install channel factors from the host (c128 / double):
+ *   ranks  P x P ints, z_pq at p P + q (diagonal entries ignored); NULL: every
+ *          off-diagonal channel has rank `rank`.  0 <= z_pq <= rank <= Nk.
+ *   U, V   P x P x Nk x rank: U^pq[k, j] at ((p P + q) Nk + k) rank + j (columns j >= z_pq
+ *          and the diagonal channels are ignored); may be NULL when rank = 0.
+ *   S      P x P x rank, S^pq[j] at (p P + q) rank + j.
+ *   D      P x Nk x Nk, K^pp[k, k'] at (p Nk + k) Nk + k'; NULL: taken from the built kernel.
+ * Errors: INVALID_ARG for ranks out of range or a NULL factor array with rank > 0;
+ * NOT_BUILT when D is NULL before tdagw_build_kernel. */
+int tdagw_set_channel_factors(tdagw_ctx* ctx, int rank, const int* ranks, const double* U,
+                              const double* S, const double* V, const double* D);
+
+/* Copy the channel factors to the host in the layout of tdagw_set_channel_factors with
+ * rank = the largest z_pq (*rank), zero beyond each channel's own rank (ranks: P x P,
+ * 0 on the diagonal).  Any pointer may be NULL.  Synchronises.  Errors: NO_FACTORS if no
+ * channel factors are installed and an array is requested. */
+int tdagw_get_channel_factors(tdagw_ctx* ctx, int* rank, int* ranks, double* U, double* S,
+                              double* V, double* D);
+
+/* One kernel application y = K x (mode FULL), y = K^diag x + U (S (V^H x)) (LOWRANK) or the
+ * channel-wise form above (CHANNEL) on device vectors of N elements in the context dtype. */
 int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
 
 /* Propagate B trajectories by classical RK4 (four stages per step, dSigma re-evaluated at
@@ -160,10 +200,15 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * With TDAGW_FLAG_SPLIT_F16 (LOWRANK, complex64, any B) the two products of Eq. svd_acc run
  * on the tensor cores with the factors split into FP16 hi + lo pairs and FP32
  * accumulation; P(t) then agrees with the FP32 path to about 1e-6 relative.
- * Errors: NO_FACTORS for LOWRANK without factors; NOT_BUILT before tdagw_build_kernel;
+ * Mode CHANNEL (channel-wise factors) runs the single-trajectory path only (B = 1, no
+ * TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16): one persistent launch for complex64 when
+ * every input pair's channels hold at most 2048 columns in all, else stage-wise kernels.
+ * Errors: NO_FACTORS for LOWRANK or CHANNEL without the matching factors; NOT_BUILT before
+ * tdagw_build_kernel;
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
- * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT; INVALID_ARG for TDAGW_FLAG_SPLIT_F16
- * with FULL. */
+ * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT, and for CHANNEL with B > 1,
+ * TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16; INVALID_ARG for TDAGW_FLAG_SPLIT_F16 with
+ * FULL. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
 

@@ -25,11 +25,27 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg
 
+from oracle import kernel as ok
+
 
 def channel_block(K: np.ndarray, Nb: int, p: int, q: int) -> np.ndarray:
     """K^ch for ch = p -> q: rows k Nb^2 + p, columns k' Nb^2 + q (Nk x Nk copy)."""
     P = Nb * Nb
     return K[p::P, q::P].copy()
+
+
+def channel_block_from_model(model, p: int, q: int) -> np.ndarray:
+    """K^pq straight from the kernel's entry formula, without the dense N x N kernel (for
+    large grids): with p = (n1, n2), q = (n3, n4) and O_ab[k, k'] = (U_k^+ U_k')_{ab},
+        K^pq[k, k'] = -W(k - k') O_{n1 n3}[k, k'] conj(O_{n2 n4}[k, k']),
+    since (U_k'^+ U_k)_{n4 n2} = conj((U_k^+ U_k')_{n2 n4})."""
+    Nb = model.Nb
+    n1, n2 = divmod(p, Nb)
+    n3, n4 = divmod(q, Nb)
+    U = model.U
+    o13 = U[:, :, n1].conj() @ U[:, :, n3].T
+    o24 = U[:, :, n2].conj() @ U[:, :, n4].T
+    return -ok.W_matrix(model.p) * o13 * o24.conj()
 
 
 def channel_svd(K: np.ndarray, Nb: int, rank: int):

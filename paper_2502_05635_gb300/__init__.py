@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtdagw.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_BUILT, ERR_NO_FACTORS, ERR_TIMEOUT, \
     ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
-FULL, LOWRANK = 0, 1
+FULL, LOWRANK, CHANNEL = 0, 1, 2
 FIELD_GAUSS_COS, FIELD_CONST, FIELD_SIN2_SIN, FIELD_TABLE = 0, 1, 2, 3
 FLAG_RESET, FLAG_NO_GRAPH, FLAG_NO_KAHAN, FLAG_STAGEWISE, FLAG_TEST_TIMEOUT, FLAG_CHECKPOINT, \
     FLAG_SPLIT_F16 = 1, 2, 4, 8, 16, 32, 64
@@ -56,6 +56,9 @@ _SIGS = {
     "tdagw_compress_svd": [_P, ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, ct.c_int],
     "tdagw_set_factors": [_P, ct.c_int, _D, _D, _D, _D],
     "tdagw_get_factors": [_P, ct.POINTER(ct.c_int), _D, _D, _D, _D],
+    "tdagw_compress_channels": [_P, ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, ct.c_double],
+    "tdagw_set_channel_factors": [_P, ct.c_int, ct.POINTER(ct.c_int), _D, _D, _D, _D],
+    "tdagw_get_channel_factors": [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), _D, _D, _D, _D],
     "tdagw_apply": [_P, ct.c_int, _P, _P],
     "tdagw_propagate": [_P, ct.POINTER(Field), ct.c_int, ct.POINTER(ct.c_int), ct.c_double,
                         ct.c_int, ct.c_int],
@@ -170,6 +173,48 @@ def tdagw_get_factors(ctx: int):
     d = np.empty(N, np.complex128)
     _check(lib().tdagw_get_factors(_P(ctx), None, _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
     return U, S, V, d
+
+
+def tdagw_compress_channels(ctx: int, rank: int, oversample: int = 64, power_iters: int = 2,
+                            seed: int = 1, rel_tol: float = 0.0):
+    _check(lib().tdagw_compress_channels(_P(ctx), rank, oversample, power_iters, seed, rel_tol))
+
+
+def tdagw_set_channel_factors(ctx: int, U, S, V, D=None, ranks=None):
+    """U, V: (P, P, Nk, r) complex; S: (P, P, r); D: (P, Nk, Nk) or None; ranks: (P, P)
+    ints or None (every off-diagonal channel rank r)."""
+    U = np.ascontiguousarray(U, np.complex128)
+    V = np.ascontiguousarray(V, np.complex128)
+    S = np.ascontiguousarray(S, np.float64)
+    d = None if D is None else np.ascontiguousarray(D, np.complex128)
+    rk = None
+    if ranks is not None:
+        ra = np.ascontiguousarray(ranks, np.int32)
+        rk = ra.ctypes.data_as(ct.POINTER(ct.c_int))
+    _check(lib().tdagw_set_channel_factors(_P(ctx), U.shape[-1], rk, _dptr(U), _dptr(S), _dptr(V),
+                                           _dptr(d)))
+
+
+def tdagw_get_channel_factors(ctx: int, arrays: bool = True):
+    """(ranks (P, P), U, S, V, D) in the layout of tdagw_set_channel_factors; with
+    arrays=False only the ranks."""
+    _, Nb, Nk = tdagw_model_info(ctx)
+    P = Nb * Nb
+    r = ct.c_int()
+    ranks = np.zeros((P, P), np.int32)
+    if not arrays:
+        _check(lib().tdagw_get_channel_factors(_P(ctx), ct.byref(r), ranks.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                               None, None, None, None))
+        return ranks
+    _check(lib().tdagw_get_channel_factors(_P(ctx), ct.byref(r), None, None, None, None, None))
+    r = r.value
+    U = np.empty((P, P, Nk, r), np.complex128)
+    V = np.empty((P, P, Nk, r), np.complex128)
+    S = np.empty((P, P, r))
+    D = np.empty((P, Nk, Nk), np.complex128)
+    _check(lib().tdagw_get_channel_factors(_P(ctx), None, ranks.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                           _dptr(U), _dptr(S), _dptr(V), _dptr(D)))
+    return ranks, U, S, V, D
 
 
 def tdagw_apply(ctx: int, mode: int, x, y):

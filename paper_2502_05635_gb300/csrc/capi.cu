@@ -193,12 +193,14 @@ template <typename R> void get_factors(Ctx& c, double* U, double* S, double* V, 
     }
 }
 
-// y = K x (full) or diag o x + U (S o (V^H x)) (low-rank): the kernel contraction of one
-// RK4 stage (Eq. sigma-from-k / Eq. svd_acc).
+// y = K x (full), diag o x + U (S o (V^H x)) (low-rank) or the channel-wise form: the
+// kernel contraction of one RK4 stage (Eq. sigma-from-k / Eq. svd_acc / Eq. svd-channel-wise).
 template <typename R> void apply(Ctx& c, int mode, const void* x, void* y, cudaStream_t s) {
     const int64_t N = c.hm.N;
     if (mode == TDAGW_FULL) {
         launch_gemv<R>(c.K.p, N, N, N, x, y, 1, nullptr, nullptr, s);
+    } else if (mode == TDAGW_CHANNEL) {
+        launch_ch_apply<R>(c, x, y, s);
     } else {
         const int r = c.rank;
         const int64_t ldu = r + (r & 1);
@@ -239,8 +241,12 @@ template <typename R> void propagate(Ctx& c, const tdagw_field& f, int T, double
     const bool kahan = !(flags & TDAGW_FLAG_NO_KAHAN);
     const double dirx = f.dir_x, diry = f.dir_y;
     int done = 0;
+    const bool test_timeout = (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0;
     if (mode == TDAGW_LOWRANK && !(flags & TDAGW_FLAG_STAGEWISE) && T > 0 &&
-        launch_lr_persistent(c, T, dt, dirx, diry, kahan, (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0, s))
+        launch_lr_persistent(c, T, dt, dirx, diry, kahan, test_timeout, s))
+        done = T;
+    if (mode == TDAGW_CHANNEL && !(flags & TDAGW_FLAG_STAGEWISE) && T > 0 &&
+        launch_ch_persistent(c, T, dt, dirx, diry, kahan, test_timeout, s))
         done = T;
     if (!(flags & TDAGW_FLAG_NO_GRAPH) && T - done >= 2) {
         const int G = std::min(T, 32);
@@ -451,12 +457,51 @@ int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V
     });
 }
 
+int tdagw_compress_channels(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
+                            uint64_t seed, double rel_tol) {
+    return guard([&] {
+        TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
+        require_built(ctx->c);
+        TDAGW_REQUIRE(rank >= 0 && rank <= ctx->c.hm.Nk && oversample >= 0 && power_iters >= 0 &&
+                          rel_tol >= 0.0,
+                      TDAGW_ERR_INVALID_ARG, "need 0 <= rank <= Nk, oversample, power_iters, rel_tol >= 0");
+        DISPATCH(ctx, rsvd_channels, ctx->c, rank, oversample, power_iters, seed, rel_tol);
+    });
+}
+
+int tdagw_set_channel_factors(tdagw_ctx* ctx, int rank, const int* ranks, const double* U,
+                              const double* S, const double* V, const double* D) {
+    return guard([&] {
+        TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
+        TDAGW_REQUIRE(rank >= 0 && rank <= ctx->c.hm.Nk, TDAGW_ERR_INVALID_ARG, "need 0 <= rank <= Nk");
+        TDAGW_REQUIRE(rank == 0 || (U && S && V), TDAGW_ERR_INVALID_ARG, "NULL factor array");
+        if (!D) require_built(ctx->c);
+        DISPATCH(ctx, set_channel_factors, ctx->c, rank, ranks, U, S, V, D);
+    });
+}
+
+int tdagw_get_channel_factors(tdagw_ctx* ctx, int* rank, int* ranks, double* U, double* S, double* V,
+                              double* D) {
+    return guard([&] {
+        TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
+        const bool any = ranks || U || S || V || D;
+        if (!ctx->c.ch.valid) {
+            if (rank) *rank = 0;
+            TDAGW_REQUIRE(!any, TDAGW_ERR_NO_FACTORS, "no channel factors installed");
+            return;
+        }
+        DISPATCH(ctx, get_channel_factors, ctx->c, rank, ranks, U, S, V, D);
+    });
+}
+
 int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y) {
     return guard([&] {
         TDAGW_REQUIRE(ctx && x && y, TDAGW_ERR_INVALID_ARG, "NULL argument");
         require_built(ctx->c);
-        TDAGW_REQUIRE(mode == TDAGW_FULL || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG, "bad mode");
-        TDAGW_REQUIRE(mode == TDAGW_FULL || ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS, "no factors");
+        TDAGW_REQUIRE(mode == TDAGW_FULL || mode == TDAGW_LOWRANK || mode == TDAGW_CHANNEL,
+                      TDAGW_ERR_INVALID_ARG, "bad mode");
+        TDAGW_REQUIRE(mode != TDAGW_LOWRANK || ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS, "no factors");
+        TDAGW_REQUIRE(mode != TDAGW_CHANNEL || ctx->c.ch.valid, TDAGW_ERR_NO_FACTORS, "no channel factors");
         TDAGW_REQUIRE(((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0), TDAGW_ERR_INVALID_ARG,
                       "x and y must be 16-byte aligned");
         TDAGW_REQUIRE(x != y, TDAGW_ERR_INVALID_ARG, "x and y must not alias");
@@ -473,9 +518,17 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
         for (int b = 0; b < B; ++b)
             TDAGW_REQUIRE(steps[b] >= 0 && steps[b] <= (1 << 26), TDAGW_ERR_INVALID_ARG, "bad step count");
         TDAGW_REQUIRE(dt > 0 && dt < 1e6, TDAGW_ERR_INVALID_ARG, "bad dt");
-        TDAGW_REQUIRE(mode == TDAGW_FULL || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG, "bad mode");
-        TDAGW_REQUIRE(mode == TDAGW_FULL || ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS,
+        TDAGW_REQUIRE(mode == TDAGW_FULL || mode == TDAGW_LOWRANK || mode == TDAGW_CHANNEL,
+                      TDAGW_ERR_INVALID_ARG, "bad mode");
+        TDAGW_REQUIRE(mode != TDAGW_LOWRANK || ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS,
                       "low-rank mode needs factors (tdagw_compress_svd or tdagw_set_factors)");
+        TDAGW_REQUIRE(mode != TDAGW_CHANNEL || ctx->c.ch.valid, TDAGW_ERR_NO_FACTORS,
+                      "channel mode needs channel factors (tdagw_compress_channels or "
+                      "tdagw_set_channel_factors)");
+        TDAGW_REQUIRE(mode != TDAGW_CHANNEL ||
+                          (B == 1 && !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16))),
+                      TDAGW_ERR_UNSUPPORTED,
+                      "channel mode runs one trajectory without checkpoints or split-FP16 factors");
         for (int b = 0; b < B; ++b) {
             const tdagw_field& f = fields[b];
             TDAGW_REQUIRE(f.kind >= 0 && f.kind <= 3, TDAGW_ERR_INVALID_ARG, "bad field kind");

@@ -1,0 +1,411 @@
+// Persistent channel-wise TD-aGW propagation (single trajectory, complex64): one
+// cooperative launch runs all RK4 steps of a call with the kernel in the channel-wise form
+// of Eq. svd-channel-wise (dense diagonal channels, truncated SVDs of the off-diagonal
+// channels).  Per stage:
+//
+//   V pass   for each input pair q:  y_c = sum_{k' of this CTA} conj(V_q[k']) x[k' P + q]
+//   grid barrier; x by pair (Xt[p][k]) from this CTA's rows; S o sum_c y_c (column slice)
+//   grid barrier; U pass  for each output pair p:
+//            dSigma[k P + p] = U_p[k] . [S o y of the channels out of p ; x_p]   (own k)
+//   commutator, RK4 stage update, observables for the same k
+//
+// Each CTA owns a contiguous range of k-points with all their pair elements, so the
+// commutators use only rows it computed and the next V pass needs only its own stage
+// input.  The dense diagonal channels need all of x_p: every CTA publishes its rows of the
+// stage input by pair after the first barrier (when no CTA still reads the previous
+// stage's), and reads x_p after the second.  A producer warp streams the CTA's rows of the
+// 2 P factor segments through a shared-memory ring with 1D bulk copies (L2 evict-first:
+// the factors are read once per stage), sixteen consumer warps compute from shared memory.
+// Every wait is bounded; on expiry the CTA records an error word and returns.
+#include <algorithm>
+
+#include "common.cuh"
+#include "persist.cuh"
+#include "stage.cuh"
+
+namespace tdagw {
+
+namespace {
+
+using namespace persist;
+
+constexpr int kCW = 16;              // consumer warps
+constexpr int kCons = kCW * 32;
+constexpr int kThr = kCons + 32;
+constexpr int kSlotMin = 32768;      // bytes per ring slot (at least one whole row)
+
+struct CHArgs {
+    ChMeta m;
+    const float2* V;
+    const float2* U;
+    const float* S;
+    const int* gidx;
+    StageParams<float> sp;
+    float2* dSw;   // dSigma written by the U pass (sp.dS reads it)
+    float2* part;  // gridDim x stot partial y vectors
+    float2* ytil;  // stot, S o y
+    float2* Xt;    // P x Nk, stage input by pair
+    unsigned long long* bar_count;
+    int* err;
+    int T, nslots, slot_bytes, kmax, zs_len;
+    int extra_arrivals;  // > 0 only for the timeout test: the barrier can never complete
+    unsigned long long wait_ns;
+};
+
+// rows of a segment per ring slot: the largest power of two (<= 64) whose rows fit
+__device__ __forceinline__ int seg_rps(int ld, int slot_bytes) {
+    int r = 1;
+    while (r < 64 && 2 * r * ld * 8 <= slot_bytes) r *= 2;
+    return r;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int P = NB * NB;
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int Nk = a.m.Nk;
+    const int ka = (int)((int64_t)cta * Nk / G), kb = (int)((int64_t)(cta + 1) * Nk / G);
+    const int nk = kb - ka;
+    const int64_t ra = (int64_t)ka * P, rb = (int64_t)kb * P;
+    const int ns = a.nslots;
+
+    unsigned char* ring = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
+    uint64_t* empty = full + ns;
+    float2* zs = reinterpret_cast<float2*>(empty + ns);  // U-pass vector, zs_len
+    float2* upart = zs + a.zs_len;                       // kmax x kCW partial dot products
+    float2* xs = upart + a.kmax * kCW;                   // kmax x P, this CTA's stage input
+    double* wred = reinterpret_cast<double*>(xs + a.kmax * P);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kCW);
+
+    if (tid == 0) {
+        for (int s = 0; s < ns; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kCW);
+        }
+        *abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kCW) {
+        // ------------------------------------------------------------ producer warp
+        if (lane == 0) {
+            RingPos pos{0, 0u};
+            uint64_t issued = 0;
+            bool ok = true;
+            const uint64_t policy = policy_evict_first();
+            for (int n = 0; n < a.T && ok; ++n)
+                for (int st = 0; st < 4 && ok; ++st)
+                    for (int sg = 0; sg < 2 * P && ok; ++sg) {
+                        const bool vseg = sg < P;
+                        const int e = vseg ? sg : sg - P;
+                        const int ld = vseg ? a.m.ldv[e] : a.m.ldw[e];
+                        if (ld == 0) continue;
+                        const float2* base =
+                            (vseg ? a.V + a.m.vbase[e] : a.U + a.m.ubase[e]) + (int64_t)ka * ld;
+                        const int rps = seg_rps(ld, a.slot_bytes);
+                        for (int r0 = 0; r0 < nk; r0 += rps) {
+                            if (issued >= (uint64_t)ns &&
+                                !mbar_wait(empty + pos.slot, pos.phase ^ 1u, abort_s, a.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            const int nr = min(rps, nk - r0);
+                            const uint32_t bytes = (uint32_t)nr * ld * 8u;
+                            mbar_expect_tx(full + pos.slot, bytes);
+                            bulk_g2s_hint(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ld, bytes,
+                                          full + pos.slot, policy);
+                            ++issued;
+                            pos.advance(1, ns);
+                        }
+                    }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                *abort_s = 1;
+            }
+            // every issued copy must land before the CTA may exit
+            const int back = issued < (uint64_t)ns ? (int)issued : ns;
+            for (int j = 1; j <= back; ++j) {
+                int s2 = pos.slot - j;
+                uint32_t ph = pos.phase;
+                if (s2 < 0) {
+                    s2 += ns;
+                    ph ^= 1u;
+                }
+                mbar_wait(full + s2, ph, nullptr, a.wait_ns);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ consumer warps
+        const int64_t stot = a.m.stot;
+        const int j0 = (int)(cta * stot / G), j1 = (int)((cta + 1) * stot / G);
+        unsigned lgen = 0;
+        RingPos pos{0, 0u};
+        bool ok = true;
+        for (int e = tid; e < nk * P; e += kCons) xs[e] = __ldcg(a.sp.X + ra + e);
+        named_sync<kCons>();
+        for (int n = 0; n < a.T && ok; ++n) {
+            for (int st = 0; st < 4 && ok; ++st) {
+                // ---- V pass: per input pair q, every warp reads every row; thread owns
+                //      column pairs tid and tid + 512 of the segment (ldv <= 2048)
+                for (int q = 0; q < P; ++q) {
+                    const int ld = a.m.ldv[q];
+                    if (ld == 0) continue;
+                    const int rps = seg_rps(ld, a.slot_bytes);
+                    float2 acc[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+                    for (int r0 = 0; r0 < nk; r0 += rps) {
+                        if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
+                        const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
+                        const int nr = min(rps, nk - r0);
+                        for (int rr = 0; rr < nr; ++rr) {
+                            const float2 xi = xs[(r0 + rr) * P + q];
+                            const float2* row = tile + (size_t)rr * ld;
+#pragma unroll
+                            for (int m = 0; m < 2; ++m) {
+                                const int p2 = tid + m * kCons;
+                                if (2 * p2 < ld) {
+                                    const float4 v = *reinterpret_cast<const float4*>(row + 2 * p2);
+                                    acc[2 * m] = cfmac(make_float2(v.x, v.y), xi, acc[2 * m]);
+                                    acc[2 * m + 1] = cfmac(make_float2(v.z, v.w), xi, acc[2 * m + 1]);
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty + pos.slot);
+                        pos.advance(1, ns);
+                    }
+                    float2* dst = a.part + (size_t)cta * stot + a.m.sbase[q];
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        const int p2 = tid + m * kCons;
+                        if (2 * p2 < ld)
+                            *reinterpret_cast<float4*>(dst + 2 * p2) =
+                                make_float4(acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
+                    }
+                }
+                if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
+                // ---- every CTA has finished the previous stage: publish this stage's input
+                //      by pair for the dense diagonal channels
+                for (int e = tid; e < nk * P; e += kCons) {
+                    const int kk = e / P, p = e % P;
+                    a.Xt[(int64_t)p * Nk + ka + kk] = xs[e];
+                }
+                // observables of the previous step (all partials were published at its last
+                // stage, before this barrier); the last warp is idle in the sums below
+                if (st == 0 && n > 0 && cta == 0 && warp == kCW - 1)
+                    reduce_obs_row(a.sp.red, G, 1.0 / (double)Nk, a.sp.obs + 3 * (int64_t)n, lane);
+                // ---- S o sum_c y_c for this CTA's columns, fixed summation order
+                for (int j = j0 + warp; j < j1; j += kCW) {
+                    float2 s = make_float2(0.f, 0.f);
+                    for (int c2 = lane; c2 < G; c2 += 32) s = cadd(s, __ldcg(a.part + (size_t)c2 * stot + j));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s = cadd(s, shfl_xor(s, o));
+                    if (lane == 0) a.ytil[j] = cscale(s, a.S[j]);
+                }
+                if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
+                // ---- U pass, per output pair p: the rows of a tile are split over the
+                //      consumer warps by column parts ((row in tile) x parts = 16 warps)
+                for (int p = 0; p < P; ++p) {
+                    const int ld = a.m.ldw[p], nl = a.m.nlr[p];
+                    const int* g = a.gidx + a.m.gbase[p];
+                    for (int c = tid; c < ld; c += kCons)
+                        zs[c] = c < nl ? __ldcg(a.ytil + g[c])
+                                       : (c < nl + Nk ? __ldcg(a.Xt + (int64_t)p * Nk + (c - nl))
+                                                      : make_float2(0.f, 0.f));
+                    named_sync<kCons>();
+                    const int rps = seg_rps(ld, a.slot_bytes);
+                    const int cp = rps >= kCW ? 1 : kCW / rps;
+                    const int pw = ((ld + cp - 1) / cp + 1) / 2 * 2;
+                    const int myq = warp % cp, myr = warp / cp, rstride = kCW / cp;
+                    const int c0 = myq * pw, c1 = min(ld, c0 + pw);
+                    for (int r0 = 0; r0 < nk; r0 += rps) {
+                        if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
+                        const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
+                        const int nr = min(rps, nk - r0);
+                        for (int rr = myr; rr < nr; rr += rstride) {
+                            const float2* ur = tile + (size_t)rr * ld;
+                            float2 d = make_float2(0.f, 0.f), d1 = d;
+                            for (int col = c0 + 2 * lane; col < c1; col += 64) {
+                                const float4 u = *reinterpret_cast<const float4*>(ur + col);
+                                const float4 zv = *reinterpret_cast<const float4*>(zs + col);
+                                d = cfma(make_float2(u.x, u.y), make_float2(zv.x, zv.y), d);
+                                d1 = cfma(make_float2(u.z, u.w), make_float2(zv.z, zv.w), d1);
+                            }
+                            d = cadd(d, d1);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) d = cadd(d, shfl_xor(d, o));
+                            if (lane == 0) upart[(r0 + rr) * cp + myq] = d;
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty + pos.slot);
+                        pos.advance(1, ns);
+                    }
+                    named_sync<kCons>();  // every part of every row of pair p is in
+                    for (int kk = tid; kk < nk; kk += kCons) {
+                        float2 s = upart[kk * cp];
+                        for (int qq = 1; qq < cp; ++qq) s = cadd(s, upart[kk * cp + qq]);
+                        a.dSw[(int64_t)(ka + kk) * P + p] = s;
+                    }
+                    // the next pair's zs writes follow this pass's reads (barrier above);
+                    // its upart writes follow the sums here (barrier after its zs build)
+                }
+                named_sync<kCons>();  // this CTA's dSigma rows are complete
+                // ---- commutator + RK4 stage update for k in [ka, kb)
+                const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
+                const float E = (float)a.sp.Etab[2 * (int64_t)n + eoff];
+                double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+                for (int64_t b = ra; b < rb; b += kCons) {
+                    const int64_t i = b + tid;
+                    const Obs3 ob = stage_element<float, NB>(a.sp, i, i < rb, lane, st, E);
+                    o0 += ob.p;
+                    o1 += ob.j;
+                    o2 += ob.o;
+                }
+                if (st == 3) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        o0 += __shfl_xor_sync(0xffffffffu, o0, o);
+                        o1 += __shfl_xor_sync(0xffffffffu, o1, o);
+                        o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+                    }
+                    if (lane == 0) {
+                        wred[3 * warp] = o0;
+                        wred[3 * warp + 1] = o1;
+                        wred[3 * warp + 2] = o2;
+                    }
+                    named_sync<kCons>();
+                    if (tid == 0) {
+                        double s0 = 0, s1 = 0, s2 = 0;
+                        for (int w = 0; w < kCW; ++w) {
+                            s0 += wred[3 * w];
+                            s1 += wred[3 * w + 1];
+                            s2 += wred[3 * w + 2];
+                        }
+                        a.sp.red[3 * cta] = s0;
+                        a.sp.red[3 * cta + 1] = s1;
+                        a.sp.red[3 * cta + 2] = s2;
+                    }
+                }
+                named_sync<kCons>();
+                for (int e = tid; e < nk * P; e += kCons) xs[e] = __ldcg(a.sp.X + ra + e);
+                named_sync<kCons>();
+            }
+        }
+        // observables of the last step: every CTA's partial is published by one more barrier
+        if (ok && a.T > 0) {
+            ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s);
+            if (ok && cta == 0 && warp == 0)
+                reduce_obs_row(a.sp.red, G, 1.0 / (double)Nk, a.sp.obs + 3 * (int64_t)a.T, lane);
+        }
+        // ok is uniform here: it only changes through grid_sync, which every consumer
+        // thread enters in the same order and which returns the same shared flag to all
+        if (!ok && tid == 0) {
+            atomicExch(a.err, 1);
+            *abort_s = 1;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// Host side: launch geometry, ring sizing, cooperative launch.  Returns false when the path
+// does not apply (complex128, an input pair with more than 2048 low-rank columns, too
+// little shared memory); the caller then runs the stage-wise kernels.
+bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
+                          bool test_timeout, cudaStream_t s) {
+    const HostModel& h = c.hm;
+    ChannelFactors& f = c.ch;
+    const ChMeta& m = f.m;
+    if (c.dtype != TDAGW_C64 || !f.valid) return false;
+    const int P = h.Nb * h.Nb;
+    int maxv = 0, maxw = 0;
+    for (int e = 0; e < P; ++e) {
+        maxv = std::max(maxv, m.ldv[e]);
+        maxw = std::max(maxw, m.ldw[e]);
+    }
+    if (maxv > 4 * kCons) return false;  // V pass: two column pairs per consumer thread
+    int dev = 0, nsm = 0, smem_max = 0, coop = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return false;
+    const int G = (int)std::min<int64_t>(nsm, h.Nk);  // every CTA owns >= 1 k-point
+    const int kmax = (h.Nk + G - 1) / G;
+    const int row_max = std::max(maxv, maxw) * 8;
+    const int slot_bytes = (std::max(kSlotMin, row_max) + 127) / 128 * 128;
+    const int zs_len = maxw;  // even
+    const size_t extras = (size_t)zs_len * 8 + (size_t)kmax * kCW * 8 + (size_t)kmax * P * 8 + 3 * kCW * 8 + 16;
+    const size_t avail = (size_t)smem_max - 1024;
+    if (avail < extras + 4 * ((size_t)slot_bytes + 16)) return false;
+    const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
+    const size_t smem = (size_t)nslots * slot_bytes + 16 * (size_t)nslots + extras;
+
+    CHArgs a{};
+    a.m = m;
+    a.V = f.V.as<float2>();
+    a.U = f.U.as<float2>();
+    a.S = f.S.as<float>();
+    a.gidx = f.gidx.as<int>();
+    StageParams<float>& p = a.sp;
+    p.X = c.X.as<float2>();
+    p.dS = c.dS.as<float2>();
+    p.dx = c.dx.as<float2>();
+    p.dy = c.dy.as<float2>();
+    p.vx = c.vx.as<float2>();
+    p.gap = c.gap.as<float2>();
+    p.acc = c.acc.as<float2>();
+    p.Ssum = c.Ssum.as<float2>();
+    p.Ccomp = c.Ccomp.as<float2>();
+    p.Xnext = c.X.as<float2>();
+    p.Etab = c.Etab.as<double>();
+    p.step = nullptr;
+    p.obs = c.obs.as<double>();
+    c.red.ensure((size_t)std::max<int64_t>(G, (h.N + 255) / 256) * 3 * sizeof(double));
+    p.red = c.red.as<double>();
+    p.counter = nullptr;
+    p.N = h.N;
+    p.Nk = h.Nk;
+    p.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) p.occ[q] = (float)h.occ[q];
+    p.dt = (float)dt;
+    p.dirx = (float)dirx;
+    p.diry = (float)diry;
+    p.stage = 0;
+    p.kahan = kahan ? 1 : 0;
+    f.part.ensure((size_t)G * std::max<long long>(m.stot, 1) * sizeof(float2));
+    f.Xt.ensure((size_t)h.N * sizeof(float2));
+    c.sync.ensure(4 * sizeof(unsigned));
+    TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+    a.dSw = c.dS.as<float2>();
+    a.part = f.part.as<float2>();
+    a.ytil = f.Y.as<float2>();
+    a.Xt = f.Xt.as<float2>();
+    a.bar_count = reinterpret_cast<unsigned long long*>(c.sync.p);
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.T = T;
+    a.nslots = nslots;
+    a.slot_bytes = slot_bytes;
+    a.kmax = kmax;
+    a.zs_len = zs_len;
+    a.extra_arrivals = test_timeout ? 1 : 0;
+    a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
+    void* args[] = {&a};
+    const void* fn = h.Nb == 2 ? (const void*)ch_persistent_kernel<2> : (const void*)ch_persistent_kernel<4>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThr, smem));
+    if (per_sm < 1) return false;
+    TDAGW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThr), args, smem, s));
+    c.persistent_launched = true;
+    return true;
+}
+
+}  // namespace tdagw

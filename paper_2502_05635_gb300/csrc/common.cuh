@@ -148,6 +148,32 @@ struct AdjointState {
 };
 
 
+// Channel-wise factors (Eq. svd-channel-wise), P = Nb^2 pairs.  Channel p -> q (output
+// pair p, input pair q) has rank z[p P + q] (0 on the diagonal: diagonal channels are dense).
+//   V segment q: Nk rows x ldv[q]; row k' = V^pq[k', 0:z_pq] for p != q, ascending p
+//   U segment p: Nk rows x ldw[p]; row k  = U^pq[k, 0:z_pq] for q != p, ascending q
+//                (nlr[p] columns), then K^pp[k, 0:Nk]
+//   S, S o y, partials: sum_q ldv[q] entries aligned with the V columns (from sbase[q])
+//   gidx: for each p (from gbase[p]), the S o y index of each low-rank column of its U rows
+// Row lengths are even (a zero pad column) so every row starts on a 16-byte boundary.
+constexpr int kMaxPairs = 16;
+struct ChMeta {
+    int P, Nk;
+    int ldv[kMaxPairs], ldw[kMaxPairs], nlr[kMaxPairs];
+    long long vbase[kMaxPairs], ubase[kMaxPairs], sbase[kMaxPairs], gbase[kMaxPairs];
+    long long vtot, utot, stot, gtot;
+};
+struct ChannelFactors {
+    bool valid = false;
+    int zmax = 0;
+    std::vector<int> z;     // P x P ranks
+    std::vector<int> voff;  // [q P + p]: first column of channel p -> q in V segment q
+    std::vector<int> uoff;  // [p P + q]: first column of channel p -> q in U segment p
+    std::vector<int> gidx_host;
+    ChMeta m{};
+    DevBuf V, U, S, Y, gidx, part, Xt;
+};
+
 struct Ctx {
     tdagw_model_desc desc{};
     cudaStream_t stream = nullptr;
@@ -162,6 +188,7 @@ struct Ctx {
     // (ldu = rank rounded up to even, zero pad column), S (rank, real of the dtype)
     DevBuf U, V, S, diagF;
     int rank = 0;
+    ChannelFactors ch;
     // propagation state (trajectory 0): compensated sum (Ssum + Ccomp), stage input X,
     // RK4 accumulator, dSigma, low-rank partials and projected vector
     DevBuf Ssum, Ccomp, X, acc, dS, ypart, ytil;
@@ -293,5 +320,35 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
 
 template <typename R>
 void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed);
+
+// ---- channel-wise factors (channel.cu, rsvd.cu, ch_persistent.cu)
+// Offsets and row lengths of the channel layout for ranks z (P x P); allocates and zeroes
+// the factor arrays in the context dtype.
+void ch_layout(Ctx& c, const std::vector<int>& z);
+// dst[k ld + k'] = K[(k P + p) N + k' P + q] for the Nk x Nk channel p -> q (context dtype)
+template <typename R>
+void launch_ch_gather(const Ctx& c, int p, int q, void* dst, int64_t ld, cudaStream_t s);
+// dst[k ld + off + j] = src[k z + j] (FP64 Nk x z into a segment of the context dtype)
+template <typename R>
+void launch_ch_place(const double2* src, int Nk, int z, void* dst, int64_t ld, int off,
+                     cudaStream_t s);
+// the dense diagonal channels of the built kernel into the U segments
+template <typename R>
+void ch_fill_diag_from_kernel(Ctx& c);
+template <typename R>
+void set_channel_factors(Ctx& c, int rank, const int* ranks, const double* U, const double* S,
+                         const double* V, const double* D);
+template <typename R>
+void get_channel_factors(Ctx& c, int* rank, int* ranks, double* U, double* S, double* V,
+                         double* D);
+// y = K~ x with the channel-wise factors (stage-wise kernels)
+template <typename R>
+void launch_ch_apply(Ctx& c, const void* x, void* y, cudaStream_t s);
+template <typename R>
+void rsvd_channels(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed,
+                   double rel_tol);
+// Persistent single-trajectory channel-wise propagation (complex64); false if not applicable.
+bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
+                          bool test_timeout, cudaStream_t s);
 
 }  // namespace tdagw

@@ -33,6 +33,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+uint64_t splitmix64_host(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 __global__ void gauss_kernel(double2* __restrict__ out, int64_t n, uint64_t seed) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -555,5 +562,139 @@ void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t s
 
 template void rsvd_compress<float>(Ctx&, int, int, int, uint64_t);
 template void rsvd_compress<double>(Ctx&, int, int, int, uint64_t);
+
+// Channel-wise factors (Eq. svd-channel-wise).  Every off-diagonal channel A = K^pq (p < q,
+// Nk x Nk, gathered contiguously in the context precision) gets a randomised truncated SVD
+// by the same range finder as above, now for a general (non-Hermitian) matrix:
+//   Q = orth(A Omega); repeat power_iters times: Q = orth(A orth(A^H Q))
+//   Z = A^H Q = B^H (B = Q^H A, l x Nk);  B B^H = Z^H Z = W diag(lambda) W^H (Jacobi)
+//   sigma_j = sqrt(lambda_j),  U = Q W_r,  V = Z W_r diag(1 / sigma)   (B = W Sigma V^H)
+// The core squares the singular values, so sigma_j below 1e-7 sigma_0 is not resolved in
+// FP64 and is dropped together with those below rel_tol sigma_0 (a vanishing channel keeps
+// nothing).  Channel q -> p is (K^pq)^H = V^pq S^pq (U^pq)^H.
+template <typename R>
+void rsvd_channels(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed, double rel_tol) {
+    using C = cplx_t<R>;
+    Ws w;
+    w.s = c.stream;
+    const HostModel& h = c.hm;
+    const int P = h.Nb * h.Nb, Nk = h.Nk;
+    const int l = std::max(1, std::min(rank + oversample, Nk));
+    const double floor_rel = std::max(rel_tol, 1e-7);
+    struct Fac {
+        DevBuf U, V;
+        std::vector<double> S;
+    };
+    std::vector<Fac> fac(P * P);
+    std::vector<int> z(P * P, 0);
+    DevBuf A, Q, Z, H, P2, Gb, Mb, Bm, Wm, Wr;
+    if (rank > 0) {
+        A.ensure((size_t)Nk * Nk * sizeof(C));
+        Q.ensure((size_t)Nk * l * sizeof(double2));
+        Z.ensure((size_t)Nk * l * sizeof(double2));
+        Bm.ensure((size_t)l * l * sizeof(double2));
+        Wm.ensure((size_t)l * l * sizeof(double2));
+    }
+    std::vector<double2> hb((size_t)l * l), hw((size_t)l * l);
+    for (int p = 0; p < P && rank > 0; ++p)
+        for (int q = p + 1; q < P; ++q) {
+            launch_ch_gather<R>(c, p, q, A.p, Nk, w.s);
+            const C* Ap = A.as<C>();
+            gauss_kernel<<<152 * 8, 256, 0, w.s>>>(Z.as<double2>(), (int64_t)Nk * l,
+                                                   seed ^ splitmix64_host((uint64_t)(p * P + q) + 1));
+            check_launch("gauss_kernel");
+            gemm<C, double2, R, false, false>(w, Nk, l, Nk, Ap, Nk, Z.as<double2>(), l, Q.as<double2>(), l,
+                                              kOne, kZero);
+            orthonormalise(w, Q.as<double2>(), Nk, l, H, P2, Gb, Mb);
+            for (int it = 0; it < power_iters; ++it) {
+                gemm<C, double2, R, true, false>(w, Nk, l, Nk, Ap, Nk, Q.as<double2>(), l, Z.as<double2>(), l,
+                                                 kOne, kZero);
+                orthonormalise(w, Z.as<double2>(), Nk, l, H, P2, Gb, Mb);
+                gemm<C, double2, R, false, false>(w, Nk, l, Nk, Ap, Nk, Z.as<double2>(), l, Q.as<double2>(),
+                                                  l, kOne, kZero);
+                orthonormalise(w, Q.as<double2>(), Nk, l, H, P2, Gb, Mb);
+            }
+            gemm<C, double2, R, true, false>(w, Nk, l, Nk, Ap, Nk, Q.as<double2>(), l, Z.as<double2>(), l,
+                                             kOne, kZero);
+            gemm<double2, double2, double, true, false>(w, l, l, Nk, Z.as<double2>(), l, Z.as<double2>(), l,
+                                                        Bm.as<double2>(), l, kOne, kZero);
+            hermitise_kernel<<<(unsigned)(((int64_t)l * l + 255) / 256), 256, 0, w.s>>>(Bm.as<double2>(), l);
+            check_launch("hermitise_kernel");
+            jacobi_eigh(w, Bm.as<double2>(), Wm.as<double2>(), l);
+            TDAGW_CUDA(cudaMemcpyAsync(hb.data(), Bm.p, hb.size() * sizeof(double2), cudaMemcpyDeviceToHost, w.s));
+            TDAGW_CUDA(cudaMemcpyAsync(hw.data(), Wm.p, hw.size() * sizeof(double2), cudaMemcpyDeviceToHost, w.s));
+            TDAGW_CUDA(cudaStreamSynchronize(w.s));
+            std::vector<int> idx(l);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::stable_sort(idx.begin(), idx.end(),
+                             [&](int a, int b) { return hb[(size_t)a * l + a].x > hb[(size_t)b * l + b].x; });
+            const double s0 = std::sqrt(std::max(0.0, hb[(size_t)idx[0] * l + idx[0]].x));
+            std::vector<double> sv;
+            for (int j = 0; j < std::min(rank, l); ++j) {
+                const double sj = std::sqrt(std::max(0.0, hb[(size_t)idx[j] * l + idx[j]].x));
+                if (!(sj > 0.0) || sj <= floor_rel * s0) break;
+                sv.push_back(sj);
+            }
+            const int zz = (int)sv.size();
+            z[p * P + q] = z[q * P + p] = zz;
+            if (zz == 0) continue;
+            // U = Q W_r and V = Z W_r diag(1 / sigma), FP64
+            std::vector<double2> wr((size_t)l * zz), wv((size_t)l * zz);
+            for (int j = 0; j < zz; ++j)
+                for (int i = 0; i < l; ++i) {
+                    const double2 e = hw[(size_t)i * l + idx[j]];
+                    wr[(size_t)i * zz + j] = e;
+                    wv[(size_t)i * zz + j] = make_double2(e.x / sv[j], e.y / sv[j]);
+                }
+            Fac& fc = fac[p * P + q];
+            fc.S = sv;
+            fc.U.ensure((size_t)Nk * zz * sizeof(double2));
+            fc.V.ensure((size_t)Nk * zz * sizeof(double2));
+            Wr.ensure((size_t)l * zz * sizeof(double2));
+            TDAGW_CUDA(cudaMemcpyAsync(Wr.p, wr.data(), wr.size() * sizeof(double2), cudaMemcpyHostToDevice, w.s));
+            gemm<double2, double2, double, false, false>(w, Nk, zz, l, Q.as<double2>(), l, Wr.as<double2>(), zz,
+                                                         fc.U.as<double2>(), zz, kOne, kZero);
+            TDAGW_CUDA(cudaStreamSynchronize(w.s));
+            TDAGW_CUDA(cudaMemcpyAsync(Wr.p, wv.data(), wv.size() * sizeof(double2), cudaMemcpyHostToDevice, w.s));
+            gemm<double2, double2, double, false, false>(w, Nk, zz, l, Z.as<double2>(), l, Wr.as<double2>(), zz,
+                                                         fc.V.as<double2>(), zz, kOne, kZero);
+            TDAGW_CUDA(cudaStreamSynchronize(w.s));
+        }
+    A.release();
+    Q.release();
+    Z.release();
+    P2.release();
+    w.work.release();
+    // segment layout for the final ranks, then every channel into place
+    ch_layout(c, z);
+    ChannelFactors& f = c.ch;
+    const ChMeta& m = f.m;
+    std::vector<R> hs((size_t)std::max<long long>(m.stot, 1), (R)0);
+    C* Vd = f.V.as<C>();
+    C* Ud = f.U.as<C>();
+    for (int p = 0; p < P; ++p)
+        for (int q = p + 1; q < P; ++q) {
+            const int zz = z[p * P + q];
+            if (zz == 0) continue;
+            const Fac& fc = fac[p * P + q];
+            // channel p -> q: U^pq into U segment p, V^pq into V segment q
+            launch_ch_place<R>(fc.U.as<double2>(), Nk, zz, Ud + m.ubase[p], m.ldw[p], f.uoff[p * P + q], w.s);
+            launch_ch_place<R>(fc.V.as<double2>(), Nk, zz, Vd + m.vbase[q], m.ldv[q], f.voff[q * P + p], w.s);
+            // channel q -> p = (K^pq)^H: U^qp = V^pq into U segment q, V^qp = U^pq into V segment p
+            launch_ch_place<R>(fc.V.as<double2>(), Nk, zz, Ud + m.ubase[q], m.ldw[q], f.uoff[q * P + p], w.s);
+            launch_ch_place<R>(fc.U.as<double2>(), Nk, zz, Vd + m.vbase[p], m.ldv[p], f.voff[p * P + q], w.s);
+            for (int j = 0; j < zz; ++j) {
+                hs[m.sbase[q] + f.voff[q * P + p] + j] = (R)fc.S[j];
+                hs[m.sbase[p] + f.voff[p * P + q] + j] = (R)fc.S[j];
+            }
+        }
+    ch_fill_diag_from_kernel<R>(c);
+    TDAGW_CUDA(cudaMemcpyAsync(f.S.p, hs.data(), hs.size() * sizeof(R), cudaMemcpyHostToDevice, w.s));
+    TDAGW_CUDA(cudaStreamSynchronize(w.s));
+    f.valid = true;
+}
+
+template void rsvd_channels<float>(Ctx&, int, int, int, uint64_t, double);
+template void rsvd_channels<double>(Ctx&, int, int, int, uint64_t, double);
 
 }  // namespace tdagw

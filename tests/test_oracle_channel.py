@@ -41,6 +41,16 @@ def test_channel_block_indexing_by_integer_matrix():
                     assert blk[k, kp] == (k * P + p) * N + kp * P + q
 
 
+@pytest.mark.parametrize("name", ["k2", "k4"])
+def test_channel_block_from_model_matches_dense_kernel(name, request):
+    m, K = request.getfixturevalue(name)
+    Nb = m.p.Nb
+    for p in range(Nb * Nb):
+        for q in range(Nb * Nb):
+            np.testing.assert_allclose(oc.channel_block_from_model(m, p, q), oc.channel_block(K, Nb, p, q),
+                                       atol=1e-15 * np.abs(K).max())
+
+
 def test_apply_channel_by_scalar_loops():
     """The channel apply against the sum written out element by element (random factors,
     tiny sizes), with the conjugate on V and the dense diagonal channels."""

@@ -12,6 +12,9 @@ kernels, which are not available):
                  2000 RK4 steps of dt=0.2, Gaussian*cos pulse E0=1e-3, w=0.1, t0=200,
                  sigma=60.  The parity workload; the paper's MoS2 runs use the same
                  narrow-pulse linear-response setup (Sec. "SVD acceleration of TD-aGW").
+  mos2size_nb4_l36_channel
+                 the same model with channel-wise factors: dense diagonal channels,
+                 off-diagonal channels truncated to rank 65 (5 % of Nk).
   mos2size_nb4_l36
                  four-band model (two copies, energy offsets 0 and 0.03 Ha), 36x36 grid
                  (Nk=1296, N=20736 -- the size of the paper's 2v+2c, 36x36 MoS2 kernel,
@@ -109,6 +112,14 @@ def tiny_nb2_l12(steps: int = 2000) -> Workload:
 def mos2size_nb4_l36(steps: int = 10000) -> Workload:
     mp = ModelParams(L=36, nb_copies=2, offsets=(0.0, 0.03, 0.0, 0.0))
     return Workload("mos2size_nb4_l36", mp, 0.2, (steps,), (Pulse(),), rank=1024)
+
+
+def mos2size_channel(steps: int = 10000) -> Workload:
+    """The mos2-size model with the channel-wise compression: dense diagonal channels and
+    every off-diagonal channel truncated to 5 % of Nk (65 of 1296 singular values), the
+    "K_0^diag-ch + 5 % K_0^off-ch" kernel of the paper's TDA spectra."""
+    mp = ModelParams(L=36, nb_copies=2, offsets=(0.0, 0.03, 0.0, 0.0))
+    return Workload("mos2size_nb4_l36_channel", mp, 0.2, (steps,), (Pulse(),), rank=65)
 
 
 def sweep_nb2_l24(B: int = 256) -> Workload:
