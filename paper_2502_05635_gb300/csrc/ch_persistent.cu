@@ -32,7 +32,9 @@ using namespace persist;
 constexpr int kCW = 16;              // consumer warps
 constexpr int kCons = kCW * 32;
 constexpr int kThr = kCons + 32;
-constexpr int kSlotMin = 32768;      // bytes per ring slot (at least one whole row)
+constexpr int kSlotMin = 32768;      // bytes per ring slot (at least one whole row) ...
+constexpr int kSlotMax = 65536;      // ... up to four U rows when those are long
+constexpr int kZPre = 8;             // U-pass vector entries prefetched per thread (<= 4096)
 
 struct CHArgs {
     ChMeta m;
@@ -74,9 +76,9 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
     unsigned char* ring = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
-    float2* zs = reinterpret_cast<float2*>(empty + ns);  // U-pass vector, zs_len
-    float2* upart = zs + a.zs_len;                       // kmax x kCW partial dot products
-    float2* xs = upart + a.kmax * kCW;                   // kmax x P, this CTA's stage input
+    float2* zbuf = reinterpret_cast<float2*>(empty + ns);  // 2 x zs_len U-pass vectors
+    float2* ubuf = zbuf + 2 * a.zs_len;                    // 2 x kmax x kCW partial dots
+    float2* xs = ubuf + 2 * a.kmax * kCW;                  // kmax x P, this CTA's stage input
     double* wred = reinterpret_cast<double*>(xs + a.kmax * P);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kCW);
 
@@ -210,15 +212,37 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                 }
                 if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
                 // ---- U pass, per output pair p: the rows of a tile are split over the
-                //      consumer warps by column parts ((row in tile) x parts = 16 warps)
-                for (int p = 0; p < P; ++p) {
-                    const int ld = a.m.ldw[p], nl = a.m.nlr[p];
-                    const int* g = a.gidx + a.m.gbase[p];
-                    for (int c = tid; c < ld; c += kCons)
-                        zs[c] = c < nl ? __ldcg(a.ytil + g[c])
-                                       : (c < nl + Nk ? __ldcg(a.Xt + (int64_t)p * Nk + (c - nl))
+                //      consumer warps by column parts ((row in tile) x parts = 16 warps).
+                //      The vector of pair p + 1 is loaded into registers while pair p's
+                //      tiles are consumed (its S o y entries and x_{p+1} come from L2), and
+                //      stored into the other buffer before the barrier that ends pair p.
+                float2 zr[kZPre];
+                auto zload = [&](int pp) {
+                    const int nl = a.m.nlr[pp];
+                    const int* g = a.gidx + a.m.gbase[pp];
+#pragma unroll
+                    for (int j = 0; j < kZPre; ++j) {
+                        const int c = tid + j * kCons;
+                        zr[j] = c < nl ? __ldcg(a.ytil + __ldg(g + c))
+                                       : (c < nl + Nk ? __ldcg(a.Xt + (int64_t)pp * Nk + (c - nl))
                                                       : make_float2(0.f, 0.f));
-                    named_sync<kCons>();
+                    }
+                };
+                auto zstore = [&](float2* dst, int ld) {
+#pragma unroll
+                    for (int j = 0; j < kZPre; ++j) {
+                        const int c = tid + j * kCons;
+                        if (c < ld) dst[c] = zr[j];
+                    }
+                };
+                zload(0);
+                zstore(zbuf, a.m.ldw[0]);
+                named_sync<kCons>();
+                for (int p = 0; p < P; ++p) {
+                    const int ld = a.m.ldw[p];
+                    const float2* zs = zbuf + (p & 1) * a.zs_len;
+                    float2* upart = ubuf + (p & 1) * a.kmax * kCW;
+                    if (p + 1 < P) zload(p + 1);
                     const int rps = seg_rps(ld, a.slot_bytes);
                     const int cp = rps >= kCW ? 1 : kCW / rps;
                     const int pw = ((ld + cp - 1) / cp + 1) / 2 * 2;
@@ -246,14 +270,16 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                         if (lane == 0) mbar_arrive(empty + pos.slot);
                         pos.advance(1, ns);
                     }
-                    named_sync<kCons>();  // every part of every row of pair p is in
+                    if (p + 1 < P) zstore(zbuf + ((p + 1) & 1) * a.zs_len, a.m.ldw[p + 1]);
+                    // every part of every row of pair p is in, and the vector of p + 1; the
+                    // buffers written next (pair p + 2) were last read before this barrier's
+                    // predecessor
+                    named_sync<kCons>();
                     for (int kk = tid; kk < nk; kk += kCons) {
                         float2 s = upart[kk * cp];
                         for (int qq = 1; qq < cp; ++qq) s = cadd(s, upart[kk * cp + qq]);
                         a.dSw[(int64_t)(ka + kk) * P + p] = s;
                     }
-                    // the next pair's zs writes follow this pass's reads (barrier above);
-                    // its upart writes follow the sums here (barrier after its zs build)
                 }
                 named_sync<kCons>();  // this CTA's dSigma rows are complete
                 // ---- commutator + RK4 stage update for k in [ka, kb)
@@ -316,8 +342,9 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
 }  // namespace
 
 // Host side: launch geometry, ring sizing, cooperative launch.  Returns false when the path
-// does not apply (complex128, an input pair with more than 2048 low-rank columns, too
-// little shared memory); the caller then runs the stage-wise kernels.
+// does not apply (complex128, an input pair with more than 2048 low-rank columns, U rows
+// longer than 4096 entries, too little shared memory); the caller then runs the stage-wise
+// kernels.
 bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
                           bool test_timeout, cudaStream_t s) {
     const HostModel& h = c.hm;
@@ -340,11 +367,20 @@ bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     const int G = (int)std::min<int64_t>(nsm, h.Nk);  // every CTA owns >= 1 k-point
     const int kmax = (h.Nk + G - 1) / G;
     const int row_max = std::max(maxv, maxw) * 8;
-    const int slot_bytes = (std::max(kSlotMin, row_max) + 127) / 128 * 128;
     const int zs_len = maxw;  // even
-    const size_t extras = (size_t)zs_len * 8 + (size_t)kmax * kCW * 8 + (size_t)kmax * P * 8 + 3 * kCW * 8 + 16;
+    if (zs_len > kZPre * kCons) return false;  // the U-pass vector prefetch covers 4096 entries
+    const size_t extras = 2 * (size_t)zs_len * 8 + 2 * (size_t)kmax * kCW * 8 + (size_t)kmax * P * 8 +
+                          3 * kCW * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
-    if (avail < extras + 4 * ((size_t)slot_bytes + 16)) return false;
+    if (avail < extras) return false;
+    // slots of up to four U rows (fewer partial dot products per row), as long as at least
+    // four slots fit; at least one whole row
+    int slot_bytes = 0;
+    for (int rows = 4; rows >= 1 && !slot_bytes; rows /= 2) {
+        const int sb = (std::max(kSlotMin, std::max(row_max, std::min(rows * maxw * 8, kSlotMax))) + 127) / 128 * 128;
+        if ((avail - extras) / ((size_t)sb + 16) >= 4) slot_bytes = sb;
+    }
+    if (!slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
     const size_t smem = (size_t)nslots * slot_bytes + 16 * (size_t)nslots + extras;
 
