@@ -36,6 +36,24 @@ constexpr int kSlotMin = 32768;      // bytes per ring slot (at least one whole 
 constexpr int kSlotMax = 65536;      // ... up to four U rows when those are long
 constexpr int kZPre = 8;             // U-pass vector entries prefetched per thread (<= 4096)
 
+// Optional phase timestamps (build with -DTDAGW_TRACE): thread 0 of every CTA records
+// %globaltimer at nine points of each of the first kChTraceStages stages, and when its
+// waits for the first V-pass slots return (points 9 ...).
+#ifdef TDAGW_TRACE
+constexpr int kChTraceStages = 16;
+constexpr int kChTracePts = 16;
+__device__ unsigned long long g_trace_ch[160 * kChTraceStages * kChTracePts];
+#define CH_TRACE(k)                                                                         \
+    do {                                                                                    \
+        if (tid == 0 && cta < 160 && n * 4 + st < kChTraceStages && (k) < kChTracePts)      \
+            g_trace_ch[(cta * kChTraceStages + n * 4 + st) * kChTracePts + (k)] = gtimer(); \
+    } while (0)
+#else
+#define CH_TRACE(k) \
+    do {            \
+    } while (0)
+#endif
+
 struct CHArgs {
     ChMeta m;
     const float2* V;
@@ -61,6 +79,31 @@ __device__ __forceinline__ int seg_rps(int ld, int slot_bytes) {
     return r;
 }
 
+// The V pass streams its chunks (up to seg_rps rows of one input pair) packed into shared
+// slots: consecutive chunks share a slot while they fit, so the short segments of the V
+// pass still fill the ring.  VWalk is the walk over those chunks that the producer and
+// the consumers both follow.
+struct VWalk {
+    int q, r0;
+    __device__ __forceinline__ void skip_empty(const ChMeta& m, int P) {
+        while (q < P && m.ldv[q] == 0) ++q;
+    }
+    // bytes of the current chunk and its row count
+    __device__ __forceinline__ uint32_t chunk(const ChMeta& m, int nk, int slot_bytes, int& nr) const {
+        const int ld = m.ldv[q];
+        nr = min(seg_rps(ld, slot_bytes), nk - r0);
+        return (uint32_t)nr * ld * 8u;
+    }
+    __device__ __forceinline__ void next(const ChMeta& m, int P, int nk, int nr) {
+        r0 += nr;
+        if (r0 >= nk) {
+            r0 = 0;
+            ++q;
+            skip_empty(m, P);
+        }
+    }
+};
+
 template <int NB>
 __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -79,7 +122,8 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
     float2* zbuf = reinterpret_cast<float2*>(empty + ns);  // 2 x zs_len U-pass vectors
     float2* ubuf = zbuf + 2 * a.zs_len;                    // 2 x kmax x kCW partial dots
     float2* xs = ubuf + 2 * a.kmax * kCW;                  // kmax x P, this CTA's stage input
-    double* wred = reinterpret_cast<double*>(xs + a.kmax * P);
+    float2* yred = xs + a.kmax * P;                         // kCons partial sums of S o y
+    double* wred = reinterpret_cast<double*>(yred + kCons);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kCW);
 
     if (tid == 0) {
@@ -100,14 +144,44 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
             bool ok = true;
             const uint64_t policy = policy_evict_first();
             for (int n = 0; n < a.T && ok; ++n)
-                for (int st = 0; st < 4 && ok; ++st)
-                    for (int sg = 0; sg < 2 * P && ok; ++sg) {
-                        const bool vseg = sg < P;
-                        const int e = vseg ? sg : sg - P;
-                        const int ld = vseg ? a.m.ldv[e] : a.m.ldw[e];
-                        if (ld == 0) continue;
-                        const float2* base =
-                            (vseg ? a.V + a.m.vbase[e] : a.U + a.m.ubase[e]) + (int64_t)ka * ld;
+                for (int st = 0; st < 4 && ok; ++st) {
+                    // V pass: chunks of consecutive input pairs packed into shared slots
+                    VWalk vw{0, 0};
+                    vw.skip_empty(a.m, P);
+                    while (vw.q < P) {
+                        if (issued >= (uint64_t)ns &&
+                            !mbar_wait(empty + pos.slot, pos.phase ^ 1u, abort_s, a.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        VWalk end = vw;
+                        uint32_t tot = 0;
+                        while (end.q < P) {
+                            int nr;
+                            const uint32_t b = end.chunk(a.m, nk, a.slot_bytes, nr);
+                            if (tot > 0 && tot + b > (uint32_t)a.slot_bytes) break;
+                            tot += b;
+                            end.next(a.m, P, nk, nr);
+                        }
+                        mbar_expect_tx(full + pos.slot, tot);
+                        uint32_t off = 0;
+                        while (vw.q != end.q || vw.r0 != end.r0) {
+                            int nr;
+                            const uint32_t b = vw.chunk(a.m, nk, a.slot_bytes, nr);
+                            const int ld = a.m.ldv[vw.q];
+                            bulk_g2s_hint(ring + (size_t)pos.slot * a.slot_bytes + off,
+                                          a.V + a.m.vbase[vw.q] + (int64_t)(ka + vw.r0) * ld, b, full + pos.slot,
+                                          policy);
+                            off += b;
+                            vw.next(a.m, P, nk, nr);
+                        }
+                        ++issued;
+                        pos.advance(1, ns);
+                    }
+                    // U pass: one chunk of rows per slot
+                    for (int e = 0; e < P && ok; ++e) {
+                        const int ld = a.m.ldw[e];
+                        const float2* base = a.U + a.m.ubase[e] + (int64_t)ka * ld;
                         const int rps = seg_rps(ld, a.slot_bytes);
                         for (int r0 = 0; r0 < nk; r0 += rps) {
                             if (issued >= (uint64_t)ns &&
@@ -124,6 +198,7 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                             pos.advance(1, ns);
                         }
                     }
+                }
             if (!ok) {
                 atomicExch(a.err, 1);
                 *abort_s = 1;
@@ -145,6 +220,7 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
         // ------------------------------------------------------------ consumer warps
         const int64_t stot = a.m.stot;
         const int j0 = (int)(cta * stot / G), j1 = (int)((cta + 1) * stot / G);
+        const int nj = j1 - j0, nsub = nj > 0 ? kCons / nj : 0;  // nj <= 512: stot <= 16 x 2048
         unsigned lgen = 0;
         RingPos pos{0, 0u};
         bool ok = true;
@@ -152,46 +228,83 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
         named_sync<kCons>();
         for (int n = 0; n < a.T && ok; ++n) {
             for (int st = 0; st < 4 && ok; ++st) {
-                // ---- V pass: per input pair q, every warp reads every row; thread owns
-                //      column pairs tid and tid + 512 of the segment (ldv <= 2048)
-                for (int q = 0; q < P; ++q) {
-                    const int ld = a.m.ldv[q];
-                    if (ld == 0) continue;
-                    const int rps = seg_rps(ld, a.slot_bytes);
+                CH_TRACE(0);
+                // ---- V pass: every warp reads every row; thread owns column pairs tid and
+                //      tid + 512 of the current input pair's segment (ldv <= 2048); one
+                //      slot may hold chunks of several consecutive pairs
+                {
+                    VWalk vw{0, 0};
+                    vw.skip_empty(a.m, P);
                     float2 acc[4];
 #pragma unroll
                     for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-                    for (int r0 = 0; r0 < nk; r0 += rps) {
+                    int vslot = 0;
+                    while (vw.q < P) {
                         if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
-                        const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
-                        const int nr = min(rps, nk - r0);
-                        for (int rr = 0; rr < nr; ++rr) {
-                            const float2 xi = xs[(r0 + rr) * P + q];
-                            const float2* row = tile + (size_t)rr * ld;
+                        CH_TRACE(9 + vslot);
+                        ++vslot;
+                        const unsigned char* sbase = ring + (size_t)pos.slot * a.slot_bytes;
+                        uint32_t off = 0;
+                        while (vw.q < P) {
+                            int nr;
+                            const uint32_t b = vw.chunk(a.m, nk, a.slot_bytes, nr);
+                            if (off > 0 && off + b > (uint32_t)a.slot_bytes) break;
+                            const int q = vw.q, ld = a.m.ldv[q];
+                            const float2* tile = reinterpret_cast<const float2*>(sbase + off);
+                            // warps without columns of this pair skip the rows (they still
+                            // wait for and release every slot); two rows per iteration
+                            if (64 * warp < ld) {
+                                const float2* xr = xs + vw.r0 * P + q;
 #pragma unroll
-                            for (int m = 0; m < 2; ++m) {
-                                const int p2 = tid + m * kCons;
-                                if (2 * p2 < ld) {
-                                    const float4 v = *reinterpret_cast<const float4*>(row + 2 * p2);
-                                    acc[2 * m] = cfmac(make_float2(v.x, v.y), xi, acc[2 * m]);
-                                    acc[2 * m + 1] = cfmac(make_float2(v.z, v.w), xi, acc[2 * m + 1]);
+                                for (int m = 0; m < 2; ++m) {
+                                    const int c = 2 * (tid + m * kCons);
+                                    if (c < ld) {
+                                        float2 a0 = acc[2 * m], a1 = acc[2 * m + 1];
+                                        float2 b0 = make_float2(0.f, 0.f), b1 = b0;
+                                        int rr = 0;
+                                        for (; rr + 1 < nr; rr += 2) {
+                                            const float4 v = *reinterpret_cast<const float4*>(tile + (size_t)rr * ld + c);
+                                            const float4 w = *reinterpret_cast<const float4*>(tile + (size_t)(rr + 1) * ld + c);
+                                            const float2 x0 = xr[rr * P], x1 = xr[(rr + 1) * P];
+                                            a0 = cfmac(make_float2(v.x, v.y), x0, a0);
+                                            a1 = cfmac(make_float2(v.z, v.w), x0, a1);
+                                            b0 = cfmac(make_float2(w.x, w.y), x1, b0);
+                                            b1 = cfmac(make_float2(w.z, w.w), x1, b1);
+                                        }
+                                        if (rr < nr) {
+                                            const float4 v = *reinterpret_cast<const float4*>(tile + (size_t)rr * ld + c);
+                                            const float2 x0 = xr[rr * P];
+                                            a0 = cfmac(make_float2(v.x, v.y), x0, a0);
+                                            a1 = cfmac(make_float2(v.z, v.w), x0, a1);
+                                        }
+                                        acc[2 * m] = cadd(a0, b0);
+                                        acc[2 * m + 1] = cadd(a1, b1);
+                                    }
                                 }
                             }
+                            off += b;
+                            if (vw.r0 + nr >= nk) {  // last chunk of pair q: publish its partials
+                                float2* dst = a.part + (size_t)cta * stot + a.m.sbase[q];
+#pragma unroll
+                                for (int m = 0; m < 2; ++m) {
+                                    const int p2 = tid + m * kCons;
+                                    if (2 * p2 < ld)
+                                        *reinterpret_cast<float4*>(dst + 2 * p2) = make_float4(
+                                            acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
+                                }
+#pragma unroll
+                                for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+                            }
+                            vw.next(a.m, P, nk, nr);
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(empty + pos.slot);
                         pos.advance(1, ns);
                     }
-                    float2* dst = a.part + (size_t)cta * stot + a.m.sbase[q];
-#pragma unroll
-                    for (int m = 0; m < 2; ++m) {
-                        const int p2 = tid + m * kCons;
-                        if (2 * p2 < ld)
-                            *reinterpret_cast<float4*>(dst + 2 * p2) =
-                                make_float4(acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
-                    }
                 }
+                CH_TRACE(1);
                 if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
+                CH_TRACE(2);
                 // ---- every CTA has finished the previous stage: publish this stage's input
                 //      by pair for the dense diagonal channels
                 for (int e = tid; e < nk * P; e += kCons) {
@@ -202,15 +315,25 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                 // stage, before this barrier); the last warp is idle in the sums below
                 if (st == 0 && n > 0 && cta == 0 && warp == kCW - 1)
                     reduce_obs_row(a.sp.red, G, 1.0 / (double)Nk, a.sp.obs + 3 * (int64_t)n, lane);
-                // ---- S o sum_c y_c for this CTA's columns, fixed summation order
-                for (int j = j0 + warp; j < j1; j += kCW) {
-                    float2 s = make_float2(0.f, 0.f);
-                    for (int c2 = lane; c2 < G; c2 += 32) s = cadd(s, __ldcg(a.part + (size_t)c2 * stot + j));
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) s = cadd(s, shfl_xor(s, o));
-                    if (lane == 0) a.ytil[j] = cscale(s, a.S[j]);
+                // ---- S o sum_c y_c for this CTA's columns: thread = (column, subset of the
+                //      partials), then the subsets in a fixed order
+                if (nj > 0) {
+                    const int sub = tid / nj, col = tid % nj;
+                    if (sub < nsub) {
+                        float2 s = make_float2(0.f, 0.f);
+                        for (int c2 = sub; c2 < G; c2 += nsub) s = cadd(s, __ldcg(a.part + (size_t)c2 * stot + j0 + col));
+                        yred[sub * nj + col] = s;
+                    }
+                    named_sync<kCons>();
+                    if (tid < nj) {
+                        float2 s = yred[tid];
+                        for (int u = 1; u < nsub; ++u) s = cadd(s, yred[u * nj + tid]);
+                        a.ytil[j0 + tid] = cscale(s, a.S[j0 + tid]);
+                    }
                 }
+                CH_TRACE(3);
                 if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
+                CH_TRACE(4);
                 // ---- U pass, per output pair p: the rows of a tile are split over the
                 //      consumer warps by column parts ((row in tile) x parts = 16 warps).
                 //      The vector of pair p + 1 is loaded into registers while pair p's
@@ -238,6 +361,7 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                 zload(0);
                 zstore(zbuf, a.m.ldw[0]);
                 named_sync<kCons>();
+                CH_TRACE(5);
                 for (int p = 0; p < P; ++p) {
                     const int ld = a.m.ldw[p];
                     const float2* zs = zbuf + (p & 1) * a.zs_len;
@@ -282,6 +406,7 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                     }
                 }
                 named_sync<kCons>();  // this CTA's dSigma rows are complete
+                CH_TRACE(6);
                 // ---- commutator + RK4 stage update for k in [ka, kb)
                 const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
                 const float E = (float)a.sp.Etab[2 * (int64_t)n + eoff];
@@ -319,8 +444,10 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                     }
                 }
                 named_sync<kCons>();
+                CH_TRACE(7);
                 for (int e = tid; e < nk * P; e += kCons) xs[e] = __ldcg(a.sp.X + ra + e);
                 named_sync<kCons>();
+                CH_TRACE(8);
             }
         }
         // observables of the last step: every CTA's partial is published by one more barrier
@@ -340,6 +467,12 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
 }
 
 }  // namespace
+
+#ifdef TDAGW_TRACE
+extern "C" int tdagw_debug_trace_ch(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_trace_ch, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
+}
+#endif
 
 // Host side: launch geometry, ring sizing, cooperative launch.  Returns false when the path
 // does not apply (complex128, an input pair with more than 2048 low-rank columns, U rows
@@ -370,7 +503,7 @@ bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     const int zs_len = maxw;  // even
     if (zs_len > kZPre * kCons) return false;  // the U-pass vector prefetch covers 4096 entries
     const size_t extras = 2 * (size_t)zs_len * 8 + 2 * (size_t)kmax * kCW * 8 + (size_t)kmax * P * 8 +
-                          3 * kCW * 8 + 16;
+                          (size_t)kCons * 8 + 3 * kCW * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
     if (avail < extras) return false;
     // slots of up to four U rows (fewer partial dot products per row), as long as at least
