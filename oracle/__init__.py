@@ -16,5 +16,6 @@ function.  Modules:
              the K^diag / K^off split, and an FFT form of K.x (an identity of this kernel)
   lowrank    truncated SVD of K^off, the low-rank apply, R^2 and Eckart-Young error
   channel    channel-wise truncated SVD (dense diagonal channels) and its apply
+  hhg        high-harmonic spectrum of a recorded current
   propagate  pulses, the TD-aGW right-hand side, classical RK4, observables
 """
