@@ -267,6 +267,21 @@ int tdagw_apply_lowrank_noalloc(const void* U, const void* V, int64_t ld, const 
                                 const void* diag, int64_t N, int rank, const void* x, void* y,
                                 void* stream);
 
+/* High-harmonic spectra (Sec. "SVD acceleration of TD-aGW": HHG(w) = |w int J(t) e^{-i w t} dt|^2)
+ * of B recorded currents, e.g. the J column of tdagw_observables after an angle or
+ * frequency sweep (Appendix C).  Integral by the rectangle rule over t_n = n dt,
+ * n = 0 .. steps[b].
+ *   J       host doubles; J_b(t_n) at J[(n B + b) stride] (stride 3 and J = obs + 1 for the
+ *           observables array of tdagw_observables, stride 1 for a plain rows x B array).
+ *   rows    rows of J (at least max steps + 1).
+ *   omega   host, nfreq angular frequencies;  out: host, nfreq x B, HHG_b(omega_f) at f B + b.
+ *   stream  cudaStream_t the work is queued on (NULL = legacy default stream).
+ * FP64 on the GPU; allocates and frees its device buffers; synchronises.  Errors:
+ * INVALID_ARG for NULL pointers, B, nfreq, stride or rows < 1, dt <= 0, a negative step
+ * count, or rows < max steps + 1. */
+int tdagw_hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps,
+                       double dt, const double* omega, int nfreq, double* out, void* stream);
+
 /* Wait for all work queued on the context's stream.  Reports TDAGW_ERR_TIMEOUT if a bounded
  * device-side wait of the last propagation gave up (also reported by tdagw_observables to
  * host memory and tdagw_get_state). */

@@ -68,6 +68,8 @@ _SIGS = {
     "tdagw_sync": [_P],
     "tdagw_apply_lowrank_noalloc": [_P, _P, ct.c_int64, _P, _P, ct.c_int64, ct.c_int, _P, _P, _P],
     "tdagw_adjoint": [_P, _D, _D, _D],
+    "tdagw_hhg_spectrum": [_D, ct.c_int64, ct.c_int64, ct.c_int, ct.POINTER(ct.c_int), ct.c_double, _D,
+                           ct.c_int, _D, _P],
 }
 EXPORTED = sorted(list(_SIGS) + ["tdagw_last_error", "tdagw_destroy"])
 
@@ -279,6 +281,23 @@ def tdagw_adjoint(ctx: int, dJdobs, steps_max: int, B: int):
     gp = np.empty((B, 4))
     _check(lib().tdagw_adjoint(_P(ctx), _dptr(d), _dptr(gE), _dptr(gp)))
     return gE, gp
+
+
+def tdagw_hhg_spectrum(J, steps, dt: float, omega, component: int | None = None,
+                       stream: int | None = None) -> np.ndarray:
+    """HHG spectra of B currents: J is (rows, B) or, with `component`, the (rows, B, 3)
+    observables array (component 1 = J).  Returns (nfreq, B)."""
+    J = np.ascontiguousarray(J, np.float64)
+    rows, B = J.shape[0], J.shape[1]
+    stride, off = (1, 0) if component is None else (J.shape[2], int(component))
+    flat = J.reshape(-1)[off:]
+    flat = np.ascontiguousarray(flat) if off else flat
+    st = np.ascontiguousarray(steps, np.int32)
+    w = np.ascontiguousarray(omega, np.float64)
+    out = np.empty((w.size, B))
+    _check(lib().tdagw_hhg_spectrum(_dptr(flat), rows, stride, B, st.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                    float(dt), _dptr(w), w.size, _dptr(out), _P(stream or 0)))
+    return out
 
 
 def tdagw_sync(ctx: int):

@@ -604,6 +604,17 @@ int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int
     });
 }
 
+int tdagw_hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps, double dt,
+                       const double* omega, int nfreq, double* out, void* stream) {
+    return guard([&] {
+        TDAGW_REQUIRE(J && steps && omega && out, TDAGW_ERR_INVALID_ARG, "NULL argument");
+        TDAGW_REQUIRE(B >= 1 && nfreq >= 1 && stride >= 1 && rows >= 1 && dt > 0, TDAGW_ERR_INVALID_ARG,
+                      "need B, nfreq, stride, rows >= 1 and dt > 0");
+        for (int b = 0; b < B; ++b) TDAGW_REQUIRE(steps[b] >= 0, TDAGW_ERR_INVALID_ARG, "negative step count");
+        hhg_spectrum(J, rows, stride, B, steps, dt, omega, nfreq, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
 int tdagw_sync(tdagw_ctx* ctx) {
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");

@@ -347,6 +347,9 @@ void launch_ch_apply(Ctx& c, const void* x, void* y, cudaStream_t s);
 template <typename R>
 void rsvd_channels(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed,
                    double rel_tol);
+// High-harmonic spectra of B recorded currents (host arrays in and out; synchronises).
+void hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps, double dt,
+                  const double* omega, int nfreq, double* out, cudaStream_t s);
 // Persistent single-trajectory channel-wise propagation (complex64); false if not applicable.
 bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,
                           bool test_timeout, cudaStream_t s);

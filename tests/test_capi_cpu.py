@@ -65,6 +65,7 @@ def test_invalid_arguments_return_codes(lib):
     assert lib.tdagw_compress_channels(None, 1, 0, 0, 1, 0.0) == tg.ERR_INVALID_ARG
     assert lib.tdagw_set_channel_factors(None, 0, None, None, None, None, None) == tg.ERR_INVALID_ARG
     assert lib.tdagw_get_channel_factors(None, None, None, None, None, None, None) == tg.ERR_INVALID_ARG
+    assert lib.tdagw_hhg_spectrum(None, 1, 1, 1, None, 0.2, None, 1, None, None) == tg.ERR_INVALID_ARG
     lib.tdagw_destroy(None)
 
 

@@ -20,6 +20,8 @@ kernels, which are not available):
                  (Nk=1296, N=20736 -- the size of the paper's 2v+2c, 36x36 MoS2 kernel,
                  Appendix A), one trajectory, 10000 steps, truncation rank 1024 (~5%,
                  the rank the paper finds sufficient for linear absorption).
+  angle_nb4_l36  the mos2-size model driven along 60 directions (1 .. 60 degrees), strong
+                 sin^2 pulse, 2000 steps each, rank 1024: the angle-resolved HHG sweep.
   sweep_nb2_l24  two-band, 24x24 grid (N=2304), rank 256, 256 trajectories with seeded
                  pulse parameters and uneven lengths 500..4000 steps (field sweep).
   prec_nb4_l48   four-band, 48x48 grid (N=36864), rank 2048, 64 trajectories, 5000 steps.
@@ -120,6 +122,17 @@ def mos2size_channel(steps: int = 10000) -> Workload:
     "K_0^diag-ch + 5 % K_0^off-ch" kernel of the paper's TDA spectra."""
     mp = ModelParams(L=36, nb_copies=2, offsets=(0.0, 0.03, 0.0, 0.0))
     return Workload("mos2size_nb4_l36_channel", mp, 0.2, (steps,), (Pulse(),), rank=65)
+
+
+def angle_nb4_l36(B: int = 60, steps: int = 2000) -> Workload:
+    """Angle-resolved HHG sweep (Appendix C) at the mos2 size: B field directions evenly
+    spaced over 1 .. 60 degrees, strong sin^2-envelope pulse (E0 5e-3, omega 0.1, the whole
+    run long), rank 1024."""
+    mp = ModelParams(L=36, nb_copies=2, offsets=(0.0, 0.03, 0.0, 0.0))
+    th = np.deg2rad(np.linspace(1.0, 60.0, B))
+    pulses = tuple(Pulse(E0=5e-3, omega=0.1, T_pulse=steps * 0.2, dir_x=float(np.cos(a)),
+                         dir_y=float(np.sin(a)), kind=2) for a in th)
+    return Workload("angle_nb4_l36", mp, 0.2, (steps,) * B, pulses, rank=1024)
 
 
 def sweep_nb2_l24(B: int = 256) -> Workload:
