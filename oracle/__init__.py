@@ -12,8 +12,9 @@ function.  Modules:
 
   model      tight-binding stand-in for the first-principles bands: eigenpairs,
              dipoles (finite-difference Berry connection), velocity
-  kernel     screened interaction W(q), its q=0 cell average, the dense direct kernel,
-             the K^diag / K^off split, and an FFT form of K.x (an identity of this kernel)
+  kernel     screened interaction W(q), its q=0 cell average, the dense direct kernel, the
+             optional exchange term, the K^diag / K^off split (strict diagonal or k = k'
+             blocks), and an FFT form of K.x (an identity of this kernel)
   lowrank    truncated SVD of K^off, the low-rank apply, R^2 and Eckart-Young error
   channel    channel-wise truncated SVD (dense diagonal channels) and its apply
   hhg        high-harmonic spectrum of a recorded current

@@ -19,7 +19,19 @@ Readings (paper silent or garbled):
     Brillouin zone"): the average of W over the k-grid's own mini-cell, the square
     |qx|, |qy| <= h with h = pi / (L a).
   * Eq. sigma-from-k is applied to drho = rho - rho0 (dSigma = Sigma[G] - Sigma[G0]).
-  * K^diag (Sec. "SVD analysis", "n1,n2,k = n3,n4,k'") is the strict matrix diagonal.
+  * K^diag (Sec. "SVD analysis", "n1,n2,k = n3,n4,k'") is the strict matrix diagonal;
+    split_kblocks gives the other reading, the k = k' blocks of Nb^2 x Nb^2.
+
+Exchange term (Eq. bse-exchange-def at Q = 0), optional (ModelParams.exchange = lambda_x,
+0 by default):
+
+  K^x_{(k n m),(k' n' m')} = lambda_x sum_G v(G) M_nm(k, G) conj(M_n'm'(k', G)),
+  M_nm(k, G) = sum_o conj(U_k[o, n]) U_k[o, m] exp(i G . tau_o),  v(G) = 2 pi / (A |G|).
+
+Readings for the lattice model (no plane-wave basis): orbitals are points, orbital o of
+each copy at tau_o = (o mod 2) (a/2, a/2); G runs over the first two shells of reciprocal
+vectors (2 pi / a)(i, j), |i|, |j| <= 1, (i, j) != 0 (the G = 0 term, divergent at Q = 0,
+is left out as in the paper's TDA absorption kernels).
 """
 from __future__ import annotations
 
@@ -74,6 +86,31 @@ def W_matrix(p) -> np.ndarray:
     return W_of_offsets(di, dj, p)
 
 
+def exchange_vectors(model):
+    """(M, v): M (Nk, nG, Nb, Nb) = M_nm(k, G) and v (nG,) = lambda_x v(G) for the eight
+    reciprocal vectors of the exchange term (see the module header)."""
+    p = model.p
+    A = p.Nk * p.a * p.a
+    Gs = [(i, j) for i in (-1, 0, 1) for j in (-1, 0, 1) if (i, j) != (0, 0)]
+    no = model.U.shape[1]
+    tau = np.array([[(o % 2) * p.a / 2, (o % 2) * p.a / 2] for o in range(no)])
+    M = np.empty((model.Nk, len(Gs), model.Nb, model.Nb), complex)
+    v = np.empty(len(Gs))
+    for g, (i, j) in enumerate(Gs):
+        G = 2 * np.pi / p.a * np.array([i, j], float)
+        ph = np.exp(1j * tau @ G)                                    # (no,)
+        M[:, g] = np.einsum("kon,o,kom->knm", model.U.conj(), ph, model.U)
+        v[g] = p.exchange * 2 * np.pi / (A * np.linalg.norm(G))
+    return M, v
+
+
+def exchange_kernel(model) -> np.ndarray:
+    """The dense exchange term K^x (N x N), zero when lambda_x = 0."""
+    M, v = exchange_vectors(model)
+    Mf = M.reshape(model.Nk, len(v), -1).transpose(1, 0, 2).reshape(len(v), -1)   # (nG, N)
+    return np.einsum("g,gi,gj->ij", v, Mf, Mf.conj())
+
+
 def dense_kernel(model) -> np.ndarray:
     """The full N x N kernel (complex128), straight from the entry formula."""
     p, Nk, Nb = model.p, model.Nk, model.Nb
@@ -84,6 +121,8 @@ def dense_kernel(model) -> np.ndarray:
     K = -W[:, :, None, None, None, None] * O[:, :, :, None, :, None] * \
         np.conj(O)[:, :, None, :, None, :]               # [k,k',n,m,n',m']
     K = np.transpose(K, (0, 2, 3, 1, 4, 5)).reshape(Nk * Nb * Nb, Nk * Nb * Nb)
+    if getattr(p, "exchange", 0.0):
+        K = K + exchange_kernel(model)
     return np.ascontiguousarray(K)
 
 
@@ -101,7 +140,12 @@ def kernel_entry(model, row: int, col: int) -> complex:
     Uk, Ukp = model.U[k], model.U[kp]
     o1 = np.vdot(Uk[:, n], Ukp[:, n2])
     o2 = np.vdot(Ukp[:, m2], Uk[:, m])
-    return complex(-W * o1 * o2)
+    val = complex(-W * o1 * o2)
+    if getattr(p, "exchange", 0.0):
+        M, v = exchange_vectors(model)
+        for g in range(len(v)):
+            val += v[g] * M[k, g, n, m] * np.conj(M[kp, g, n2, m2])
+    return val
 
 
 def kernel_row(model, row: int) -> np.ndarray:
@@ -114,7 +158,11 @@ def kernel_row(model, row: int) -> np.ndarray:
     W = W_of_offsets(min_image(k // L - kp // L, L), min_image(k % L - kp % L, L), p)
     o1 = np.einsum("i,qip->qp", model.U[k, :, n].conj(), model.U)        # (Nk, n')
     o2 = np.einsum("qip,i->qp", model.U.conj(), model.U[k, :, m])        # (Nk, m')
-    return (-W[:, None, None] * o1[:, :, None] * o2[:, None, :]).reshape(-1)
+    row_ = (-W[:, None, None] * o1[:, :, None] * o2[:, None, :]).reshape(-1)
+    if getattr(p, "exchange", 0.0):
+        M, v = exchange_vectors(model)
+        row_ = row_ + np.einsum("g,g,qgab->qab", v, M[k, :, n, m], M.conj()).reshape(-1)
+    return row_
 
 
 def kernel_diag(model) -> np.ndarray:
@@ -122,7 +170,23 @@ def kernel_diag(model) -> np.ndarray:
     p = model.p
     W0 = cell_average_W0(np.pi / (p.L * p.a), p.Nk * p.a * p.a, p.r0)
     g = np.einsum("kin,kin->kn", model.U.conj(), model.U).real
-    return (-W0 * g[:, :, None] * g[:, None, :]).reshape(-1).astype(np.complex128)
+    d = (-W0 * g[:, :, None] * g[:, None, :]).reshape(-1).astype(np.complex128)
+    if getattr(p, "exchange", 0.0):
+        M, v = exchange_vectors(model)
+        d = d + np.einsum("g,kgab->kab", v, np.abs(M) ** 2).reshape(-1)
+    return d
+
+
+def split_kblocks(K: np.ndarray, Nb: int):
+    """The other reading of K^diag: the k = k' blocks.  Returns (B, Koff) with B
+    (Nk, P, P) the blocks K[k P + p, k P + q] (P = Nb^2) and Koff = K without them."""
+    P = Nb * Nb
+    Nk = K.shape[0] // P
+    B = np.stack([K[k * P:(k + 1) * P, k * P:(k + 1) * P] for k in range(Nk)])
+    Koff = K.copy()
+    for k in range(Nk):
+        Koff[k * P:(k + 1) * P, k * P:(k + 1) * P] = 0.0
+    return B, Koff
 
 
 def split_diag_off(K: np.ndarray):
@@ -153,11 +217,19 @@ def fft_applier(model):
     di, dj = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
     What = np.fft.fft2(W_of_offsets(min_image(di, L), min_image(dj, L), p))[:, :, None, None]
 
+    exch = bool(getattr(p, "exchange", 0.0))
+    if exch:
+        M, v = exchange_vectors(model)
+        Mf = M.reshape(model.Nk, len(v), -1).transpose(1, 0, 2).reshape(len(v), -1)   # (nG, N)
+
     def apply(x: np.ndarray) -> np.ndarray:
         X = x.reshape(model.Nk, Nb, Nb)
         Y = (U @ X @ Uh).reshape(L, L, no, no)                       # orbital basis
         Z = np.fft.ifft2(What * np.fft.fft2(Y, axes=(0, 1)), axes=(0, 1))
-        return (-(Uh @ Z.reshape(model.Nk, no, no) @ U)).reshape(-1)
+        out = (-(Uh @ Z.reshape(model.Nk, no, no) @ U)).reshape(-1)
+        if exch:   # the exchange term through its rank-nG form
+            out = out + Mf.T @ (v * (Mf.conj() @ x))
+        return out
 
     return apply
 

@@ -30,6 +30,15 @@ def apply_lowrank(diag: np.ndarray, U: np.ndarray, S: np.ndarray, V: np.ndarray,
     return diag * x + U @ (S * y)
 
 
+def apply_lowrank_kblocks(B: np.ndarray, U: np.ndarray, S: np.ndarray, V: np.ndarray,
+                          x: np.ndarray) -> np.ndarray:
+    """dSigma = K^diag x + U (S * (V^H x)) with K^diag read as the k = k' blocks B (Nk, P, P):
+    (K^diag x)[k P + p] = sum_q B[k, p, q] x[k P + q]."""
+    Nk, P = B.shape[0], B.shape[1]
+    y = V.conj().T @ x
+    return np.einsum("kpq,kq->kp", B, x.reshape(Nk, P)).reshape(-1) + U @ (S * y)
+
+
 def reconstruct(diag, U, S, V) -> np.ndarray:
     return np.diag(diag) + (U * S) @ V.conj().T
 

@@ -121,3 +121,17 @@ def test_unconjugated_v_breaks_channel_apply_pin():
                 bad[:, p] += U[p, q] @ (S[p, q] * (V[p, q].T @ xs[:, q]))
     good = oc.assemble(D, U, S, V) @ x
     assert np.abs(bad.reshape(-1) - good).max() > 1e-6 * np.abs(good).max()
+
+
+def test_exchange_orbitals_at_one_site_break_rank_pin(monkeypatch):
+    """Slip: both orbitals of a copy placed at the cell origin (no exp(i G . tau) phase).
+    Every shell then gives the same matrix elements and K^x drops to rank 1."""
+    import dataclasses
+
+    import scipy.linalg
+    m = om.Model(dataclasses.replace(wl.small_model(4, 1), exchange=1.0))
+    M, v = ok.exchange_vectors(m)
+    Mbad = np.broadcast_to(np.einsum("kon,kom->knm", m.U.conj(), m.U)[:, None], M.shape)
+    monkeypatch.setattr(ok, "exchange_vectors", lambda model: (Mbad, v))
+    ev = np.abs(scipy.linalg.eigvalsh(ok.exchange_kernel(m)))
+    assert (ev > 1e-12 * ev.max()).sum() != 2

@@ -49,6 +49,7 @@ class ModelParams:
     m: float = 0.1
     a: float = 6.0              # lattice constant (bohr)
     r0: float = 20.0            # Rytova-Keldysh screening length (bohr)
+    exchange: float = 0.0       # scale of the exchange term (0: direct kernel only)
 
     @property
     def Nb(self) -> int:
