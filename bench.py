@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--full-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid", "channel", "angle_hhg"], default=None,
+    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid", "channel", "angle_hhg", "kblock"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=None, help="step count of the --leg run")
     return ap.parse_args()
@@ -138,7 +138,7 @@ def _profiled_traffic(stages: int):
     import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2502_05635_gb300", "csrc")
-    for f in ("lr_persistent.cu", "stage.cuh"):
+    for f in ("lr_persistent.cu", "persist.cuh", "stage.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     # the device helpers of the common header (everything before its host-side sections)
     common = open(os.path.join(csrc, "common.cuh"), "rb").read()
@@ -385,6 +385,39 @@ def bench_angle_hhg(tg, torch, stream, sh, steps=2000, nfreq=512):
             "third_harmonic_vs_angle_min_max": [float(spec[h3].min()), float(spec[h3].max())]}
 
 
+def bench_kblock_split(tg, torch, stream, sh, hbm, steps=1000, cmp_steps=200):
+    """The two readings of K^diag on the direct + exchange kernel at the mos2 size (rank
+    1024 from the GPU's randomised SVD for each split): P(t) of each low-rank run against
+    the dense kernel over a prefix, and the persistent launch with the k = k' blocks."""
+    import dataclasses
+    w = wl.mos2size_nb4_l36()
+    model = dataclasses.replace(w.model, exchange=1.0)
+    ctx = tg.Context(model, tg.C64, stream=sh)
+    field = [tg.make_field(w.pulses[0])]
+    out = {"workload": "mos2size_nb4_l36 + exchange (lambda_x = 1)", "N": ctx.N, "rank": w.rank}
+    tg.tdagw_propagate(ctx.h, field, [cmp_steps], w.dt, tg.FULL, tg.FLAG_RESET)
+    full = tg.tdagw_observables(ctx.h)
+    for name, on in (("strict_diagonal", False), ("k_blocks", True)):
+        tg.tdagw_set_kdiag_blocks(ctx.h, on)
+        tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+        tg.tdagw_propagate(ctx.h, field, [cmp_steps], w.dt, tg.LOWRANK, tg.FLAG_RESET)
+        lr = tg.tdagw_observables(ctx.h)
+        out[name] = {"p_rel_err_vs_full_gpu": float(np.linalg.norm(lr[:, 0] - full[:, 0]) /
+                                                    np.linalg.norm(full[:, 0]))}
+    # k-block persistent launch (the last split installed)
+    ms = _time_propagate(tg, torch, stream, ctx, field, [steps], w.dt, tg.LOWRANK, tg.FLAG_RESET)
+    P = ctx.Nb * ctx.Nb
+    per_stage = 8 * (2 * ctx.N * (w.rank + (w.rank & 1)) + ctx.Nk * P * P + 2 * ctx.N)
+    gbs = 4 * steps * per_stage / (ms * 1e-3) / 1e9
+    out["k_blocks"].update({"value": steps / (ms * 1e-3), "unit": "steps*traj/s", "steps": steps,
+                            "bytes_per_stage": per_stage,
+                            "roofline": {"bound": "hbm", "kernel": "lr_persistent_kernel (k-block term)",
+                                         "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}})
+    out["steps_compared"] = cmp_steps
+    ctx.close()
+    return out
+
+
 # ---------------------------------------------------------------- our arm -----------
 
 def run_leg(a):
@@ -413,6 +446,8 @@ def run_leg(a):
         out = bench_channel(tg, torch, stream, sh, hbm, n or 1000)
     elif a.leg == "angle_hhg":
         out = bench_angle_hhg(tg, torch, stream, sh, n or 2000)
+    elif a.leg == "kblock":
+        out = bench_kblock_split(tg, torch, stream, sh, hbm, n or 1000)
     else:
         out = bench_tc_mid(tg, torch, stream, sh, hbm, n or 20)
     print(json.dumps({"leg": a.leg, **out}), flush=True)
@@ -567,6 +602,7 @@ def run_ours(a):
         line["adjoint"] = bench_adjoint(tg, torch, stream, sh)
         line["channel_wise"] = bench_channel(tg, torch, stream, sh, hbm)
         line["angle_hhg"] = bench_angle_hhg(tg, torch, stream, sh)
+        line["kdiag_split"] = bench_kblock_split(tg, torch, stream, sh, hbm)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -78,7 +78,12 @@ typedef struct tdagw_ctx tdagw_ctx;
  * h(k) = Delta sz + t (sin(kx a) sx + sin(ky a) sy) + m (2 - cos kx a - cos ky a) sz,
  * copy c shifted by offsets[c]; Nb = 2 nb_copies bands, lower half occupied.  W(q) is the
  * 2D Rytova-Keldysh interaction 2 pi / (A |q| (1 + r0 |q|)), A = Nk a^2, with W(0) the
- * mean over the grid's mini-cell (Appendix B). */
+ * mean over the grid's mini-cell (Appendix B).  With exchange = lambda_x > 0 the kernel
+ * also holds the exchange term of Eq. bse-exchange-def at Q = 0 for point orbitals (orbital
+ * o of each copy at (o mod 2) (a/2, a/2)) and the eight reciprocal vectors
+ * G = (2 pi / a)(i, j), |i|, |j| <= 1, G != 0:
+ *   K^x_{(k n m),(k' n' m')} = lambda_x sum_G v(G) M_nm(k, G) conj(M_n'm'(k', G)),
+ *   M_nm(k, G) = sum_o conj(U_k[o, n]) U_k[o, m] exp(i G . tau_o), v(G) = 2 pi / (A |G|). */
 typedef struct {
     int L;                /* grid is L x L, 1 <= L <= 4096                                */
     int nb_copies;        /* 1 (Nb = 2) or 2 (Nb = 4)                                     */
@@ -87,6 +92,7 @@ typedef struct {
     double a;             /* lattice constant (bohr)                                      */
     double r0;            /* screening length (bohr)                                      */
     int dtype;            /* TDAGW_C64 or TDAGW_C128                                      */
+    double exchange;      /* lambda_x >= 0: scale of the exchange term (0 = direct only)  */
 } tdagw_model_desc;
 
 /* One driving pulse (atomic units).  The field is E(t) (dir_x, dir_y) and couples as
@@ -135,13 +141,27 @@ int tdagw_get_kernel_entries(tdagw_ctx* ctx, const int64_t* rows, const int64_t*
 int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
                        uint64_t seed, int precision);
 
+/* Reading of K^diag in the low-rank form (Sec. "SVD analysis": "n1, n2, k = n3, n4, k'"):
+ * on = 0 (default) the strict matrix diagonal; on = 1 the k = k' blocks, Nb^2 x Nb^2 per
+ * k-point, so K^off = K minus those blocks and dSigma_k = B_k drho_k + (U (S o (V^H drho)))_k.
+ * Changing it removes installed low-rank factors (they split K the other way).  With on = 1,
+ * tdagw_compress_svd factors K minus the blocks, and the diag argument of tdagw_set_factors /
+ * tdagw_get_factors holds the blocks (Nk x P x P c128, block k row p column q at
+ * (k P + p) P + q, P = Nb^2; NULL in set: the blocks of the built kernel).  Supported by
+ * tdagw_apply and single-trajectory tdagw_propagate; batched propagation, checkpoints and
+ * split-FP16 factors return UNSUPPORTED while it is on.  Errors: INVALID_ARG for on not 0
+ * or 1. */
+int tdagw_set_kdiag_blocks(tdagw_ctx* ctx, int on);
+
 /* Install factors K^off ~ U diag(S) V^H from the host (c128 U, V: N x rank row-major;
- * S: rank doubles; diag: N c128 or NULL to keep diag(K) of the built kernel). */
+ * S: rank doubles; diag: N c128 or NULL to keep diag(K) of the built kernel; the k-block
+ * form of tdagw_set_kdiag_blocks when that is on). */
 int tdagw_set_factors(tdagw_ctx* ctx, int rank, const double* U, const double* S,
                       const double* V, const double* diag);
 
-/* Copy the installed factors to the host in c128 (U, V: N x rank; S: rank; diag: N).
- * *rank receives the rank; any array pointer may be NULL. */
+/* Copy the installed factors to the host in c128 (U, V: N x rank; S: rank; diag: N, or the
+ * Nk x P x P blocks with the k-block reading of K^diag).  *rank receives the rank; any array
+ * pointer may be NULL. */
 int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V, double* diag);
 
 /* Channel-wise compression (Sec. "SVD analysis of electron-hole kernel", Eq.

@@ -34,7 +34,8 @@ class TdagwError(RuntimeError):
 class ModelDesc(ct.Structure):
     _fields_ = [("L", ct.c_int), ("nb_copies", ct.c_int), ("offsets", ct.c_double * 4),
                 ("Delta", ct.c_double), ("t", ct.c_double), ("m", ct.c_double),
-                ("a", ct.c_double), ("r0", ct.c_double), ("dtype", ct.c_int)]
+                ("a", ct.c_double), ("r0", ct.c_double), ("dtype", ct.c_int),
+                ("exchange", ct.c_double)]
 
 
 class Field(ct.Structure):
@@ -56,6 +57,7 @@ _SIGS = {
     "tdagw_compress_svd": [_P, ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, ct.c_int],
     "tdagw_set_factors": [_P, ct.c_int, _D, _D, _D, _D],
     "tdagw_get_factors": [_P, ct.POINTER(ct.c_int), _D, _D, _D, _D],
+    "tdagw_set_kdiag_blocks": [_P, ct.c_int],
     "tdagw_compress_channels": [_P, ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, ct.c_double],
     "tdagw_set_channel_factors": [_P, ct.c_int, ct.POINTER(ct.c_int), _D, _D, _D, _D],
     "tdagw_get_channel_factors": [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), _D, _D, _D, _D],
@@ -164,15 +166,21 @@ def tdagw_set_factors(ctx: int, U, S, V, diag=None):
     _check(lib().tdagw_set_factors(_P(ctx), U.shape[1], _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
 
 
-def tdagw_get_factors(ctx: int):
-    N = tdagw_model_info(ctx)[0]
+def tdagw_set_kdiag_blocks(ctx: int, on: int):
+    _check(lib().tdagw_set_kdiag_blocks(_P(ctx), int(on)))
+
+
+def tdagw_get_factors(ctx: int, kblocks: bool = False):
+    """(U, S, V, diag); with kblocks (the k-block reading of K^diag is on) diag is the
+    (Nk, P, P) array of k = k' blocks."""
+    N, Nb, Nk = tdagw_model_info(ctx)
     r = ct.c_int()
     _check(lib().tdagw_get_factors(_P(ctx), ct.byref(r), None, None, None, None))
     r = r.value
     U = np.empty((N, r), np.complex128)
     V = np.empty((N, r), np.complex128)
     S = np.empty(r)
-    d = np.empty(N, np.complex128)
+    d = np.empty((Nk, Nb * Nb, Nb * Nb) if kblocks else N, np.complex128)
     _check(lib().tdagw_get_factors(_P(ctx), None, _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
     return U, S, V, d
 
@@ -315,10 +323,12 @@ def tdagw_destroy(ctx: int):
 # ---------------------------------------------------------------- convenience -----------
 
 def model_desc(p, dtype: int = C64) -> ModelDesc:
-    """ModelDesc from an object with L, nb_copies, offsets, Delta, t, m, a, r0."""
+    """ModelDesc from an object with L, nb_copies, offsets, Delta, t, m, a, r0 (and
+    optionally exchange)."""
     offs = list(p.offsets) + [0.0] * (4 - len(p.offsets))
     return ModelDesc(L=p.L, nb_copies=p.nb_copies, offsets=(ct.c_double * 4)(*offs[:4]),
-                     Delta=p.Delta, t=p.t, m=p.m, a=p.a, r0=p.r0, dtype=dtype)
+                     Delta=p.Delta, t=p.t, m=p.m, a=p.a, r0=p.r0, dtype=dtype,
+                     exchange=float(getattr(p, "exchange", 0.0)))
 
 
 def propagate_autograd(context: "Context", params, pulses, steps, dt: float, mode: int = 1):

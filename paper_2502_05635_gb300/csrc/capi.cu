@@ -98,6 +98,12 @@ template <typename R> void build(Ctx& c) {
     TDAGW_CUDA(cudaMemcpyAsync(c.Ud.p, h.U.data(), h.U.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     c.Wd.ensure(h.Wtab.size() * sizeof(double));
     TDAGW_CUDA(cudaMemcpyAsync(c.Wd.p, h.Wtab.data(), h.Wtab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (!h.Mx.empty()) {
+        c.Mxd.ensure(h.Mx.size() * sizeof(double2));
+        c.vGd.ensure(8 * sizeof(double));
+        TDAGW_CUDA(cudaMemcpyAsync(c.Mxd.p, h.Mx.data(), h.Mx.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+        TDAGW_CUDA(cudaMemcpyAsync(c.vGd.p, h.vG, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     c.K.ensure((size_t)N * (size_t)N * sizeof(cplx_t<R>));
     launch_build_kernel<R>(c, s);
     // diag(K): every (N+1)-th element
@@ -146,8 +152,22 @@ template <typename R> void set_factors(Ctx& c, int r, const double* U, const dou
     for (int j = 0; j < r; ++j) hs[j] = (R)S[j];
     c.S.ensure(r * sizeof(R));
     TDAGW_CUDA(cudaMemcpyAsync(c.S.p, hs.data(), r * sizeof(R), cudaMemcpyHostToDevice, s));
+    if (c.kdiag) {
+        // the k = k' blocks: Nk x P x P
+        const int64_t nb = (int64_t)c.hm.Nk * c.hm.Nb * c.hm.Nb * c.hm.Nb * c.hm.Nb;
+        c.kblkF.ensure(nb * sizeof(C));
+        if (diag) {
+            DevBuf t2;
+            t2.ensure(nb * sizeof(double2));
+            TDAGW_CUDA(cudaMemcpyAsync(t2.p, diag, nb * sizeof(double2), cudaMemcpyHostToDevice, s));
+            launch_convert_in<R>(t2.as<double2>(), c.kblkF.p, nb, s);
+            TDAGW_CUDA(cudaStreamSynchronize(s));
+        } else {
+            launch_gather_kblocks<R>(c, c.kblkF.p, s);
+        }
+    }
     c.diagF.ensure(N * sizeof(C));
-    if (diag) {
+    if (diag && !c.kdiag) {
         TDAGW_CUDA(cudaMemcpyAsync(tmp.p, diag, N * sizeof(double2), cudaMemcpyHostToDevice, s));
         launch_convert_in<R>(tmp.as<double2>(), c.diagF.p, N, s);
     } else {
@@ -186,7 +206,14 @@ template <typename R> void get_factors(Ctx& c, double* U, double* S, double* V, 
         TDAGW_CUDA(cudaStreamSynchronize(s));
         for (int64_t j = 0; j < r; ++j) S[j] = (double)hs[j];
     }
-    if (diag) {
+    if (diag && c.kdiag) {
+        const int64_t nb = (int64_t)c.hm.Nk * c.hm.Nb * c.hm.Nb * c.hm.Nb * c.hm.Nb;
+        DevBuf t2;
+        t2.ensure(nb * sizeof(double2));
+        launch_convert_out<R>(c.kblkF.p, t2.as<double2>(), nb, s);
+        TDAGW_CUDA(cudaMemcpyAsync(diag, t2.p, nb * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        TDAGW_CUDA(cudaStreamSynchronize(s));
+    } else if (diag) {
         launch_convert_out<R>(c.diagF.p, tmp.as<double2>(), N, s);
         TDAGW_CUDA(cudaMemcpyAsync(diag, tmp.p, N * sizeof(double2), cudaMemcpyDeviceToHost, s));
         TDAGW_CUDA(cudaStreamSynchronize(s));
@@ -206,7 +233,12 @@ template <typename R> void apply(Ctx& c, int mode, const void* x, void* y, cudaS
         const int64_t ldu = r + (r & 1);
         launch_vcols<R>(c.V.p, ldu, N, r, x, c.ypart.p, c.ysplit, s);
         launch_yreduce<R>(c.ypart.p, c.ysplit, r, c.S.p, c.ytil.p, s);
-        launch_gemv<R>(c.U.p, ldu, N, r, c.ytil.p, y, 1, c.diagF.p, x, s);
+        if (c.kdiag) {
+            launch_gemv<R>(c.U.p, ldu, N, r, c.ytil.p, y, 1, nullptr, nullptr, s);
+            launch_kblock_add<R>(c.kblkF.p, x, y, c.hm.Nk, c.hm.Nb * c.hm.Nb, s);
+        } else {
+            launch_gemv<R>(c.U.p, ldu, N, r, c.ytil.p, y, 1, c.diagF.p, x, s);
+        }
     }
 }
 
@@ -337,6 +369,8 @@ void check_desc(const tdagw_model_desc* d) {
                   "dtype must be TDAGW_C64 or TDAGW_C128");
     TDAGW_REQUIRE(d->a > 0 && d->r0 > 0 && d->Delta > 0, TDAGW_ERR_INVALID_ARG,
                   "a, r0 and Delta must be positive");
+    TDAGW_REQUIRE(d->exchange >= 0.0 && d->exchange < 1e6, TDAGW_ERR_INVALID_ARG,
+                  "exchange must be in [0, 1e6)");
 }
 
 }  // namespace
@@ -430,7 +464,17 @@ int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters
         TDAGW_REQUIRE(precision == 0 || precision == 1, TDAGW_ERR_INVALID_ARG, "precision must be 0 or 1");
         TDAGW_REQUIRE(precision == 0 || ctx->c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED,
                       "split-FP16 factors need a complex64 context");
+        TDAGW_REQUIRE(precision == 0 || !ctx->c.kdiag, TDAGW_ERR_UNSUPPORTED,
+                      "split-FP16 factors need the strict-diagonal reading of K^diag");
         ctx->c.tc_valid = false;
+        if (ctx->c.kdiag) {
+            const HostModel& h = ctx->c.hm;
+            ctx->c.kblkF.ensure((size_t)h.Nk * h.Nb * h.Nb * h.Nb * h.Nb * ctx->c.csz);
+            if (ctx->c.dtype == TDAGW_C64)
+                launch_gather_kblocks<float>(ctx->c, ctx->c.kblkF.p, ctx->c.stream);
+            else
+                launch_gather_kblocks<double>(ctx->c, ctx->c.kblkF.p, ctx->c.stream);
+        }
         DISPATCH(ctx, rsvd_compress, ctx->c, rank, oversample, power_iters, seed);
         if (precision == 1) pack_factors_tc(ctx->c);
     });
@@ -454,6 +498,19 @@ int tdagw_get_factors(tdagw_ctx* ctx, int* rank, double* U, double* S, double* V
         if (!U && !S && !V && !diag) return;
         TDAGW_REQUIRE(ctx->c.rank > 0, TDAGW_ERR_NO_FACTORS, "no factors installed");
         DISPATCH(ctx, get_factors, ctx->c, U, S, V, diag);
+    });
+}
+
+int tdagw_set_kdiag_blocks(tdagw_ctx* ctx, int on) {
+    return guard([&] {
+        TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
+        TDAGW_REQUIRE(on == 0 || on == 1, TDAGW_ERR_INVALID_ARG, "on must be 0 or 1");
+        Ctx& c = ctx->c;
+        if (c.kdiag != on) {
+            c.kdiag = on;
+            c.rank = 0;        // installed factors split K the other way
+            c.tc_valid = false;
+        }
     });
 }
 
@@ -541,6 +598,10 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
         }
         TDAGW_REQUIRE(!(flags & TDAGW_FLAG_SPLIT_F16) || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG,
                       "TDAGW_FLAG_SPLIT_F16 applies to the low-rank kernel");
+        TDAGW_REQUIRE(mode != TDAGW_LOWRANK || !ctx->c.kdiag ||
+                          (B == 1 && !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16))),
+                      TDAGW_ERR_UNSUPPORTED,
+                      "the k-block reading of K^diag runs one trajectory without checkpoints or split-FP16 factors");
         if (flags & TDAGW_FLAG_SPLIT_F16) {
             int tmax = 0;
             for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);

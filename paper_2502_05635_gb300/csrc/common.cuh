@@ -128,6 +128,10 @@ struct HostModel {
     std::vector<zd> dx, dy, vx;  // Nk * Nb * Nb
     std::vector<double> Wtab;    // L * L, W at grid offset (di, dj) (minimum image), W0 at 0
     double W0 = 0.0;
+    // exchange term (lambda_x > 0 only): M_nm(k, G) for the eight G, [k][g][n Nb + m], and
+    // lambda_x v(G)
+    std::vector<zd> Mx;
+    double vG[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double occ[4] = {0, 0, 0, 0};
     int c1 = 0;
 };
@@ -183,11 +187,15 @@ struct Ctx {
     size_t csz = 8;  // bytes per complex element
 
     // model on device (context dtype)
-    DevBuf K, diagK, dx, dy, vx, gap, Ud, Wd;
+    DevBuf K, diagK, dx, dy, vx, gap, Ud, Wd, Mxd, vGd;
     // low-rank factors K^off ~ U diag(S) V^H: U and V stored N x ldu row-major
     // (ldu = rank rounded up to even, zero pad column), S (rank, real of the dtype)
     DevBuf U, V, S, diagF;
     int rank = 0;
+    // reading of K^diag in the low-rank form: 0 the strict diagonal (diagF), 1 the k = k'
+    // blocks (kblkF: Nk x P x P, block k row p column q at (k P + p) P + q, P = Nb^2)
+    int kdiag = 0;
+    DevBuf kblkF;
     ChannelFactors ch;
     // propagation state (trajectory 0): compensated sum (Ssum + Ccomp), stage input X,
     // RK4 accumulator, dSigma, low-rank partials and projected vector
@@ -347,6 +355,12 @@ void launch_ch_apply(Ctx& c, const void* x, void* y, cudaStream_t s);
 template <typename R>
 void rsvd_channels(Ctx& c, int rank, int oversample, int power_iters, uint64_t seed,
                    double rel_tol);
+// the k = k' blocks of the built kernel into dst (Nk x P x P, context dtype)
+template <typename R>
+void launch_gather_kblocks(const Ctx& c, void* dst, cudaStream_t s);
+// y[k P + p] += sum_q B[k][p][q] x[k P + q] (context dtype; y may not alias x)
+template <typename R>
+void launch_kblock_add(const void* B, const void* x, void* y, int Nk, int P, cudaStream_t s);
 // High-harmonic spectra of B recorded currents (host arrays in and out; synchronises).
 void hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps, double dt,
                   const double* omega, int nfreq, double* out, cudaStream_t s);

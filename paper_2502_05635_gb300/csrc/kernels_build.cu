@@ -1,4 +1,5 @@
-// Device construction of the dense direct kernel (Eq. bse-direct-def for the lattice model),
+// Device construction of the dense kernel (Eq. bse-direct-def for the lattice model, plus the
+// optional exchange term of Eq. bse-exchange-def),
 // sampled reads of it, precision conversions at the boundary, and the pulse sample table.
 #include <algorithm>
 #include <cmath>
@@ -16,16 +17,22 @@ constexpr int kBuildThreads = 128;
 //   K[(k n m), (k' n' m')] = -W(k - k') O[n][n'] conj(O[m][m'])
 // row by row; consecutive threads hold consecutive k', so each row segment of the block
 // (Nb^2 complex) is adjacent to its neighbour's and the stores coalesce.
+// With the exchange term (Mx != nullptr) every entry also gets
+//   sum_g vG[g] Mx[k][g][n m] conj(Mx[k'][g][n' m'])   (Eq. bse-exchange-def, eight G).
 template <typename R, int NB>
 __global__ void __launch_bounds__(kBuildThreads)
 build_kernel_kernel(const double2* __restrict__ U, const double* __restrict__ Wtab, int L,
-                    int Nk, cplx_t<R>* __restrict__ K) {
+                    int Nk, const double2* __restrict__ Mx, const double* __restrict__ vG,
+                    cplx_t<R>* __restrict__ K) {
     using C = cplx_t<R>;
     constexpr int NB2 = NB * NB;
     __shared__ double2 Uk[NB * NB];
+    __shared__ double2 Mk[8 * NB2];
     const int k = blockIdx.y;
     const int kp = blockIdx.x * blockDim.x + threadIdx.x;
     if (threadIdx.x < NB * NB) Uk[threadIdx.x] = U[(size_t)k * NB * NB + threadIdx.x];
+    if (Mx)
+        for (int e = threadIdx.x; e < 8 * NB2; e += blockDim.x) Mk[e] = Mx[(size_t)k * 8 * NB2 + e];
     __syncthreads();
     if (kp >= Nk) return;
     double2 Ukp[NB * NB];
@@ -56,7 +63,12 @@ build_kernel_kernel(const double2* __restrict__ U, const double* __restrict__ Wt
             for (int np = 0; np < NB; ++np)
 #pragma unroll
                 for (int mp = 0; mp < NB; ++mp) {
-                    const double2 v = cscale(cmulc(O[n][np], O[m][mp]), w);
+                    double2 v = cscale(cmulc(O[n][np], O[m][mp]), w);
+                    if (Mx) {
+                        const double2* Mkp = Mx + (size_t)kp * 8 * NB2 + np * NB + mp;
+                        for (int g = 0; g < 8; ++g)
+                            v = cadd(v, cscale(cmulc(Mk[g * NB2 + n * NB + m], Mkp[g * NB2]), vG[g]));
+                    }
                     row[np * NB + mp] = mk((R)v.x, (R)v.y);
                 }
         }
@@ -142,12 +154,14 @@ void launch_build_kernel(const Ctx& c, cudaStream_t s) {
     const HostModel& hm = c.hm;
     dim3 grid((hm.Nk + kBuildThreads - 1) / kBuildThreads, hm.Nk);
     auto* K = c.K.as<cplx_t<R>>();
+    const double2* Mx = hm.Mx.empty() ? nullptr : c.Mxd.as<double2>();
+    const double* vG = hm.Mx.empty() ? nullptr : c.vGd.as<double>();
     if (hm.Nb == 2)
-        build_kernel_kernel<R, 2><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(),
-                                                                 c.Wd.as<double>(), hm.L, hm.Nk, K);
+        build_kernel_kernel<R, 2><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(), c.Wd.as<double>(), hm.L,
+                                                                 hm.Nk, Mx, vG, K);
     else
-        build_kernel_kernel<R, 4><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(),
-                                                                 c.Wd.as<double>(), hm.L, hm.Nk, K);
+        build_kernel_kernel<R, 4><<<grid, kBuildThreads, 0, s>>>(c.Ud.as<double2>(), c.Wd.as<double>(), hm.L,
+                                                                 hm.Nk, Mx, vG, K);
     check_launch("build_kernel_kernel");
 }
 

@@ -237,7 +237,53 @@ observables_kernel(const cplx_t<R>* __restrict__ X, const cplx_t<R>* __restrict_
     reduce_observables(a, b, c, red, counter, obs_row, 1.0 / (double)Nk, nullptr, 0);
 }
 
+// the k = k' blocks of K: out[(k P + p) P + q] = K[(k P + p) N + k P + q]
+template <typename R>
+__global__ void gather_kblocks_kernel(const cplx_t<R>* __restrict__ K, int64_t N, int Nk, int P,
+                                      cplx_t<R>* __restrict__ out) {
+    const int64_t n = (int64_t)Nk * P * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / (P * P), r = e % (P * P);
+        const int p = (int)(r / P), q = (int)(r % P);
+        out[e] = K[(k * P + p) * N + k * P + q];
+    }
+}
+
+// y[k P + p] += sum_q B[k][p][q] x[k P + q]: the k-block reading of K^diag x
+template <typename R>
+__global__ void kblock_add_kernel(const cplx_t<R>* __restrict__ B, const cplx_t<R>* __restrict__ x,
+                                  cplx_t<R>* __restrict__ y, int Nk, int P) {
+    using C = cplx_t<R>;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Nk * P) return;
+    const int64_t k = i / P;
+    const int p = (int)(i % P);
+    const C* b = B + (k * P + p) * P;
+    const C* xk = x + k * P;
+    C s = y[i];
+    for (int q = 0; q < P; ++q) s = cfma(b[q], xk[q], s);
+    y[i] = s;
+}
+
 }  // namespace
+
+template <typename R>
+void launch_gather_kblocks(const Ctx& c, void* dst, cudaStream_t s) {
+    const HostModel& h = c.hm;
+    gather_kblocks_kernel<R><<<152 * 4, 256, 0, s>>>(c.K.as<cplx_t<R>>(), h.N, h.Nk, h.Nb * h.Nb,
+                                                     static_cast<cplx_t<R>*>(dst));
+    check_launch("gather_kblocks_kernel");
+}
+
+template <typename R>
+void launch_kblock_add(const void* B, const void* x, void* y, int Nk, int P, cudaStream_t s) {
+    using C = cplx_t<R>;
+    const int64_t n = (int64_t)Nk * P;
+    kblock_add_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        static_cast<const C*>(B), static_cast<const C*>(x), static_cast<C*>(y), Nk, P);
+    check_launch("kblock_add_kernel");
+}
 
 template <typename R>
 void launch_gemv(const void* A, int64_t lda, int64_t nrows, int64_t ncols, const void* x,
@@ -335,6 +381,10 @@ void launch_observables_row(Ctx& c, const void* X, int64_t row, cudaStream_t s) 
     template void launch_observables_row<R>(Ctx&, const void*, int64_t, cudaStream_t);
 INST(float)
 INST(double)
+template void launch_gather_kblocks<float>(const Ctx&, void*, cudaStream_t);
+template void launch_gather_kblocks<double>(const Ctx&, void*, cudaStream_t);
+template void launch_kblock_add<float>(const void*, const void*, void*, int, int, cudaStream_t);
+template void launch_kblock_add<double>(const void*, const void*, void*, int, int, cudaStream_t);
 #undef INST
 
 }  // namespace tdagw

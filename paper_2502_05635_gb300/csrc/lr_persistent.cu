@@ -21,11 +21,14 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "persist.cuh"
 #include "stage.cuh"
 
 namespace tdagw {
 
 namespace {
+
+using namespace persist;
 
 constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
@@ -53,6 +56,7 @@ struct LRArgs {
     const float2* V;
     const float* S;
     const float2* diag;
+    const float2* kblk;  // k-block reading of K^diag (Nk x P x P), or nullptr: diag
     StageParams<float> sp;
     float2* dSw;         // dSigma written by the U pass (sp.dS reads it)
     float2* part;        // gridDim x ldu partial y vectors
@@ -67,152 +71,20 @@ struct LRArgs {
     unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// wait for the phase of the given parity; false if the budget ran out or abort was raised
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
-                                          unsigned long long budget) {
-    if (mbar_try(b, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_try(b, parity)) return true;
-        if ((i & 63) == 0) {
-            if (abort_s && *abort_s) return false;
-            if (gtimer() - t0 > budget) return false;
-        }
-    }
-}
 #ifndef TDAGW_LR_EVICT_FIRST
 #define TDAGW_LR_EVICT_FIRST 1  // factor rows streamed with an L2 evict-first policy (read once per stage)
 #endif
-__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                              uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            saddr(dst)),
-        "l"(src), "r"(bytes), "r"(saddr(bar)), "l"(policy)
-        : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            saddr(dst)),
-        "l"(src), "r"(bytes), "r"(saddr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void consumer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_release_add64(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+__device__ __forceinline__ void consumer_sync() { named_sync<kConsumers>(); }
 
-// Grid-wide barrier among the consumer threads of all CTAs.  The arrival counter only
-// grows: barrier number g (1, 2, ...) is complete once it reaches g * gridDim.x, so no
-// reset is needed and arrivals are fire-and-forget reductions at L2 (no serialised
-// round trips).  bar.sync orders this CTA's prior stores before thread 0's release
-// (cumulative); the acquire load orders the CTA's later loads after the other CTAs'
-// releases.  Returns false (and raises abort) if the barrier could not complete within
-// the budget.
-__device__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s) {
-    consumer_sync();
-    if (threadIdx.x == 0 && !*abort_s) {
-        const unsigned long long target =
-            (unsigned long long)(lgen + 1) * (gridDim.x + (unsigned)a.extra_arrivals);
-        red_release_add64(a.bar_count, 1ull);
-        if (ld_acquire64(a.bar_count) < target) {
-            const uint64_t t0 = gtimer();
-            while (ld_acquire64(a.bar_count) < target) {
-                if (gtimer() - t0 > a.wait_ns || *(volatile int*)a.err) {
-                    atomicExch(a.err, 1);
-                    *abort_s = 1;
-                    break;
-                }
-                __nanosleep(20);
-            }
-        }
-        lgen += 1;
-    }
-    consumer_sync();
-    return !*abort_s;
+// Grid-wide barrier among the consumer threads of all CTAs (monotonic arrival counter; see
+// persist::grid_sync).  Returns false (and raises abort) if it did not complete in time.
+__device__ __forceinline__ bool grid_sync(const LRArgs& a, unsigned& lgen, volatile int* abort_s) {
+    return persist::grid_sync<kConsumers>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s);
 }
 
 // Observables row `row` from the per-CTA partials (one warp; fixed summation order).
-__device__ void reduce_step_obs(const LRArgs& a, int G, int lane, int row) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int c = lane; c < G; c += 32) {
-        s0 += __ldcg(a.sp.red + 3 * c);
-        s1 += __ldcg(a.sp.red + 3 * c + 1);
-        s2 += __ldcg(a.sp.red + 3 * c + 2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) {
-        const double inv = 1.0 / (double)a.Nk;
-        double* o = a.sp.obs + 3 * (int64_t)row;
-        o[0] = s0 * inv;
-        o[1] = s1 * inv;
-        o[2] = s2 * inv;
-    }
-}
-
-// Position in the shared-memory ring: slot index and the parity of its current use.
-struct RingPos {
-    int slot;
-    uint32_t phase;
-    __device__ __forceinline__ void advance(int by, int ns) {
-        slot += by;
-        while (slot >= ns) {
-            slot -= ns;
-            phase ^= 1u;
-        }
-    }
-};
-
-// One lane waits for the tile, then the warp proceeds (bar.warp.sync orders the lanes'
-// shared-memory reads after lane 0's acquire of the mbarrier phase).
-__device__ __forceinline__ bool warp_wait_full(uint64_t* full, RingPos p, volatile int* abort_s,
-                                               unsigned long long budget, int lane) {
-    int ok = 1;
-    if (lane == 0) ok = (!*abort_s && mbar_wait(full + p.slot, p.phase, abort_s, budget)) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok && lane == 0) *abort_s = 1;
-    return ok != 0;
+__device__ __forceinline__ void reduce_step_obs(const LRArgs& a, int G, int lane, int row) {
+    reduce_obs_row(a.sp.red, G, 1.0 / (double)a.Nk, a.sp.obs + 3 * (int64_t)row, lane);
 }
 
 template <int NB>
@@ -404,12 +276,22 @@ __global__ void __launch_bounds__(kThreads, 1) lr_persistent_kernel(LRArgs a) {
                 }
                 TDAGW_TRACE_POINT(5);
                 consumer_sync();  // all partial dot products of this CTA's rows are in
-                // dSigma = sum of the parts (fixed order) + K^diag o x
+                // dSigma = sum of the parts (fixed order) + K^diag x (the strict diagonal, or
+                // the k = k' block of the row's k-point)
                 for (int row = tid; row < nrows; row += kConsumers) {
                     float2 sum = upart[row * cp];
                     for (int q = 1; q < cp; ++q) sum = cadd(sum, upart[row * cp + q]);
                     const int64_t i = ra + row;
-                    a.dSw[i] = cfma(a.diag[i], xs[row], sum);
+                    if (a.kblk) {
+                        constexpr int P = NB * NB;
+                        const int kk = row / P;
+                        const float2* bk = a.kblk + (ra + row) * P;
+#pragma unroll
+                        for (int q = 0; q < P; ++q) sum = cfma(bk[q], xs[kk * P + q], sum);
+                        a.dSw[i] = sum;
+                    } else {
+                        a.dSw[i] = cfma(a.diag[i], xs[row], sum);
+                    }
                 }
                 consumer_sync();  // this CTA's dSigma rows are complete
                 TDAGW_TRACE_POINT(6);
@@ -516,6 +398,7 @@ bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.V = c.V.as<float2>();
     a.S = c.S.as<float>();
     a.diag = c.diagF.as<float2>();
+    a.kblk = c.kdiag ? c.kblkF.as<float2>() : nullptr;
     StageParams<float>& p = a.sp;
     p.X = c.X.as<float2>();
     p.dS = c.dS.as<float2>();

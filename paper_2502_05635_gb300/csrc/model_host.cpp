@@ -170,6 +170,31 @@ void build_host_model(const tdagw_model_desc& d, HostModel& hm) {
             hm.Wtab[(size_t)di * L + dj] =
                 (di == 0 && dj == 0) ? hm.W0 : 2.0 * kPi / (A * q * (1.0 + d.r0 * q));
         }
+    // exchange: point orbitals, orbital o at (o mod 2)(a/2, a/2), so exp(i G . tau_o) =
+    // (-1)^((i + j)(o mod 2)) for G = (2 pi / a)(i, j)
+    hm.Mx.clear();
+    if (d.exchange > 0.0) {
+        hm.Mx.assign((size_t)Nk * 8 * nb * nb, 0.0);
+        int g = 0;
+        for (int i = -1; i <= 1; ++i)
+            for (int j = -1; j <= 1; ++j) {
+                if (i == 0 && j == 0) continue;
+                const double G = 2.0 * kPi / d.a * std::hypot((double)i, (double)j);
+                hm.vG[g] = d.exchange * 2.0 * kPi / (A * G);
+                const double odd = ((i + j) % 2 != 0) ? -1.0 : 1.0;
+                for (int k = 0; k < Nk; ++k)
+                    for (int n = 0; n < nb; ++n)
+                        for (int m = 0; m < nb; ++m) {
+                            zd s = 0.0;
+                            for (int o = 0; o < nb; ++o) {
+                                const double ph = (o % 2) ? odd : 1.0;
+                                s += std::conj(hm.U[((size_t)k * nb + o) * nb + n]) * hm.U[((size_t)k * nb + o) * nb + m] * ph;
+                            }
+                            hm.Mx[(((size_t)k * 8 + g) * nb + n) * nb + m] = s;
+                        }
+                ++g;
+            }
+    }
     for (int n = 0; n < 4; ++n) hm.occ[n] = n < nb / 2 ? 1.0 : 0.0;
     hm.c1 = nb / 2;
 }

@@ -1,5 +1,5 @@
 // Randomised truncated SVD of K^off = K - diag(K) on the device (setup of Eq.
-// svd_diag_offdiag).  K^off is Hermitian, so its singular triplets follow from an
+// svd_diag_offdiag; with the k-block reading of K^diag, K^off = K minus its k = k' blocks).  K^off is Hermitian, so its singular triplets follow from an
 // eigen-decomposition: sigma_j = |lambda_j|, u_j = q_j, v_j = sign(lambda_j) q_j.
 //
 // Range finder (Halko, Martinsson, Tropp 2011, randomised subspace iteration with
@@ -168,6 +168,24 @@ __global__ void sub_diag_kernel(double2* __restrict__ Y, const double2* __restri
         const int64_t i = e / l;
         const double2 di = make_double2((double)d[i].x, (double)d[i].y);
         Y[e] = csub(Y[e], cmul(di, X[e]));
+    }
+}
+
+// Y -= (k-diagonal blocks) X for X, Y (N x l, FP64, ld l): the k-block reading of K^diag
+template <typename R>
+__global__ void sub_kblock_kernel(double2* __restrict__ Y, const double2* __restrict__ X, int64_t N, int l,
+                                  const cplx_t<R>* __restrict__ B, int P) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * l;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / l, c = e % l;
+        const int64_t k = i / P;
+        const int p = (int)(i % P);
+        double2 s = Y[e];
+        for (int q = 0; q < P; ++q) {
+            const cplx_t<R> b = B[(k * P + p) * P + q];
+            s = csub(s, cmul(make_double2((double)b.x, (double)b.y), X[(k * P + q) * l + c]));
+        }
+        Y[e] = s;
     }
 }
 
@@ -442,14 +460,20 @@ void orthonormalise(Ws& w, double2* Y, int64_t N, int l, DevBuf& H, DevBuf& P2, 
     }
 }
 
-// Y = K^off X for X (N x l, FP64): the product with K in the context precision.
+// Y = K^off X for X (N x l, FP64): the product with K in the context precision; K^off is K
+// minus its strict diagonal, or minus its k = k' blocks (kblkF holds them) in k-block mode.
 template <typename R>
 void apply_koff(Ws& w, const Ctx& c, const double2* X, double2* Y, int l) {
     const int64_t N = c.hm.N;
     gemm<cplx_t<R>, double2, R, false, false>(w, (int)N, l, (int)N, c.K.as<cplx_t<R>>(), N, X, l, Y,
                                               l, kOne, kZero);
-    sub_diag_kernel<R><<<152 * 8, 256, 0, w.s>>>(Y, X, N, l, c.diagK.as<cplx_t<R>>());
-    check_launch("sub_diag_kernel");
+    if (c.kdiag) {
+        sub_kblock_kernel<R><<<152 * 8, 256, 0, w.s>>>(Y, X, N, l, c.kblkF.as<cplx_t<R>>(), c.hm.Nb * c.hm.Nb);
+        check_launch("sub_kblock_kernel");
+    } else {
+        sub_diag_kernel<R><<<152 * 8, 256, 0, w.s>>>(Y, X, N, l, c.diagK.as<cplx_t<R>>());
+        check_launch("sub_diag_kernel");
+    }
 }
 
 // Hermitian eigen-decomposition of B (n x n, FP64, overwritten by its diagonal form),

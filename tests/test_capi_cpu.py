@@ -42,8 +42,8 @@ def test_binding_names_match_header(lib):
 
 def test_struct_layouts():
     import paper_2502_05635_gb300 as tg
-    # int, int, double[4], 5 doubles, int (+ padding) and int + 7 doubles + pointer
-    assert ct.sizeof(tg.ModelDesc) == 4 + 4 + 32 + 40 + 8
+    # int, int, double[4], 5 doubles, int (+ padding), double and int + 7 doubles + pointer
+    assert ct.sizeof(tg.ModelDesc) == 4 + 4 + 32 + 40 + 8 + 8
     assert ct.sizeof(tg.Field) == 8 + 7 * 8 + 8
 
 
