@@ -34,7 +34,7 @@ def channel_block(K: np.ndarray, Nb: int, p: int, q: int) -> np.ndarray:
     return K[p::P, q::P].copy()
 
 
-def channel_block_from_model(model, p: int, q: int) -> np.ndarray:
+def channel_block_from_model(model, p: int, q: int, W: np.ndarray | None = None) -> np.ndarray:
     """K^pq straight from the kernel's entry formula, without the dense N x N kernel (for
     large grids): with p = (n1, n2), q = (n3, n4) and O_ab[k, k'] = (U_k^+ U_k')_{ab},
         K^pq[k, k'] = -W(k - k') O_{n1 n3}[k, k'] conj(O_{n2 n4}[k, k']),
@@ -45,7 +45,9 @@ def channel_block_from_model(model, p: int, q: int) -> np.ndarray:
     U = model.U
     o13 = U[:, :, n1].conj() @ U[:, :, n3].T
     o24 = U[:, :, n2].conj() @ U[:, :, n4].T
-    return -ok.W_matrix(model.p) * o13 * o24.conj()
+    if W is None:
+        W = ok.W_matrix(model.p)
+    return -W * o13 * o24.conj()
 
 
 def channel_svd(K: np.ndarray, Nb: int, rank: int):
@@ -72,6 +74,29 @@ def channel_svd(K: np.ndarray, Nb: int, rank: int):
             U[p, q] = u[:, :rank]
             S[p, q] = s[:rank]
             V[p, q] = vh[:rank].conj().T
+    return D, U, S, V
+
+
+def channel_svd_from_model(model, rank: int):
+    """channel_svd without the dense N x N kernel (large grids): every channel from the
+    kernel's entry formula (channel_block_from_model); vanishing channels keep zero factors."""
+    Nb, Nk = model.Nb, model.Nk
+    P = Nb * Nb
+    D = np.zeros((P, Nk, Nk), complex)
+    U = np.zeros((P, P, Nk, rank), complex)
+    V = np.zeros((P, P, Nk, rank), complex)
+    S = np.zeros((P, P, rank))
+    W = ok.W_matrix(model.p)
+    for p in range(P):
+        for q in range(P):
+            blk = channel_block_from_model(model, p, q, W)
+            if p == q:
+                D[p] = blk
+            elif rank > 0 and np.abs(blk).max() > 0:
+                u, s, vh = scipy.linalg.svd(blk, full_matrices=False, lapack_driver="gesdd")
+                U[p, q] = u[:, :rank]
+                S[p, q] = s[:rank]
+                V[p, q] = vh[:rank].conj().T
     return D, U, S, V
 
 

@@ -51,6 +51,23 @@ def test_channel_block_from_model_matches_dense_kernel(name, request):
                                        atol=1e-15 * np.abs(K).max())
 
 
+def test_channel_svd_from_model_matches_dense_route(k4):
+    """The large-grid route (blocks from the formula, vanishing channels skipped) gives the
+    same diagonal channels and the same truncated channels as the dense-kernel route."""
+    m, K = k4
+    r = 4
+    D1, U1, S1, V1 = oc.channel_svd(K, m.Nb, r)
+    D2, U2, S2, V2 = oc.channel_svd_from_model(m, r)
+    np.testing.assert_allclose(D2, D1, atol=1e-15)
+    np.testing.assert_allclose(S2, S1, atol=1e-14)
+    for p in range(m.Nb ** 2):
+        for q in range(m.Nb ** 2):
+            if p != q:
+                a = (U1[p, q] * S1[p, q]) @ V1[p, q].conj().T
+                b = (U2[p, q] * S2[p, q]) @ V2[p, q].conj().T
+                np.testing.assert_allclose(b, a, atol=1e-14)
+
+
 def test_apply_channel_by_scalar_loops():
     """The channel apply against the sum written out element by element (random factors,
     tiny sizes), with the conjugate on V and the dense diagonal channels."""
