@@ -148,7 +148,7 @@ int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters
  * tdagw_compress_svd factors K minus the blocks, and the diag argument of tdagw_set_factors /
  * tdagw_get_factors holds the blocks (Nk x P x P c128, block k row p column q at
  * (k P + p) P + q, P = Nb^2; NULL in set: the blocks of the built kernel).  Supported by
- * tdagw_apply and single-trajectory tdagw_propagate; batched propagation, checkpoints and
+ * tdagw_apply, tdagw_propagate (single trajectory and batched FP32) and tdagw_adjoint;
  * split-FP16 factors return UNSUPPORTED while it is on.  Errors: INVALID_ARG for on not 0
  * or 1. */
 int tdagw_set_kdiag_blocks(tdagw_ctx* ctx, int on);

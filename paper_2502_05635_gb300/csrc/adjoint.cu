@@ -12,7 +12,8 @@
 //   dJ/dx_n = lam + mu1 + mu2 + mu3 + mu4 + (direct terms of the observables at n)
 // with, per k block, for f(X) = -i [A, rho], A = diag(eps) + E D + dSigma, rho = rho0 + X:
 //   VJP(g) = i (A^+ g - g A^+) + K^H [ i (g rho^+ - rho^+ g) ],   Ebar = <g, -i [D, rho]>.
-// K^H = conj(K^diag) + V diag(S) U^H for the low-rank factors; the dense kernel of the
+// K^H = conj(K^diag) + V diag(S) U^H for the low-rank factors (with the k-block reading of
+// K^diag, its blocks conjugate-transposed); the dense kernel of the
 // model is exactly Hermitian (its builder evaluates each entry and its transpose as exact
 // conjugates), so K^H = K there.  The K^H products use the same block decomposition and
 // register-tiled products as the forward kernel (U and V exchange roles).
@@ -183,8 +184,12 @@ __global__ void __launch_bounds__(kBThreads, 1) adjoint_kernel(AdjArgs a) {
                 if (!(ok = bgrid_sync(m, gen, &abort_s))) break;
                 if (nb > 0)
                     block_gemm<false>(m.V + ra * m.ldu, m.ldu, nrows, m.r, m.Y + b0, m.Bp, nb,
-                                      a.khm + ra * m.Bp + b0, m.Bp, true, a.diagc + ra, a.mm + ra * m.Bp + b0,
-                                      sA, sB);
+                                      a.khm + ra * m.Bp + b0, m.Bp, m.kblk == nullptr, a.diagc + ra,
+                                      a.mm + ra * m.Bp + b0, sA, sB);
+                if (m.kblk) {  // K^H: the conjugate-transposed k = k' blocks
+                    __syncthreads();
+                    if (nb > 0) kblock_term<NB, true>(m.kblk, a.mm, a.khm, m.Bp, ra, nrows, b0, nb);
+                }
             } else {
                 if (nb > 0)
                     block_gemm<false>(m.K + ra * m.N, m.N, nrows, (int)m.N, a.mm + b0, m.Bp, nb,

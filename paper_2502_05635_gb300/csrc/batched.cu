@@ -185,11 +185,16 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                     a.Y[(int64_t)j * a.Bp + b] = cscale(s, a.S[j]);
                 }
                 if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
-                // D: dSigma = U Y + diag o X for this row group
+                // D: dSigma = U Y + K^diag X for this row group (the strict diagonal fused
+                // into the product, or the k = k' blocks added after it)
                 if (nb > 0)
                     block_gemm<false>(a.U + ra * a.ldu, a.ldu, nrows, a.r, a.Y + b0, a.Bp, nb,
-                                      a.dS + ra * a.Bp + b0, a.Bp, true, a.diag + ra, a.X + ra * a.Bp + b0,
-                                      sA, sB);
+                                      a.dS + ra * a.Bp + b0, a.Bp, a.kblk == nullptr, a.diag + ra,
+                                      a.X + ra * a.Bp + b0, sA, sB);
+                if (a.kblk) {
+                    __syncthreads();  // this CTA's U Y rows are written
+                    if (nb > 0) kblock_term<NB, false>(a.kblk, a.X, a.dS, a.Bp, ra, nrows, b0, nb);
+                }
             } else {
                 if (nb > 0)
                     block_gemm<false>(a.K + ra * a.N, a.N, nrows, (int)a.N, a.X + b0, a.Bp, nb,
@@ -481,6 +486,7 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     a.V = c.V.as<float2>();
     a.S = c.S.as<float>();
     a.diag = c.diagF.as<float2>();
+    a.kblk = c.kdiag ? c.kblkF.as<float2>() : nullptr;
     a.K = c.K.as<float2>();
     a.dx = c.dx.as<float2>();
     a.dy = c.dy.as<float2>();

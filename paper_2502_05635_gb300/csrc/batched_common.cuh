@@ -24,6 +24,7 @@ struct BatchArgs {
     const float2* V;      // N x ldu
     const float* S;       // r
     const float2* diag;   // N
+    const float2* kblk;   // k-block reading of K^diag (Nk x P x P, (k P + p) P + q) or nullptr
     const float2* K;      // N x N (dense mode)
     // model (per pair element)
     const float2* dx;
@@ -216,6 +217,28 @@ static __device__ void block_gemm_split(const float2* __restrict__ A, int64_t ld
                 }
             }
         if (ks > 1) __syncthreads();  // staging memory is reused by the next pass
+    }
+}
+
+// k-block reading of K^diag: out[row][b] += sum_q B_k[p][q] x[k P + q][b] (CT: the conjugate
+// transpose, conj(B_k[q][p]), for K^H) for rows [ra, ra + nrows) (whole k-points) and columns
+// [b0, b0 + nb); row = k P + p, B_k[p][q] at kblk[(k P + p) P + q].
+template <int NB, bool CT>
+static __device__ void kblock_term(const float2* __restrict__ kblk, const float2* __restrict__ x,
+                                   float2* __restrict__ out, int64_t ld, int64_t ra, int nrows, int b0, int nb) {
+    constexpr int P = NB * NB;
+    for (int e = threadIdx.x; e < nrows * nb; e += kBThreads) {
+        const int64_t row = ra + e / nb;
+        const int b = b0 + e % nb;
+        const int64_t k0 = row - row % P;
+        const int p = (int)(row % P);
+        float2 s = __ldcg(out + row * ld + b);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 bq = CT ? cconj(kblk[(k0 + q) * P + p]) : kblk[row * P + q];
+            s = cfma(bq, __ldcg(x + (k0 + q) * ld + b), s);
+        }
+        out[row * ld + b] = s;
     }
 }
 

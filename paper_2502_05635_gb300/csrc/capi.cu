@@ -598,10 +598,8 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
         }
         TDAGW_REQUIRE(!(flags & TDAGW_FLAG_SPLIT_F16) || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG,
                       "TDAGW_FLAG_SPLIT_F16 applies to the low-rank kernel");
-        TDAGW_REQUIRE(mode != TDAGW_LOWRANK || !ctx->c.kdiag ||
-                          (B == 1 && !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16))),
-                      TDAGW_ERR_UNSUPPORTED,
-                      "the k-block reading of K^diag runs one trajectory without checkpoints or split-FP16 factors");
+        TDAGW_REQUIRE(mode != TDAGW_LOWRANK || !ctx->c.kdiag || !(flags & TDAGW_FLAG_SPLIT_F16),
+                      TDAGW_ERR_UNSUPPORTED, "split-FP16 factors need the strict-diagonal reading of K^diag");
         if (flags & TDAGW_FLAG_SPLIT_F16) {
             int tmax = 0;
             for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);

@@ -136,14 +136,77 @@ def test_kblock_mode_errors_and_reset():
         tg.tdagw_propagate(c.h, [tg.make_field(q)], [5], 0.2, tg.LOWRANK)
     assert e.value.code == tg.ERR_NO_FACTORS
     tg.tdagw_compress_svd(c.h, 5, 8, 1, 1)
-    for flags, B in ((tg.FLAG_RESET, 2), (tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 1),
-                     (tg.FLAG_RESET | tg.FLAG_SPLIT_F16, 1)):
-        with pytest.raises(tg.TdagwError) as e:
-            tg.tdagw_propagate(c.h, [tg.make_field(q)] * B, [5] * B, 0.2, tg.LOWRANK, flags)
-        assert e.value.code == tg.ERR_UNSUPPORTED
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_propagate(c.h, [tg.make_field(q)] * 2, [5] * 2, 0.2, tg.LOWRANK,
+                           tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    assert e.value.code == tg.ERR_UNSUPPORTED
     with pytest.raises(tg.TdagwError) as e:
         tg.tdagw_compress_svd(c.h, 5, 8, 1, 1, precision=1)
     assert e.value.code == tg.ERR_UNSUPPORTED
     tg.tdagw_set_kdiag_blocks(c.h, False)
     tg.tdagw_compress_svd(c.h, 5, 8, 1, 1)
     c.propagate(q, 5, 0.2, tg.LOWRANK)
+
+
+def _kblock_case(L, nc, lx, rank):
+    p = dataclasses.replace(wl.small_model(L, nc), exchange=lx)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    B, Koff = ok.split_kblocks(K, p.Nb)
+    U, S, V = olr.truncated_svd(Koff, rank)
+    apply = lambda v: olr.apply_lowrank_kblocks(B, U, S, V, v)  # noqa: E731
+    BH = np.conj(np.swapaxes(B, 1, 2))
+    applyH = lambda v: (np.einsum("kpq,kq->kp", BH, v.reshape(B.shape[0], B.shape[1])).reshape(-1)  # noqa: E731
+                        + V @ (S * (U.conj().T @ v)))
+    return p, mdl, B, U, S, V, apply, applyH
+
+
+@pytest.mark.parametrize("L,nc,lx,rank", [(5, 2, 1.0, 19), (12, 1, 0.5, 29)])
+def test_kblock_batched_vs_oracle(L, nc, lx, rank):
+    """The batched FP32 path with the k-block term: four trajectories of uneven length in
+    one launch, each against the oracle with the same factors and blocks."""
+    p, mdl, B, U, S, V, apply, _ = _kblock_case(L, nc, lx, rank)
+    c = _ctx(p, tg.C64)
+    tg.tdagw_set_kdiag_blocks(c.h, True)
+    tg.tdagw_set_factors(c.h, U, S, V, B)
+    pulses = [wl.Pulse(E0=4e-3, omega=0.12, t0=8.0, sigma=4.0),
+              wl.Pulse(E0=2e-3, omega=0.09, t0=6.0, sigma=3.0, dir_x=0.6, dir_y=0.8),
+              wl.Pulse(E0=6e-3, omega=0.14, t0=5.0, sigma=2.0),
+              wl.Pulse(E0=1e-3, omega=0.11, t0=7.0, sigma=5.0, dir_x=0.0, dir_y=1.0)]
+    steps = [90, 37, 90, 61]
+    got = c.propagate_batch(pulses, steps, 0.2, tg.LOWRANK)
+    for b, (q, T) in enumerate(zip(pulses, steps)):
+        s = op.half_step_samples(q, 0.2, T)
+        ref, _ = op.rk4(mdl, apply, s, 0.2, T, direction=(q.dir_x, q.dir_y))
+        for j in range(3):
+            assert op.rel_l2(got[:T + 1, b, j], ref[:, j]) < 1e-5, (b, j)
+        assert np.all(np.isnan(got[T + 1:, b]))
+
+
+@pytest.mark.parametrize("L,nc,lx,rank", [(4, 1, 1.0, 9), (3, 2, 1.0, 20)])
+def test_kblock_adjoint_vs_oracle(L, nc, lx, rank):
+    """The discrete adjoint with the k-block term (K^H applies the conjugate-transposed
+    blocks) against the oracle adjoint: field-sample and pulse-parameter gradients."""
+    from oracle import adjoint as oa
+    p, mdl, B, U, S, V, apply, applyH = _kblock_case(L, nc, lx, rank)
+    c = _ctx(p, tg.C64)
+    tg.tdagw_set_kdiag_blocks(c.h, True)
+    tg.tdagw_set_factors(c.h, U, S, V, B)
+    pulses = [wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0),
+              wl.Pulse(E0=0.015, omega=0.11, t0=4.0, sigma=2.5, dir_x=0.6, dir_y=0.8)]
+    dt, steps = 0.2, [60, 45]
+    tg.tdagw_propagate(c.h, [tg.make_field(q) for q in pulses], steps, dt, tg.LOWRANK,
+                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
+    dJ = np.zeros((61, 2, 3))
+    refs = []
+    for b, (q, T) in enumerate(zip(pulses, steps)):
+        s = op.half_step_samples(q, dt, T)
+        obs, _ = op.rk4(mdl, apply, s, dt, T, direction=(q.dir_x, q.dir_y))
+        _, dJdP = oa.spectral_objective(obs[:, 0], dt, q.omega)
+        dJ[:T + 1, b, 0] = dJdP
+        gE = oa.adjoint(mdl, apply, applyH, s, dt, T, (q.dir_x, q.dir_y), dJdP)
+        refs.append((gE, oa.pulse_param_jacobian(q, dt, T).T @ gE))
+    gE_gpu, gp_gpu = tg.tdagw_adjoint(c.h, dJ, 60, 2)
+    for b, (T, (gE, gp)) in enumerate(zip(steps, refs)):
+        assert np.linalg.norm(gE_gpu[:2 * T + 1, b] - gE) / np.linalg.norm(gE) < 1e-4, b
+        np.testing.assert_allclose(gp_gpu[b], gp, rtol=1e-4, atol=1e-4 * np.abs(gp).max())

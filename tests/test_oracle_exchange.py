@@ -122,3 +122,18 @@ def test_strict_split_compresses_better_with_exchange():
     ss = np.sort(np.abs(scipy.linalg.eigvalsh(Koff_s)))[::-1]
     for r in (20, 51, 102):
         assert np.sum(ss[r:] ** 2) < np.sum(sb[r:] ** 2)
+
+
+def test_kblock_adjoint_operator_dot_product(mx):
+    """<u, K~ v> = <K~^H u, v> for the k-block low-rank form, with K~^H applying the
+    conjugate-transposed blocks and V S U^H."""
+    K = ok.dense_kernel(mx)
+    B, Koff = ok.split_kblocks(K, mx.Nb)
+    U, S, V = olr.truncated_svd(Koff, 11)
+    BH = np.conj(np.swapaxes(B, 1, 2))
+    rng = np.random.default_rng(8)
+    u = rng.standard_normal(mx.N) + 1j * rng.standard_normal(mx.N)
+    v = rng.standard_normal(mx.N) + 1j * rng.standard_normal(mx.N)
+    Kv = olr.apply_lowrank_kblocks(B, U, S, V, v)
+    KHu = np.einsum("kpq,kq->kp", BH, u.reshape(mx.Nk, -1)).reshape(-1) + V @ (S * (U.conj().T @ u))
+    assert abs(np.vdot(u, Kv) - np.vdot(KHu, v)) < 1e-12 * np.abs(np.vdot(u, Kv))
