@@ -12,6 +12,13 @@ and reported beside it.  `--impl reference` times the FP64 CPU oracle (the only 
 program here that computes this) on the host cores, on a bounded prefix of the same
 trajectory.
 
+Secondary legs, run after the headline region and reported in the same JSON line (each
+also alone with `--leg NAME`): `batched_sweep` (256 uneven trajectories: FP32, split-FP16
+tensor cores, dense), `precision_study` (N = 36864, rank 2048, B = 64), `adjoint`
+(checkpointed forward + backward sweep), `channel_wise` (the channel-wise compressed
+kernel at the mos2 size), `angle_hhg` (60 field directions, then their HHG spectra) and
+`kdiag_split` (the two readings of K^diag on the direct + exchange kernel).
+
 Multi-GPU (torchrun, one rank per GPU): independent replicas, one trajectory per rank
 (the single-trajectory path has no exchange step), value = sum over ranks.
 """
