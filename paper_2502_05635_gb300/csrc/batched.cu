@@ -99,7 +99,8 @@ __device__ Obs3 stage_kb(const BatchArgs& a, int k, int b, int st, float E, floa
     return ob;
 }
 
-template <int NB>
+// CH: the channel-wise mode (a separate instantiation, so the other modes' code is unchanged)
+template <int NB, bool CH>
 __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     float2* sA = sm;                       // kChunk x kLdA
@@ -153,12 +154,24 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                     o[2] = s2 / a.Nk;
                 }
             }
-            if (a.mode == TDAGW_LOWRANK) {
-                // A: partial V^H X over this row group
-                if (nb > 0)
-                    block_gemm<true>(a.V + ra * a.ldu, a.ldu, a.r, nrows, a.X + ra * a.Bp + b0, a.Bp, nb,
-                                     a.P + (int64_t)rg * a.r * a.Bp + b0, a.Bp, false, nullptr, nullptr,
-                                     sA, sB);
+            if (a.mode != TDAGW_FULL) {
+                // A: partial V^H X over this row group (channel-wise: one product per input
+                // pair q, its V segment's rows of this row group with the rows k P + q of X)
+                if constexpr (!CH) {
+                    if (nb > 0)
+                        block_gemm<true>(a.V + ra * a.ldu, a.ldu, a.r, nrows, a.X + ra * a.Bp + b0, a.Bp, nb,
+                                         a.P + (int64_t)rg * a.r * a.Bp + b0, a.Bp, false, nullptr, nullptr,
+                                         sA, sB);
+                } else if (nb > 0) {
+                    for (int q = 0; q < NB2; ++q) {
+                        const int ldv = a.chm->ldv[q];
+                        if (ldv == 0) continue;
+                        block_gemm<true>(a.Vch + a.chm->vbase[q] + (int64_t)ka * ldv, ldv, ldv, kb - ka,
+                                         a.X + (ra + q) * a.Bp + b0, (int64_t)NB2 * a.Bp, nb,
+                                         a.P + ((int64_t)rg * a.r + a.chm->sbase[q]) * a.Bp + b0, a.Bp, false,
+                                         nullptr, nullptr, sA, sB);
+                    }
+                }
                 if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
                 if (st == 0 && n > 0 && rg == 0) {
                     int p0, p1;
@@ -185,15 +198,40 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                     a.Y[(int64_t)j * a.Bp + b] = cscale(s, a.S[j]);
                 }
                 if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
-                // D: dSigma = U Y + K^diag X for this row group (the strict diagonal fused
-                // into the product, or the k = k' blocks added after it)
-                if (nb > 0)
-                    block_gemm<false>(a.U + ra * a.ldu, a.ldu, nrows, a.r, a.Y + b0, a.Bp, nb,
-                                      a.dS + ra * a.Bp + b0, a.Bp, a.kblk == nullptr, a.diag + ra,
-                                      a.X + ra * a.Bp + b0, sA, sB);
-                if (a.kblk) {
-                    __syncthreads();  // this CTA's U Y rows are written
-                    if (nb > 0) kblock_term<NB, false>(a.kblk, a.X, a.dS, a.Bp, ra, nrows, b0, nb);
+                if constexpr (!CH) {
+                    // D: dSigma = U Y + K^diag X for this row group (the strict diagonal fused
+                    // into the product, or the k = k' blocks added after it)
+                    if (nb > 0)
+                        block_gemm<false>(a.U + ra * a.ldu, a.ldu, nrows, a.r, a.Y + b0, a.Bp, nb,
+                                          a.dS + ra * a.Bp + b0, a.Bp, a.kblk == nullptr, a.diag + ra,
+                                          a.X + ra * a.Bp + b0, sA, sB);
+                    if (a.kblk) {
+                        __syncthreads();  // this CTA's U Y rows are written
+                        if (nb > 0) kblock_term<NB, false>(a.kblk, a.X, a.dS, a.Bp, ra, nrows, b0, nb);
+                    }
+                } else {
+                    // D (channel-wise), per output pair p, rows k P + p of this row group: the
+                    // dense diagonal channel with x_p over all k, then each off-diagonal
+                    // channel's U^pq with its block of S o Y added
+                    const int64_t ldo = (int64_t)NB2 * a.Bp;
+                    if (nb > 0)
+                        for (int p = 0; p < NB2; ++p) {
+                            const int ldw = a.chm->ldw[p], nl = a.chm->nlr[p];
+                            const float2* Ub = a.Uch + a.chm->ubase[p] + (int64_t)ka * ldw;
+                            float2* o = a.dS + (ra + p) * a.Bp + b0;
+                            block_gemm<false>(Ub + nl, ldw, kb - ka, a.Nk, a.X + (int64_t)p * a.Bp + b0, ldo, nb, o,
+                                              ldo, false, nullptr, nullptr, sA, sB);
+                            for (int q = 0; q < NB2; ++q) {
+                                const int z = a.choff[2 * NB2 * NB2 + p * NB2 + q];
+                                if (q == p || z == 0) continue;
+                                const int64_t yrow = a.chm->sbase[q] + a.choff[NB2 * NB2 + q * NB2 + p];
+                                block_gemm<false, true>(Ub + a.choff[p * NB2 + q], ldw, kb - ka, z,
+                                                        a.Y + yrow * a.Bp + b0, a.Bp, nb, o, ldo, false, nullptr,
+                                                        nullptr, sA, sB);
+                            }
+                        }
+                    // every CTA has read all rows of X before any CTA rewrites its rows
+                    if (!(ok = bgrid_sync(a, gen, &abort_s))) break;
                 }
             } else {
                 if (nb > 0)
@@ -466,7 +504,8 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     const int Bp = bs.Bp;
     const int64_t ldE = bs.ldE;
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
-    const int r = mode == TDAGW_LOWRANK ? c.rank : 0;
+    // channel-wise mode: S, the partials and Y span the stot columns of the V segments
+    const int r = mode == TDAGW_LOWRANK ? c.rank : (mode == TDAGW_CHANNEL ? (int)c.ch.m.stot : 0);
     const int ldu = r + (r & 1);
 
     int dev = 0, nsm = 0;
@@ -474,7 +513,9 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const size_t smem = (size_t)kGemmSmem * sizeof(float2) +
                         (size_t)(kBThreads / kTileB) * kTileB * 3 * sizeof(double);
-    const void* fn = h.Nb == 2 ? (const void*)batched_kernel<2> : (const void*)batched_kernel<4>;
+    const bool ch = mode == TDAGW_CHANNEL;
+    const void* fn = h.Nb == 2 ? (ch ? (const void*)batched_kernel<2, true> : (const void*)batched_kernel<2, false>)
+                               : (ch ? (const void*)batched_kernel<4, true> : (const void*)batched_kernel<4, false>);
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBThreads, smem));
@@ -484,8 +525,26 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
     BatchArgs a{};
     a.U = c.U.as<float2>();
     a.V = c.V.as<float2>();
-    a.S = c.S.as<float>();
+    a.S = mode == TDAGW_CHANNEL ? c.ch.S.as<float>() : c.S.as<float>();
     a.diag = c.diagF.as<float2>();
+    if (mode == TDAGW_CHANNEL) {
+        // layout tables on the device: ChMeta, then uoff, voff and z (P x P each)
+        const int P = h.Nb * h.Nb;
+        std::vector<int> tab(3 * P * P);
+        for (int e = 0; e < P * P; ++e) {
+            tab[e] = c.ch.uoff[e];
+            tab[P * P + e] = c.ch.voff[e];
+            tab[2 * P * P + e] = c.ch.z[e];
+        }
+        c.bchm.ensure(sizeof(ChMeta) + tab.size() * sizeof(int));
+        TDAGW_CUDA(cudaMemcpyAsync(c.bchm.p, &c.ch.m, sizeof(ChMeta), cudaMemcpyHostToDevice, s));
+        TDAGW_CUDA(cudaMemcpyAsync(static_cast<char*>(c.bchm.p) + sizeof(ChMeta), tab.data(), tab.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+        a.Vch = c.ch.V.as<float2>();
+        a.Uch = c.ch.U.as<float2>();
+        a.chm = c.bchm.as<ChMeta>();
+        a.choff = reinterpret_cast<const int*>(static_cast<char*>(c.bchm.p) + sizeof(ChMeta));
+    }
     a.kblk = c.kdiag ? c.kblkF.as<float2>() : nullptr;
     a.K = c.K.as<float2>();
     a.dx = c.dx.as<float2>();

@@ -26,6 +26,12 @@ struct BatchArgs {
     const float2* diag;   // N
     const float2* kblk;   // k-block reading of K^diag (Nk x P x P, (k P + p) P + q) or nullptr
     const float2* K;      // N x N (dense mode)
+    // channel-wise mode (Eq. svd-channel-wise): V and U segments, the layout, and the P x P
+    // tables uoff [p P + q], voff [q P + p], z [p P + q] (S, P, Y then span m->stot columns)
+    const float2* Vch;
+    const float2* Uch;
+    const ChMeta* chm;
+    const int* choff;
     // model (per pair element)
     const float2* dx;
     const float2* dy;
@@ -112,7 +118,7 @@ __device__ __forceinline__ void group_range(int Bact, int Tg, int tg, int& b0, i
 // covering 256 / ks rows with its own staged chunk; the slices' partial tiles are added in
 // fixed slice order through the (then idle) staging memory, so results are deterministic.
 // sA: kChunk x kLdA float2 followed by sB: kKSplitMax x kChunk x kTileB float2 (contiguous).
-template <bool TRANS, int LKS>
+template <bool TRANS, int LKS, bool ACC>
 static __device__ void block_gemm_split(const float2* __restrict__ A, int64_t lda, int M, int Q,
                            const float2* __restrict__ Bm, int64_t ldb, int nb,
                            float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
@@ -213,6 +219,7 @@ static __device__ void block_gemm_split(const float2* __restrict__ A, int64_t ld
                     if (b >= nb) continue;
                     float2 r = c[u][v];
                     if (accumulate_diag) r = cfma(diag[m], __ldcg(xd + (int64_t)m * ldb + b), r);
+                    if (ACC) r = cadd(r, out[(int64_t)m * ldo + b]);
                     out[(int64_t)m * ldo + b] = r;
                 }
             }
@@ -242,7 +249,8 @@ static __device__ void kblock_term(const float2* __restrict__ kblk, const float2
     }
 }
 
-template <bool TRANS>
+// ACC: add the product to out instead of overwriting it
+template <bool TRANS, bool ACC = false>
 static __device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int M, int Q,
                            const float2* __restrict__ Bm, int64_t ldb, int nb,
                            float2* __restrict__ out, int64_t ldo, bool accumulate_diag,
@@ -250,11 +258,11 @@ static __device__ void block_gemm(const float2* __restrict__ A, int64_t lda, int
                            float2* sA, float2* sB) {
     static_assert(kKSplitMax == 4, "split variants below");
     if (4 * M <= 256)
-        block_gemm_split<TRANS, 2>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
+        block_gemm_split<TRANS, 2, ACC>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
     else if (2 * M <= 256)
-        block_gemm_split<TRANS, 1>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
+        block_gemm_split<TRANS, 1, ACC>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
     else
-        block_gemm_split<TRANS, 0>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
+        block_gemm_split<TRANS, 0, ACC>(A, lda, M, Q, Bm, ldb, nb, out, ldo, accumulate_diag, diag, xd, sA, sB);
 }
 
 

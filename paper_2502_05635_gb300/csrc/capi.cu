@@ -582,10 +582,8 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
         TDAGW_REQUIRE(mode != TDAGW_CHANNEL || ctx->c.ch.valid, TDAGW_ERR_NO_FACTORS,
                       "channel mode needs channel factors (tdagw_compress_channels or "
                       "tdagw_set_channel_factors)");
-        TDAGW_REQUIRE(mode != TDAGW_CHANNEL ||
-                          (B == 1 && !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16))),
-                      TDAGW_ERR_UNSUPPORTED,
-                      "channel mode runs one trajectory without checkpoints or split-FP16 factors");
+        TDAGW_REQUIRE(mode != TDAGW_CHANNEL || !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16)),
+                      TDAGW_ERR_UNSUPPORTED, "channel mode runs without checkpoints or split-FP16 factors");
         for (int b = 0; b < B; ++b) {
             const tdagw_field& f = fields[b];
             TDAGW_REQUIRE(f.kind >= 0 && f.kind <= 3, TDAGW_ERR_INVALID_ARG, "bad field kind");

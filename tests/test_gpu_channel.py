@@ -214,11 +214,44 @@ def test_channel_errors():
         tg.tdagw_compress_channels(c.h, 17, 8, 1)
     assert e.value.code == tg.ERR_INVALID_ARG
     tg.tdagw_compress_channels(c.h, 3, 8, 1)
-    for flags, B in ((tg.FLAG_RESET, 2), (tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 1),
-                     (tg.FLAG_RESET | tg.FLAG_SPLIT_F16, 1)):
+    for flags, B in ((tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 1), (tg.FLAG_RESET | tg.FLAG_SPLIT_F16, 1),
+                     (tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 3)):
         with pytest.raises(tg.TdagwError) as e:
             tg.tdagw_propagate(c.h, [tg.make_field(q)] * B, [5] * B, 0.2, tg.CHANNEL, flags)
         assert e.value.code == tg.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("L,nc,rank", [(12, 1, 9), (6, 2, 5), (9, 2, 7)])
+def test_channel_batched_vs_oracle(L, nc, rank):
+    """B trajectories of uneven length in one batched launch with the channel-wise kernel
+    (per-channel ranks, vanishing cross-copy channels for four bands): every trajectory
+    against the oracle with the same factors, and against the single-trajectory path."""
+    p = wl.small_model(L, nc)
+    mdl = om.Model(p)
+    P = p.Nb ** 2
+    D, U, S, V = oc.channel_svd(ok.dense_kernel(mdl), p.Nb, rank)
+    ranks = np.random.default_rng(L).integers(1, rank + 1, (P, P)).astype(np.int32)
+    np.fill_diagonal(ranks, 0)
+    mask = np.arange(rank)[None, None, :] < ranks[:, :, None]
+    U, V, S = U * mask[:, :, None, :], V * mask[:, :, None, :], S * mask
+    c = _ctx(p, tg.C64)
+    tg.tdagw_set_channel_factors(c.h, U, S, V, D, ranks=ranks)
+    pulses = [wl.Pulse(E0=5e-3, omega=0.12, t0=8.0, sigma=4.0),
+              wl.Pulse(E0=2e-3, omega=0.09, t0=6.0, sigma=3.0, dir_x=0.6, dir_y=0.8),
+              wl.Pulse(E0=8e-3, omega=0.14, t0=5.0, sigma=2.0),
+              wl.Pulse(E0=1e-3, omega=0.11, t0=7.0, sigma=5.0, dir_x=0.0, dir_y=1.0),
+              wl.Pulse(E0=3e-3, omega=0.10, t0=4.0, sigma=2.5)]
+    steps = [80, 23, 80, 57, 1]
+    got = c.propagate_batch(pulses, steps, 0.2, tg.CHANNEL)
+    apply = lambda v: oc.apply_channel(D, U, S, V, v)  # noqa: E731
+    for b, (q, T) in enumerate(zip(pulses, steps)):
+        s = op.half_step_samples(q, 0.2, T)
+        ref, _ = op.rk4(mdl, apply, s, 0.2, T, direction=(q.dir_x, q.dir_y))
+        for j in range(3):
+            assert op.rel_l2(got[:T + 1, b, j], ref[:, j]) < 1e-5, (b, j)
+        assert np.all(np.isnan(got[T + 1:, b]))
+    one = c.propagate(pulses[0], steps[0], 0.2, tg.CHANNEL)
+    assert op.rel_l2(got[:, 0, 0], one[:, 0]) < 1e-6
 
 
 def test_full_size_channel_propagation():
