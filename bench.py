@@ -17,6 +17,7 @@ also alone with `--leg NAME`): `batched_sweep` (256 uneven trajectories: FP32, s
 tensor cores, dense), `precision_study` (N = 36864, rank 2048, B = 64), `adjoint`
 (checkpointed forward + backward sweep), `channel_wise` (the channel-wise compressed
 kernel at the mos2 size), `angle_hhg` (60 field directions, then their HHG spectra) and
+`channel_wise_sweep` (the field sweep with the channel-wise kernel, batched) and
 `kdiag_split` (the two readings of K^diag on the direct + exchange kernel).
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas, one trajectory per rank
@@ -53,7 +54,8 @@ def _args():
     ap.add_argument("--full-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid", "channel", "angle_hhg", "kblock"], default=None,
+    ap.add_argument("--leg", choices=["sweep", "precision", "adjoint", "tc_mid", "channel", "channel_sweep", "angle_hhg",
+                                       "kblock"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=None, help="step count of the --leg run")
     return ap.parse_args()
@@ -335,6 +337,25 @@ def bench_tc_mid(tg, torch, stream, sh, hbm, steps=20):
             "hbm_frac": gbs / hbm}
 
 
+def bench_channel_sweep(tg, torch, stream, sh):
+    """The field sweep (two-band 24 x 24, N = 2304, 256 uneven trajectories) with the
+    channel-wise kernel: dense diagonal channels, off-diagonal channels at rank 29 (5 % of
+    Nk), in one batched launch; P(t) against the batched dense kernel."""
+    w = wl.sweep_nb2_l24()
+    ctx = tg.Context(w.model, tg.C64, stream=sh)
+    tg.tdagw_compress_channels(ctx.h, 29, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    fields = [tg.make_field(p) for p in w.pulses]
+    total = int(sum(w.steps))
+    ms = _time_propagate(tg, torch, stream, ctx, fields, w.steps, w.dt, tg.CHANNEL, tg.FLAG_RESET)
+    ch = tg.tdagw_observables(ctx.h, B=w.B)
+    tg.tdagw_propagate(ctx.h, fields, list(w.steps), w.dt, tg.FULL, tg.FLAG_RESET)
+    full = tg.tdagw_observables(ctx.h, B=w.B)
+    ctx.close()
+    return {"workload": "sweep_nb2_l24, channel-wise rank 29", "N": w.model.N, "B": w.B, "traj_steps": total,
+            "value": total / (ms * 1e-3), "unit": "traj*steps/s", "ms": ms,
+            "p_rel_err_vs_full_gpu": _rel_errs(ch, full, w.steps)}
+
+
 def bench_channel(tg, torch, stream, sh, hbm, steps=1000, cmp_steps=200):
     """Channel-wise kernel at the mos2 size (four-band 36 x 36, N = 20736): dense diagonal
     channels and off-diagonal channels truncated to rank 65 by the GPU's randomised channel
@@ -451,6 +472,8 @@ def run_leg(a):
         out = bench_adjoint(tg, torch, stream, sh, n or 1000)
     elif a.leg == "channel":
         out = bench_channel(tg, torch, stream, sh, hbm, n or 1000)
+    elif a.leg == "channel_sweep":
+        out = bench_channel_sweep(tg, torch, stream, sh)
     elif a.leg == "angle_hhg":
         out = bench_angle_hhg(tg, torch, stream, sh, n or 2000)
     elif a.leg == "kblock":
@@ -608,6 +631,7 @@ def run_ours(a):
         line["precision_study"] = bench_precision(tg, torch, stream, sh, hbm)
         line["adjoint"] = bench_adjoint(tg, torch, stream, sh)
         line["channel_wise"] = bench_channel(tg, torch, stream, sh, hbm)
+        line["channel_wise_sweep"] = bench_channel_sweep(tg, torch, stream, sh)
         line["angle_hhg"] = bench_angle_hhg(tg, torch, stream, sh)
         line["kdiag_split"] = bench_kblock_split(tg, torch, stream, sh, hbm)
     if rank == 0:

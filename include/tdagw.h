@@ -220,13 +220,14 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * With TDAGW_FLAG_SPLIT_F16 (LOWRANK, complex64, any B) the two products of Eq. svd_acc run
  * on the tensor cores with the factors split into FP16 hi + lo pairs and FP32
  * accumulation; P(t) then agrees with the FP32 path to about 1e-6 relative.
- * Mode CHANNEL (channel-wise factors) runs the single-trajectory path only (B = 1, no
- * TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16): one persistent launch for complex64 when
- * every input pair's channels hold at most 2048 columns in all, else stage-wise kernels.
+ * Mode CHANNEL (channel-wise factors) runs without TDAGW_FLAG_CHECKPOINT and
+ * TDAGW_FLAG_SPLIT_F16; for B = 1 one persistent launch for complex64 when every input
+ * pair's channels hold at most 2048 columns in all (else stage-wise kernels), for B > 1 the
+ * batched FP32 launch.
  * Errors: NO_FACTORS for LOWRANK or CHANNEL without the matching factors; NOT_BUILT before
  * tdagw_build_kernel;
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
- * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT, and for CHANNEL with B > 1,
+ * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT, and for CHANNEL with
  * TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16; INVALID_ARG for TDAGW_FLAG_SPLIT_F16 with
  * FULL. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
