@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "persist.cuh"
 #include "stage.cuh"
 
 namespace tdagw {
@@ -69,29 +70,15 @@ struct BatchArgs {
     float2* recDS;
 };
 
-__device__ __forceinline__ uint64_t gtimer_b() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_rel(unsigned long long* p) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
-}
-
-// grid barrier with a monotonic arrival counter (see lr_persistent.cu); all threads call
+// grid barrier with a monotonic arrival counter (see persist::grid_sync); all threads call
 static __device__ bool bgrid_sync(const BatchArgs& a, unsigned& gen, int* abort_s) {
     __syncthreads();
     if (threadIdx.x == 0 && !*abort_s) {
         const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
-        red_rel(a.bar);
-        const uint64_t t0 = gtimer_b();
-        while (ld_acq(a.bar) < target) {
-            if (gtimer_b() - t0 > a.wait_ns || *(volatile int*)a.err) {
+        persist::red_release_add64(a.bar, 1ull);
+        const uint64_t t0 = persist::gtimer();
+        while (persist::ld_acquire64(a.bar) < target) {
+            if (persist::gtimer() - t0 > a.wait_ns || *(volatile int*)a.err) {
                 atomicExch(a.err, 1);
                 *abort_s = 1;
                 break;

@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "batched_common.cuh"
+#include "persist.cuh"
 #include "tc_ptx.cuh"
 
 namespace tdagw {
@@ -49,6 +50,7 @@ namespace tdagw {
 namespace {
 
 using namespace batched;
+using namespace persist;
 
 constexpr int kWorkers = 256;
 constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
@@ -119,12 +121,6 @@ struct TcArgs {
     unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Optional phase timestamps (build with -DTDAGW_TRACE): one thread per CTA and role records
 // %globaltimer at the phase boundaries of stages kTraceFirst .. kTraceFirst + kTraceStages - 1
 // (points 0-6: stage start, end of A items, after barrier 1, end of B, after barrier 2, end
@@ -137,7 +133,7 @@ __device__ unsigned long long g_trace_tc[160 * kTraceStages * 9];
     do {                                                                                         \
         const int ts_ = 4 * n + st - kTraceFirst;                                                \
         if ((who) && blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                         \
-            g_trace_tc[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] = gtime();                   \
+            g_trace_tc[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] = gtimer();                   \
     } while (0)
 // per-chunk timestamps of phase A in CTA 0, stage kTraceFirst + 1, first item:
 // [chunk][0] MMA thread has the chunk's tiles and B block, [1] its MMAs are issued,
@@ -147,18 +143,18 @@ __device__ unsigned long long g_trace_a[64 * 4];
 #define TC_TRACE_A(who, cc, k)                                                                   \
     do {                                                                                         \
         if ((who) && blockIdx.x == 0 && 4 * n + st == kTraceFirst + 1 && item == (int)blockIdx.x && (cc) < 64) \
-            g_trace_a[(cc) * 4 + (k)] = gtime();                                                 \
+            g_trace_a[(cc) * 4 + (k)] = gtimer();                                                 \
     } while (0)
 // wait/issue time accumulators per CTA and traced stage: [0] MMA thread waiting for tiles,
 // [1] for B blocks, [2] for a free accumulator, [3] issuing MMAs and commits, [4] copy
 // thread waiting for a free slot, [5] issuing copies
 __device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
-#define TC_W_BEGIN(id) const uint64_t tw_##id = gtime()
+#define TC_W_BEGIN(id) const uint64_t tw_##id = gtimer()
 #define TC_W_END(id, k)                                                                          \
     do {                                                                                         \
         const int ts_ = 4 * n + st - kTraceFirst;                                                \
         if (blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                                  \
-            g_trace_w[(blockIdx.x * kTraceStages + ts_) * 6 + (k)] += gtime() - tw_##id;         \
+            g_trace_w[(blockIdx.x * kTraceStages + ts_) * 6 + (k)] += gtimer() - tw_##id;         \
     } while (0)
 #else
 #define TC_TRACE(who, k) \
@@ -175,32 +171,12 @@ __device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
     } while (0)
 #endif
 
-__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mb_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
-}
 // non-blocking test (copy and MMA threads poll) and potentially blocking test (workers:
 // the hardware may suspend the thread until the phase completes)
 __device__ __forceinline__ bool mb_test(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(tc::smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(tc::smem_u32(b)), "r"(parity)
@@ -214,41 +190,19 @@ __device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
 template <bool POLL>
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
                                         unsigned long long budget) {
-    if (POLL ? mb_test(b, parity) : mb_try(b, parity)) return true;
-    const uint64_t t0 = gtime();
+    if (POLL ? mb_test(b, parity) : mbar_try(b, parity)) return true;
+    const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
-        if (POLL ? mb_test(b, parity) : mb_try(b, parity)) return true;
+        if (POLL ? mb_test(b, parity) : mbar_try(b, parity)) return true;
         if ((i & 63) == 0) {
             if (abort_s && *abort_s) return false;
-            if (gtime() - t0 > budget) return false;
+            if (gtimer() - t0 > budget) return false;
         }
     }
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            tc::smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
-        : "memory");
 }
 #ifndef TDAGW_TC_EVICT_FIRST
 #define TDAGW_TC_EVICT_FIRST 1  // factor tiles are streamed with an L2 evict-first policy
 #endif
-// bulk copy with an L2 cache policy (factor tiles: read once per stage, should not displace
-// the reused state, partials and S o Y tiles)
-__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                               uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            tc::smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar)), "l"(policy)
-        : "memory");
-}
-__device__ __forceinline__ uint64_t evict_first_policy() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 __device__ __forceinline__ void workers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
 }
@@ -271,10 +225,10 @@ __device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
     __syncthreads();
     if (threadIdx.x == 0 && !*abort_s) {
         const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
-        red_rel(a.bar);
-        const uint64_t t0 = gtime();
-        while (ld_acq(a.bar) < target) {
-            if (gtime() - t0 > a.wait_ns || *(volatile int*)a.err) {
+        red_release_add64(a.bar, 1ull);
+        const uint64_t t0 = gtimer();
+        while (ld_acquire64(a.bar) < target) {
+            if (gtimer() - t0 > a.wait_ns || *(volatile int*)a.err) {
                 atomicExch(a.err, 1);
                 *abort_s = 1;
                 break;
@@ -450,14 +404,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 
     if (tid == 0) {
         abort_s = 0;
-        for (int s = 0; s < kRing; ++s) mb_init(full + s, 1);
-        for (int s = 0; s < kCmb; ++s) mb_init(cmb + s, 1);
-        for (int s = 0; s < kBBuf; ++s) mb_init(bfull + s, kWorkers);
+        for (int s = 0; s < kRing; ++s) mbar_init(full + s, 1);
+        for (int s = 0; s < kCmb; ++s) mbar_init(cmb + s, 1);
+        for (int s = 0; s < kBBuf; ++s) mbar_init(bfull + s, kWorkers);
         for (int s = 0; s < 2; ++s) {
-            mb_init(accf + s, 1);
-            mb_init(acce + s, kWorkers);
+            mbar_init(accf + s, 1);
+            mbar_init(acce + s, kWorkers);
         }
-        mb_init(fin, 1);
+        mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
@@ -488,7 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         return poll ? mb_wait<true>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget)
                     : mb_wait<TDAGW_TC_WORKER_POLL != 0>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
     };
-    const uint64_t ef_policy = TDAGW_TC_EVICT_FIRST ? evict_first_policy() : 0ull;
+    const uint64_t ef_policy = TDAGW_TC_EVICT_FIRST ? policy_evict_first() : 0ull;
     // producer: one tile of chunk gch into the next ring slot (factor tiles may carry an
     // evict-first L2 policy)
     auto issue = [&](const unsigned char* src, bool factor) {
@@ -499,11 +453,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             return;
         }
         slot_ch[slot] = gch;
-        mb_expect_tx(full + slot, kTile);
+        mbar_expect_tx(full + slot, kTile);
         if (TDAGW_TC_EVICT_FIRST && factor)
-            bulk_load_hint(ring + slot * kTile, src, kTile, full + slot, ef_policy);
+            bulk_g2s_hint(ring + slot * kTile, src, kTile, full + slot, ef_policy);
         else
-            bulk_load(ring + slot * kTile, src, kTile, full + slot);
+            bulk_g2s(ring + slot * kTile, src, kTile, full + slot);
         ++ppos;
     };
     // MMA thread: wait for the next tile; returns its shared-memory address (0 on failure)
@@ -633,7 +587,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             }
                         }
                         tc::fence_proxy_async();
-                        mb_arrive(bfull + bs);
+                        mbar_arrive(bfull + bs);
                         TC_TRACE_A(wt == 0, c - it.c0, 3);
                         ++bu;
                         ++gch;
@@ -696,7 +650,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     }
                     workers_sync();  // staging reads done before the next item's B blocks
                     tc::fence_before_sync();
-                    for (int u = 0; u < nuse; ++u) mb_arrive(acce + ((acnt + u) & 1u));
+                    for (int u = 0; u < nuse; ++u) mbar_arrive(acce + ((acnt + u) & 1u));
                     TC_TRACE_A(wt == 0, 63, 1);
                     acnt += nuse;
                 }
@@ -892,7 +846,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         }
                     }
                     tc::fence_before_sync();
-                    mb_arrive(acce + ab);
+                    mbar_arrive(acce + ab);
                     ++acnt;
                     if (kg < kgroups) {
                         atomicMax(smx + bl, __float_as_uint(xm));
