@@ -135,3 +135,32 @@ def test_exchange_orbitals_at_one_site_break_rank_pin(monkeypatch):
     monkeypatch.setattr(ok, "exchange_vectors", lambda model: (Mbad, v))
     ev = np.abs(scipy.linalg.eigvalsh(ok.exchange_kernel(m)))
     assert (ev > 1e-12 * ev.max()).sum() != 2
+
+
+def test_field_samples_shifted_half_step_break_commuting_closed_form(monkeypatch):
+    """Slip: stage samples taken half a step early (E((j - 1) dt / 2)): the time-dependent
+    commuting closed form then converges at first order only."""
+    import copy
+    import scipy.integrate
+    import scipy.linalg
+
+    def shifted(pulse, dt, T):
+        return np.array([op.field_value(pulse, 0.5 * (j - 1) * dt) for j in range(2 * T + 1)])
+    monkeypatch.setattr(op, "half_step_samples", shifted)
+    mdl = om.Model(wl.small_model(3, 1))
+    m0 = copy.copy(mdl)
+    m0.eps = np.zeros_like(mdl.eps)
+    pulse = wl.Pulse(E0=0.05, omega=0.3, t0=8.0, sigma=3.0)
+    th, Ttot = (0.6, 0.8), 16.0
+    A = scipy.integrate.quad(lambda t: op.field_value(pulse, t), 0.0, Ttot, epsabs=1e-14, limit=200)[0]
+    rho0 = mdl.rho0()
+    D = th[0] * mdl.dx + th[1] * mdl.dy
+    exact = np.array([scipy.linalg.expm(-1j * A * D[k]) @ rho0[k] @ scipy.linalg.expm(1j * A * D[k])
+                      for k in range(mdl.Nk)])
+    errs = []
+    for dt in (0.4, 0.2, 0.1):
+        T = int(round(Ttot / dt))
+        _, x = op.rk4(m0, lambda v: np.zeros_like(v), op.half_step_samples(pulse, dt, T), dt, T, direction=th)
+        errs.append(np.abs(rho0 + x.reshape(mdl.Nk, mdl.Nb, mdl.Nb) - exact).max())
+    assert errs[2] > 1e-9 or not all(12.0 < a / b < 20.0 for a, b in zip(errs, errs[1:]))
+    assert errs[0] / errs[1] < 4.0
