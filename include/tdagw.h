@@ -193,7 +193,7 @@ int tdagw_compress_channels(tdagw_ctx* ctx, int rank, int oversample, int power_
  *   S      P x P x rank, S^pq[j] at (p P + q) rank + j.
  *   D      P x Nk x Nk, K^pp[k, k'] at (p Nk + k) Nk + k'; NULL: taken from the built kernel.
  * Errors: INVALID_ARG for ranks out of range or a NULL factor array with rank > 0;
- * NOT_BUILT when D is NULL before tdagw_build_kernel. */
+ * NOT_BUILT before tdagw_build_kernel (the layout takes Nb and Nk from the built model). */
 int tdagw_set_channel_factors(tdagw_ctx* ctx, int rank, const int* ranks, const double* U,
                               const double* S, const double* V, const double* D);
 

@@ -530,9 +530,9 @@ int tdagw_set_channel_factors(tdagw_ctx* ctx, int rank, const int* ranks, const 
                               const double* S, const double* V, const double* D) {
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
+        require_built(ctx->c);  // the channel layout takes Nb and Nk from the built model
         TDAGW_REQUIRE(rank >= 0 && rank <= ctx->c.hm.Nk, TDAGW_ERR_INVALID_ARG, "need 0 <= rank <= Nk");
         TDAGW_REQUIRE(rank == 0 || (U && S && V), TDAGW_ERR_INVALID_ARG, "NULL factor array");
-        if (!D) require_built(ctx->c);
         DISPATCH(ctx, set_channel_factors, ctx->c, rank, ranks, U, S, V, D);
     });
 }

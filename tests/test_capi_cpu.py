@@ -75,3 +75,89 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(tg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(tg.TdagwError):
         tg.lib()
+
+
+def test_unbuilt_context_host_checks(lib):
+    """A created but unbuilt context: queries that need no model answer, everything that
+    needs the built model returns NOT_BUILT, and argument checks come before any CUDA call."""
+    import numpy as np
+
+    import paper_2502_05635_gb300 as tg
+    import workloads as wl
+    D = ct.POINTER(ct.c_double)
+    buf = (ct.c_double * 64)()
+    dp = ct.cast(buf, D)
+    h = ct.c_void_p()
+    d = tg.model_desc(wl.small_model(4, 1))
+    assert lib.tdagw_create(ct.byref(d), None, ct.byref(h)) == tg.OK
+    try:
+        N, Nb, Nk = ct.c_int64(), ct.c_int(), ct.c_int()
+        assert lib.tdagw_model_info(h, ct.byref(N), ct.byref(Nb), ct.byref(Nk)) == tg.OK
+        assert (N.value, Nb.value, Nk.value) == (64, 2, 16)
+        rows = (ct.c_int64 * 1)(0)
+        assert lib.tdagw_get_model(h, None, None, None, None, None) == tg.ERR_NOT_BUILT
+        assert "tdagw_build_kernel" in tg.tdagw_last_error()
+        assert lib.tdagw_get_kernel_entries(h, rows, rows, 1, dp) == tg.ERR_NOT_BUILT
+        assert lib.tdagw_compress_svd(h, 4, 0, 0, 1, 0) == tg.ERR_NOT_BUILT
+        assert lib.tdagw_set_factors(h, 1, dp, dp, dp, None) == tg.ERR_NOT_BUILT
+        assert lib.tdagw_compress_channels(h, 1, 0, 0, 1, 0.0) == tg.ERR_NOT_BUILT
+        # dense diagonal channels given: the layout still needs the built model's sizes
+        assert lib.tdagw_set_channel_factors(h, 0, None, None, None, None, dp) == tg.ERR_NOT_BUILT
+        x = (ct.c_double * 8)()
+        y = (ct.c_double * 8)()
+        assert lib.tdagw_apply(h, tg.FULL, ct.cast(x, ct.c_void_p), ct.cast(y, ct.c_void_p)) == tg.ERR_NOT_BUILT
+        f = tg.Field(kind=1, E0=1e-3, dir_x=1.0)
+        st = (ct.c_int * 1)(4)
+        assert lib.tdagw_propagate(h, ct.byref(f), 1, st, 0.2, tg.FULL, 0) == tg.ERR_NOT_BUILT
+        assert lib.tdagw_adjoint(h, dp, None, None) == tg.ERR_NOT_BUILT
+        step = ct.c_int64(-1)
+        assert lib.tdagw_get_state(h, None, None, ct.byref(step)) == tg.ERR_NOT_BUILT
+        assert lib.tdagw_set_state(h, dp, None, 0) == tg.ERR_NOT_BUILT
+        # factor queries: no factors yet
+        r = ct.c_int(-1)
+        assert lib.tdagw_get_factors(h, ct.byref(r), None, None, None, None) == tg.OK and r.value == 0
+        assert lib.tdagw_get_factors(h, ct.byref(r), dp, None, None, None) == tg.ERR_NO_FACTORS
+        r.value = -1
+        assert lib.tdagw_get_channel_factors(h, ct.byref(r), None, None, None, None, None) == tg.OK
+        assert r.value == 0
+        assert lib.tdagw_get_channel_factors(h, ct.byref(r), None, dp, None, None, None) == tg.ERR_NO_FACTORS
+        nrows = ct.c_int64(-1)
+        assert lib.tdagw_observables(h, None, 0, ct.byref(nrows), 1) == tg.OK and nrows.value == 0
+        # the K^diag switch is a host flag
+        assert lib.tdagw_set_kdiag_blocks(h, 2) == tg.ERR_INVALID_ARG
+        assert lib.tdagw_set_kdiag_blocks(h, 1) == tg.OK
+        assert lib.tdagw_set_kdiag_blocks(h, 0) == tg.OK
+        # propagate argument checks come after the build check
+        assert lib.tdagw_propagate(h, ct.byref(f), 0, st, 0.2, tg.FULL, 0) == tg.ERR_NOT_BUILT
+    finally:
+        lib.tdagw_destroy(h)
+
+
+def test_hhg_and_noalloc_argument_checks(lib):
+    """Host-side checks of the two context-free entry points (no pointer is dereferenced)."""
+    import paper_2502_05635_gb300 as tg
+    D = ct.POINTER(ct.c_double)
+    J = ct.cast((ct.c_double * 16)(), D)
+    w = ct.cast((ct.c_double * 2)(), D)
+    out = ct.cast((ct.c_double * 2)(), D)
+    st = (ct.c_int * 1)(5)
+    # rows must cover steps + 1 recorded samples
+    assert lib.tdagw_hhg_spectrum(J, 3, 1, 1, st, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
+    assert "rows" in tg.tdagw_last_error()
+    neg = (ct.c_int * 1)(-1)
+    assert lib.tdagw_hhg_spectrum(J, 6, 1, 1, neg, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
+    assert lib.tdagw_hhg_spectrum(J, 6, 1, 1, st, 0.0, w, 2, out, None) == tg.ERR_INVALID_ARG
+    assert lib.tdagw_hhg_spectrum(J, 6, 0, 1, st, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
+    # allocation-free apply: addresses are only checked, never read
+    a16, b16, s16, odd = 0x10000, 0x20000, 0x30000, 0x10008
+    f = lib.tdagw_apply_lowrank_noalloc
+    assert f(None, b16, 8, s16, s16, 64, 8, a16, b16, None) == tg.ERR_INVALID_ARG
+    assert f(a16, b16, 8, s16, s16, 0, 8, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert f(a16, b16, 8, s16, s16, 64, 0, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert f(a16, b16, 8, s16, s16, 64, 4096, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert f(a16, b16, 7, s16, s16, 64, 6, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert f(a16, b16, 4, s16, s16, 64, 6, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert f(odd, b16, 8, s16, s16, 64, 8, a16 + 0x100, b16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert "aligned" in tg.tdagw_last_error()
+    assert f(a16, b16, 8, s16, s16, 64, 8, a16 + 0x100, a16 + 0x100, None) == tg.ERR_INVALID_ARG
+    assert "alias" in tg.tdagw_last_error()
