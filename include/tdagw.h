@@ -298,8 +298,8 @@ int tdagw_apply_lowrank_noalloc(const void* U, const void* V, int64_t ld, const 
  *   omega   host, nfreq angular frequencies;  out: host, nfreq x B, HHG_b(omega_f) at f B + b.
  *   stream  cudaStream_t the work is queued on (NULL = legacy default stream).
  * FP64 on the GPU; allocates and frees its device buffers; synchronises.  Errors:
- * INVALID_ARG for NULL pointers, B, nfreq, stride or rows < 1, dt <= 0, a negative step
- * count, or rows < max steps + 1. */
+ * INVALID_ARG for NULL pointers, B, nfreq, stride or rows < 1, B > 65535, dt <= 0, a
+ * negative step count, or rows < max steps + 1. */
 int tdagw_hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps,
                        double dt, const double* omega, int nfreq, double* out, void* stream);
 

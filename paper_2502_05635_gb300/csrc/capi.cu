@@ -667,6 +667,7 @@ int tdagw_hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, con
         TDAGW_REQUIRE(J && steps && omega && out, TDAGW_ERR_INVALID_ARG, "NULL argument");
         TDAGW_REQUIRE(B >= 1 && nfreq >= 1 && stride >= 1 && rows >= 1 && dt > 0, TDAGW_ERR_INVALID_ARG,
                       "need B, nfreq, stride, rows >= 1 and dt > 0");
+        TDAGW_REQUIRE(B <= 65535, TDAGW_ERR_INVALID_ARG, "B must be at most 65535");
         for (int b = 0; b < B; ++b) TDAGW_REQUIRE(steps[b] >= 0, TDAGW_ERR_INVALID_ARG, "negative step count");
         hhg_spectrum(J, rows, stride, B, steps, dt, omega, nfreq, out, static_cast<cudaStream_t>(stream));
     });

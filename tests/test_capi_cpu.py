@@ -148,6 +148,8 @@ def test_hhg_and_noalloc_argument_checks(lib):
     assert lib.tdagw_hhg_spectrum(J, 6, 1, 1, neg, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
     assert lib.tdagw_hhg_spectrum(J, 6, 1, 1, st, 0.0, w, 2, out, None) == tg.ERR_INVALID_ARG
     assert lib.tdagw_hhg_spectrum(J, 6, 0, 1, st, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
+    assert lib.tdagw_hhg_spectrum(J, 6, 1, 65536, st, 0.2, w, 2, out, None) == tg.ERR_INVALID_ARG
+    assert "65535" in tg.tdagw_last_error()
     # allocation-free apply: addresses are only checked, never read
     a16, b16, s16, odd = 0x10000, 0x20000, 0x30000, 0x10008
     f = lib.tdagw_apply_lowrank_noalloc
