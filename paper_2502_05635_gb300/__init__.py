@@ -116,11 +116,29 @@ def _devptr(t) -> int:
     return t.data_ptr()
 
 
+def _need(cond: bool, msg: str):
+    """Argument check of the binding: the C side cannot see the extent of a host or device
+    array, so shapes are checked here before any pointer is passed."""
+    if not cond:
+        raise TdagwError(ERR_INVALID_ARG, msg)
+
+
+def _dev_vec(t, n: int, dtype, name: str):
+    """A contiguous CUDA-or-host tensor of n elements of dtype (device checked last)."""
+    _need(t.dtype == dtype, f"{name} must be {dtype}")
+    _need(t.is_contiguous() and t.numel() == n, f"{name} must be contiguous with {n} elements")
+
+
+# per-handle facts the binding needs for its checks: dtype, K^diag reading, last batch size
+_CTX_INFO: dict[int, dict] = {}
+
+
 # ---------------------------------------------------------------- one-to-one names ------
 
 def tdagw_create(desc: ModelDesc, stream: int | None = None) -> int:
     h = _P()
     _check(lib().tdagw_create(ct.byref(desc), _P(stream or 0), ct.byref(h)))
+    _CTX_INFO[h.value] = {"dtype": int(desc.dtype), "kdiag": 0, "B": 1}
     return h.value
 
 
@@ -159,15 +177,25 @@ def tdagw_compress_svd(ctx: int, rank: int, oversample: int = 64, power_iters: i
 
 
 def tdagw_set_factors(ctx: int, U, S, V, diag=None):
+    """U, V: (N, rank) complex; S: (rank,); diag: (N,), or (Nk, P, P) with the k-block
+    reading of K^diag, or None (taken from the built kernel)."""
     U = np.ascontiguousarray(U, np.complex128)
     V = np.ascontiguousarray(V, np.complex128)
     S = np.ascontiguousarray(S, np.float64)
     d = None if diag is None else np.ascontiguousarray(diag, np.complex128)
+    N, Nb, Nk = tdagw_model_info(ctx)
+    _need(U.ndim == 2 and U.shape[0] == N, f"U must be (N = {N}, rank)")
+    _need(V.shape == U.shape, "V must have the shape of U")
+    _need(S.shape == (U.shape[1],), "S must be (rank,)")
+    if d is not None:
+        nd = Nk * Nb ** 4 if _CTX_INFO.get(ctx, {}).get("kdiag") else N
+        _need(d.size == nd, f"diag must have {nd} entries")
     _check(lib().tdagw_set_factors(_P(ctx), U.shape[1], _dptr(U), _dptr(S), _dptr(V), _dptr(d)))
 
 
 def tdagw_set_kdiag_blocks(ctx: int, on: int):
     _check(lib().tdagw_set_kdiag_blocks(_P(ctx), int(on)))
+    _CTX_INFO.setdefault(ctx, {})["kdiag"] = int(on)
 
 
 def tdagw_get_factors(ctx: int, kblocks: bool = False):
@@ -197,9 +225,16 @@ def tdagw_set_channel_factors(ctx: int, U, S, V, D=None, ranks=None):
     V = np.ascontiguousarray(V, np.complex128)
     S = np.ascontiguousarray(S, np.float64)
     d = None if D is None else np.ascontiguousarray(D, np.complex128)
+    _, Nb, Nk = tdagw_model_info(ctx)
+    P = Nb * Nb
+    _need(U.ndim == 4 and U.shape[:3] == (P, P, Nk), f"U must be (P, P, Nk, rank) = ({P}, {P}, {Nk}, rank)")
+    _need(V.shape == U.shape, "V must have the shape of U")
+    _need(S.shape == (P, P, U.shape[3]), "S must be (P, P, rank)")
+    _need(d is None or d.shape == (P, Nk, Nk), f"D must be (P, Nk, Nk) = ({P}, {Nk}, {Nk})")
     rk = None
     if ranks is not None:
         ra = np.ascontiguousarray(ranks, np.int32)
+        _need(ra.shape == (P, P), f"ranks must be (P, P) = ({P}, {P})")
         rk = ra.ctypes.data_as(ct.POINTER(ct.c_int))
     _check(lib().tdagw_set_channel_factors(_P(ctx), U.shape[-1], rk, _dptr(U), _dptr(S), _dptr(V),
                                            _dptr(d)))
@@ -228,6 +263,13 @@ def tdagw_get_channel_factors(ctx: int, arrays: bool = True):
 
 
 def tdagw_apply(ctx: int, mode: int, x, y):
+    """y = K x on the device: x, y contiguous CUDA tensors of N complex64 (C64 context) or
+    complex128 (C128) entries."""
+    import torch
+    N = tdagw_model_info(ctx)[0]
+    dt = torch.complex128 if _CTX_INFO.get(ctx, {}).get("dtype") == C128 else torch.complex64
+    _dev_vec(x, N, dt, "x")
+    _dev_vec(y, N, dt, "y")
     _check(lib().tdagw_apply(_P(ctx), mode, _P(_devptr(x)), _P(_devptr(y))))
 
 
@@ -236,15 +278,26 @@ def make_field(pulse, table=None) -> Field:
     f = Field(kind=int(pulse.kind), E0=pulse.E0, omega=pulse.omega, t0=pulse.t0,
               sigma=pulse.sigma, T_pulse=pulse.T_pulse, dir_x=pulse.dir_x, dir_y=pulse.dir_y)
     if table is not None:
+        table = np.ascontiguousarray(table, np.float64)
         f.kind = FIELD_TABLE
         f.table = _dptr(table)
+        f._table = table  # keeps the samples alive and lets tdagw_propagate check their count
     return f
 
 
 def tdagw_propagate(ctx: int, fields, steps, dt: float, mode: int, flags: int = FLAG_RESET):
+    """B = len(fields) trajectories of steps[b] RK4 steps; a table field (make_field with a
+    table) needs E(j dt / 2) for j = 0 .. 2 steps[b]."""
+    fields, steps = list(fields), list(steps)
+    _need(len(steps) == len(fields), "one step count per field")
+    for f, n in zip(fields, steps):
+        tab = getattr(f, "_table", None)
+        if f.kind == FIELD_TABLE and tab is not None:
+            _need(tab.size >= 2 * int(n) + 1, "a table field needs 2 steps + 1 samples")
     arr = (Field * len(fields))(*fields)
     st = (ct.c_int * len(steps))(*[int(s) for s in steps])
     _check(lib().tdagw_propagate(_P(ctx), arr, len(fields), st, float(dt), mode, flags))
+    _CTX_INFO.setdefault(ctx, {})["B"] = len(fields)
 
 
 def tdagw_observables(ctx: int, out=None, B: int = 1) -> np.ndarray:
@@ -253,6 +306,10 @@ def tdagw_observables(ctx: int, out=None, B: int = 1) -> np.ndarray:
     _check(lib().tdagw_observables(_P(ctx), None, 0, ct.byref(rows), 1))
     if out is None:
         out = np.empty((rows.value, 3) if B == 1 else (rows.value, B, 3))
+    last_B = _CTX_INFO.get(ctx, {}).get("B", B)
+    _need(out.dtype == np.float64 and out.flags["C_CONTIGUOUS"], "out must be C-contiguous float64")
+    _need(out.size >= min(out.shape[0], rows.value) * last_B * 3,
+          f"out rows must hold the {last_B} x 3 observables of the last propagate")
     _check(lib().tdagw_observables(_P(ctx), _dptr(out), out.shape[0], ct.byref(rows), 1))
     return out
 
@@ -269,13 +326,24 @@ def tdagw_get_state(ctx: int):
 def tdagw_set_state(ctx: int, drho, carry=None, step: int = 0):
     drho = np.ascontiguousarray(drho, np.complex128)
     c = None if carry is None else np.ascontiguousarray(carry, np.complex128)
+    N = tdagw_model_info(ctx)[0]
+    _need(drho.size == N and (c is None or c.size == N), f"drho and carry must have N = {N} entries")
     _check(lib().tdagw_set_state(_P(ctx), _dptr(drho), _dptr(c), int(step)))
 
 
 def tdagw_apply_lowrank_noalloc(U, V, S, diag, x, y, stream: int | None = None):
     """Allocation-free low-rank contraction on caller-owned CUDA tensors: U, V complex64
     (N, ld) with ld even, S float32 (rank,), diag/x/y complex64 (N,); rank = len(S)."""
+    import torch
+    _need(U.dim() == 2 and U.dtype == torch.complex64 and U.is_contiguous(), "U must be contiguous complex64 (N, ld)")
     N, ld = U.shape
+    _need(V.shape == U.shape and V.dtype == torch.complex64 and V.is_contiguous(), "V must match U")
+    _need(S.dim() == 1 and S.dtype == torch.float32 and S.is_contiguous() and S.shape[0] <= ld,
+          "S must be contiguous float32 (rank,) with rank <= ld")
+    for t, name in ((diag, "diag"), (x, "x"), (y, "y")):
+        _dev_vec(t, N, torch.complex64, name)
+    devs = {t.device for t in (U, V, S, diag, x, y)}
+    _need(len(devs) == 1, "all tensors must be on one device")
     _check(lib().tdagw_apply_lowrank_noalloc(
         _P(_devptr(U)), _P(_devptr(V)), ld, _P(_devptr(S)), _P(_devptr(diag)), N, S.shape[0],
         _P(_devptr(x)), _P(_devptr(y)), _P(stream or 0)))
@@ -284,6 +352,10 @@ def tdagw_apply_lowrank_noalloc(U, V, S, diag, x, y, stream: int | None = None):
 def tdagw_adjoint(ctx: int, dJdobs, steps_max: int, B: int):
     """Gradients through the last checkpointed propagate: returns (dJ/dE_j of shape
     (2 steps_max + 1, B), dJ/d(E0, omega, t0, sigma) of shape (B, 4))."""
+    rows = ct.c_int64()
+    _check(lib().tdagw_observables(_P(ctx), None, 0, ct.byref(rows), 1))
+    _need(steps_max + 1 == rows.value and B == _CTX_INFO.get(ctx, {}).get("B", B),
+          "steps_max and B must be those of the last checkpointed propagate")
     d = np.ascontiguousarray(dJdobs, np.float64).reshape(steps_max + 1, B, 3)
     gE = np.empty((2 * steps_max + 1, B))
     gp = np.empty((B, 4))
@@ -296,11 +368,14 @@ def tdagw_hhg_spectrum(J, steps, dt: float, omega, component: int | None = None,
     """HHG spectra of B currents: J is (rows, B) or, with `component`, the (rows, B, 3)
     observables array (component 1 = J).  Returns (nfreq, B)."""
     J = np.ascontiguousarray(J, np.float64)
+    _need(J.ndim == (2 if component is None else 3), "J must be (rows, B), or (rows, B, 3) with a component")
     rows, B = J.shape[0], J.shape[1]
+    _need(component is None or 0 <= int(component) < J.shape[2], "component out of range")
     stride, off = (1, 0) if component is None else (J.shape[2], int(component))
     flat = J.reshape(-1)[off:]
     flat = np.ascontiguousarray(flat) if off else flat
     st = np.ascontiguousarray(steps, np.int32)
+    _need(st.shape == (B,), "one step count per current")
     w = np.ascontiguousarray(omega, np.float64)
     out = np.empty((w.size, B))
     _check(lib().tdagw_hhg_spectrum(_dptr(flat), rows, stride, B, st.ctypes.data_as(ct.POINTER(ct.c_int)),
@@ -318,6 +393,7 @@ def tdagw_last_error() -> str:
 
 def tdagw_destroy(ctx: int):
     lib().tdagw_destroy(_P(ctx))
+    _CTX_INFO.pop(ctx, None)
 
 
 # ---------------------------------------------------------------- convenience -----------

@@ -163,3 +163,62 @@ def test_hhg_and_noalloc_argument_checks(lib):
     assert "aligned" in tg.tdagw_last_error()
     assert f(a16, b16, 8, s16, s16, 64, 8, a16 + 0x100, a16 + 0x100, None) == tg.ERR_INVALID_ARG
     assert "alias" in tg.tdagw_last_error()
+
+
+def test_binding_checks_shapes_before_passing_pointers(lib):
+    """The binding checks array shapes, dtypes and counts (the C side cannot see extents);
+    a created but unbuilt context answers model_info, so no GPU is needed."""
+    import numpy as np
+    import torch
+
+    import paper_2502_05635_gb300 as tg
+    import workloads as wl
+
+    h = tg.tdagw_create(tg.model_desc(wl.small_model(4, 1)))   # N = 64, Nb = 2, Nk = 16, P = 4
+
+    def bad(fn, *args, match="", **kw):
+        with pytest.raises(tg.TdagwError) as e:
+            fn(*args, **kw)
+        assert e.value.code == tg.ERR_INVALID_ARG and match in str(e.value), str(e.value)
+
+    try:
+        c = np.zeros
+        bad(tg.tdagw_set_factors, h, c((63, 4), complex), c(4), c((63, 4), complex), match="U must be")
+        bad(tg.tdagw_set_factors, h, c((64, 4), complex), c(4), c((64, 5), complex), match="V must")
+        bad(tg.tdagw_set_factors, h, c((64, 4), complex), c(3), c((64, 4), complex), match="S must")
+        bad(tg.tdagw_set_factors, h, c((64, 4), complex), c(4), c((64, 4), complex), c(63, complex),
+            match="64 entries")
+        tg.tdagw_set_kdiag_blocks(h, 1)                            # blocks: Nk x P x P = 256
+        bad(tg.tdagw_set_factors, h, c((64, 4), complex), c(4), c((64, 4), complex), c(64, complex),
+            match="256 entries")
+        tg.tdagw_set_kdiag_blocks(h, 0)
+        U = c((4, 4, 16, 3), complex)
+        bad(tg.tdagw_set_channel_factors, h, c((4, 4, 15, 3), complex), c((4, 4, 3)), U, match="U must be")
+        bad(tg.tdagw_set_channel_factors, h, U, c((4, 4, 2)), U, match="S must")
+        bad(tg.tdagw_set_channel_factors, h, U, c((4, 4, 3)), U, c((4, 16, 15), complex), match="D must")
+        bad(tg.tdagw_set_channel_factors, h, U, c((4, 4, 3)), U, None, c((4, 3), int), match="ranks")
+        bad(tg.tdagw_set_state, h, c(63, complex), match="N = 64")
+        bad(tg.tdagw_set_state, h, c(64, complex), c(32, complex), match="N = 64")
+        pulse = wl.Pulse()
+        bad(tg.tdagw_propagate, h, [tg.make_field(pulse)] * 2, [10], 0.2, tg.FULL, match="step count")
+        f = tg.make_field(pulse, table=c(20))
+        bad(tg.tdagw_propagate, h, [f], [10], 0.2, tg.FULL, match="2 steps + 1")
+        x = torch.zeros(64, dtype=torch.complex64)
+        bad(tg.tdagw_apply, h, tg.FULL, torch.zeros(63, dtype=torch.complex64), x, match="64 elements")
+        bad(tg.tdagw_apply, h, tg.FULL, torch.zeros(64, dtype=torch.complex128), x, match="complex64")
+        bad(tg.tdagw_apply, h, tg.FULL, x, torch.zeros(64, dtype=torch.complex64), match="CUDA tensor")
+        bad(tg.tdagw_adjoint, h, c((11, 1, 3)), 10, 1, match="last checkpointed")
+        Ut = torch.zeros((64, 8), dtype=torch.complex64)
+        S8 = torch.ones(8, dtype=torch.float32)
+        nd = tg.tdagw_apply_lowrank_noalloc
+        bad(nd, Ut, torch.zeros((64, 6), dtype=torch.complex64), S8, x, x.clone(), x.clone(), match="V must")
+        bad(nd, Ut, Ut, torch.ones(9, dtype=torch.float32), x, x.clone(), x.clone(), match="rank <= ld")
+        bad(nd, Ut, Ut, S8.double(), x, x.clone(), x.clone(), match="float32")
+        bad(nd, Ut, Ut, S8, x, x.clone(), torch.zeros(65, dtype=torch.complex64), match="y must")
+        bad(nd, Ut, Ut, S8, x, x.clone(), x.clone(), match="CUDA tensor")
+        J = c((11, 2))
+        bad(tg.tdagw_hhg_spectrum, J, [10], 0.2, np.ones(3), match="one step count")
+        bad(tg.tdagw_hhg_spectrum, J, [10, 10], 0.2, np.ones(3), component=1, match="J must be")
+        bad(tg.tdagw_hhg_spectrum, c((11, 2, 3)), [10, 10], 0.2, np.ones(3), component=3, match="component")
+    finally:
+        tg.tdagw_destroy(h)
