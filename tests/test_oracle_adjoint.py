@@ -143,3 +143,65 @@ def test_observable_gradients_match_observables(setup):
     got = op.observables(mdl, X) - base
     for g, v in zip(oa.observable_gradients(mdl), got):
         assert abs(_inner(g, X) - v) < 1e-13
+
+
+@pytest.mark.parametrize("lowrank", [False, True])
+def test_adjoint_matches_reverse_mode_ad_of_the_forward(setup, lowrank):
+    """The hand-derived discrete adjoint against torch float64 reverse-mode AD of the RK4
+    forward written from the equation of motion (no finite-difference noise: agreement to
+    rounding).  The torch forward is first checked against the oracle's P(t)."""
+    torch = pytest.importorskip("torch")
+    mdl, K = setup
+    if lowrank:
+        d, Koff = ok.split_diag_off(K)
+        U, S, V = olr.truncated_svd(Koff, 9)
+        Kt = np.diag(d) + (U * S) @ V.conj().T
+    else:
+        Kt = K
+    apply, applyH = (lambda v: Kt @ v), (lambda v: Kt.conj().T @ v)
+    pulse = wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0, dir_x=0.8, dir_y=0.6)
+    dt, T = 0.2, 50
+    direction = (pulse.dir_x, pulse.dir_y)
+    samples = op.half_step_samples(pulse, dt, T)
+    obs, _ = op.rk4(mdl, apply, samples, dt, T, direction=direction)
+    _, dJdP = oa.spectral_objective(obs[:, 0], dt, pulse.omega)
+    gE = oa.adjoint(mdl, apply, applyH, samples, dt, T, direction, dJdP)
+
+    Nk, Nb = mdl.Nk, mdl.Nb
+    c = lambda a: torch.as_tensor(np.array(a), dtype=torch.complex128)  # noqa: E731
+    Kq = c(Kt)
+    Dq = c(direction[0] * mdl.dx + direction[1] * mdl.dy)
+    H0 = torch.diag_embed(c(mdl.eps))
+    R0 = torch.diag_embed(c(np.broadcast_to(mdl.occ, (Nk, Nb))))
+    dxT = c(np.swapaxes(mdl.dx, 1, 2))
+    s = torch.tensor(samples, dtype=torch.float64, requires_grad=True)
+
+    def f(X, E):                                   # -i [H0 + E D + (K X), rho0 + X] per k
+        H = H0 + E * Dq + (Kq @ X.reshape(-1)).reshape(Nk, Nb, Nb)
+        rho = R0 + X
+        return -1j * (H @ rho - rho @ H)
+
+    def pol(X):                                    # P_x = (1/Nk) Re sum_k Tr(rho_k d_k)
+        return ((R0 + X) * dxT).sum().real / Nk
+
+    X = torch.zeros((Nk, Nb, Nb), dtype=torch.complex128)
+    P = [pol(X)]
+    for n in range(T):
+        k1 = f(X, s[2 * n])
+        k2 = f(X + 0.5 * dt * k1, s[2 * n + 1])
+        k3 = f(X + 0.5 * dt * k2, s[2 * n + 1])
+        k4 = f(X + dt * k3, s[2 * n + 2])
+        X = X + (dt / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+        P.append(pol(X))
+    P = torch.stack(P)
+    np.testing.assert_allclose(P.detach().numpy(), obs[:, 0], rtol=0, atol=1e-14 * np.abs(obs[:, 0]).max())
+    # the spectral objective on the DFT grid of the T + 1 samples (weights fixed)
+    w = 2 * np.pi * np.arange(T + 1) / ((T + 1) * dt)
+    Em = torch.as_tensor(np.exp(-1j * np.outer(w, np.arange(T + 1) * dt)) * dt)
+    wgt = torch.as_tensor(oa.harmonic_window(w, pulse.omega))
+    F = Em @ P.to(torch.complex128)
+    J = (wgt * F.abs() ** 2).sum()
+    J.backward()
+    g_ad = s.grad.numpy()
+    assert np.abs(gE).max() > 0
+    np.testing.assert_allclose(gE, g_ad, rtol=0, atol=1e-10 * np.abs(g_ad).max())
