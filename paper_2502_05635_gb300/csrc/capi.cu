@@ -6,6 +6,8 @@
 #include <memory>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 struct tdagw_ctx {
@@ -13,9 +15,6 @@ struct tdagw_ctx {
 };
 
 namespace tdagw {
-namespace {
-
-}  // namespace
 
 // message of the last failing call on this thread (tdagw_last_error)
 std::string& last_error_message() {
@@ -27,6 +26,15 @@ namespace {
 
 std::string& g_err_ref() { return last_error_message(); }
 #define g_err g_err_ref()
+
+// NVTX range over one entry point: the setup, propagation, adjoint and HHG calls show up by
+// name on a profiler's timeline (NVTX is header-only and does nothing without a tool)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 template <class F> int guard(F&& f) {
     try {
@@ -398,6 +406,7 @@ int tdagw_create(const tdagw_model_desc* desc, void* stream, tdagw_ctx** out) {
 }
 
 int tdagw_build_kernel(tdagw_ctx* ctx) {
+    const Range nv("tdagw_build_kernel");
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
         DISPATCH(ctx, build, ctx->c);
@@ -455,6 +464,7 @@ int tdagw_get_kernel_entries(tdagw_ctx* ctx, const int64_t* rows, const int64_t*
 
 int tdagw_compress_svd(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
                        uint64_t seed, int precision) {
+    const Range nv("tdagw_compress_svd");
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
         require_built(ctx->c);
@@ -516,6 +526,7 @@ int tdagw_set_kdiag_blocks(tdagw_ctx* ctx, int on) {
 
 int tdagw_compress_channels(tdagw_ctx* ctx, int rank, int oversample, int power_iters,
                             uint64_t seed, double rel_tol) {
+    const Range nv("tdagw_compress_channels");
     return guard([&] {
         TDAGW_REQUIRE(ctx, TDAGW_ERR_INVALID_ARG, "ctx is NULL");
         require_built(ctx->c);
@@ -568,6 +579,7 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y) {
 
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags) {
+    const Range nv("tdagw_propagate");
     return guard([&] {
         TDAGW_REQUIRE(ctx && fields && steps, TDAGW_ERR_INVALID_ARG, "NULL argument");
         require_built(ctx->c);
@@ -617,6 +629,7 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
 }
 
 int tdagw_adjoint(tdagw_ctx* ctx, const double* dJdobs, double* dJdE, double* dJdparams) {
+    const Range nv("tdagw_adjoint");
     return guard([&] {
         TDAGW_REQUIRE(ctx && dJdobs, TDAGW_ERR_INVALID_ARG, "NULL argument");
         require_built(ctx->c);
@@ -663,6 +676,7 @@ int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int
 
 int tdagw_hhg_spectrum(const double* J, int64_t rows, int64_t stride, int B, const int* steps, double dt,
                        const double* omega, int nfreq, double* out, void* stream) {
+    const Range nv("tdagw_hhg_spectrum");
     return guard([&] {
         TDAGW_REQUIRE(J && steps && omega && out, TDAGW_ERR_INVALID_ARG, "NULL argument");
         TDAGW_REQUIRE(B >= 1 && nfreq >= 1 && stride >= 1 && rows >= 1 && dt > 0, TDAGW_ERR_INVALID_ARG,
