@@ -594,16 +594,18 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         c.persistent_launched = true;
     };
 
-    const int key = (mode << 28) ^ (B << 12) ^ r;
+    const std::tuple<int, int, int> key(mode, B, r);
+    const int tg_min = (B + kTileB - 1) / kTileB;  // at most kTileB trajectories per block
     BatchPlan plan;
     auto it = c.batch_plans.find(key);
     if (it != c.batch_plans.end()) {
         plan.Rg = it->second.first;
         plan.Tg = it->second.second;
+        TDAGW_REQUIRE(plan.Tg >= tg_min && plan.Rg >= 1 && plan.Rg <= h.Nk && plan.Rg * plan.Tg <= max_ctas,
+                      TDAGW_ERR_CUDA, "cached batched launch plan does not fit the call");
     } else {
         // candidates: at most 32 trajectories per block (the register tile), CTAs <= SMs
         std::vector<BatchPlan> cands;
-        const int tg_min = (B + kTileB - 1) / kTileB;
         for (int tg = tg_min; tg <= std::min(B, 8 * tg_min); tg *= 2) {
             const int rg = std::min(h.Nk, max_ctas / tg);
             if (rg >= 1) cands.push_back({rg, tg});

@@ -6,6 +6,7 @@
 
 #include <complex>
 #include <map>
+#include <tuple>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -210,7 +211,7 @@ struct Ctx {
     bool persistent_launched = false;
     // batched propagation: states N x Bp, intermediates, per-trajectory tables
     DevBuf bX, bS, bC, bA, bdS, bP, bY, bred, bobs, bEtab, bdir, bact, bperm, bfield, bchm;
-    std::map<int, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
     int last_plan_rg = 0, last_plan_tg = 0;
     int obs_B = 1;           // trajectories in the recorded observables
     // split-FP16 tiled factors for the tensor-core batched path, its intermediates, and
