@@ -164,3 +164,28 @@ def test_field_samples_shifted_half_step_break_commuting_closed_form(monkeypatch
         errs.append(np.abs(rho0 + x.reshape(mdl.Nk, mdl.Nb, mdl.Nb) - exact).max())
     assert errs[2] > 1e-9 or not all(12.0 < a / b < 20.0 for a, b in zip(errs, errs[1:]))
     assert errs[0] / errs[1] < 4.0
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")  # the slip oscillates fast
+@pytest.mark.parametrize("slip", ["envelope_product", "cos_carrier"])
+def test_garbled_strong_field_pulse_breaks_area_pin(monkeypatch, slip):
+    """Slips in the sin^2-envelope pulse: the printed sin^2(pi t T_pulse) taken literally, or
+    a cos carrier; either misses the closed-form pulse area."""
+    import scipy.integrate
+    good = op.field_value
+
+    def bad(pulse, t):
+        if pulse.kind != 2:
+            return good(pulse, t)
+        if t < 0.0 or t > pulse.T_pulse:
+            return 0.0
+        if slip == "envelope_product":
+            return pulse.E0 * np.sin(np.pi * t * pulse.T_pulse) ** 2 * np.sin(pulse.omega * t)
+        return pulse.E0 * np.sin(np.pi * t / pulse.T_pulse) ** 2 * np.cos(pulse.omega * t)
+    monkeypatch.setattr(op, "field_value", bad)
+    w, T = 0.13, 250.0
+    p = wl.Pulse(E0=0.01, omega=w, T_pulse=T, kind=2)
+    q = scipy.integrate.quad(lambda t: op.field_value(p, t), 0.0, T, limit=400, epsabs=1e-14)[0]
+    a = np.pi / T
+    area = 2 * a * a * p.E0 * (1 - np.cos(w * T)) / (w * (4 * a * a - w * w))
+    assert abs(q - area) > 1e-3 * abs(area)

@@ -263,6 +263,24 @@ def test_time_dependent_field_commuting_closed_form():
         assert 12.0 < a / b < 20.0, errs
 
 
+def _sin2_pulse_area(E0, w, T):
+    """int_0^T E0 sin^2(pi t / T) sin(w t) dt by product-to-sum identities (a = pi / T,
+    2 a T = 2 pi): 2 a^2 E0 (1 - cos w T) / (w (4 a^2 - w^2))."""
+    a = np.pi / T
+    return 2 * a * a * E0 * (1 - np.cos(w * T)) / (w * (4 * a * a - w * w))
+
+
+@pytest.mark.parametrize("w,T", [(0.057, 400.0), (0.13, 250.0), (0.31, 97.3)])
+def test_strong_field_pulse_area_closed_form(w, T):
+    """The sin^2-envelope pulse (envelope sin^2(pi t / T_pulse) on [0, T_pulse], carrier
+    sin(w t)): its time integral against the closed form, and zero outside the window."""
+    p = wl.Pulse(E0=0.01, omega=w, T_pulse=T, kind=2)
+    q = scipy.integrate.quad(lambda t: op.field_value(p, t), 0.0, T, limit=400, epsabs=1e-14)[0]
+    assert abs(q - _sin2_pulse_area(p.E0, w, T)) < 1e-9 * abs(q)
+    assert op.field_value(p, -0.5) == 0.0 and op.field_value(p, T + 0.5) == 0.0
+    assert abs(op.field_value(p, 0.0)) < 1e-15 and abs(op.field_value(p, T)) < 1e-12 * p.E0
+
+
 def test_stationary_without_field(m4):
     K = ok.dense_kernel(m4)
     s = np.zeros(2 * 20 + 1)
