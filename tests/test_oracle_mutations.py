@@ -189,3 +189,28 @@ def test_garbled_strong_field_pulse_breaks_area_pin(monkeypatch, slip):
     a = np.pi / T
     area = 2 * a * a * p.E0 * (1 - np.cos(w * T)) / (w * (4 * a * a - w * w))
     assert abs(q - area) > 1e-3 * abs(area)
+
+
+@pytest.mark.parametrize("slip", ["sigma_squared", "no_shift", "sin_carrier"])
+def test_garbled_gaussian_pulse_breaks_area_pin(monkeypatch, slip):
+    """Slips in the Gaussian * cos pulse (width sigma^2 instead of 2 sigma^2, carrier on
+    t - t0, sine carrier) miss the Fourier-transform area."""
+    import scipy.integrate
+    good = op.field_value
+
+    def bad(pulse, t):
+        if pulse.kind != 0:
+            return good(pulse, t)
+        env = np.exp(-((t - pulse.t0) ** 2) / ((1.0 if slip == "sigma_squared" else 2.0) * pulse.sigma ** 2))
+        if slip == "no_shift":
+            return pulse.E0 * env * np.cos(pulse.omega * (t - pulse.t0))
+        if slip == "sin_carrier":
+            return pulse.E0 * env * np.sin(pulse.omega * t)
+        return pulse.E0 * env * np.cos(pulse.omega * t)
+    monkeypatch.setattr(op, "field_value", bad)
+    w, sigma, t0 = 0.1, 5.0, 60.0
+    p = wl.Pulse(E0=0.01, omega=w, t0=t0, sigma=sigma, kind=0)
+    q = scipy.integrate.quad(lambda t: op.field_value(p, t), 0.0, t0 + 14 * sigma, limit=800,
+                             epsabs=1e-16, points=[t0])[0]
+    want = p.E0 * sigma * np.sqrt(2 * np.pi) * np.exp(-(w * sigma) ** 2 / 2) * np.cos(w * t0)
+    assert abs(q - want) > 1e-3 * abs(want)

@@ -263,6 +263,18 @@ def test_time_dependent_field_commuting_closed_form():
         assert 12.0 < a / b < 20.0, errs
 
 
+@pytest.mark.parametrize("w,sigma,t0", [(0.1, 5.0, 60.0), (0.06, 30.0, 320.0), (0.3, 2.0, 25.0)])
+def test_gaussian_pulse_area_is_its_fourier_transform(w, sigma, t0):
+    """Gaussian * cos pulse: int E dt = E0 sigma sqrt(2 pi) exp(-w^2 sigma^2 / 2) cos(w t0)
+    (the Fourier transform of a Gaussian; t0 >= 10 sigma makes the part before t = 0
+    negligible).  Fixes the width convention 2 sigma^2, the shift t - t0 and the carrier."""
+    p = wl.Pulse(E0=0.01, omega=w, t0=t0, sigma=sigma, kind=0)
+    q = scipy.integrate.quad(lambda t: op.field_value(p, t), 0.0, t0 + 14 * sigma, limit=800,
+                             epsabs=1e-16, points=[t0])[0]
+    want = p.E0 * sigma * np.sqrt(2 * np.pi) * np.exp(-(w * sigma) ** 2 / 2) * np.cos(w * t0)
+    assert abs(q - want) < 1e-11 * abs(want)
+
+
 def _sin2_pulse_area(E0, w, T):
     """int_0^T E0 sin^2(pi t / T) sin(w t) dt by product-to-sum identities (a = pi / T,
     2 a T = 2 pi): 2 a^2 E0 (1 - cos w T) / (w (4 a^2 - w^2))."""
