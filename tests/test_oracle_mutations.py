@@ -214,3 +214,13 @@ def test_garbled_gaussian_pulse_breaks_area_pin(monkeypatch, slip):
                              epsabs=1e-16, points=[t0])[0]
     want = p.E0 * sigma * np.sqrt(2 * np.pi) * np.exp(-(w * sigma) ** 2 / 2) * np.cos(w * t0)
     assert abs(q - want) > 1e-3 * abs(want)
+
+
+def test_unconjugated_bra_in_velocity_breaks_heisenberg_pin():
+    """Slip: <u_n| taken without complex conjugation in the band-basis velocity."""
+    p = wl.small_model(5, 1)
+    mdl = om.Model(p)
+    v = np.einsum("kin,kij,kjm->knm", mdl.U, om.dh_dk(mdl.k, p, 0), mdl.U)
+    want = 1j * (mdl.eps[:, :, None] - mdl.eps[:, None, :]) * mdl.dx
+    off = ~np.eye(mdl.Nb, dtype=bool)
+    assert np.abs(v[:, off] - want[:, off]).max() > 1e-3

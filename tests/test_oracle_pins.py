@@ -82,6 +82,20 @@ def test_velocity_diagonal_is_band_slope(m4):
     np.testing.assert_allclose(np.diagonal(m4.vx, axis1=1, axis2=2).real, slope, atol=1e-8)
 
 
+@pytest.mark.parametrize("nc", [1, 2])
+def test_velocity_is_commutator_with_position(nc):
+    """Heisenberg relation v = i [H, r] in the band basis: v_nm = i (eps_n - eps_m) d_nm for
+    n != m, with d the finite-difference Berry dipole (computed independently of the
+    analytic velocity); v Hermitian."""
+    mdl = om.Model(wl.small_model(5, nc))
+    v, d, eps = mdl.vx, mdl.dx, mdl.eps
+    want = 1j * (eps[:, :, None] - eps[:, None, :]) * d
+    off = ~np.eye(mdl.Nb, dtype=bool)
+    assert np.abs(v[:, off]).max() > 0.1
+    np.testing.assert_allclose(v[:, off], want[:, off], atol=2e-8)
+    np.testing.assert_allclose(v, np.conj(np.swapaxes(v, 1, 2)), atol=1e-15)
+
+
 def test_four_band_copies_decouple(m4):
     """Bands of different copies have zero overlap, dipole and velocity."""
     # bands 0, 2 are copy 0 (lower/upper); 1, 3 are copy 1 (offset 0.03)
