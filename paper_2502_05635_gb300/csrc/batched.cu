@@ -594,7 +594,7 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         c.persistent_launched = true;
     };
 
-    const std::tuple<int, int, int> key(mode, B, r);
+    const uint64_t key = ((uint64_t)mode << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
     const int tg_min = (B + kTileB - 1) / kTileB;  // at most kTileB trajectories per block
     BatchPlan plan;
     auto it = c.batch_plans.find(key);

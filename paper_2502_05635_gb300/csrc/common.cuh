@@ -6,7 +6,6 @@
 
 #include <complex>
 #include <map>
-#include <tuple>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -211,7 +210,8 @@ struct Ctx {
     bool persistent_launched = false;
     // batched propagation: states N x Bp, intermediates, per-trajectory tables
     DevBuf bX, bS, bC, bA, bdS, bP, bY, bred, bobs, bEtab, bdir, bact, bperm, bfield, bchm;
-    std::map<std::tuple<int, int, int>, std::pair<int, int>> batch_plans;  // (mode, B, rank) -> (row groups, traj groups)
+    // (mode << 56 | B << 32 | rank) -> (row groups, traj groups); B <= 65536, rank < 2^32
+    std::map<uint64_t, std::pair<int, int>> batch_plans;
     int last_plan_rg = 0, last_plan_tg = 0;
     int obs_B = 1;           // trajectories in the recorded observables
     // split-FP16 tiled factors for the tensor-core batched path, its intermediates, and
