@@ -179,3 +179,62 @@ def test_ring_model_detects_missing_release():
     full.complete_tx(16)                        # use 1 in the same slot, no release wait
     with pytest.raises(AssertionError):
         full.try_wait_parity(0, 0)              # a warp still waiting for use 0
+
+
+# ---------------------------------------------------------------- grid barrier ----------
+
+def run_grid_barrier(G, barriers, seed, extra=0, budget=None, bug=None):
+    """Monotonic arrival counter (no reset): barrier g (1, 2, ...) completes once the
+    counter reaches g (G + extra).  Returns the per-CTA outcome ('done' or 'timeout')."""
+    rng = random.Random(seed)
+    counter = 0
+    gen = [0] * G                    # barriers passed
+    arrived = [False] * G            # arrived at the current barrier, now polling
+    polls = [0] * G
+    arrivals = [0] * (barriers + 1)  # CTAs that arrived at barrier g
+    state = ["run"] * G
+    for _ in range(10 ** 6):
+        live = [c for c in range(G) if state[c] == "run"]
+        if not live:
+            break
+        c = rng.choice(live)
+        if gen[c] == barriers:
+            state[c] = "done"
+            continue
+        g = gen[c] + 1
+        if not arrived[c]:
+            counter += 1             # red.release.gpu.add
+            arrivals[g] += 1
+            arrived[c] = True
+            polls[c] = 0
+            if bug == "reset" and arrivals[g] == G:
+                counter = 0          # a counter reset at each barrier, as a planted bug
+        target = (g if bug != "reset" else 1) * (G + extra)
+        if counter >= target:        # ld.acquire.gpu poll
+            assert arrivals[g] == G, f"CTA {c} left barrier {g} after {arrivals[g]} of {G} arrivals"
+            gen[c] += 1
+            arrived[c] = False
+        else:
+            polls[c] += 1
+            if budget is not None and polls[c] > budget:
+                state[c] = "timeout"
+    return state
+
+
+@pytest.mark.parametrize("G", [1, 2, 7, 152])
+@pytest.mark.parametrize("seed", range(3))
+def test_grid_barrier_orders_every_generation(G, seed):
+    assert run_grid_barrier(G, barriers=9, seed=seed) == ["done"] * G
+
+
+def test_grid_barrier_extra_arrival_times_out_everywhere():
+    """The test hook's extra arrival can never come: every CTA's wait runs out its budget
+    (the kernel then records TDAGW_ERR_TIMEOUT) instead of hanging or passing."""
+    assert run_grid_barrier(5, barriers=3, seed=1, extra=1, budget=200) == ["timeout"] * 5
+
+
+def test_grid_barrier_model_catches_a_reset_counter():
+    """Resetting the counter at each barrier lets a late CTA miss the completion; the model
+    reports it as a timeout (or an early exit) on some schedule."""
+    outcomes = [run_grid_barrier(6, barriers=6, seed=s, budget=5000, bug="reset") for s in range(10)]
+    assert any(o != ["done"] * 6 for o in outcomes)
