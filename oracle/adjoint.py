@@ -34,12 +34,15 @@ from . import propagate as op
 
 
 def harmonic_window(w: np.ndarray, w0: float) -> np.ndarray:
+    """Weight of the objective around harmonics 3-7 of w0 (a reading: the paper differentiates
+    nothing; its spectra, Sec. "SVD acceleration of TD-aGW", are transforms of P(t), J(t))."""
     s = w0 / 8.0
     return sum(np.exp(-((w - h * w0) ** 2) / (2 * s * s)) for h in range(3, 8))
 
 
 def spectral_objective(P: np.ndarray, dt: float, w0: float):
-    """J and dJ/dP_n for the samples P_n, n = 0..T."""
+    """J and dJ/dP_n for the samples P_n, n = 0..T (spectral weight of the Fourier transform
+    of P(t), Sec. "SVD acceleration of TD-aGW"; window as in harmonic_window)."""
     n = np.arange(P.size)
     w = 2 * np.pi * np.arange(P.size) / (P.size * dt)
     E = np.exp(-1j * np.outer(w, n * dt)) * dt          # (freq, time)
@@ -59,7 +62,8 @@ def _herm(a):
 
 
 def vjp(model, apply_K, apply_KH, E, direction, X, g):
-    """(Xbar, Ebar) of f(X, E) = -i [A(X), rho0 + X] for the cotangent g (see module doc)."""
+    """(Xbar, Ebar) of the right-hand side of Eq. tdagw, f(X, E) = -i [A(X), rho0 + X], for
+    the cotangent g (derivation in the module doc)."""
     Nb = model.Nb
     D = direction[0] * model.dx + direction[1] * model.dy
     A = _blocks(model, apply_K(X)) + E * D
@@ -77,14 +81,15 @@ def vjp(model, apply_K, apply_KH, E, direction, X, g):
 
 
 def forward_states(model, apply_K, samples, dt, T, direction):
-    """States x_0..x_T and observables of the RK4 run (the oracle forward)."""
+    """States x_0..x_T and observables of the RK4 run of Eq. tdagw (the oracle forward)."""
     obs, _, states = op.rk4(model, apply_K, samples, dt, T, direction=direction,
                             record_states=True)
     return obs, states
 
 
 def observable_gradients(model):
-    """Gradients of (P_x, J_x, occ_c1) with respect to the state X in the real inner product
+    """Gradients of the observables of Sec. "SVD acceleration of TD-aGW" (P_x, J_x, occ_c1)
+    with respect to the state X in the real inner product
     <a, b> = Re sum conj(a_i) b_i.  Each observable is Re sum_k sum_nm X_nm O_mn / Nk with O
     Hermitian (d^x, v^x, the projector on c1), so its gradient is O_nm / Nk."""
     occ = np.zeros((model.Nk, model.Nb, model.Nb), dtype=np.complex128)
@@ -93,7 +98,8 @@ def observable_gradients(model):
 
 
 def adjoint(model, apply_K, apply_KH, samples, dt, T, direction, dJdP, dJdJ=None, dJdocc=None):
-    """dJ/dE_j for the half-step field samples j = 0..2T, given the derivatives of the
+    """Exact adjoint of the discrete RK4 map of Eq. tdagw: dJ/dE_j for the half-step field
+    samples j = 0..2T, given the derivatives of the
     objective with respect to the observables P_x, J_x and occ_c1 at steps n = 0..T (the
     last two optional, zero by default)."""
     _, states = forward_states(model, apply_K, samples, dt, T, direction)
@@ -136,7 +142,8 @@ def adjoint(model, apply_K, apply_KH, samples, dt, T, direction, dJdP, dJdJ=None
 
 
 def pulse_param_jacobian(pulse, dt: float, T: int) -> np.ndarray:
-    """dE_j / d(E0, omega, t0, sigma) for the Gaussian * cos pulse; shape (2T+1, 4)."""
+    """dE_j / d(E0, omega, t0, sigma) for the Gaussian * cos pulse of Sec. "SVD acceleration
+    of TD-aGW"; shape (2T+1, 4)."""
     t = 0.5 * dt * np.arange(2 * T + 1)
     g = np.exp(-((t - pulse.t0) ** 2) / (2 * pulse.sigma ** 2))
     c, s = np.cos(pulse.omega * t), np.sin(pulse.omega * t)
@@ -148,7 +155,8 @@ def pulse_param_jacobian(pulse, dt: float, T: int) -> np.ndarray:
 
 
 def objective_and_gradients(model, apply_K, apply_KH, pulse, dt, T):
-    """J, dJ/d(E0, omega, t0, sigma) and dJ/dE_j for one Gaussian * cos trajectory."""
+    """J, dJ/d(E0, omega, t0, sigma) and dJ/dE_j for one trajectory of Eq. tdagw driven by the
+    Gaussian * cos pulse of Sec. "SVD acceleration of TD-aGW"."""
     direction = (pulse.dir_x, pulse.dir_y)
     samples = op.half_step_samples(pulse, dt, T)
     obs, _ = op.rk4(model, apply_K, samples, dt, T, direction=direction)

@@ -29,13 +29,15 @@ from oracle import kernel as ok
 
 
 def channel_block(K: np.ndarray, Nb: int, p: int, q: int) -> np.ndarray:
-    """K^ch for ch = p -> q: rows k Nb^2 + p, columns k' Nb^2 + q (Nk x Nk copy)."""
+    """K^ch of Eq. svd-channel-wise for ch = p -> q: rows k Nb^2 + p, columns k' Nb^2 + q
+    (Nk x Nk copy)."""
     P = Nb * Nb
     return K[p::P, q::P].copy()
 
 
 def channel_block_from_model(model, p: int, q: int, W: np.ndarray | None = None) -> np.ndarray:
-    """K^pq straight from the kernel's entry formula, without the dense N x N kernel (for
+    """K^pq (Eq. svd-channel-wise) straight from the entry formula of Eq. bse-direct-def,
+    without the dense N x N kernel (for
     large grids): with p = (n1, n2), q = (n3, n4) and O_ab[k, k'] = (U_k^+ U_k')_{ab},
         K^pq[k, k'] = -W(k - k') O_{n1 n3}[k, k'] conj(O_{n2 n4}[k, k']),
     since (U_k'^+ U_k)_{n4 n2} = conj((U_k^+ U_k')_{n2 n4})."""
@@ -78,7 +80,8 @@ def channel_svd(K: np.ndarray, Nb: int, rank: int):
 
 
 def channel_svd_from_model(model, rank: int):
-    """channel_svd without the dense N x N kernel (large grids): every channel from the
+    """Eq. svd-channel-wise as channel_svd, without the dense N x N kernel (large grids):
+    every channel from the
     kernel's entry formula (channel_block_from_model); vanishing channels keep zero factors."""
     Nb, Nk = model.Nb, model.Nk
     P = Nb * Nb
@@ -101,7 +104,7 @@ def channel_svd_from_model(model, rank: int):
 
 
 def apply_channel(D, U, S, V, x: np.ndarray) -> np.ndarray:
-    """dSigma = K~ x for the channel-wise kernel:
+    """dSigma = K~ x (Eq. sigma-from-k) for the channel-wise kernel of Eq. svd-channel-wise:
 
         dSigma[(k, p)] = sum_k' D^p[k, k'] x[(k', p)]
                        + sum_{q != p} U^{pq} diag(S^{pq}) (V^{pq})^H x_q,
@@ -121,7 +124,8 @@ def apply_channel(D, U, S, V, x: np.ndarray) -> np.ndarray:
 
 
 def assemble(D, U, S, V) -> np.ndarray:
-    """The dense N x N matrix of the channel-wise kernel, channel by channel."""
+    """The dense N x N matrix of the channel-wise kernel (Eq. svd-channel-wise), channel by
+    channel."""
     P, Nk = D.shape[0], D.shape[1]
     K = np.zeros((P * Nk, P * Nk), complex)
     for p in range(P):

@@ -14,7 +14,8 @@ import numpy as np
 
 
 def hhg_spectrum(J: np.ndarray, dt: float, omega: np.ndarray) -> np.ndarray:
-    """| w sum_n J(t_n) e^{-i w t_n} dt |^2 for each w in omega; J of length T + 1."""
+    """HHG(w) of Sec. "SVD acceleration of TD-aGW" (and Appendix C):
+    | w sum_n J(t_n) e^{-i w t_n} dt |^2 for each w in omega; J of length T + 1."""
     J = np.asarray(J, dtype=np.float64)
     omega = np.asarray(omega, dtype=np.float64)
     t = np.arange(J.size) * dt
@@ -23,5 +24,6 @@ def hhg_spectrum(J: np.ndarray, dt: float, omega: np.ndarray) -> np.ndarray:
 
 
 def harmonic_grid(omega0: float, max_order: float, n: int) -> np.ndarray:
-    """n frequencies evenly spaced on (0, max_order * omega0]."""
+    """n frequencies evenly spaced on (0, max_order * omega0] (spectra in harmonic orders of
+    the driving frequency, Fig. svd_time_freq, Appendix C)."""
     return omega0 * max_order * np.arange(1, n + 1) / n

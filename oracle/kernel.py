@@ -39,12 +39,14 @@ import numpy as np
 
 
 def coulomb_W(qabs: np.ndarray, A: float, r0: float) -> np.ndarray:
-    """2D Rytova-Keldysh interaction 2 pi / (A |q| (1 + r0 |q|)) for |q| > 0."""
+    """2D Rytova-Keldysh interaction 2 pi / (A |q| (1 + r0 |q|)) for |q| > 0 (the screened
+    W of Eq. bse-direct-def for the lattice model; Appendix B)."""
     return 2.0 * np.pi / (A * qabs * (1.0 + r0 * qabs))
 
 
 def cell_average_W0(h: float, A: float, r0: float, npts: int = 64) -> float:
-    """Mean of W(q) over the square |qx|,|qy| <= h.
+    """W(q = 0) as the average over a small region (Appendix B): the mean of W(q) over the
+    square |qx|,|qy| <= h.
 
     In polar coordinates the square is 8 triangles 0 <= theta <= pi/4,
     0 <= |q| <= h / cos(theta); the radial integral of |q| W(q) is closed-form,
@@ -59,12 +61,14 @@ def cell_average_W0(h: float, A: float, r0: float, npts: int = 64) -> float:
 
 
 def min_image(d: np.ndarray, L: int) -> np.ndarray:
-    """Integer offset wrapped into [-L/2, L/2)."""
+    """Integer offset wrapped into [-L/2, L/2) (q = k - k' on the periodic grid of Eq.
+    bse-direct-def)."""
     return (d + L // 2) % L - L // 2
 
 
 def W_of_offsets(di: np.ndarray, dj: np.ndarray, p) -> np.ndarray:
-    """W on integer grid offsets (already minimum-image); W0 at the origin."""
+    """W of Eq. bse-direct-def on integer grid offsets (already minimum-image); the Appendix B
+    average W0 at the origin."""
     L, a = p.L, p.a
     A = p.Nk * a * a
     qx = di * (2.0 * np.pi / (L * a))
@@ -78,7 +82,7 @@ def W_of_offsets(di: np.ndarray, dj: np.ndarray, p) -> np.ndarray:
 
 
 def W_matrix(p) -> np.ndarray:
-    """W(k - k') for all pairs of grid points; (Nk, Nk)."""
+    """W(k - k') of Eq. bse-direct-def for all pairs of grid points; (Nk, Nk)."""
     L = p.L
     ii, jj = np.divmod(np.arange(p.Nk), L)
     di = min_image(ii[:, None] - ii[None, :], L)
@@ -88,7 +92,7 @@ def W_matrix(p) -> np.ndarray:
 
 def exchange_vectors(model):
     """(M, v): M (Nk, nG, Nb, Nb) = M_nm(k, G) and v (nG,) = lambda_x v(G) for the eight
-    reciprocal vectors of the exchange term (see the module header)."""
+    reciprocal vectors of the exchange term of Eq. bse-exchange-def (see the module header)."""
     p = model.p
     A = p.Nk * p.a * p.a
     Gs = [(i, j) for i in (-1, 0, 1) for j in (-1, 0, 1) if (i, j) != (0, 0)]
@@ -105,14 +109,15 @@ def exchange_vectors(model):
 
 
 def exchange_kernel(model) -> np.ndarray:
-    """The dense exchange term K^x (N x N), zero when lambda_x = 0."""
+    """The dense exchange term K^x of Eq. bse-exchange-def (N x N), zero when lambda_x = 0."""
     M, v = exchange_vectors(model)
     Mf = M.reshape(model.Nk, len(v), -1).transpose(1, 0, 2).reshape(len(v), -1)   # (nG, N)
     return np.einsum("g,gi,gj->ij", v, Mf, Mf.conj())
 
 
 def dense_kernel(model) -> np.ndarray:
-    """The full N x N kernel (complex128), straight from the entry formula."""
+    """The full N x N kernel of Eq. sigma-from-k (complex128), straight from the entry
+    formula of Eq. bse-direct-def (plus Eq. bse-exchange-def when lambda_x > 0)."""
     p, Nk, Nb = model.p, model.Nk, model.Nb
     W = W_matrix(p)
     U = model.U
@@ -127,7 +132,8 @@ def dense_kernel(model) -> np.ndarray:
 
 
 def kernel_entry(model, row: int, col: int) -> complex:
-    """One entry K[row, col] by the formula (scalar loop; for sampled checks)."""
+    """One entry K[row, col] by the formula of Eq. bse-direct-def (and Eq.
+    bse-exchange-def) as a scalar loop, for sampled checks."""
     p, Nb = model.p, model.Nb
     k, rem = divmod(row, Nb * Nb)
     n, m = divmod(rem, Nb)
@@ -149,7 +155,8 @@ def kernel_entry(model, row: int, col: int) -> complex:
 
 
 def kernel_row(model, row: int) -> np.ndarray:
-    """Row `row` of K (length N), vectorised over columns; for sampled-row checks."""
+    """Row `row` of K (Eq. bse-direct-def, and Eq. bse-exchange-def), length N, vectorised
+    over columns; for sampled-row checks."""
     p, Nb, Nk = model.p, model.Nb, model.Nk
     k, rem = divmod(row, Nb * Nb)
     n, m = divmod(rem, Nb)
@@ -166,7 +173,8 @@ def kernel_row(model, row: int) -> np.ndarray:
 
 
 def kernel_diag(model) -> np.ndarray:
-    """diag(K): -W0 (U_k^+U_k)_{nn} (U_k^+U_k)_{mm}; length N."""
+    """diag(K), the strict-diagonal K^diag of Eq. svd_diag_offdiag, of the direct kernel:
+    -W0 (U_k^+U_k)_{nn} (U_k^+U_k)_{mm}; length N."""
     p = model.p
     W0 = cell_average_W0(np.pi / (p.L * p.a), p.Nk * p.a * p.a, p.r0)
     g = np.einsum("kin,kin->kn", model.U.conj(), model.U).real
@@ -178,7 +186,8 @@ def kernel_diag(model) -> np.ndarray:
 
 
 def split_kblocks(K: np.ndarray, Nb: int):
-    """The other reading of K^diag: the k = k' blocks.  Returns (B, Koff) with B
+    """The other reading of K^diag in Sec. "SVD analysis of electron-hole kernel": the
+    k = k' blocks.  Returns (B, Koff) with B
     (Nk, P, P) the blocks K[k P + p, k P + q] (P = Nb^2) and Koff = K without them."""
     P = Nb * Nb
     Nk = K.shape[0] // P
@@ -203,7 +212,8 @@ def apply_dense(K: np.ndarray, x: np.ndarray) -> np.ndarray:
 
 
 def fft_applier(model):
-    """K . x through the convolution structure of this kernel (an identity, not a model).
+    """K . x of Eq. sigma-from-k through the convolution structure of Eq. bse-direct-def (an
+    identity, not a model).
 
     Summing the entry formula over n', m':
         (K x)_k = - U_k^+ [ sum_k' W(k - k') U_k' X_k' U_k'^+ ] U_k ,
@@ -235,5 +245,5 @@ def fft_applier(model):
 
 
 def apply_fft(model, x: np.ndarray) -> np.ndarray:
-    """One K . x by the FFT form (see fft_applier)."""
+    """One K . x of Eq. sigma-from-k by the FFT form (see fft_applier)."""
     return fft_applier(model)(x)

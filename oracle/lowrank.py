@@ -14,12 +14,14 @@ import scipy.linalg
 
 
 def truncated_svd(Koff: np.ndarray, rank: int):
-    """Top-`rank` singular triplets of K^off by LAPACK (gesdd): U (N,r), S (r,), V (N,r)."""
+    """Eq. svd_diag_offdiag: the top-`rank` singular triplets of K^off by LAPACK (gesdd):
+    U (N,r), S (r,), V (N,r)."""
     U, S, Vh = scipy.linalg.svd(Koff, full_matrices=False, lapack_driver="gesdd")
     return U[:, :rank].copy(), S[:rank].copy(), Vh[:rank].conj().T.copy()
 
 
 def singular_values(Koff: np.ndarray) -> np.ndarray:
+    """Singular values of K^off, descending (the spectra of Fig. svd_analysis)."""
     return scipy.linalg.svdvals(Koff)
 
 
@@ -32,7 +34,8 @@ def apply_lowrank(diag: np.ndarray, U: np.ndarray, S: np.ndarray, V: np.ndarray,
 
 def apply_lowrank_kblocks(B: np.ndarray, U: np.ndarray, S: np.ndarray, V: np.ndarray,
                           x: np.ndarray) -> np.ndarray:
-    """dSigma = K^diag x + U (S * (V^H x)) with K^diag read as the k = k' blocks B (Nk, P, P):
+    """Eq. svd_acc with K^diag read as the k = k' blocks (Sec. "SVD analysis of
+    electron-hole kernel"): dSigma = K^diag x + U (S * (V^H x)) with B (Nk, P, P):
     (K^diag x)[k P + p] = sum_q B[k, p, q] x[k P + q]."""
     Nk, P = B.shape[0], B.shape[1]
     y = V.conj().T @ x
@@ -40,6 +43,7 @@ def apply_lowrank_kblocks(B: np.ndarray, U: np.ndarray, S: np.ndarray, V: np.nda
 
 
 def reconstruct(diag, U, S, V) -> np.ndarray:
+    """The dense kernel of Eq. svd_diag_offdiag: diag(K) + U diag(S) V^H."""
     return np.diag(diag) + (U * S) @ V.conj().T
 
 

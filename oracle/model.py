@@ -30,14 +30,16 @@ SZ = np.array([[1, 0], [0, -1]], dtype=np.complex128)
 
 
 def kgrid(L: int, a: float) -> np.ndarray:
-    """Gamma-centred unshifted L x L grid, k = (2 pi / (L a)) (i, j); index k = i*L + j."""
+    """Gamma-centred unshifted L x L grid (the k-grids of Appendix A), k = (2 pi / (L a)) (i, j);
+    index k = i*L + j."""
     i, j = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
     k = np.stack([i.ravel(), j.ravel()], axis=1).astype(np.float64)
     return k * (2.0 * np.pi / (L * a))
 
 
 def h_orbital(k: np.ndarray, p) -> np.ndarray:
-    """Orbital-basis Hamiltonian, shape (..., Norb, Norb), Norb = 2 * nb_copies."""
+    """Orbital-basis lattice Hamiltonian standing in for the quasiparticle bands H^QP of Eq.
+    tdagw (Appendix A's are first-principles); shape (..., Norb, Norb), Norb = 2 nb_copies."""
     k = np.asarray(k, dtype=np.float64)
     kx, ky = k[..., 0] * p.a, k[..., 1] * p.a
     dx = p.t * np.sin(kx)
@@ -52,7 +54,8 @@ def h_orbital(k: np.ndarray, p) -> np.ndarray:
 
 
 def dh_dk(k: np.ndarray, p, axis: int) -> np.ndarray:
-    """Analytic derivative dh/dk_axis (orbital basis), shape (..., Norb, Norb)."""
+    """Analytic derivative dh/dk_axis of the stand-in bands of H^QP (Eq. tdagw), orbital
+    basis, shape (..., Norb, Norb)."""
     k = np.asarray(k, dtype=np.float64)
     kx, ky = k[..., 0] * p.a, k[..., 1] * p.a
     ka = kx if axis == 0 else ky
@@ -66,7 +69,8 @@ def dh_dk(k: np.ndarray, p, axis: int) -> np.ndarray:
 
 
 def fix_gauge(U: np.ndarray) -> np.ndarray:
-    """Rephase each column so that its largest-modulus component is real and positive."""
+    """Rephase each column so that its largest-modulus component is real and positive (a
+    gauge choice; the observables of Eq. tdagw do not depend on it)."""
     U = np.array(U, dtype=np.complex128, copy=True)
     idx = np.argmax(np.abs(U), axis=-2)                       # (..., Nb)
     piv = np.take_along_axis(U, idx[..., None, :], axis=-2)   # (..., 1, Nb)
@@ -74,7 +78,8 @@ def fix_gauge(U: np.ndarray) -> np.ndarray:
 
 
 def eigensystem(k: np.ndarray, p):
-    """Bands sorted ascending and gauge-fixed eigenvectors (columns), via LAPACK eigh."""
+    """Quasiparticle energies and states of the stand-in H^QP (Eq. tdagw): bands sorted
+    ascending and gauge-fixed eigenvectors (columns), via LAPACK eigh."""
     eps, U = np.linalg.eigh(h_orbital(k, p))
     return eps, fix_gauge(U)
 
@@ -86,7 +91,9 @@ def _transported(Uk: np.ndarray, Ush: np.ndarray) -> np.ndarray:
 
 
 def berry_dipole(k: np.ndarray, p, axis: int, delta: float | None = None) -> np.ndarray:
-    """Finite-difference Berry connection A_nm = i<u_n|du_m/dk>, Hermitised; (Nk, Nb, Nb)."""
+    """The k-local position operator r of Eq. tdagw (length gauge; r in C^{Nb^2 Nk x 3},
+    Appendix A.1) as the finite-difference Berry connection A_nm = i<u_n|du_m/dk>,
+    Hermitised; (Nk, Nb, Nb)."""
     if delta is None:
         delta = 1e-5 / p.a
     e = np.zeros(2)
@@ -107,7 +114,8 @@ def berry_dipole(k: np.ndarray, p, axis: int, delta: float | None = None) -> np.
 
 
 def velocity(k: np.ndarray, p, axis: int) -> np.ndarray:
-    """v_nm = <u_n| dh/dk_axis |u_m> in the band basis; (Nk, Nb, Nb)."""
+    """The velocity operator of the current J = Tr(rho v) (Sec. "SVD acceleration of
+    TD-aGW"): v_nm = <u_n| dh/dk_axis |u_m> in the band basis; (Nk, Nb, Nb)."""
     _, U = eigensystem(k, p)
     return np.einsum("...in,...ij,...jm->...nm", U.conj(), dh_dk(k, p, axis), U)
 

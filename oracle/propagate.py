@@ -26,7 +26,8 @@ import numpy as np
 
 
 def field_value(pulse, t: float) -> float:
-    """Scalar amplitude E(t) of a pulse (direction handled separately)."""
+    """Scalar amplitude E(t) of the pulses of Sec. "SVD acceleration of TD-aGW" (direction
+    handled separately)."""
     if pulse.kind == 0:
         return pulse.E0 * np.exp(-((t - pulse.t0) ** 2) / (2.0 * pulse.sigma ** 2)) * np.cos(pulse.omega * t)
     if pulse.kind == 1:
@@ -39,12 +40,13 @@ def field_value(pulse, t: float) -> float:
 
 
 def half_step_samples(pulse, dt: float, T: int) -> np.ndarray:
-    """E(n dt / 2) for n = 0..2T: every RK4 stage time of a T-step run."""
+    """E(n dt / 2) for n = 0..2T: every RK4 stage time of a T-step run of Eq. tdagw."""
     return np.array([field_value(pulse, 0.5 * j * dt) for j in range(2 * T + 1)])
 
 
 def rhs(model, apply_K, Ex: float, Ey: float, X: np.ndarray) -> np.ndarray:
-    """-i [diag(eps) + Ex d^x + Ey d^y + (K X), rho0 + X] per k, flattened like X."""
+    """Right-hand side of Eq. tdagw with dSigma of Eq. sigma-from-k:
+    -i [diag(eps) + Ex d^x + Ey d^y + (K X), rho0 + X] per k, flattened like X."""
     Nk, Nb = model.Nk, model.Nb
     Xk = X.reshape(Nk, Nb, Nb)
     dS = apply_K(X).reshape(Nk, Nb, Nb)
@@ -57,7 +59,8 @@ def rhs(model, apply_K, Ex: float, Ey: float, X: np.ndarray) -> np.ndarray:
 
 
 def observables(model, X: np.ndarray) -> np.ndarray:
-    """(P_x, J_x, occ_c1) of the state rho0 + X."""
+    """(P_x, J_x, occ_c1) of the state rho0 + X: the polarization and current of Sec. "SVD
+    acceleration of TD-aGW" and the conduction occupation of Fig. svd_time_freq."""
     rho = model.rho0() + X.reshape(model.Nk, model.Nb, model.Nb)
     P = np.sum(rho * np.swapaxes(model.dx, 1, 2)).real / model.Nk     # sum_nm rho_nm d_mn
     J = np.sum(rho * np.swapaxes(model.vx, 1, 2)).real / model.Nk
@@ -67,7 +70,7 @@ def observables(model, X: np.ndarray) -> np.ndarray:
 
 def rk4(model, apply_K, samples: np.ndarray, dt: float, T: int, direction=(1.0, 0.0),
         x0: np.ndarray | None = None, record_states: bool = False):
-    """T classical RK4 steps from drho = x0 (default 0).
+    """T classical RK4 steps of Eq. tdagw from drho = x0 (default 0).
 
     samples[j] = E(j dt / 2), j = 0..2T (see half_step_samples); the two middle stages
     of a step share the sample at t_n + dt/2.  Returns (obs (T+1, 3), final state) and,
@@ -98,5 +101,6 @@ def rk4(model, apply_K, samples: np.ndarray, dt: float, T: int, direction=(1.0, 
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
-    """||a - b||_2 / ||b||_2 (the P(t) error measure)."""
+    """||a - b||_2 / ||b||_2: the relative error of P(t) (Sec. "SVD acceleration of TD-aGW"
+    compares spectra; every comparison here uses P(t) itself)."""
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
