@@ -1,6 +1,8 @@
-// Exact discrete adjoint of the batched RK4 propagation (complex64): gradients of an
-// objective of the recorded observables with respect to the per-trajectory field samples
-// E(j dt/2) (and, on the host, the pulse parameters).
+// Exact discrete adjoint of the batched RK4 propagation of Eq. tdagw (complex64):
+// gradients of an objective of the recorded observables (P, J and occupation, Sec. "SVD
+// acceleration of TD-aGW") with respect to the per-trajectory field samples E(j dt/2) (and,
+// on the host, the pulse parameters).  The paper differentiates nothing; the kernel term
+// is the transpose of Eq. sigma-from-k / Eq. svd_acc.
 //
 // With the real inner product <a, b> = Re sum conj(a_i) b_i and lam = dJ/dx_{n+1}, one RK4
 // step is reversed stage by stage (stage inputs X_s and dSigma_s = K X_s recorded by a

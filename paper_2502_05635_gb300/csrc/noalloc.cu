@@ -1,6 +1,6 @@
-// Low-rank kernel contraction that allocates nothing: y = diag o x + U (S o (V^H x)) on
-// caller-owned device arrays, with its intermediate vectors in a fixed, file-scope device
-// array instead of memory from cudaMalloc.
+// Low-rank kernel contraction of Eq. svd_acc that allocates nothing:
+// y = diag o x + U (S o (V^H x)) on caller-owned device arrays, with its intermediate
+// vectors in a fixed, file-scope device array instead of memory from cudaMalloc.
 //
 // Who needs this: callers that must not allocate device memory on the call path -- code
 // whose device memory is owned by another framework's pool (a plain cudaMalloc would
