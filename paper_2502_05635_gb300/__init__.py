@@ -136,6 +136,8 @@ _CTX_INFO: dict[int, dict] = {}
 # ---------------------------------------------------------------- one-to-one names ------
 
 def tdagw_create(desc: ModelDesc, stream: int | None = None) -> int:
+    """New context for one model (no device memory yet); returns the handle.  stream: a
+    cudaStream_t as an int (None: the legacy default stream)."""
     h = _P()
     _check(lib().tdagw_create(ct.byref(desc), _P(stream or 0), ct.byref(h)))
     _CTX_INFO[h.value] = {"dtype": int(desc.dtype), "kdiag": 0, "B": 1}
@@ -143,16 +145,20 @@ def tdagw_create(desc: ModelDesc, stream: int | None = None) -> int:
 
 
 def tdagw_build_kernel(ctx: int):
+    """Builds the model on the host and the dense kernel K on the device (Eq. bse-direct-def,
+    plus the exchange term when the model has one)."""
     _check(lib().tdagw_build_kernel(_P(ctx)))
 
 
 def tdagw_model_info(ctx: int):
+    """(N, Nb, Nk) of the context's model (no GPU needed)."""
     n, nb, nk = ct.c_int64(), ct.c_int(), ct.c_int()
     _check(lib().tdagw_model_info(_P(ctx), ct.byref(n), ct.byref(nb), ct.byref(nk)))
     return n.value, nb.value, nk.value
 
 
 def tdagw_get_model(ctx: int):
+    """Host copies of the built model: eps (Nk, Nb), dx, dy, vx and U (Nk, Nb, Nb)."""
     N, Nb, Nk = tdagw_model_info(ctx)
     eps = np.empty(Nk * Nb)
     dx, dy, vx, U = (np.empty(Nk * Nb * Nb, np.complex128) for _ in range(4))
@@ -163,6 +169,7 @@ def tdagw_get_model(ctx: int):
 
 
 def tdagw_get_kernel_entries(ctx: int, rows, cols) -> np.ndarray:
+    """K[rows[i], cols[i]] from the device kernel, complex128."""
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     cols = np.ascontiguousarray(cols, dtype=np.int64)
     out = np.empty(rows.size, np.complex128)
@@ -173,6 +180,8 @@ def tdagw_get_kernel_entries(ctx: int, rows, cols) -> np.ndarray:
 
 def tdagw_compress_svd(ctx: int, rank: int, oversample: int = 64, power_iters: int = 2,
                        seed: int = 1, precision: int = 0):
+    """Randomised truncated SVD of K^off on the device (Eq. svd_diag_offdiag); precision 1
+    also emits split-FP16 factors for TDAGW_FLAG_SPLIT_F16."""
     _check(lib().tdagw_compress_svd(_P(ctx), rank, oversample, power_iters, seed, precision))
 
 
@@ -194,6 +203,8 @@ def tdagw_set_factors(ctx: int, U, S, V, diag=None):
 
 
 def tdagw_set_kdiag_blocks(ctx: int, on: int):
+    """Selects the reading of K^diag: 0 the strict diagonal, 1 the k = k' blocks (removes
+    installed low-rank factors when it changes)."""
     _check(lib().tdagw_set_kdiag_blocks(_P(ctx), int(on)))
     _CTX_INFO.setdefault(ctx, {})["kdiag"] = int(on)
 
@@ -215,6 +226,8 @@ def tdagw_get_factors(ctx: int, kblocks: bool = False):
 
 def tdagw_compress_channels(ctx: int, rank: int, oversample: int = 64, power_iters: int = 2,
                             seed: int = 1, rel_tol: float = 0.0):
+    """Channel-wise compression (Eq. svd-channel-wise): a randomised SVD of every off-diagonal
+    channel, rank <= `rank`, dropping singular values below rel_tol of the channel's largest."""
     _check(lib().tdagw_compress_channels(_P(ctx), rank, oversample, power_iters, seed, rel_tol))
 
 
@@ -315,6 +328,7 @@ def tdagw_observables(ctx: int, out=None, B: int = 1) -> np.ndarray:
 
 
 def tdagw_get_state(ctx: int):
+    """(drho, Kahan carry, step) of the single-trajectory state, complex128 host arrays."""
     N = tdagw_model_info(ctx)[0]
     drho = np.empty(N, np.complex128)
     carry = np.empty(N, np.complex128)
@@ -324,6 +338,7 @@ def tdagw_get_state(ctx: int):
 
 
 def tdagw_set_state(ctx: int, drho, carry=None, step: int = 0):
+    """Installs a single-trajectory state (to resume a run); carry None means zero."""
     drho = np.ascontiguousarray(drho, np.complex128)
     c = None if carry is None else np.ascontiguousarray(carry, np.complex128)
     N = tdagw_model_info(ctx)[0]
@@ -384,14 +399,18 @@ def tdagw_hhg_spectrum(J, steps, dt: float, omega, component: int | None = None,
 
 
 def tdagw_sync(ctx: int):
+    """Waits for the context's stream; raises TDAGW_ERR_TIMEOUT if a bounded device wait
+    of the last propagation gave up."""
     _check(lib().tdagw_sync(_P(ctx)))
 
 
 def tdagw_last_error() -> str:
+    """Message of the last failing call on this thread."""
     return lib().tdagw_last_error().decode()
 
 
 def tdagw_destroy(ctx: int):
+    """Frees the context and everything it allocated."""
     lib().tdagw_destroy(_P(ctx))
     _CTX_INFO.pop(ctx, None)
 
