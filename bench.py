@@ -163,6 +163,14 @@ def _profiled_traffic(stages: int):
     return int(per.group(1)) * stages
 
 
+def workload_config(n_gpus: int) -> dict:
+    """The headline workload's `config`, the same on both arms."""
+    w = wl.mos2size_nb4_l36()
+    return {"workload": w.name, "N": w.model.N, "Nk": w.model.Nk, "Nb": w.model.Nb, "rank": w.rank,
+            "B": 1, "dt": w.dt, "parallelism": f"replicas x{n_gpus}",
+            "l2": "inputs larger than L2 (low-rank factors 340 MB, dense kernel 3.44 GB)"}
+
+
 # ---------------------------------------------------------------- oracle leg --------
 
 def oracle_lowrank_rate(max_seconds: float, max_steps: int, warmup: int = 1):
@@ -199,8 +207,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus,
             "steps": n, "warmup": warm, "ms_per_step": 1e3 / rate, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)", "data": "synthetic",
-            "config": {"workload": "mos2size_nb4_l36", "N": 20736, "rank": 1024, "B": 1,
-                       "mode": "low-rank"},
+            "config": workload_config(a.gpus),
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {n} RK4 steps of the mos2size_nb4_l36 trajectory, "
                                        f"low-rank apply with seeded rank-1024 factors ({secs:.1f} s)"},
@@ -605,9 +612,7 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": ms_lr / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32, Kahan-compensated state)",
         "data": "synthetic",
-        "config": {"workload": "mos2size_nb4_l36", "N": N, "Nk": 1296, "Nb": 4, "rank": r,
-                   "B": 1, "dt": dt, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (low-rank factors 340 MB, dense kernel 3.44 GB)"},
+        "config": workload_config(ws),
         "full_kernel": {"value": full_value, "unit": UNIT, "steps": nf,
                         "ms_per_step": ms_full / nf,
                         "apply_gbs": achieved_full, "apply_ms": ms_apply_full},
