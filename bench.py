@@ -16,7 +16,7 @@ Secondary legs, run after the headline region and reported in the same JSON line
 also alone with `--leg NAME`): `batched_sweep` (256 uneven trajectories: FP32, split-FP16
 tensor cores, dense), `precision_study` (N = 36864, rank 2048, B = 64), `adjoint`
 (checkpointed forward + backward sweep), `channel_wise` (the channel-wise compressed
-kernel at the mos2 size), `angle_hhg` (60 field directions, then their HHG spectra) and
+kernel at the mos2 size), `angle_hhg` (60 field directions, then their HHG spectra),
 `channel_wise_sweep` (the field sweep with the channel-wise kernel, batched) and
 `kdiag_split` (the two readings of K^diag on the direct + exchange kernel).
 
