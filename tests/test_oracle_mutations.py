@@ -224,3 +224,51 @@ def test_unconjugated_bra_in_velocity_breaks_heisenberg_pin():
     want = 1j * (mdl.eps[:, :, None] - mdl.eps[:, None, :]) * mdl.dx
     off = ~np.eye(mdl.Nb, dtype=bool)
     assert np.abs(v[:, off] - want[:, off]).max() > 1e-3
+
+
+def _W_slipped(slip):
+    """A copy of W_of_offsets with one plausible slip planted."""
+    good_W0 = ok.cell_average_W0
+
+    def W(di, dj, p):
+        L, a = p.L, p.a
+        A = (a * a) if slip == "area_a2" else p.Nk * a * a
+        step = 2.0 * np.pi / L if slip == "q_without_a" else 2.0 * np.pi / (L * a)
+        q = np.hypot(di * step, dj * step)
+        out = np.empty_like(q)
+        nz = q > 0
+        if slip == "screening_over_r0":
+            out[nz] = 2.0 * np.pi / (A * q[nz] * (1.0 + q[nz] / p.r0))
+        elif slip == "no_two_pi":
+            out[nz] = 1.0 / (A * q[nz] * (1.0 + p.r0 * q[nz]))
+        else:
+            out[nz] = 2.0 * np.pi / (A * q[nz] * (1.0 + p.r0 * q[nz]))
+        out[~nz] = good_W0(np.pi / (L * a), A, p.r0)
+        return out
+    return W
+
+
+@pytest.mark.parametrize("slip", ["area_a2", "q_without_a", "screening_over_r0", "no_two_pi"])
+def test_slipped_W_breaks_brillouin_zone_pin(monkeypatch, slip):
+    """Slips in W(q != 0): the area a^2 instead of Nk a^2, the q spacing 2 pi / L without the
+    lattice constant, the screening factor (1 + |q| / r0), a dropped 2 pi.  Each misses the
+    Brillouin-zone integral of the Rytova-Keldysh interaction."""
+    import test_oracle_pins as pins
+    monkeypatch.setattr(ok, "W_of_offsets", _W_slipped(slip))
+    raw, rich = pins.bz_sum_errors(Ls=(48, 96, 192))
+    assert np.abs(rich).max() > 1e-2 or np.abs(raw[:, -1]).max() > 1e-1
+
+
+@pytest.mark.parametrize("slip", ["over_N", "over_Nk_Nb", "plain_sum"])
+def test_wrong_observables_normalisation_breaks_pin(monkeypatch, slip):
+    """Slips in the k-sum normalisation of P, J and occupation: 1/N, 1/(Nk Nb), no 1/Nk."""
+    import test_oracle_pins as pins
+    good = op.observables
+
+    def bad(model, X):
+        o = good(model, X)
+        scale = {"over_N": 1.0 / (model.Nb * model.Nb), "over_Nk_Nb": 1.0 / model.Nb,
+                 "plain_sum": float(model.Nk)}[slip]
+        return o * scale
+    monkeypatch.setattr(op, "observables", bad)
+    assert pins.observables_normalisation_errors() > 1e-3

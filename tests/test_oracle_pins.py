@@ -4,6 +4,8 @@ Each test fixes a part of the oracle with something other than the oracle itself
 that a dropped term, a wrong sign or index, or a transposed operand fails one of them.
 No GPU.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.integrate
@@ -128,6 +130,75 @@ def test_cell_average_unscreened_limit():
     got = ok.cell_average_W0(h, A, 1e-10)
     want = (2 * np.pi / A) * 2 * np.log1p(np.sqrt(2.0)) / h
     assert abs(got - want) / want < 1e-8
+
+
+def bz_lattice_sum(L, R, r0=20.0, a=6.0):
+    """sum_q W(q) cos(q . R) over the L x L grid with the oracle's W (W0 at q = 0)."""
+    p = dataclasses.replace(wl.small_model(L, 1), r0=r0, a=a)
+    di = ok.min_image(np.arange(L), L)
+    DI, DJ = np.meshgrid(di, di, indexing="ij")
+    W = ok.W_of_offsets(DI, DJ, p)
+    dq = 2 * np.pi / (L * a)
+    return float(np.sum(W * np.cos(dq * (DI * R[0] + DJ * R[1]))))
+
+
+def bz_continuum(R, r0=20.0, a=6.0):
+    """int over the square Brillouin zone |qx|,|qy| <= pi/a of d^2q/(2 pi)^2 of the 2D
+    Rytova-Keldysh interaction 2 pi / (|q| (1 + r0 |q|)) times cos(q . R), by adaptive
+    quadrature in polar coordinates (the 1/|q| singularity cancels against the Jacobian)."""
+    qm = np.pi / a
+    rmax = lambda th: qm / max(abs(np.cos(th)), abs(np.sin(th)))
+    f = lambda q, th: np.cos(q * (np.cos(th) * R[0] + np.sin(th) * R[1])) / (2 * np.pi * (1 + r0 * q))
+    edges = [k * np.pi / 4 for k in range(9)]                  # split at the square's corners
+    return sum(scipy.integrate.dblquad(f, t0, t1, lambda th: 0.0, rmax, epsabs=1e-13, epsrel=1e-11)[0]
+               for t0, t1 in zip(edges, edges[1:]))
+
+
+BZ_R = [(0.0, 0.0), (6.0, 0.0), (12.0, 0.0), (6.0, 6.0), (30.0, 0.0)]
+
+
+def bz_sum_errors(Ls=(96, 192, 384)):
+    """Relative deviation of the lattice sums from the continuum integral, per R and L, and
+    of the Richardson extrapolation 2 s(L_max) - s(L_max / 2)."""
+    raw, rich = [], []
+    for R in BZ_R:
+        c = bz_continuum(R)
+        s = [bz_lattice_sum(L, R) for L in Ls]
+        raw.append([(x - c) / c for x in s])
+        rich.append((2 * s[-1] - s[-2] - c) / c)
+    return np.array(raw), np.array(rich)
+
+
+def test_W_lattice_sum_converges_to_brillouin_zone_integral():
+    """W(q) at q != 0 (Eq. bse-direct-def with the Rytova-Keldysh screening of Appendix B):
+    with the Born-von Karman area A = Nk a^2 the sum over the k-grid of W(q) e^{iq.R} is a
+    Riemann sum of the continuum integral over the Brillouin zone (spacing 2 pi / (L a),
+    cell area (2 pi)^2 / A), so it must converge to that integral, computed here by adaptive
+    quadrature, with an error falling as 1/L at every lattice vector R.  A wrong area
+    (a^2), screening factor (1 + |q| / r0), prefactor or q spacing misses the integral by
+    a factor, whatever the grid."""
+    raw, rich = bz_sum_errors()
+    assert np.abs(raw[:, -1]).max() < 1e-2, raw
+    ratio = raw[:, 1] / raw[:, 2]
+    assert np.all((ratio > 1.8) & (ratio < 2.2)), ratio       # first order in 1/L
+    assert np.abs(rich).max() < 2e-4, rich
+
+
+def test_W_real_space_tail_is_rytova_keldysh():
+    """Far from the origin the potential of 2 pi / (|q| (1 + r0 |q|)) is the Rytova-Keldysh
+    form (pi / (2 r0)) [H0(R / r0) - Y0(R / r0)] (Struve H0, Neumann Y0; the 2D Fourier
+    transform of the interaction).  Leaving out |q| > pi/a changes it by a share that decays
+    with R, so at R = 10 a .. 30 a both the Brillouin-zone integral and the oracle's lattice
+    sums (extrapolated from L = 384, 768) must land on the closed form: this ties the
+    oracle's q-grid scale and prefactors to real-space distance without any quadrature."""
+    import scipy.special
+    r0, a = 20.0, 6.0
+    for n in (10, 20, 30):
+        R = (n * a, 0.0)
+        want = np.pi / (2 * r0) * (scipy.special.struve(0, R[0] / r0) - scipy.special.y0(R[0] / r0))
+        s1, s2 = bz_lattice_sum(384, R), bz_lattice_sum(768, R)
+        assert abs(2 * s2 - s1 - want) < 3e-3 * want, (n, 2 * s2 - s1, want)
+        assert abs(bz_continuum(R) - want) < 3e-3 * want
 
 
 # ---------------------------------------------------------------- kernel -------------
@@ -305,6 +376,48 @@ def test_strong_field_pulse_area_closed_form(w, T):
     assert abs(q - _sin2_pulse_area(p.E0, w, T)) < 1e-9 * abs(q)
     assert op.field_value(p, -0.5) == 0.0 and op.field_value(p, T + 0.5) == 0.0
     assert abs(op.field_value(p, 0.0)) < 1e-15 and abs(op.field_value(p, T)) < 1e-12 * p.E0
+
+
+def observables_normalisation_errors():
+    """Largest deviation of the oracle's (P_x, J_x, occ) from the single-k-point expectation
+    values Tr(rho d), Tr(rho v), rho_c1c1 (scalar loops) for states that are the same at
+    every k-point: the four-band model with one k-point's dipole, velocity and state copied
+    to all 16 k-points, and the one-k-point two-band model.  Observables per unit cell
+    (the 1/Nk reading of the k-sum) do not change when a k-point is repeated."""
+    import copy
+    rng = np.random.default_rng(8)
+    errs = []
+    for p, k0 in ((wl.small_model(4, 2), 5), (wl.small_model(1, 1), 0)):
+        m = om.Model(p)
+        Nb = m.Nb
+        mt = copy.copy(m)
+        mt.dx = np.broadcast_to(m.dx[k0], m.dx.shape).copy()
+        mt.vx = np.broadcast_to(m.vx[k0], m.vx.shape).copy()
+        X0 = rng.standard_normal((Nb, Nb)) + 1j * rng.standard_normal((Nb, Nb))
+        X0 = 0.01 * (X0 + X0.conj().T)
+        X = np.broadcast_to(X0, (m.Nk, Nb, Nb)).reshape(-1).copy()
+        rho = np.diag(m.occ) + X0
+        want = [0.0, 0.0, rho[m.c1, m.c1].real]
+        for n in range(Nb):
+            for mm in range(Nb):
+                want[0] += (rho[n, mm] * m.dx[k0][mm, n]).real
+                want[1] += (rho[n, mm] * m.vx[k0][mm, n]).real
+        errs.append(np.abs(op.observables(mt, X) - np.array(want)).max())
+    # physical case: a fraction f of each k-point's valence population moved to c1 gives
+    # occupation f per unit cell on the real (k-dependent) model
+    m = om.Model(wl.small_model(4, 2))
+    f = 0.125
+    X = np.zeros((m.Nk, m.Nb, m.Nb), complex)
+    X[:, 0, 0], X[:, m.c1, m.c1] = -f, f
+    errs.append(abs(op.observables(m, X.reshape(-1))[2] - f))
+    return max(errs)
+
+
+def test_observables_are_per_k_point_expectation_values():
+    """P, J and occupation are per-unit-cell expectation values (the reading of the
+    paper's unnormalised k-sums as (1/Nk) sum_k): a k-uniform state gives the one-k-point
+    values; 1/N, 1/(Nk Nb) or a plain sum would scale them by Nb^-2, Nb^-1 or Nk."""
+    assert observables_normalisation_errors() < 1e-15
 
 
 def test_stationary_without_field(m4):
