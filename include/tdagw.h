@@ -281,8 +281,10 @@ int tdagw_set_state(tdagw_ctx* ctx, const double* drho, const double* carry, int
  * All calls share the array and it keeps the last call's contents; every value a call
  * reads from it is written by the same call first, so nothing needs clearing.  Calls
  * whose work overlaps on the GPU (other streams, other host threads) race on the array:
- * serialise them.  Errors: TDAGW_ERR_INVALID_ARG for NULL or misaligned pointers, N < 1,
- * rank outside [1, 2048], odd ld or ld < rank; TDAGW_ERR_CUDA if the address lookup or a
+ * serialise them.  The work runs on the current device; every array must be device (or
+ * managed) memory of that device.  Errors: TDAGW_ERR_INVALID_ARG for NULL or misaligned
+ * pointers, N < 1, rank outside [1, 2048], odd ld or ld < rank, and for a pointer that is
+ * host memory or memory of another device; TDAGW_ERR_CUDA if the address lookup or a
  * launch fails. */
 int tdagw_apply_lowrank_noalloc(const void* U, const void* V, int64_t ld, const float* S,
                                 const void* diag, int64_t N, int rank, const void* x, void* y,

@@ -357,11 +357,14 @@ def tdagw_apply_lowrank_noalloc(U, V, S, diag, x, y, stream: int | None = None):
           "S must be contiguous float32 (rank,) with rank <= ld")
     for t, name in ((diag, "diag"), (x, "x"), (y, "y")):
         _dev_vec(t, N, torch.complex64, name)
+    ptrs = [_devptr(t) for t in (U, V, S, diag, x, y)]          # CUDA tensors only
     devs = {t.device for t in (U, V, S, diag, x, y)}
     _need(len(devs) == 1, "all tensors must be on one device")
-    _check(lib().tdagw_apply_lowrank_noalloc(
-        _P(_devptr(U)), _P(_devptr(V)), ld, _P(_devptr(S)), _P(_devptr(diag)), N, S.shape[0],
-        _P(_devptr(x)), _P(_devptr(y)), _P(stream or 0)))
+    # the library launches on the current device: make it the tensors' device
+    with torch.cuda.device(U.device):
+        _check(lib().tdagw_apply_lowrank_noalloc(
+            _P(ptrs[0]), _P(ptrs[1]), ld, _P(ptrs[2]), _P(ptrs[3]), N, S.shape[0],
+            _P(ptrs[4]), _P(ptrs[5]), _P(stream or 0)))
 
 
 def tdagw_adjoint(ctx: int, dJdobs, steps_max: int, B: int):

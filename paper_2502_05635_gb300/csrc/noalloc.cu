@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -33,9 +34,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-float2* scratch_for_current_device() {
-    int dev = 0;
-    TDAGW_CUDA(cudaGetDevice(&dev));
+// Every array must live on the device the work is launched on (the current one): the
+// kernels and the scratch address are per device, so a pointer into another GPU's memory
+// or into host memory is rejected instead of being dereferenced across the bus.
+void require_on_device(const void* p, int dev, const char* name) {
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error(TDAGW_ERR_INVALID_ARG, std::string(name) + ": not a CUDA pointer (" +
+                                               cudaGetErrorString(e) + ")");
+    }
+    const bool ok = (a.type == cudaMemoryTypeDevice && a.device == dev) ||
+                    a.type == cudaMemoryTypeManaged;
+    TDAGW_REQUIRE(ok, TDAGW_ERR_INVALID_ARG,
+                  std::string(name) + " is not device memory of the current device (" +
+                      std::to_string(dev) + ")");
+}
+
+float2* scratch_for_device(int dev) {
     TDAGW_REQUIRE(dev >= 0 && dev < kMaxDevices, TDAGW_ERR_UNSUPPORTED, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ptr[dev]) {
@@ -69,7 +86,12 @@ extern "C" int tdagw_apply_lowrank_noalloc(const void* U, const void* V, int64_t
                           ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0),
                       TDAGW_ERR_INVALID_ARG, "U, V, x and y must be 16-byte aligned");
         TDAGW_REQUIRE(x != y, TDAGW_ERR_INVALID_ARG, "x and y must not alias");
-        float2* scratch = scratch_for_current_device();
+        int dev = 0;
+        TDAGW_CUDA(cudaGetDevice(&dev));
+        const void* arrays[6] = {U, V, S, diag, x, y};
+        const char* names[6] = {"U", "V", "S", "diag", "x", "y"};
+        for (int i = 0; i < 6; ++i) require_on_device(arrays[i], dev, names[i]);
+        float2* scratch = scratch_for_device(dev);
         float2* part = scratch;                                        // blocks x rank
         float2* ytil = scratch + (size_t)kNoallocBlocks * kNoallocMaxRank;  // rank
         cudaStream_t s = static_cast<cudaStream_t>(stream);

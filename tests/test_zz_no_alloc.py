@@ -57,6 +57,46 @@ def test_noalloc_matches_context_apply_twice(L, nc, rank):
     ctx.close()
 
 
+def test_noalloc_small_N_wide_ld_vs_numpy():
+    """N below the 152 row blocks of the V^H x pass (one block per row) and a row stride
+    far above the rank, against a NumPy complex128 evaluation of diag o x + U (S o (V^H x))."""
+    N, rank, ld = 64, 24, 40
+    rng = np.random.default_rng(21)
+    U = (rng.standard_normal((N, ld)) + 1j * rng.standard_normal((N, ld))) / 20
+    V = (rng.standard_normal((N, ld)) + 1j * rng.standard_normal((N, ld))) / 20
+    S = rng.uniform(0.1, 1.0, rank).astype(np.float32)
+    d = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    Ud, Vd, dd = _c64(U), _c64(V), _c64(d)
+    Sd = torch.from_numpy(S).cuda()
+    # the padding columns [rank, ld) hold values that must not enter the result
+    for seed in (31, 32):
+        xh = wl.random_state(N, seed)
+        x = _c64(xh)
+        y = torch.empty_like(x)
+        tg.tdagw_apply_lowrank_noalloc(Ud, Vd, Sd, dd, x, y)
+        torch.cuda.synchronize()
+        Uc, Vc = U.astype(np.complex64).astype(complex), V.astype(np.complex64).astype(complex)
+        xc = xh.astype(np.complex64).astype(complex)
+        want = d.astype(np.complex64) * xc + Uc[:, :rank] @ (S * (Vc[:, :rank].conj().T @ xc))
+        err = np.abs(y.cpu().numpy() - want).max() / np.abs(want).max()
+        assert err < 2e-6, (seed, err)
+
+
+def test_noalloc_rejects_host_pointers():
+    """Host memory passed where device memory is expected is refused before any launch."""
+    import ctypes as ct
+    N, rank = 64, 8
+    Ud = torch.zeros((N, rank), dtype=torch.complex64, device="cuda")
+    Sd = torch.ones(rank, dtype=torch.float32, device="cuda")
+    dd = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    y = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    xh = np.zeros(N, np.complex64)
+    rc = tg.lib().tdagw_apply_lowrank_noalloc(
+        ct.c_void_p(Ud.data_ptr()), ct.c_void_p(Ud.data_ptr()), rank, ct.c_void_p(Sd.data_ptr()),
+        ct.c_void_p(dd.data_ptr()), N, rank, ct.c_void_p(xh.ctypes.data), ct.c_void_p(y.data_ptr()), None)
+    assert rc == tg.ERR_INVALID_ARG and "x" in tg.tdagw_last_error()
+
+
 def test_noalloc_takes_no_device_memory_after_first_call():
     N, rank = 1296, 64
     rng = np.random.default_rng(3)
@@ -68,11 +108,15 @@ def test_noalloc_takes_no_device_memory_after_first_call():
     y = torch.empty_like(x)
     tg.tdagw_apply_lowrank_noalloc(Ud, Vd, Sd, dd, x, y)
     torch.cuda.synchronize()
+    # device-wide free memory (sees any cudaMalloc of the library, which torch's own
+    # counters would not) and torch's allocator, which this process alone uses
+    alloc0 = torch.cuda.memory_allocated()
     free0 = torch.cuda.mem_get_info()[0]
     for _ in range(3):
         tg.tdagw_apply_lowrank_noalloc(Ud, Vd, Sd, dd, x, y)
     torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] >= free0
 
 
 def test_noalloc_rejects_bad_sizes():
