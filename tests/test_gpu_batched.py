@@ -143,3 +143,34 @@ def test_sweep_full_size_sampled_vs_oracle():
         assert op.rel_l2(split[:T + 1, b, 0], ref[:, 0]) < 1e-4, b
     for b, T in enumerate(w.steps):
         assert np.all(np.isnan(fp32[T + 1:, b])) and np.all(np.isnan(split[T + 1:, b]))
+
+
+@pytest.mark.parametrize("mode,flags", [(tg.LOWRANK, tg.FLAG_RESET), (tg.FULL, tg.FLAG_RESET),
+                                        (tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16)])
+def test_zero_step_trajectories_inside_a_batch(mode, flags):
+    """Trajectories of zero steps next to running ones: their only row is the equilibrium
+    observables at t = 0 and every later row is NaN; the others match the oracle."""
+    p = wl.small_model(12, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, 29)
+    ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(ctx.h, U, S, V, d)
+    steps = [40, 0, 25, 0, 7]
+    pulses = _pulses(len(steps), 5)
+    got = ctx.propagate_batch(pulses, steps, 0.2, mode, flags)
+    assert got.shape == (41, 5, 3)
+    eq = op.observables(mdl, np.zeros(mdl.N, complex))
+    apply = (lambda v: olr.apply_lowrank(d, U, S, V, v)) if mode == tg.LOWRANK else (lambda v: K @ v)
+    tol = 1e-4 if flags & tg.FLAG_SPLIT_F16 else 1e-5
+    for b, (pl, T) in enumerate(zip(pulses, steps)):
+        if T == 0:
+            np.testing.assert_allclose(got[0, b], eq, atol=1e-7)
+            assert np.all(np.isnan(got[1:, b]))
+            continue
+        s = op.half_step_samples(pl, 0.2, T)
+        ref, _ = op.rk4(mdl, apply, s, 0.2, T, direction=(pl.dir_x, pl.dir_y))
+        assert op.rel_l2(got[:T + 1, b, 0], ref[:, 0]) < tol, b
+        assert np.all(np.isnan(got[T + 1:, b]))
+    ctx.close()

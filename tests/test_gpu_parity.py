@@ -174,6 +174,41 @@ def test_persistent_lowrank_vs_oracle_and_stagewise(L, nc, rank):
         assert op.rel_l2(a[:, j], b[:, j]) < 1e-6, j
 
 
+@pytest.mark.parametrize("L,nc,rank,kblocks", [(13, 1, 40, False), (14, 2, 64, False), (14, 2, 33, True),
+                                                (40, 1, 128, True)])
+def test_persistent_uneven_shares_vs_oracle(L, nc, rank, kblocks):
+    """More k-points than CTAs (169, 196 and 1600 k-points over at most 152 CTAs: CTAs own
+    one or two more k-points than others), with and without the k = k' block term.  Seeded
+    factors (and seeded Hermitian blocks) on both sides; vs the oracle and vs the
+    stage-wise kernels."""
+    p = wl.small_model(L, nc)
+    mdl = om.Model(p)
+    U, S, V, d = wl.random_factors(mdl.N, rank, seed=L + rank)
+    P = mdl.Nb * mdl.Nb
+    if kblocks:
+        rng = np.random.default_rng(L)
+        Bk = 0.004 * (rng.standard_normal((mdl.Nk, P, P)) + 1j * rng.standard_normal((mdl.Nk, P, P)))
+        Bk = Bk + np.conj(np.swapaxes(Bk, 1, 2))
+        apply = lambda v: olr.apply_lowrank_kblocks(Bk, U, S, V, v)  # noqa: E731
+    else:
+        apply = lambda v: olr.apply_lowrank(d, U, S, V, v)  # noqa: E731
+    pulse = wl.Pulse(E0=3e-3, omega=0.1, t0=10.0, sigma=4.0)
+    T = 120
+    ref, _ = op.rk4(mdl, apply, op.half_step_samples(pulse, 0.2, T), 0.2, T)
+    c = _ctx(p, tg.C64)
+    if kblocks:
+        tg.tdagw_set_kdiag_blocks(c.h, True)
+        tg.tdagw_set_factors(c.h, U, S, V, Bk)
+    else:
+        tg.tdagw_set_factors(c.h, U, S, V, d)
+    a = c.propagate(pulse, T, 0.2, tg.LOWRANK)
+    b = c.propagate(pulse, T, 0.2, tg.LOWRANK, flags=tg.FLAG_RESET | tg.FLAG_STAGEWISE)
+    assert np.abs(ref[:, 0]).max() > 1e-7
+    for j in range(3):
+        assert op.rel_l2(a[:, j], ref[:, j]) < 1e-5, j
+        assert op.rel_l2(a[:, j], b[:, j]) < 1e-6, j
+
+
 def test_persistent_timeout_is_reported_and_context_survives(cfg0):
     """Fault injection on the host side of a bounded wait: the grid barrier waits for a
     block that does not exist; every wait gives up after its budget, the call reports
@@ -284,6 +319,31 @@ def test_error_codes_on_device():
 
 
 # ---------------------------------------------------------------- randomised SVD -------
+
+@pytest.mark.parametrize("L,rank", [(24, 256), (36, 512)])
+def test_rsvd_near_optimal_at_sweep_and_gradient_sizes(L, rank):
+    """The randomised SVD (p = 64, q = 2) at the field-sweep size (two-band 24 x 24, N = 2304,
+    rank 256) and the differentiation size (36 x 36, N = 5184, rank 512): its truncation
+    error against the Eckart-Young optimum from an exact LAPACK eigendecomposition of the
+    oracle's K^off (Hermitian: sigma = |lambda|), and the leading singular values."""
+    import scipy.linalg
+    p = wl.small_model(L, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    del K
+    lam = scipy.linalg.eigvalsh(Koff)
+    sv = np.sort(np.abs(lam))[::-1]
+    c = _ctx(p, tg.C64)
+    tg.tdagw_compress_svd(c.h, rank, 64, 2, 1)
+    U, S, V, d2 = tg.tdagw_get_factors(c.h)
+    err = np.linalg.norm(Koff - (U * S) @ V.conj().T)
+    opt = np.sqrt(np.sum(sv[rank:] ** 2))
+    print(f"N = {mdl.N}, rank {rank}: error / optimal = {err / opt:.5f}")
+    assert err <= 1.01 * opt
+    np.testing.assert_allclose(S[:rank // 4], sv[:rank // 4], rtol=1e-3)
+    c.close()
+
 
 @pytest.mark.parametrize("dtype", [tg.C64, tg.C128])
 def test_rsvd_near_optimal(dtype):
