@@ -1,13 +1,17 @@
 // Randomised truncated SVD of K^off = K - diag(K) on the device (setup of Eq.
-// svd_diag_offdiag; with the k-block reading of K^diag, K^off = K minus its k = k' blocks).  K^off is Hermitian, so its singular triplets follow from an
-// eigen-decomposition: sigma_j = |lambda_j|, u_j = q_j, v_j = sign(lambda_j) q_j.
+// svd_diag_offdiag; with the k-block reading of K^diag, K^off = K minus its k = k' blocks).
 //
 // Range finder (Halko, Martinsson, Tropp 2011, randomised subspace iteration with
 // re-orthonormalisation after every product):
 //   Y = K^off Omega (Omega: N x l complex Gaussian, l = rank + oversample), Q = orth(Y)
 //   repeat 2 * power_iters times:  Q = orth(K^off Q)
-//   B = Q^H K^off Q (l x l Hermitian), B = W diag(lambda) W^H (parallel two-sided Jacobi)
-//   keep the `rank` largest |lambda|:  U = Q W_r,  S = |lambda|,  V = U diag(sign lambda)
+// then the SVD of B = Q^H K^off (l x N), the one-sided projection whose truncation error
+// follows the HMT bounds: K^off is Hermitian, so Z = K^off Q is B^H, and
+//   B B^H = Z^H Z = W diag(lambda) W^H (parallel two-sided Jacobi),
+//   sigma_j = sqrt(lambda_j),  U = Q W_r,  V = Z W_r diag(1 / sigma)   (B = W Sigma V^H)
+// keeping the `rank` largest.  The core squares the singular values, so sigma_j below
+// 1e-7 sigma_0 is not resolved in FP64: such a triplet is kept with sigma_j = 0 (a zero V
+// column) and contributes nothing.
 // Products with K run in the context precision; Q, B, W and all orthogonalisation are FP64
 // (block classical Gram-Schmidt with reorthogonalisation, panels of 64 columns, each panel
 // made orthonormal by two Cholesky-QR passes).
@@ -365,21 +369,18 @@ __global__ void eye_kernel(double2* __restrict__ W, int n) {
     W[e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
 }
 
-// Final factors in the context precision: U and V (N x ldu, pad column zero) with
-// V[i][j] = sign_j U[i][j] (K^off Hermitian: v_j = sign(lambda_j) u_j).
+// A final factor in the context precision: F (N x ldu, pad column zero) from the FP64
+// N x r matrix Fq.
 template <typename R>
-__global__ void emit_factors_kernel(const double2* __restrict__ Uq, int64_t N, int r, int ldu,
-                                    const double* __restrict__ sgn, cplx_t<R>* __restrict__ U,
-                                    cplx_t<R>* __restrict__ V) {
+__global__ void emit_factors_kernel(const double2* __restrict__ Fq, int64_t N, int r, int ldu,
+                                    cplx_t<R>* __restrict__ F) {
     const int64_t tot = N * ldu;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / ldu;
         const int j = (int)(e % ldu);
-        const double2 v = j < r ? Uq[i * r + j] : make_double2(0, 0);
-        const double sg = j < r ? sgn[j] : 1.0;
-        U[e] = mk((R)v.x, (R)v.y);
-        V[e] = mk((R)(sg * v.x), (R)(sg * v.y));
+        const double2 v = j < r ? Fq[i * r + j] : make_double2(0, 0);
+        F[e] = mk((R)v.x, (R)v.y);
     }
 }
 
@@ -522,16 +523,16 @@ void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t s
         std::swap(Q.bytes, Z.bytes);
         orthonormalise(w, Q.as<double2>(), N, l, H, P2, Gb, Mb);
     }
-    // B = Q^H K^off Q
+    // Z = K^off Q = B^H (B = Q^H K^off), core B B^H = Z^H Z
     apply_koff<R>(w, c, Q.as<double2>(), Z.as<double2>(), l);
     Bm.ensure((size_t)l * l * sizeof(double2));
     Wm.ensure((size_t)l * l * sizeof(double2));
-    gemm<double2, double2, double, true, false>(w, l, l, (int)N, Q.as<double2>(), l, Z.as<double2>(),
+    gemm<double2, double2, double, true, false>(w, l, l, (int)N, Z.as<double2>(), l, Z.as<double2>(),
                                                  l, Bm.as<double2>(), l, kOne, kZero);
     hermitise_kernel<<<(unsigned)(((int64_t)l * l + 255) / 256), 256, 0, w.s>>>(Bm.as<double2>(), l);
     check_launch("hermitise_kernel");
     jacobi_eigh(w, Bm.as<double2>(), Wm.as<double2>(), l);
-    // eigenvalues, order by |lambda|
+    // eigenvalues sigma^2, largest first
     std::vector<double2> hb((size_t)l * l);
     TDAGW_CUDA(cudaMemcpyAsync(hb.data(), Bm.p, hb.size() * sizeof(double2), cudaMemcpyDeviceToHost, w.s));
     std::vector<double2> hw((size_t)l * l);
@@ -541,35 +542,48 @@ void rsvd_compress(Ctx& c, int rank, int oversample, int power_iters, uint64_t s
     for (int i = 0; i < l; ++i) lam[i] = hb[(size_t)i * l + i].x;
     std::vector<int> idx(l);
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return std::fabs(lam[a]) > std::fabs(lam[b]); });
-    std::vector<double2> wr((size_t)l * rank);
-    std::vector<double> sv(rank), sg(rank);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+    const double s0 = std::sqrt(std::max(0.0, lam[idx[0]]));
+    std::vector<double2> wr((size_t)l * rank), wv((size_t)l * rank);
+    std::vector<double> sv(rank);
     for (int j = 0; j < rank; ++j) {
         const int src = idx[j];
-        for (int i = 0; i < l; ++i) wr[(size_t)i * rank + j] = hw[(size_t)i * l + src];
-        sv[j] = std::fabs(lam[src]);
-        sg[j] = lam[src] < 0 ? -1.0 : 1.0;
+        double sj = std::sqrt(std::max(0.0, lam[src]));
+        if (!(sj > 1e-7 * s0)) sj = 0.0;
+        sv[j] = sj;
+        for (int i = 0; i < l; ++i) {
+            const double2 e = hw[(size_t)i * l + src];
+            wr[(size_t)i * rank + j] = e;
+            wv[(size_t)i * rank + j] = sj > 0.0 ? make_double2(e.x / sj, e.y / sj) : make_double2(0.0, 0.0);
+        }
     }
-    // U = Q W_r (FP64), into Z
-    DevBuf Wr, dS, dG;
+    // U = Q W_r and V = Z W_r diag(1 / sigma), FP64
+    DevBuf Wr, Uq, Vq, dS;
     Wr.ensure(wr.size() * sizeof(double2));
+    Uq.ensure((size_t)N * rank * sizeof(double2));
+    Vq.ensure((size_t)N * rank * sizeof(double2));
     TDAGW_CUDA(cudaMemcpyAsync(Wr.p, wr.data(), wr.size() * sizeof(double2), cudaMemcpyHostToDevice, w.s));
     gemm<double2, double2, double, false, false>(w, (int)N, rank, l, Q.as<double2>(), l, Wr.as<double2>(),
-                                                 rank, Z.as<double2>(), rank, kOne, kZero);
+                                                 rank, Uq.as<double2>(), rank, kOne, kZero);
+    TDAGW_CUDA(cudaStreamSynchronize(w.s));
+    TDAGW_CUDA(cudaMemcpyAsync(Wr.p, wv.data(), wv.size() * sizeof(double2), cudaMemcpyHostToDevice, w.s));
+    gemm<double2, double2, double, false, false>(w, (int)N, rank, l, Z.as<double2>(), l, Wr.as<double2>(),
+                                                 rank, Vq.as<double2>(), rank, kOne, kZero);
     dS.ensure(rank * sizeof(double));
-    dG.ensure(rank * sizeof(double));
     TDAGW_CUDA(cudaMemcpyAsync(dS.p, sv.data(), rank * sizeof(double), cudaMemcpyHostToDevice, w.s));
-    TDAGW_CUDA(cudaMemcpyAsync(dG.p, sg.data(), rank * sizeof(double), cudaMemcpyHostToDevice, w.s));
+    TDAGW_CUDA(cudaStreamSynchronize(w.s));
     // release the sketch workspace before allocating the factors
     Q.release();
+    Z.release();
     P2.release();
     w.work.release();
     using C = cplx_t<R>;
     const int ldu = rank + (rank & 1);
     c.U.ensure((size_t)N * ldu * sizeof(C));
     c.V.ensure((size_t)N * ldu * sizeof(C));
-    emit_factors_kernel<R><<<152 * 8, 256, 0, w.s>>>(Z.as<double2>(), N, rank, ldu, dG.as<double>(),
-                                                    c.U.as<C>(), c.V.as<C>());
+    emit_factors_kernel<R><<<152 * 8, 256, 0, w.s>>>(Uq.as<double2>(), N, rank, ldu, c.U.as<C>());
+    check_launch("emit_factors_kernel");
+    emit_factors_kernel<R><<<152 * 8, 256, 0, w.s>>>(Vq.as<double2>(), N, rank, ldu, c.V.as<C>());
     check_launch("emit_factors_kernel");
     c.S.ensure(rank * sizeof(R));
     to_real_kernel<R><<<(rank + 255) / 256, 256, 0, w.s>>>(dS.as<double>(), c.S.as<R>(), rank);

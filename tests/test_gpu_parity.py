@@ -340,7 +340,7 @@ def test_rsvd_near_optimal_at_sweep_and_gradient_sizes(L, rank):
     err = np.linalg.norm(Koff - (U * S) @ V.conj().T)
     opt = np.sqrt(np.sum(sv[rank:] ** 2))
     print(f"N = {mdl.N}, rank {rank}: error / optimal = {err / opt:.5f}")
-    assert err <= 1.01 * opt
+    assert err <= 1.01 * opt          # HMT one-sided projection, q = 2 (the bar is 1.1)
     np.testing.assert_allclose(S[:rank // 4], sv[:rank // 4], rtol=1e-3)
     c.close()
 
@@ -427,7 +427,7 @@ def test_full_size_propagation_prefix(big):
 
 
 def test_full_size_rsvd_properties(big):
-    """rank-1024 randomised SVD at N = 20736: orthonormal factors, V = U diag(sign), and a
+    """rank-1024 randomised SVD at N = 20736: orthonormal columns of U and of V, and a
     residual on random probes (K^off x by the oracle's FFT form) well below ||K^off x||."""
     w, mdl, c = big
     tg.tdagw_compress_svd(c.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
@@ -437,7 +437,8 @@ def test_full_size_rsvd_properties(big):
     idx = rng.integers(0, w.rank, 16)
     G = U[:, idx].conj().T @ U[:, idx]
     assert np.abs(G - np.eye(16)).max() < 1e-5
-    assert np.abs(np.abs(V[:, idx]) - np.abs(U[:, idx])).max() < 1e-7
+    GV = V[:, idx].conj().T @ V[:, idx]
+    assert np.abs(GV - np.eye(16)).max() < 1e-4
     fft = ok.fft_applier(mdl)
     dK = ok.kernel_diag(mdl)
     for s_ in range(3):

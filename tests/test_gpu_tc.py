@@ -193,3 +193,36 @@ def test_precision_study_size_vs_oracle():
         ref = _oracle(mdl, apply, pulses[b], steps[b])
         assert op.rel_l2(fp32[:steps[b] + 1, b, 0], ref[:, 0]) < 1e-5, b
         assert op.rel_l2(split[:steps[b] + 1, b, 0], ref[:, 0]) < 1e-4, b
+
+
+def test_precision_study_rsvd_factors_200_steps_vs_oracle():
+    """The precision study as configured: four-band 48 x 48 model (N = 36864), rank 2048
+    from the GPU's randomised SVD of K^off (oversampling 64, two power iterations, FP64
+    orthogonalisation) emitted as split-FP16 tiles, 64 trajectories from the sweep
+    distributions, 200 RK4 steps.  Split-FP16 with Kahan-compensated RK4, FP32 with and
+    without compensation, each against the FP64 oracle run with the same factors
+    (tdagw_get_factors) on the two trajectories whose pulses are widest (largest field in
+    the prefix), and split-FP16 against FP32 on all 64."""
+    w = wl.prec_nb4_l48()
+    mdl = om.Model(w.model)
+    c = tg.Context(w.model, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_compress_svd(c.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED, precision=1)
+    U, S, V, d = tg.tdagw_get_factors(c.h)
+    T, B = 200, w.B
+    steps = [T] * B
+    split = c.propagate_batch(w.pulses, steps, w.dt, tg.LOWRANK, SPLIT)
+    fp32 = c.propagate_batch(w.pulses, steps, w.dt, tg.LOWRANK, tg.FLAG_RESET)
+    plain = c.propagate_batch(w.pulses, steps, w.dt, tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_NO_KAHAN)
+    for b in range(B):
+        assert op.rel_l2(split[:, b, 0], fp32[:, b, 0]) < 1e-4, b
+    apply = lambda v: olr.apply_lowrank(d, U, S, V, v)  # noqa: E731
+    widest = np.argsort([p.sigma for p in w.pulses])[-2:]
+    for b in widest:
+        ref = _oracle(mdl, apply, w.pulses[b], T, w.dt)
+        assert np.abs(ref[:, 0]).max() > 0
+        e_split = op.rel_l2(split[:, b, 0], ref[:, 0])
+        e_fp32 = op.rel_l2(fp32[:, b, 0], ref[:, 0])
+        e_plain = op.rel_l2(plain[:, b, 0], ref[:, 0])
+        print(f"trajectory {b}: split-FP16 {e_split:.2e}, FP32 {e_fp32:.2e}, FP32 uncompensated {e_plain:.2e}")
+        assert e_split < 1e-4 and e_fp32 < 1e-5 and e_plain < 1e-5, (b, e_split, e_fp32, e_plain)
+    c.close()
