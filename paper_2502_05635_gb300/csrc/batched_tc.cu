@@ -4,36 +4,39 @@
 //
 // Per RK4 stage the two products of the low-rank contraction,
 //   Y = V^H X  (r x B)   and   dSigma = K^diag o X + U (S o Y)  (N x B),
-// run as real tcgen05 kind::f16 MMAs with FP32 accumulation in tensor memory.  Complex
-// arithmetic: the factor (the large, streamed operand) is read as an interleaved real
-// matrix (re, im per complex column) and the small operand is expanded to 2 x 2 real
-// blocks, so one real product yields real and imaginary parts in adjacent accumulator
-// columns.  Split FP16: with a = s (a_hi + a_lo), each product is accumulated as
-// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs; the dropped a_lo b_lo is 2^-22 relative).
-// Power-of-two scales keep the FP16 values in range: 2^(13 - e) with 2^e above the largest
-// magnitude, for U and V (measured once when the tiles are made) and, per trajectory, for
-// X (the exact maximum of the stage input) and for S o Y (bound
+// run as real tcgen05 kind::f16 MMAs with FP32 accumulation in tensor memory.  Shape: the
+// small operand (a group of up to 64 trajectories, expanded to 128 real rows) is the MMA's
+// A operand and lives in tensor memory, the factor (the large, streamed operand) is the
+// B operand, 256 rows per tile, read from shared memory: M = 128, N = 256, K = 16.  Keeping
+// A out of shared memory halves the operand traffic of the shared memory per MMA, which
+// bounds the MMA rate when both operands are read from it.  Complex arithmetic: the factor
+// is read as an interleaved real matrix (re, im per complex column) and each trajectory's
+// value becomes two real rows, so one real product yields the real and imaginary parts in
+// adjacent accumulator lanes.  Split FP16: with a = s (a_hi + a_lo), each product is
+// accumulated as a_hi b_hi + a_lo b_hi + a_hi b_lo (three MMAs; the dropped a_lo b_lo is
+// 2^-22 relative).  Power-of-two scales keep the FP16 values in range: 2^(13 - e) with 2^e
+// above the largest magnitude, for U and V (measured once when the tiles are made) and,
+// per trajectory, for X (the exact maximum of the stage input) and for S o Y (bound
 // max|S| max_j ||v_j|| sqrt(2N) max|X|).
 //
 // Work of one stage (one cooperative launch for the whole propagation, one CTA per SM):
-//   A  partials of V^H X over K-ranges of rows: CTA items (trajectory group, pair of
-//      128-row tiles of V^H, K-range).  The V^H tiles (pre-tiled 16 KB blocks in the MMA's
-//      shared-memory layout) stream through a ring by bulk copies; the expanded split X
-//      block is built in shared memory by the worker warps.
+//   A  partials of V^H X over K-ranges of rows: CTA items (trajectory group, 256-row tile
+//      of V^H, K-range).  The V^H tiles (pre-tiled 32 KB blocks in the MMA's shared-memory
+//      layout) stream through a ring by bulk copies; the worker warps write the expanded
+//      split X block of every chunk straight into tensor memory.
 //   -- grid barrier --
-//   B  Y = S o sum of partials (fixed order), expanded and split into the B-operand tiles
-//      of the second product.
+//   B  S o (sum of the partials, fixed order), scaled for FP16.
 //   -- grid barrier --
-//   C  items (one or two 128-row tiles of U, trajectory group): U tiles and the Y tiles
-//      they share stream through the ring; each accumulator (128 rows x 2 columns per
-//      trajectory) is staged through shared memory in two halves and the commutator + RK4
-//      epilogue (Eq. tdagw) runs per (k, b) block.
+//   C  items (256-row tile of U, trajectory group): the U tiles stream through the ring,
+//      the workers write the expanded split S o Y blocks into tensor memory; the
+//      accumulator (128 lanes x 256 rows) is staged through shared memory in quarters and
+//      the commutator + RK4 epilogue (Eq. tdagw) runs per (k, b) block.
 //   -- grid barrier --
-// Roles: warp 0 streams tiles into the ring (running ahead across items), warp 1 issues
-// the MMAs into one of two tensor-memory accumulators, warps 2-9 build operands and drain
-// the other accumulator (epilogue of item i overlaps the MMAs of item i + 1).  Every wait
-// is bounded; on expiry the kernel records an error, lets its own copies and MMAs finish
-// (bounded waits), frees its tensor memory and returns.
+// Roles: warp 0 streams the factor tiles into the ring (it only reads static tiles, so it
+// stays out of the grid barriers and keeps copies in flight across them), warp 1 issues
+// the MMAs, warps 2-9 build the tensor-memory operands and drain the accumulator.  Every
+// wait is bounded; on expiry the kernel records an error, lets its own copies and MMAs
+// finish (bounded waits), frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -54,45 +57,46 @@ using namespace persist;
 
 constexpr int kWorkers = 256;
 constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
-// ring depth and built-B buffers (build-time tuning parameters; smem: (ring + buffers) x 16 KB)
+constexpr int kSyncThreads = kWorkers + 32;  // grid-barrier participants: MMA warp + workers
 #ifndef TDAGW_TC_RING
-#define TDAGW_TC_RING 11
+#define TDAGW_TC_RING 5
 #endif
-#ifndef TDAGW_TC_BBUF
-#define TDAGW_TC_BBUF 2
-#endif
-constexpr int kRing = TDAGW_TC_RING;       // ring slots of one tile each
-constexpr int kBBuf = TDAGW_TC_BBUF;       // built B blocks in flight (phase A)
-static_assert(kRing + kBBuf <= 13, "ring and B buffers must fit in shared memory");
-#ifndef TDAGW_TC_ATILES
-#define TDAGW_TC_ATILES 4
-#endif
-// 128-row V^H tiles per phase A item (2: one accumulator buffer; 4: both buffers, i.e. two
-// accumulator uses per item)
-constexpr int kAMc = TDAGW_TC_ATILES;
-static_assert(kAMc == 2 || kAMc == 4, "phase A items hold 2 or 4 V^H tiles");
-constexpr int kCmb = 16;                   // chunk-completion barriers (ring); every wait on
-                                           // one targets a chunk < kCmb chunks behind the
-                                           // MMA thread's next chunk, so parities cannot alias
-constexpr uint32_t kTile = 16384;          // 128 rows x 32 real columns, hi (8 KB) + lo (8 KB)
-constexpr uint32_t kHalf = 8192;
+constexpr int kRing = TDAGW_TC_RING;       // ring slots of one factor tile each
+constexpr int kAbuf = 4;                   // small-operand blocks in tensor memory
+constexpr int kCmb = 16;                   // chunk-completion barriers; every wait on one
+                                           // targets a chunk < kCmb chunks behind the
+                                           // waiter's next chunk, so parities cannot alias
+constexpr int kRows = 256;                 // factor rows per tile: the MMA's N
+constexpr uint32_t kTile = 32768;          // 256 rows x 32 real columns, hi (16 KB) + lo (16 KB)
+constexpr uint32_t kHalf = 16384;
 constexpr int kKc = 32;                    // real reduction columns per tile (16 complex)
-constexpr int kGroup = 64;                 // trajectories per group: MMA N = 2 x 64 max
+constexpr int kGroup = 64;                 // trajectories per group: the MMA's M = 2 x 64
 constexpr uint32_t kLbo = 128, kSbo = (kKc / 8) * 128;
-constexpr uint32_t kXbuf = kBBuf * kTile;  // B blocks (phase A) / staged half tile (phase C)
-constexpr int kAccCols = 256;              // columns of one accumulator buffer (two buffers)
+constexpr uint32_t kStg = 32768;           // staged quarter tile: 64 rows x 64 trajectories
 constexpr int kTmemCols = 512;
+constexpr uint32_t kAcol = 256;            // tensor-memory columns of the operand blocks
+// The workers read the values of each operand block (16 rows of X or of S o Y for their
+// trajectories) through shared memory: asynchronous copies issued kSrcAhead chunks ahead
+// into kSrcSlots slots of 8 KB (the staging buffer of the epilogue, idle while the
+// operands stream), so the block builds do not wait on L2 latency.
+constexpr int kSrcSlots = 4, kSrcAhead = 3;
+static_assert(kSrcSlots * 8192 <= (int)32768 && kSrcAhead < kSrcSlots, "operand source slots");
+static_assert(kRing >= 2 && kRing < kCmb, "ring depth");
+static_assert(kAcol + 32 * kAbuf <= (uint32_t)kTmemCols, "tensor memory");
+#ifndef TDAGW_TC_EVICT_FIRST
+#define TDAGW_TC_EVICT_FIRST 1  // factor tiles are streamed with an L2 evict-first policy
+#endif
 
-// staged half tile: 64 rows x 64 trajectories of float2, columns XOR-swizzled by row so
+// staged quarter tile: 64 rows x 64 trajectories of float2, columns XOR-swizzled by row so
 // that both the row-wise writes and the trajectory-wise reads avoid bank conflicts
 __device__ __forceinline__ int ds_index(int row, int bl) {
     return row * 64 + (bl ^ (row & 31));
 }
 
 struct TcArgs {
-    const unsigned char* tU;  // Nt x nchU tiles of U (rows) x 2r (real columns)
-    const unsigned char* tV;  // Mt x nchV tiles of V^T (rows j) x 2 Np (real columns)
-    unsigned char* tY;        // Gmax x nchU tiles: expanded split S o Y (rows 2b + c)
+    const unsigned char* tU;  // Nt x nchU tiles of U (256 rows) x 32 real columns
+    const unsigned char* tV;  // Mt x nchV tiles of V^T (256 rows j) x 32 real columns (16 rows i)
+    float2* Ys;               // rp x Bp: S o Y scaled for FP16 (phase B)
     float2* P;                // KS x rp x Bp raw partials of V^H X
     unsigned* xmax;           // 3 x Bp: max(|Re|, |Im|) of the stage input (float bits)
     const float* S;
@@ -108,12 +112,14 @@ struct TcArgs {
     const double* Etab;
     const float2* dir;
     const int* act;
-    double* red;  // Ntp x Bp x 3 (per phase C row-tile item)
+    double* red;  // Nt x Bp x 3 (per phase C row-tile item)
     double* obs;  // (Tmax + 1) x B x 3
     unsigned long long* bar;
     int* err;
     int64_t N, ldE;
-    int Nk, r, rp, Nt, Ntp, tpi, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;  // tpi: U row tiles per phase C item
+    int Nk, r, rp, Nt, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;
+    int gc_max;     // phase C trajectory groups at most (1 .. B / 8); 0: fill the CTAs
+    int ks_max;     // phase A K-ranges at most; 0: fill the CTAs
     float occ[4];
     float dt;
     float su, sv;   // power-of-two scales of the U and V tiles
@@ -121,47 +127,34 @@ struct TcArgs {
     unsigned long long wait_ns;
 };
 
-// Optional phase timestamps (build with -DTDAGW_TRACE): one thread per CTA and role records
+// Optional phase timestamps (build with -DTDAGW_TRACE): one thread per CTA records
 // %globaltimer at the phase boundaries of stages kTraceFirst .. kTraceFirst + kTraceStages - 1
 // (points 0-6: stage start, end of A items, after barrier 1, end of B, after barrier 2, end
 // of C items, after barrier 3; 7: MMA thread done with C items; 8: producer done with C
-// tiles).
+// tiles), and per-role wait totals.
 #ifdef TDAGW_TRACE
 constexpr int kTraceFirst = 40, kTraceStages = 16;
 __device__ unsigned long long g_trace_tc[160 * kTraceStages * 9];
 #define TC_TRACE(who, k)                                                                         \
     do {                                                                                         \
-        const int ts_ = 4 * n + st - kTraceFirst;                                                \
+        const int ts_ = tr_gs - kTraceFirst;                                                     \
         if ((who) && blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                         \
             g_trace_tc[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] = gtimer();                   \
     } while (0)
-// per-chunk timestamps of phase A in CTA 0, stage kTraceFirst + 1, first item:
-// [chunk][0] MMA thread has the chunk's tiles and B block, [1] its MMAs are issued,
-// [2] worker 0 may overwrite the B buffer, [3] worker 0 has built the block;
-// [63][0..3]: worker 0 accumulator ready, readout done, MMA thread item done, -
-__device__ unsigned long long g_trace_a[64 * 4];
-#define TC_TRACE_A(who, cc, k)                                                                   \
-    do {                                                                                         \
-        if ((who) && blockIdx.x == 0 && 4 * n + st == kTraceFirst + 1 && item == (int)blockIdx.x && (cc) < 64) \
-            g_trace_a[(cc) * 4 + (k)] = gtimer();                                                 \
-    } while (0)
 // wait/issue time accumulators per CTA and traced stage: [0] MMA thread waiting for tiles,
-// [1] for B blocks, [2] for a free accumulator, [3] issuing MMAs and commits, [4] copy
+// [1] for operand blocks, [2] for the accumulator, [3] issuing MMAs and commits, [4] copy
 // thread waiting for a free slot, [5] issuing copies
 __device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
 #define TC_W_BEGIN(id) const uint64_t tw_##id = gtimer()
 #define TC_W_END(id, k)                                                                          \
     do {                                                                                         \
-        const int ts_ = 4 * n + st - kTraceFirst;                                                \
+        const int ts_ = tr_gs - kTraceFirst;                                                     \
         if (blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                                  \
             g_trace_w[(blockIdx.x * kTraceStages + ts_) * 6 + (k)] += gtimer() - tw_##id;         \
     } while (0)
 #else
 #define TC_TRACE(who, k) \
     do {                 \
-    } while (0)
-#define TC_TRACE_A(who, cc, k) \
-    do {                       \
     } while (0)
 #define TC_W_BEGIN(id) \
     do {               \
@@ -171,40 +164,24 @@ __device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
     } while (0)
 #endif
 
-// non-blocking test (copy and MMA threads poll) and potentially blocking test (workers:
-// the hardware may suspend the thread until the phase completes)
-__device__ __forceinline__ bool mb_test(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(tc::smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-#ifndef TDAGW_TC_WORKER_POLL
-#define TDAGW_TC_WORKER_POLL 0  // 1: worker warps poll (test_wait) instead of try_wait
-#endif
-// bounded wait for the phase of the given parity; false on expiry or abort
-template <bool POLL>
+// bounded wait for the phase of the given parity (polling); false on expiry or abort
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, volatile int* abort_s,
                                         unsigned long long budget) {
-    if (POLL ? mb_test(b, parity) : mbar_try(b, parity)) return true;
+    if (mbar_try(b, parity)) return true;
     const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
-        if (POLL ? mb_test(b, parity) : mbar_try(b, parity)) return true;
+        if (mbar_try(b, parity)) return true;
         if ((i & 63) == 0) {
             if (abort_s && *abort_s) return false;
             if (gtimer() - t0 > budget) return false;
         }
     }
 }
-#ifndef TDAGW_TC_EVICT_FIRST
-#define TDAGW_TC_EVICT_FIRST 1  // factor tiles are streamed with an L2 evict-first policy
-#endif
 __device__ __forceinline__ void workers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
+}
+__device__ __forceinline__ void participants_sync() {
+    asm volatile("bar.sync 2, %0;" ::"n"(kSyncThreads) : "memory");
 }
 
 // 2^(13 - e) for bound < 2^e (1 for a zero bound)
@@ -219,11 +196,26 @@ __device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
     hi = __float2half_rn(v);
     lo = __float2half_rn(v - __half2float(hi));
 }
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
 
-// grid barrier over the monotonic arrival counter (all threads call)
+// 8-byte asynchronous copy global -> shared (zero-filled when src_bytes is 0) and its
+// per-thread completion groups
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// grid barrier over the monotonic arrival counter among the MMA warp and the workers (the
+// copy warp never waits on other CTAs)
 __device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
-    __syncthreads();
-    if (threadIdx.x == 0 && !*abort_s) {
+    participants_sync();
+    if (threadIdx.x == 64 && !*abort_s) {
         const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
         red_release_add64(a.bar, 1ull);
         const uint64_t t0 = gtimer();
@@ -235,29 +227,28 @@ __device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
             }
             __nanosleep(32);
         }
-        gen += 1;
     }
-    __syncthreads();
+    gen += 1;
+    participants_sync();
     return !*(volatile int*)abort_s;
 }
 
-// the three split products of one 128 x N x 32 tile pair (two K = 16 steps each)
-__device__ __forceinline__ void mma_tile(uint32_t d, uint32_t a_addr, uint32_t b_addr, uint32_t idesc, bool first) {
+// the three split products of one chunk: D (128 x 256) += A[tmem] (128 x 32) . F^T with F
+// the 256 x 32 factor tile (two K = 16 steps each)
+__device__ __forceinline__ void mma_chunk(uint32_t d, uint32_t a_tm, uint32_t f_addr, uint32_t idesc, bool first) {
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
-        const uint64_t ah = tc::sdesc(a_addr + ks * 256, kLbo, kSbo);
-        const uint64_t al = tc::sdesc(a_addr + kHalf + ks * 256, kLbo, kSbo);
-        const uint64_t bh = tc::sdesc(b_addr + ks * 256, kLbo, kSbo);
-        const uint64_t bl = tc::sdesc(b_addr + kHalf + ks * 256, kLbo, kSbo);
-        tc::mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
-        tc::mma_f16(d, ah, bl, idesc, 1u);
-        tc::mma_f16(d, al, bh, idesc, 1u);
+        const uint64_t fh = tc::sdesc(f_addr + ks * 256, kLbo, kSbo);
+        const uint64_t fl = tc::sdesc(f_addr + kHalf + ks * 256, kLbo, kSbo);
+        tc::mma_f16_ts(d, a_tm + ks * 8, fh, idesc, (first && ks == 0) ? 0u : 1u);
+        tc::mma_f16_ts(d, a_tm + 16 + ks * 8, fh, idesc, 1u);
+        tc::mma_f16_ts(d, a_tm + ks * 8, fl, idesc, 1u);
     }
 }
 
 // Commutator + RK4 stage update of one (k, trajectory) block (Eq. tdagw; the arithmetic of
-// the FP32 batched path), with the low-rank part of dSigma read from the staged half tile
-// (block rows row0 .. row0 + NB^2 - 1, trajectory column bl) and K^diag o X added here.
+// the FP32 batched path), with the low-rank part of dSigma read from the staged quarter
+// tile (block rows row0 .. row0 + NB^2 - 1, trajectory column bl) and K^diag o X added here.
 // xm: running max(|Re|, |Im|) of the values written to X (the next stage input).
 template <int NB>
 __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
@@ -340,36 +331,36 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
     return ob;
 }
 
-// Trajectory groups: at most kGroup trajectories each, and enough groups for about one
-// item of the U product per CTA (row tiles x groups <= CTAs) while groups keep >= 8.
-__host__ __device__ __forceinline__ int group_count(int Bact, int Nt, int nctas) {
+// Trajectory groups of phase C: at most kGroup trajectories each and, where the row tiles
+// leave CTAs idle, more groups (>= 8 trajectories each, at most gc_max when set).
+__host__ __device__ __forceinline__ int group_count(int Bact, int Nt, int nctas, int gc_max) {
     const int g_min = (Bact + kGroup - 1) / kGroup;
-    const int g_fill = min(max(1, nctas / Nt), (Bact + 7) / 8);
+    int g_fill = min(max(1, nctas / Nt), (Bact + 7) / 8);
+    if (gc_max > 0) g_fill = min(g_fill, gc_max);
     return max(g_min, g_fill);
 }
 struct Groups {
-    int G, MGn, KS;  // phase A: trajectory groups, groups of kAMc V^H tiles, K-ranges
-    int GC;          // phase C (and B): trajectory groups
+    int G, KS;  // phase A: trajectory groups, K-ranges
+    int GC;     // phase C: trajectory groups
 };
 __device__ __forceinline__ Groups stage_groups(const TcArgs& a, int Bact) {
     Groups q;
-    q.G = group_count(Bact, a.Nt, (int)gridDim.x);
-    q.GC = group_count(Bact, a.Ntp, (int)gridDim.x);
-    q.MGn = (a.Mt + kAMc - 1) / kAMc;
-    q.KS = max(1, min((int)gridDim.x / max(1, q.G * q.MGn), a.nchV));
+    q.G = (Bact + kGroup - 1) / kGroup;
+    q.GC = group_count(Bact, a.Nt, (int)gridDim.x, a.gc_max);
+    int ks = (int)gridDim.x / max(1, q.G * a.Mt);
+    if (a.ks_max > 0) ks = min(ks, a.ks_max);
+    q.KS = max(1, min(ks, a.nchV));
     return q;
 }
-// phase A item -> (trajectory group, first V^H tile, tile count, chunk range)
+// phase A item -> (trajectory group, V^H tile, K-range and its chunks)
 struct ItemA {
-    int g, m0, mc, ks, c0, c1;
+    int g, m, ks, c0, c1;
 };
 __device__ __forceinline__ ItemA item_a(const TcArgs& a, const Groups& q, int item) {
     ItemA it;
     it.g = item % q.G;
-    const int mg = (item / q.G) % q.MGn;
-    it.ks = item / (q.G * q.MGn);
-    it.m0 = kAMc * mg;
-    it.mc = min(kAMc, a.Mt - it.m0);
+    it.m = (item / q.G) % a.Mt;
+    it.ks = item / (q.G * a.Mt);
     it.c0 = (int)((int64_t)it.ks * a.nchV / q.KS);
     it.c1 = (int)((int64_t)(it.ks + 1) * a.nchV / q.KS);
     return it;
@@ -379,38 +370,44 @@ template <int NB>
 __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* ring = smem;
-    unsigned char* xbuf = ring + kRing * kTile;
-    float2* sDS = reinterpret_cast<float2*>(xbuf);
-    double* sred = reinterpret_cast<double*>(xbuf + kXbuf);
+    float2* sDS = reinterpret_cast<float2*>(ring + kRing * kTile);
+    double* sred = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(sDS) + kStg);
     float* ssc = reinterpret_cast<float*>(sred + kWorkers * 3);
     unsigned* smx = reinterpret_cast<unsigned*>(ssc + kGroup);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smx + kGroup);
     uint64_t* full = bars;
     uint64_t* cmb = full + kRing;     // MMAs of chunk q complete (one commit per chunk)
-    uint64_t* bfull = cmb + kCmb;
-    uint64_t* accf = bfull + kBBuf;   // accumulator written (MMA -> workers)
-    uint64_t* acce = accf + 2;    // accumulator drained (workers -> MMA)
-    uint64_t* fin = acce + 2;     // last MMAs complete (teardown)
+    uint64_t* afull = cmb + kCmb;     // operand block written (workers -> MMA)
+    uint64_t* accf = afull + kAbuf;   // accumulator written (MMA -> workers)
+    uint64_t* acce = accf + 1;        // accumulator drained (workers -> MMA)
+    uint64_t* fin = acce + 1;         // last MMAs complete (teardown)
     __shared__ uint32_t tmem_base;
     __shared__ int abort_s;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const bool producer = tid == 0, mma = tid == 32, worker = warp >= 2;
+    const bool in_sync = warp >= 1;  // grid-barrier participants (lanes 1-31 of warp 0 idle)
     const int wt = tid - 64;  // worker index
+    // worker warps: tensor-memory lane quarter (rows 32 q .. 32 q + 31 of the operand and of
+    // the accumulator) and half (which columns of a block the warp writes or reads)
+    const int wq = warp & 3, wh = (warp - 2) >> 2;
+    const int orow = 32 * wq + lane;           // operand / accumulator row: 2 bl + comp
+    const int obl = orow >> 1, ocomp = orow & 1;
     constexpr int NB2 = NB * NB;
     const unsigned long long budget = a.wait_ns;
     volatile int* vabort = &abort_s;
+    // abort flag as one value per warp (lane 0's read): guards of the warp-collective
+    // tensor-memory loads and stores must not diverge
+    auto warp_abort = [&]() { return __shfl_sync(0xffffffffu, *vabort, 0) != 0; };
 
     if (tid == 0) {
         abort_s = 0;
         for (int s = 0; s < kRing; ++s) mbar_init(full + s, 1);
         for (int s = 0; s < kCmb; ++s) mbar_init(cmb + s, 1);
-        for (int s = 0; s < kBBuf; ++s) mbar_init(bfull + s, kWorkers);
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(accf + s, 1);
-            mbar_init(acce + s, kWorkers);
-        }
+        for (int s = 0; s < kAbuf; ++s) mbar_init(afull + s, kWorkers / 32);
+        mbar_init(accf, 1);
+        mbar_init(acce, kWorkers);
         mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -422,39 +419,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 
     uint32_t ppos = 0;  // producer: tiles issued so far (ring position)
     uint32_t mpos = 0;  // MMA thread: tiles consumed so far
-    uint32_t bu = 0;    // uses of the built-B buffers (MMA thread and workers)
-    uint32_t acnt = 0;  // uses of the two accumulators (MMA thread and workers)
+    uint32_t bu = 0;    // uses of the operand blocks (MMA thread and workers)
+    uint32_t acnt = 0;  // uses of the accumulator (MMA thread and workers)
     int gch = 0;        // chunks so far (all roles count the same sequence)
     int slot_ch[kRing]; // producer: chunk that last used each ring slot
-    int buf_ch[kBBuf];  // workers: chunk that last used each B buffer
+    int buf_ch[kAbuf];  // workers: chunk that last used each operand block
     for (int q = 0; q < kRing; ++q) slot_ch[q] = -1;
-    for (int q = 0; q < kBBuf; ++q) buf_ch[q] = -1;
+    for (int q = 0; q < kAbuf; ++q) buf_ch[q] = -1;
     unsigned gen = 0;
     bool ok = true;
+    int tr_gs = 0;  // stage of the phase timestamps (traced builds)
+    (void)tr_gs;
     auto fail = [&]() {
         atomicExch(a.err, 1);
         abort_s = 1;
     };
-    // wait until the MMAs of chunk q are complete (q < 0: nothing to wait for; a chunk
-    // kCmb or more behind is complete: an accumulator wait or a grid barrier came between)
-    auto chunk_done = [&](int q, bool poll) -> bool {
+    // wait until the MMAs of chunk q are complete (q < 0: nothing to wait for)
+    auto chunk_done = [&](int q) -> bool {
         if (q < 0 || gch - q >= kCmb) return true;
-        return poll ? mb_wait<true>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget)
-                    : mb_wait<TDAGW_TC_WORKER_POLL != 0>(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
+        return mb_wait(cmb + q % kCmb, (uint32_t)(q / kCmb) & 1u, vabort, budget);
     };
     const uint64_t ef_policy = TDAGW_TC_EVICT_FIRST ? policy_evict_first() : 0ull;
-    // producer: one tile of chunk gch into the next ring slot (factor tiles may carry an
-    // evict-first L2 policy)
-    auto issue = [&](const unsigned char* src, bool factor) {
+    // producer: one factor tile (chunk gch) into the next ring slot
+    auto issue = [&](const unsigned char* src) {
         if (*vabort) return;
         const uint32_t slot = ppos % kRing;
-        if (!chunk_done(slot_ch[slot], true)) {
+        if (!chunk_done(slot_ch[slot])) {
             fail();
             return;
         }
         slot_ch[slot] = gch;
         mbar_expect_tx(full + slot, kTile);
-        if (TDAGW_TC_EVICT_FIRST && factor)
+        if (TDAGW_TC_EVICT_FIRST)
             bulk_g2s_hint(ring + slot * kTile, src, kTile, full + slot, ef_policy);
         else
             bulk_g2s(ring + slot * kTile, src, kTile, full + slot);
@@ -463,227 +459,192 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     // MMA thread: wait for the next tile; returns its shared-memory address (0 on failure)
     auto next_tile = [&]() -> uint32_t {
         const uint32_t slot = mpos % kRing, use = mpos / kRing;
-        if (*vabort || !mb_wait<true>(full + slot, use & 1u, vabort, budget)) {
+        if (*vabort || !mb_wait(full + slot, use & 1u, vabort, budget)) {
             fail();
             return 0u;
         }
         ++mpos;
         return tc::smem_u32(ring + slot * kTile);
     };
-    auto end_chunk = [&]() {  // MMA thread: the chunk's MMAs are issued
+    // MMA thread: one chunk (one factor tile and the operand block of the chunk)
+    auto mma_step = [&](uint32_t idesc, bool first) {
+        TC_W_BEGIN(t0);
+        const uint32_t f = next_tile();
+        TC_W_END(t0, 0);
+        TC_W_BEGIN(b0);
+        const uint32_t bs = bu % kAbuf;
+        if (!f || *vabort || !mb_wait(afull + bs, (bu / kAbuf) & 1u, vabort, budget)) {
+            fail();
+            return;
+        }
+        TC_W_END(b0, 1);
+        tc::fence_after_sync();
+        TC_W_BEGIN(m0);
+        mma_chunk(tm, tm + kAcol + 32 * bs, f, idesc, first);
         tc::mma_commit(cmb + gch % kCmb);
+        TC_W_END(m0, 3);
+        ++gch;
+        ++bu;
+    };
+    // MMA thread: the accumulator is free (drained by the workers after its last use)
+    auto wait_acc_free = [&]() {
+        TC_W_BEGIN(a0);
+        if (*vabort || !mb_wait(acce, (acnt & 1u) ^ 1u, vabort, budget)) fail();
+        TC_W_END(a0, 2);
+        tc::fence_after_sync();
+    };
+    // workers: write the operand block of chunk gch into tensor memory: the warp's 32 rows
+    // (2 bl + comp), its 8 of the chunk's 16 complex columns, hi and lo parts.  v[u] is the
+    // (already scaled) complex value of column 8 wh + u; conj selects the expansion:
+    //   V^H X:  row 2b: (re, im), row 2b + 1: (im, -re)
+    //   U Y:    row 2b: (re, -im), row 2b + 1: (im, re)
+    auto build_block = [&](const float2 (&v)[8], bool vhx) {
+        const uint32_t bs = bu % kAbuf;
+        if (!*vabort && !chunk_done(buf_ch[bs])) fail();
+        buf_ch[bs] = gch;
+        if (!warp_abort()) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float p0, p1;
+                if (vhx) {
+                    p0 = ocomp ? v[u].y : v[u].x;
+                    p1 = ocomp ? -v[u].x : v[u].y;
+                } else {
+                    p0 = ocomp ? v[u].y : v[u].x;
+                    p1 = ocomp ? v[u].x : -v[u].y;
+                }
+                __half h0, l0, h1, l1;
+                split16(p0, h0, l0);
+                split16(p1, h1, l1);
+                hi[u] = pack2(h0, h1);
+                lo[u] = pack2(l0, l1);
+            }
+            const uint32_t ta = tm + ((uint32_t)(32 * wq) << 16) + kAcol + 32 * bs + 8 * wh;
+            tc::tmem_st8(ta, hi);
+            tc::tmem_st8(ta + 16, lo);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(afull + bs);
+        ++bu;
+        ++gch;
     };
 
-    for (int n = 0; n < a.Tmax && ok; ++n) {
+    // workers: the source values of chunk c (rows 16 c .. 16 c + 15 of X or of S o Y, the
+    // warp's 8 of them, its 16 trajectories) into source slot k % kSrcSlots; each lane of
+    // a pair copies 4 of the pair's 8 values, one completion group per chunk (empty past
+    // the item's last chunk c_end).  Rows past N are zero-filled.
+    float2* srcbuf = sDS;  // kSrcSlots x 8 KB, warp part (warp - 2) x 1 KB
+    auto src_issue = [&](const float2* base, int c, int c_end, bool live, int b0, int k) {
+        if (c < c_end) {
+            float2* dst = srcbuf + (k % kSrcSlots) * 1024 + (warp - 2) * 128 + (obl & 15) * 8 + 4 * ocomp;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = (int64_t)c * 16 + 8 * wh + 4 * ocomp + u;
+                const bool v = live && i < a.N;
+                cp_async8(dst + u, v ? (const void*)(base + i * a.Bp + b0 + obl) : (const void*)base, v ? 8u : 0u);
+            }
+        }
+        cp_async_commit();
+    };
+    // workers: wait for the source values of the chunk in slot k (kSrcAhead - 1 newer
+    // groups may stay in flight) and read the pair's 8 values, scaled
+    auto src_read = [&](float2 (&v)[8], int k, float sc) {
+        cp_async_wait<kSrcAhead - 1>();
+        __syncwarp();
+        const float2* src = srcbuf + (k % kSrcSlots) * 1024 + (warp - 2) * 128 + (obl & 15) * 8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = make_float2(src[u].x * sc, src[u].y * sc);
+        __syncwarp();  // the slot may be refilled after every lane has read it
+    };
+
+    for (int n = 0; n < a.Tmax && ok && (in_sync || producer); ++n) {
         const int Bact = a.act[n];
         const Groups q = stage_groups(a, Bact);
         for (int st = 0; st < 4 && ok; ++st) {
             const int gs = 4 * n + st;
+            tr_gs = gs;
             const unsigned* xin = a.xmax + (gs % 3) * a.Bp;
             unsigned* xout = a.xmax + ((gs + 1) % 3) * a.Bp;
-            TC_TRACE(producer, 0);
+            TC_TRACE(worker && wt == 0, 0);
             if (blockIdx.x == 0 && worker)
                 for (int b = wt; b < a.Bp; b += kWorkers) xout[b] = 0u;
 
             // ---------------- A: partials of V^H X ----------------
-            const int nA = q.G * q.MGn * q.KS;
+            const int nA = q.G * a.Mt * q.KS;
             if (producer) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
                     for (int c = it.c0; c < it.c1; ++c, ++gch) {
                         TC_W_BEGIN(p0);
-                        for (int ml = 0; ml < it.mc; ++ml) issue(a.tV + ((int64_t)(it.m0 + ml) * a.nchV + c) * kTile, true);
+                        issue(a.tV + ((int64_t)it.m * a.nchV + c) * kTile);
                         TC_W_END(p0, 4);
                     }
                 }
             } else if (mma) {
-                for (int item = blockIdx.x; item < nA; item += gridDim.x) {
+                const uint32_t idesc = tc::idesc_f16(128, kRows);
+                for (int item = blockIdx.x; item < nA && !*vabort; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
-                    int b0, b1;
-                    group_range(Bact, q.G, it.g, b0, b1);
-                    const int nbp = (b1 - b0 + 7) & ~7;
-                    const int nuse = (it.mc + 1) / 2;  // accumulator uses (two tiles each)
-                    TC_W_BEGIN(a0);
-                    for (int u = 0; u < nuse; ++u) {
-                        const uint32_t k = acnt + u;
-                        if (*vabort || !mb_wait<true>(acce + (k & 1u), ((k >> 1) & 1u) ^ 1u, vabort, budget)) fail();
-                    }
-                    TC_W_END(a0, 2);
-                    tc::fence_after_sync();
-                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
-                    for (int c = it.c0; c < it.c1 && !*vabort; ++c) {
-                        uint32_t ta[kAMc] = {};
-                        TC_W_BEGIN(t0);
-                        for (int ml = 0; ml < it.mc; ++ml) ta[ml] = next_tile();
-                        TC_W_END(t0, 0);
-                        TC_W_BEGIN(b0);
-                        if (*vabort || !mb_wait<true>(bfull + bu % kBBuf, (bu / kBBuf) & 1u, vabort, budget)) {
-                            fail();
-                            break;
-                        }
-                        TC_W_END(b0, 1);
-                        TC_TRACE_A(true, c - it.c0, 0);
-                        tc::fence_after_sync();
-                        const uint32_t baddr = tc::smem_u32(xbuf + (bu % kBBuf) * kTile);
-                        TC_W_BEGIN(m0);
-                        for (int ml = 0; ml < it.mc; ++ml)
-                            mma_tile(tm + ((acnt + ml / 2) & 1u) * kAccCols + (ml % 2) * 128, ta[ml], baddr, idesc,
-                                     c == it.c0);
-                        TC_TRACE_A(true, c - it.c0, 1);
-                        end_chunk();
-                        TC_W_END(m0, 3);
-                        ++gch;
-                        ++bu;
-                    }
-                    for (int u = 0; u < nuse; ++u) tc::mma_commit(accf + ((acnt + u) & 1u));
-                    TC_TRACE_A(true, 63, 2);
-                    acnt += nuse;
+                    wait_acc_free();
+                    for (int c = it.c0; c < it.c1 && !*vabort; ++c) mma_step(idesc, c == it.c0);
+                    tc::mma_commit(accf);
+                    ++acnt;
                 }
             } else if (worker) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
                     int b0, b1;
                     group_range(Bact, q.G, it.g, b0, b1);
-                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                    const int nbg = b1 - b0;
                     workers_sync();  // the previous item's readers of ssc are done
                     if (wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
                     workers_sync();
-                    // expanded split X block of each chunk (16 rows x nbp trajectories); each
-                    // worker owns elements e = wt + 256 u, u < 4, and loads the values of the
-                    // chunk after next before building the current one
-                    constexpr int kPer = 16 * kGroup / kWorkers;
-                    auto load_chunk = [&](int c, float2 (&xv)[kPer]) {
-#pragma unroll
-                        for (int u = 0; u < kPer; ++u) {
-                            const int e = wt + kWorkers * u;
-                            const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
-                            const int64_t i = (int64_t)c * 16 + il;
-                            xv[u] = (bl < nbg && i < a.N) ? __ldcg(a.X + i * a.Bp + b0 + bl) : make_float2(0.f, 0.f);
-                        }
-                    };
-                    auto build_chunk = [&](int c, const float2 (&xv)[kPer]) {
-                        const uint32_t bs = bu % kBBuf;
-                        if (!*vabort && !chunk_done(buf_ch[bs], false)) fail();
-                        buf_ch[bs] = gch;
-                        TC_TRACE_A(wt == 0, c - it.c0, 2);
-                        if (!*vabort) {
-                            unsigned char* tile = xbuf + bs * kTile;
-#pragma unroll
-                            for (int u = 0; u < kPer; ++u) {
-                                const int e = wt + kWorkers * u;
-                                const int il = (e & 3) | ((e >> 8) << 2), bl = (e >> 2) & 63;
-                                if (bl >= nbp) continue;
-                                const float2 x = xv[u];
-                                const float sx = ssc[bl];
-                                __half rh, rl, ih, il2;
-                                split16(x.x * sx, rh, rl);
-                                split16(x.y * sx, ih, il2);
-                                const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * il, kKc);
-                                const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * il, kKc);
-                                *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, ih);
-                                *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, __hneg(rh));
-                                *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, il2);
-                                *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il2, __hneg(rl));
-                            }
-                        }
-                        tc::fence_proxy_async();
-                        mbar_arrive(bfull + bs);
-                        TC_TRACE_A(wt == 0, c - it.c0, 3);
-                        ++bu;
-                        ++gch;
-                    };
-                    // expanded split X block of each chunk (16 rows x nbp trajectories); each
-                    // worker owns elements e = wt + 256 u, u < 4; its loads run two chunks
-                    // ahead of the build (three rotating register sets, no copies)
-                    float2 xa[kPer], xb[kPer], xc[kPer];
-                    if (it.c0 < it.c1) load_chunk(it.c0, xa);
-                    if (it.c0 + 1 < it.c1) load_chunk(it.c0 + 1, xb);
-                    for (int c = it.c0; c < it.c1; c += 3) {
-                        if (c + 2 < it.c1) load_chunk(c + 2, xc);
-                        build_chunk(c, xa);
-                        if (c + 1 >= it.c1) break;
-                        if (c + 3 < it.c1) load_chunk(c + 3, xa);
-                        build_chunk(c + 1, xb);
-                        if (c + 2 >= it.c1) break;
-                        if (c + 4 < it.c1) load_chunk(c + 4, xb);
-                        build_chunk(c + 2, xc);
+                    const float sx = ssc[obl];
+                    const bool live = obl < nbg;
+                    // X values of the warp's columns of chunk c, kSrcAhead chunks ahead
+                    for (int c = it.c0; c < it.c0 + kSrcAhead; ++c) src_issue(a.X, c, it.c1, live, b0, c - it.c0);
+                    for (int c = it.c0; c < it.c1; ++c) {
+                        float2 v[8];
+                        src_read(v, c - it.c0, sx);
+                        build_block(v, true);
+                        src_issue(a.X, c + kSrcAhead, it.c1, live, b0, c + kSrcAhead - it.c0);
                     }
-                    // accumulators -> raw partials P[ks][j][b], 64 rows at a time staged in
-                    // the (now idle) B buffers so that the global writes run along
-                    // trajectories (coalesced)
-                    const int nuse = (it.mc + 1) / 2;
-                    for (int u = 0; u < nuse; ++u) {
-                        const uint32_t k = acnt + u;
-                        if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + (k & 1u), (k >> 1) & 1u, vabort, budget))
-                            fail();
-                    }
-                    TC_TRACE_A(wt == 0, 63, 0);
+                    cp_async_wait<0>();
+                    // accumulator -> raw partials P[ks][j][b]: lanes 2 bl and 2 bl + 1 hold the
+                    // real and imaginary parts; the warp's half of the 256 columns (rows j)
+                    if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
                     tc::fence_after_sync();
-                    float2* stg = reinterpret_cast<float2*>(xbuf);  // 64 rows x 64 float2 (32 KB)
-                    const int quarter = warp & 3, half = (warp - 2) >> 2;
-                    const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
-                    for (int ml = 0; ml < it.mc; ++ml) {
-                        TC_TRACE_A(wt == 0, 62, ml);
-                        for (int ph = 0; ph < 2; ++ph) {
-                            workers_sync();  // B buffers / the previous half no longer read
-                            if ((quarter >> 1) == ph && !*vabort) {
-                                const int row = 32 * (quarter & 1) + lane;
-                                for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
-                                    float v[16];
-                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ((acnt + ml / 2) & 1u) * kAccCols +
-                                                      (ml % 2) * 128 + 16 * u,
-                                                  v);
+                    if (!warp_abort()) {
+                        float2* pbase = a.P + ((int64_t)it.ks * a.rp + (int64_t)it.m * kRows) * a.Bp + b0 + obl;
+                        for (int u = 0; u < 8; ++u) {
+                            float v[16];
+                            const int col = 128 * wh + 16 * u;
+                            tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
 #pragma unroll
-                                    for (int p = 0; p < 8; ++p)
-                                        stg[ds_index(row, 8 * u + p)] = make_float2(v[2 * p], v[2 * p + 1]);
-                                }
-                            }
-                            workers_sync();
-                            if (!*vabort) {
-                                float2* pbase = a.P + ((int64_t)it.ks * a.rp + (it.m0 + ml) * 128 + 64 * ph) * a.Bp + b0;
-                                for (int e = wt; e < 64 * nbg; e += kWorkers) {
-                                    const int row = e / nbg, bl = e % nbg;
-                                    pbase[(int64_t)row * a.Bp + bl] = stg[ds_index(row, bl)];
-                                }
+                            for (int t = 0; t < 16; ++t) {
+                                const float im = __shfl_xor_sync(0xffffffffu, v[t], 1);
+                                if (!ocomp && live) pbase[(int64_t)(col + t) * a.Bp] = make_float2(v[t], im);
                             }
                         }
                     }
-                    workers_sync();  // staging reads done before the next item's B blocks
                     tc::fence_before_sync();
-                    for (int u = 0; u < nuse; ++u) mbar_arrive(acce + ((acnt + u) & 1u));
-                    TC_TRACE_A(wt == 0, 63, 1);
-                    acnt += nuse;
+                    mbar_arrive(acce);
+                    ++acnt;
                 }
             }
-            TC_TRACE(producer, 1);
-            if (!(ok = tc_grid_sync(a, gen, &abort_s))) break;
-            TC_TRACE(producer, 2);
+            TC_TRACE(worker && wt == 0, 1);
+            if (in_sync && !(ok = tc_grid_sync(a, gen, &abort_s))) break;
+            TC_TRACE(worker && wt == 0, 2);
 
-            // ---------------- B: Y = S o sum of partials -> split expanded tiles ----------------
-            {
-                const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
-                // elements (g, j, bl) of all groups, flattened
-                int64_t tot_el = 0;
-                for (int g = 0; g < q.GC; ++g) {
-                    int b0, b1;
-                    group_range(Bact, q.GC, g, b0, b1);
-                    tot_el += (int64_t)a.rp * ((b1 - b0 + 7) & ~7);
-                }
+            // ---------------- B: S o sum of the partials, scaled for FP16 ----------------
+            if (worker) {
+                const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
+                const int64_t tot_el = (int64_t)a.rp * Bact;
                 for (int64_t e = gt; e < tot_el; e += total) {
-                    int g = 0, b0 = 0, b1 = 0, nbp = 0;
-                    int64_t rem = e;
-                    for (;; ++g) {
-                        group_range(Bact, q.GC, g, b0, b1);
-                        nbp = (b1 - b0 + 7) & ~7;
-                        const int64_t sz = (int64_t)a.rp * nbp;
-                        if (rem < sz || g == q.GC - 1) break;
-                        rem -= sz;
-                    }
-                    const int nbg = b1 - b0;
-                    const int j = (int)(rem / nbp), bl = (int)(rem % nbp);
+                    const int j = (int)(e / Bact), b = (int)(e % Bact);
                     float2 v = make_float2(0.f, 0.f);
-                    if (bl < nbg && j < a.r) {
-                        const int b = b0 + bl;
+                    if (j < a.r) {
                         // eight independent partial sums (loads in flight), fixed order
                         const float2* pp = a.P + (int64_t)j * a.Bp + b;
                         const int64_t pstride = (int64_t)a.rp * a.Bp;
@@ -704,22 +665,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
                         v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
                     }
-                    __half rh, rl, ih, il;
-                    split16(v.x, rh, rl);
-                    split16(v.y, ih, il);
-                    unsigned char* tile = a.tY + ((int64_t)g * a.nchU + j / 16) * kTile;
-                    const uint32_t o0 = tc::kmajor_offset(2 * bl, 2 * (j % 16), kKc);
-                    const uint32_t o1 = tc::kmajor_offset(2 * bl + 1, 2 * (j % 16), kKc);
-                    *reinterpret_cast<__half2*>(tile + o0) = __halves2half2(rh, __hneg(ih));
-                    *reinterpret_cast<__half2*>(tile + o1) = __halves2half2(ih, rh);
-                    *reinterpret_cast<__half2*>(tile + kHalf + o0) = __halves2half2(rl, __hneg(il));
-                    *reinterpret_cast<__half2*>(tile + kHalf + o1) = __halves2half2(il, rl);
+                    a.Ys[(int64_t)j * a.Bp + b] = v;
                 }
                 if (st == 0 && n > 0) {
                     // observables of step n (written by the last stage of step n - 1)
                     for (int64_t b = gt; b < a.act[n - 1]; b += total) {
                         double s0 = 0, s1 = 0, s2 = 0;
-                        for (int t = 0; t < a.Ntp; ++t) {
+                        for (int t = 0; t < a.Nt; ++t) {
                             const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                             s0 += __ldcg(rr);
                             s1 += __ldcg(rr + 1);
@@ -732,66 +684,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     }
                 }
             }
-            // the tiles were written through the generic proxy and are read by bulk copies
-            asm volatile("fence.proxy.async;" ::: "memory");
-            TC_TRACE(producer, 3);
-            if (!(ok = tc_grid_sync(a, gen, &abort_s))) break;
-            TC_TRACE(producer, 4);
+            TC_TRACE(worker && wt == 0, 3);
+            if (in_sync && !(ok = tc_grid_sync(a, gen, &abort_s))) break;
+            TC_TRACE(worker && wt == 0, 4);
 
             // ---------------- C: dSigma = U (S o Y) + K^diag o X, commutator, RK4 ----------------
             const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
-            const int nC = a.Ntp * q.GC;
+            const int nC = a.Nt * q.GC;
             if (producer) {
                 for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                    const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
-                    const int tcnt = min(a.tpi, a.Nt - t0);
+                    const int t = item % a.Nt;
                     for (int c = 0; c < a.nchU; ++c, ++gch) {
                         TC_W_BEGIN(p1);
-                        for (int u = 0; u < tcnt; ++u) issue(a.tU + ((int64_t)(t0 + u) * a.nchU + c) * kTile, true);
-                        issue(a.tY + ((int64_t)g * a.nchU + c) * kTile, false);
+                        issue(a.tU + ((int64_t)t * a.nchU + c) * kTile);
                         TC_W_END(p1, 4);
                     }
                 }
                 TC_TRACE(true, 8);
             } else if (mma) {
-                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                    const int t0 = a.tpi * (item % a.Ntp), g = item / a.Ntp;
-                    const int tcnt = min(a.tpi, a.Nt - t0);
-                    int b0, b1;
-                    group_range(Bact, q.GC, g, b0, b1);
-                    const int nbp = (b1 - b0 + 7) & ~7;
-                    const uint32_t ab = acnt & 1u;
-                    TC_W_BEGIN(a0);
-                    if (*vabort || !mb_wait<true>(acce + ab, ((acnt >> 1) & 1u) ^ 1u, vabort, budget)) fail();
-                    TC_W_END(a0, 2);
-                    tc::fence_after_sync();
-                    const uint32_t idesc = tc::idesc_f16(128, 2 * nbp);
-                    for (int c = 0; c < a.nchU && !*vabort; ++c) {
-                        uint32_t tu[2] = {0u, 0u};
-                        TC_W_BEGIN(t1);
-                        for (int u = 0; u < tcnt; ++u) tu[u] = next_tile();
-                        const uint32_t ty = next_tile();
-                        TC_W_END(t1, 0);
-                        if (*vabort) break;
-                        tc::fence_after_sync();
-                        TC_W_BEGIN(m1);
-                        for (int u = 0; u < tcnt; ++u) mma_tile(tm + ab * kAccCols + u * 128, tu[u], ty, idesc, c == 0);
-                        end_chunk();
-                        TC_W_END(m1, 3);
-                        ++gch;
-                    }
-                    tc::mma_commit(accf + ab);
+                const uint32_t idesc = tc::idesc_f16(128, kRows);
+                for (int item = blockIdx.x; item < nC && !*vabort; item += gridDim.x) {
+                    wait_acc_free();
+                    for (int c = 0; c < a.nchU && !*vabort; ++c) mma_step(idesc, c == 0);
+                    tc::mma_commit(accf);
                     ++acnt;
                 }
                 TC_TRACE(true, 7);
             } else if (worker) {
                 for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                    const int tp = item % a.Ntp, t0 = a.tpi * tp, g = item / a.Ntp;
-                    const int tcnt = min(a.tpi, a.Nt - t0);
-                    gch += a.nchU;  // the item's chunks (counted like the copy and MMA threads)
+                    const int t = item % a.Nt, g = item / a.Nt;
                     int b0, b1;
                     group_range(Bact, q.GC, g, b0, b1);
-                    const int nbg = b1 - b0, nbp = (nbg + 7) & ~7;
+                    const int nbg = b1 - b0;
                     workers_sync();  // the previous item's readers of ssc, smx, sred are done
                     if (wt < kGroup) {
                         if (wt < nbg) {
@@ -801,52 +725,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         smx[wt] = 0u;
                     }
                     workers_sync();
-                    const uint32_t ab = acnt & 1u;
-                    if (!*vabort && !mb_wait<TDAGW_TC_WORKER_POLL != 0>(accf + ab, (acnt >> 1) & 1u, vabort, budget)) fail();
+                    const bool live = obl < nbg;
+                    // S o Y values of the warp's columns of chunk c, kSrcAhead chunks ahead
+                    for (int c = 0; c < kSrcAhead; ++c) src_issue(a.Ys, c, a.nchU, live, b0, c);
+                    for (int c = 0; c < a.nchU; ++c) {
+                        float2 v[8];
+                        src_read(v, c, 1.f);
+                        build_block(v, false);
+                        src_issue(a.Ys, c + kSrcAhead, a.nchU, live, b0, c + kSrcAhead);
+                    }
+                    cp_async_wait<0>();
+                    if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
                     tc::fence_after_sync();
-                    const int quarter = warp & 3, half = (warp - 2) >> 2;
-                    const int units = (2 * nbp) / 16, uh = (units + 1) / 2;
                     const int kgroups = kWorkers / nbg;
                     const int bl = wt % nbg, kg = wt / nbg;
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                     float xm = 0.f;
-                    for (int u2 = 0; u2 < a.tpi; ++u2) {
-                        const int t = t0 + u2;
-                        for (int ph = 0; ph < 2; ++ph) {
-                            // accumulator rows 64 ph .. +63 (lane quarters 2 ph, 2 ph + 1) -> staged half
-                            if (u2 < tcnt && (quarter >> 1) == ph && !*vabort) {
-                                const int row = 32 * (quarter & 1) + lane;
-                                for (int u = half * uh; u < min(units, (half + 1) * uh); ++u) {
-                                    float v[16];
-                                    tc::tmem_ld16(tm + ((uint32_t)(32 * quarter) << 16) + ab * kAccCols + u2 * 128 + 16 * u, v);
+                    for (int qq = 0; qq < kRows / 64; ++qq) {
+                        // accumulator columns 64 qq .. + 63 (the warp's 32 of them) -> staged
+                        // quarter, unscaled; lanes 2 bl and 2 bl + 1 hold re and im
+                        if (!warp_abort()) {
 #pragma unroll
-                                    for (int p = 0; p < 8; ++p) {
-                                        const int b2 = 8 * u + p;
-                                        if (b2 < nbg)
-                                            sDS[ds_index(row, b2)] = make_float2(v[2 * p] * ssc[b2], v[2 * p + 1] * ssc[b2]);
-                                    }
+                            for (int u = 0; u < 2; ++u) {
+                                float v[16];
+                                const int col = 64 * qq + 32 * wh + 16 * u;
+                                tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
+                                const float sc = live ? ssc[obl] : 0.f;
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) {
+                                    const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
+                                    if (!ocomp && live)
+                                        sDS[ds_index(32 * wh + 16 * u + e, obl)] = make_float2(v[e] * sc, im * sc);
                                 }
                             }
-                            workers_sync();
-                            // commutator + RK4 for the k-blocks of these 64 rows
-                            const int kbase = (t * 128 + 64 * ph) / NB2;
-                            const int kt = u2 < tcnt ? min(64 / NB2, a.Nk - kbase) : 0;
-                            if (kg < kgroups && !*vabort) {
-                                const int b = b0 + bl;
-                                const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
-                                const float2 dr = a.dir[b];
-                                for (int kl = kg; kl < kt; kl += kgroups) {
-                                    const Obs3 ob = stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm);
-                                    s0 += ob.p;
-                                    s1 += ob.j;
-                                    s2 += ob.o;
-                                }
-                            }
-                            workers_sync();  // the staged half is consumed before it is rewritten
                         }
+                        workers_sync();
+                        // commutator + RK4 for the k-blocks of these 64 rows
+                        const int kbase = (t * kRows + 64 * qq) / NB2;
+                        const int kt = min(64 / NB2, a.Nk - kbase);
+                        if (kg < kgroups && !*vabort) {
+                            const int b = b0 + bl;
+                            const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                            const float2 dr = a.dir[b];
+                            for (int kl = kg; kl < kt; kl += kgroups) {
+                                const Obs3 ob = stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm);
+                                s0 += ob.p;
+                                s1 += ob.j;
+                                s2 += ob.o;
+                            }
+                        }
+                        workers_sync();  // the staged quarter is consumed before it is rewritten
                     }
                     tc::fence_before_sync();
-                    mbar_arrive(acce + ab);
+                    mbar_arrive(acce);
                     ++acnt;
                     if (kg < kgroups) {
                         atomicMax(smx + bl, __float_as_uint(xm));
@@ -866,7 +797,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 r1 += sred[(k2 * nbg + wt) * 3 + 1];
                                 r2 += sred[(k2 * nbg + wt) * 3 + 2];
                             }
-                            double* rr = a.red + ((int64_t)tp * a.Bp + b0 + wt) * 3;
+                            double* rr = a.red + ((int64_t)t * a.Bp + b0 + wt) * 3;
                             rr[0] = r0;
                             rr[1] = r1;
                             rr[2] = r2;
@@ -874,18 +805,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     }
                 }
             }
-            TC_TRACE(producer, 5);
-            ok = tc_grid_sync(a, gen, &abort_s);
-            TC_TRACE(producer, 6);
+            TC_TRACE(worker && wt == 0, 5);
+            if (in_sync) ok = tc_grid_sync(a, gen, &abort_s);
+            TC_TRACE(worker && wt == 0, 6);
         }
     }
-    // observables of the last step
-    if (ok && a.Tmax > 0) {
+    // observables of the last step (workers: they passed the last grid barrier)
+    if (worker && ok && a.Tmax > 0) {
         const int n = a.Tmax;
-        const int64_t gt = (int64_t)blockIdx.x * kTcThreads + tid, total = (int64_t)gridDim.x * kTcThreads;
+        const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
         for (int64_t b = gt; b < a.act[n - 1]; b += total) {
             double s0 = 0, s1 = 0, s2 = 0;
-            for (int t = 0; t < a.Ntp; ++t) {
+            for (int t = 0; t < a.Nt; ++t) {
                 const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                 s0 += __ldcg(rr);
                 s1 += __ldcg(rr + 1);
@@ -901,11 +832,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     // issued tiles may never have been consumed)
     if (producer) {
         const uint32_t first = ppos > (uint32_t)kRing ? ppos - kRing : 0u;
-        for (uint32_t p = first; p < ppos; ++p) mb_wait<true>(full + p % kRing, (p / kRing) & 1u, nullptr, budget);
+        for (uint32_t p = first; p < ppos; ++p) mb_wait(full + p % kRing, (p / kRing) & 1u, nullptr, budget);
     }
     if (mma) {
         tc::mma_commit(fin);
-        mb_wait<true>(fin, 0u, nullptr, budget);
+        mb_wait(fin, 0u, nullptr, budget);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -933,7 +864,7 @@ __global__ void factor_stats_kernel(const float2* __restrict__ U, const float2* 
     out[2 * r + j] = (float)nv;
 }
 
-// Split-FP16 tiles of U: tile (t, c) holds rows 128 t .. +127 and complex columns
+// Split-FP16 tiles of U: tile (t, c) holds rows 256 t .. +255 and complex columns
 // 16 c .. +15 as 32 real columns (re, im), scaled by `scale`; zero outside N x r.
 __global__ void pack_u_kernel(const float2* __restrict__ U, int64_t N, int r, int ldu, int rp, int nchU,
                               float scale, unsigned char* __restrict__ out, int64_t total) {
@@ -946,13 +877,13 @@ __global__ void pack_u_kernel(const float2* __restrict__ U, int64_t N, int r, in
     __half rh, rl, ih, il;
     split16(v.x * scale, rh, rl);
     split16(v.y * scale, ih, il);
-    unsigned char* tile = out + ((i / 128) * nchU + j / 16) * (int64_t)kTile;
-    const uint32_t o = tc::kmajor_offset((uint32_t)(i % 128), 2 * (j % 16), kKc);
+    unsigned char* tile = out + ((i / kRows) * nchU + j / 16) * (int64_t)kTile;
+    const uint32_t o = tc::kmajor_offset((uint32_t)(i % kRows), 2 * (j % 16), kKc);
     *reinterpret_cast<__half2*>(tile + o) = __halves2half2(rh, ih);
     *reinterpret_cast<__half2*>(tile + kHalf + o) = __halves2half2(rl, il);
 }
 
-// Split-FP16 tiles of V^T: tile (m, c) holds rows j = 128 m .. +127 (columns of V) and
+// Split-FP16 tiles of V^T: tile (m, c) holds rows j = 256 m .. +255 (columns of V) and
 // rows i = 16 c .. +15 of V as 32 real columns (re, im), scaled by `scale`.
 __global__ void pack_v_kernel(const float2* __restrict__ V, int64_t N, int r, int ldu, int rp, int nchV,
                               float scale, unsigned char* __restrict__ out, int64_t total) {
@@ -965,8 +896,8 @@ __global__ void pack_v_kernel(const float2* __restrict__ V, int64_t N, int r, in
     __half rh, rl, ih, il;
     split16(v.x * scale, rh, rl);
     split16(v.y * scale, ih, il);
-    unsigned char* tile = out + ((int64_t)(j / 128) * nchV + i / 16) * (int64_t)kTile;
-    const uint32_t o = tc::kmajor_offset((uint32_t)(j % 128), (uint32_t)(2 * (i % 16)), kKc);
+    unsigned char* tile = out + ((int64_t)(j / kRows) * nchV + i / 16) * (int64_t)kTile;
+    const uint32_t o = tc::kmajor_offset((uint32_t)(j % kRows), (uint32_t)(2 * (i % 16)), kKc);
     *reinterpret_cast<__half2*>(tile + o) = __halves2half2(rh, ih);
     *reinterpret_cast<__half2*>(tile + kHalf + o) = __halves2half2(rl, il);
 }
@@ -976,18 +907,18 @@ struct TcDims {
 };
 TcDims tc_dims(int64_t N, int r) {
     TcDims d;
-    d.Nt = (int)((N + 127) / 128);
-    d.Np = d.Nt * 128;
-    d.rp = (r + 127) / 128 * 128;
-    d.Mt = d.rp / 128;
+    d.Nt = (int)((N + kRows - 1) / kRows);
+    d.Np = d.Nt * kRows;
+    d.rp = (r + kRows - 1) / kRows * kRows;
+    d.Mt = d.rp / kRows;
     d.nchU = 2 * d.rp / kKc;
     d.nchV = 2 * d.Np / kKc;
     return d;
 }
 
 size_t tc_smem_bytes() {
-    return (size_t)kRing * kTile + kXbuf + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
-           kGroup * sizeof(unsigned) + (kRing + kCmb + kBBuf + 5) * sizeof(uint64_t);
+    return (size_t)kRing * kTile + kStg + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
+           kGroup * sizeof(unsigned) + (kRing + kCmb + kAbuf + 3) * sizeof(uint64_t);
 }
 
 }  // namespace
@@ -998,9 +929,6 @@ extern "C" int tdagw_debug_trace_tc(unsigned long long* out, int n) {
 }
 extern "C" int tdagw_debug_trace_tc_w(unsigned long long* out) {
     return cudaMemcpyFromSymbol(out, g_trace_w, sizeof(unsigned long long) * 160 * kTraceStages * 6) == cudaSuccess ? 0 : -3;
-}
-extern "C" int tdagw_debug_trace_tc_a(unsigned long long* out) {
-    return cudaMemcpyFromSymbol(out, g_trace_a, sizeof(unsigned long long) * 64 * 4) == cudaSuccess ? 0 : -3;
 }
 #endif
 
@@ -1081,28 +1009,18 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     const int nctas = nsm;
 
     // largest split of the V^H X reduction over the run (one trajectory group)
-    const int MGn = (d.Mt + 3) / 4;
-    const int KSmax = std::max(1, std::min(nctas / MGn, d.nchV));
-    // two U row tiles per phase C item (sharing the S o Y tiles) only when each CTA has
-    // several items: the epilogue of a CTA's last item is not overlapped by MMAs
-    int tpi = d.Nt >= 4 * nctas ? 2 : 1;
-    if (const char* e = std::getenv("TDAGW_TC_TILES_PER_ITEM")) {  // tuning override (1 or 2)
-        const int v = std::atoi(e);
-        if (v == 1 || v == 2) tpi = v;
-    }
-    const int Ntp = (d.Nt + tpi - 1) / tpi;
-    const int Gmax = group_count(B, Ntp, nctas);
+    const int KSmax = std::max(1, std::min(nctas / d.Mt, d.nchV));
     c.tcP.ensure((size_t)KSmax * d.rp * Bp * sizeof(float2));
-    c.tcY.ensure((size_t)Gmax * d.nchU * kTile);
+    c.tcY.ensure((size_t)d.rp * Bp * sizeof(float2));
     c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
-    c.tcRed.ensure((size_t)Ntp * Bp * 3 * sizeof(double));
+    c.tcRed.ensure((size_t)d.Nt * Bp * 3 * sizeof(double));
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
     c.sync.ensure(4 * sizeof(unsigned));
 
     TcArgs a{};
     a.tU = c.tcU.as<unsigned char>();
     a.tV = c.tcV.as<unsigned char>();
-    a.tY = c.tcY.as<unsigned char>();
+    a.Ys = c.tcY.as<float2>();
     a.P = c.tcP.as<float2>();
     a.xmax = c.tcMax.as<unsigned>();
     a.S = c.S.as<float>();
@@ -1128,14 +1046,11 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.r = r;
     a.rp = d.rp;
     a.Nt = d.Nt;
-    a.Ntp = Ntp;
-    a.tpi = tpi;
     a.Mt = d.Mt;
     a.nchU = d.nchU;
     a.nchV = d.nchV;
     a.Bp = Bp;
     a.B = B;
-    a.Tmax = bs.Tmax;
     a.kahan = (flags & TDAGW_FLAG_NO_KAHAN) ? 0 : 1;
     a.c1 = h.c1;
     for (int q = 0; q < 4; ++q) a.occ[q] = (float)h.occ[q];
@@ -1144,13 +1059,72 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.sv = c.tc_sv;
     a.ybound = c.tc_ybound;
     a.wait_ns = 2000000000ull;
-    launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
-                   {{c.bX.p, sbytes},
-                    {c.bS.p, sbytes},
-                    {c.bC.p, sbytes},
-                    {c.tcMax.p, 3 * Bp * sizeof(unsigned)},
-                    {c.sync.p, 4 * sizeof(unsigned)}},
-                   !(flags & TDAGW_FLAG_NO_GRAPH));
+    auto run = [&](int gc_max, int ks_max, int T, bool graph) {
+        a.gc_max = gc_max;
+        a.ks_max = ks_max;
+        a.Tmax = T;
+        launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
+                       {{c.bX.p, sbytes},
+                        {c.bS.p, sbytes},
+                        {c.bC.p, sbytes},
+                        {c.tcMax.p, 3 * Bp * sizeof(unsigned)},
+                        {c.sync.p, 4 * sizeof(unsigned)}},
+                       graph);
+    };
+
+    // Work split of the launch, tuned once per (B, rank) on this context by timing a few
+    // steps of each candidate: the trajectory groups of the U product (fewer groups stream
+    // U fewer times and waste fewer MMA rows; more groups fill more CTAs when N is small)
+    // and the K-ranges of the V^H X product (all CTAs, or half as many longer ranges with
+    // half the partial sums).
+    const uint64_t key = (0xF0ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
+    int gc_max = 0, ks_max = 0;
+    auto it = c.batch_plans.find(key);
+    if (it != c.batch_plans.end()) {
+        gc_max = it->second.first;
+        ks_max = it->second.second;
+    } else {
+        const int g_min = (B + kGroup - 1) / kGroup;
+        const int g_fill = group_count(B, d.Nt, nctas, 0);
+        std::vector<int> gcs;
+        for (int gcand = g_min; gcand < g_fill; gcand *= 2) gcs.push_back(gcand);
+        gcs.push_back(0);
+        const int ks_fill = std::max(1, std::min(nctas / (g_min * d.Mt), d.nchV));
+        std::vector<int> kss = {0};
+        if (ks_fill >= 4) kss.push_back(ks_fill / 2);
+        if (gcs.size() * kss.size() == 1) {
+            c.batch_plans[key] = {0, 0};
+        } else if (bs.Tmax >= 8) {
+            cudaEvent_t e0, e1;
+            TDAGW_CUDA(cudaEventCreate(&e0));
+            TDAGW_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (int gcand : gcs)
+                for (int kcand : kss) {
+                    run(gcand, kcand, 2, false);  // warm
+                    TDAGW_CUDA(cudaEventRecord(e0, s));
+                    run(gcand, kcand, 6, false);
+                    TDAGW_CUDA(cudaEventRecord(e1, s));
+                    TDAGW_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    TDAGW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        gc_max = gcand;
+                        ks_max = kcand;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            int err = 0;
+            TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
+            TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the tensor-core kernel");
+            // the tuning runs overwrote the observables: restore the first row
+            reset_batch_observables(c, bs, B);
+            c.batch_plans[key] = {gc_max, ks_max};
+        }
+    }
+    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
     c.persistent_launched = true;
     c.adj.valid = false;
     finish_batch(c, bs, B);

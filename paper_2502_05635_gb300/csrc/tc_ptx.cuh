@@ -1,6 +1,6 @@
 // Fifth-generation tensor-core primitives (tcgen05) as inline PTX, for sm_100-family GPUs:
-// tensor-memory allocation, shared-memory matrix descriptors, the kind::f16 MMA with its
-// commit to an mbarrier, and tensor-memory loads.
+// tensor-memory allocation, shared-memory matrix descriptors, the kind::f16 MMA (A from
+// shared or tensor memory) with its commit to an mbarrier, tensor-memory loads and stores.
 //
 // Operand layout used throughout: K-major, no swizzling.  A tile of R rows x KT columns of
 // 16-bit elements is stored as core matrices of 8 rows x 8 elements (16 bytes per row,
@@ -68,6 +68,17 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// D[tmem] (+)= A[tmem] * B[smem]^T: the A operand (M x 16) read from tensor memory, row m
+// in lane m, two 16-bit elements per 32-bit column (element k in column k / 2, low half
+// for even k)
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // the mbarrier receives one arrival when all MMAs issued so far by this thread complete
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -91,6 +102,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// 8 consecutive 32-bit columns of the calling warp's 32 lanes, stored from registers; the
+// stores are complete (visible to later tcgen05 operations after a thread fence and
+// barrier) when the wait returns
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
 }
 }  // namespace tc
 }  // namespace tdagw
