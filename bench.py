@@ -331,18 +331,47 @@ def bench_batched(tg, torch, stream, sh, tflops_peak):
     return out
 
 
-def bench_precision(tg, torch, stream, sh, hbm, split_steps=300, fp32_steps=30, full_steps=6):
-    """Precision-study size: four-band 48 x 48 model (N = 36864), rank 2048, B = 64 equal
-    lengths.  Seeded synthetic factors of that shape (the throughput does not depend on
-    their values; the randomised SVD at this size takes about 26 s and is left out)."""
+def precision_oracle_job(path: str, steps: int):
+    """FP64 oracle run of one precision-study trajectory with the factors saved at `path`
+    (the GPU's own; run in a spawned process beside the GPU legs): observables rows."""
+    from oracle import lowrank as olr
+    from oracle import model as om
+    from oracle import propagate as op
+    z = np.load(path)
+    w = wl.prec_nb4_l48()
+    mdl = om.Model(w.model)
+    U, V = z["U"].astype(np.complex128), z["V"].astype(np.complex128)
+    S, d, b = z["S"].astype(np.float64), z["d"].astype(np.complex128), int(z["b"])
+    pulse = w.pulses[b]
+    t0 = time.perf_counter()
+    ref, _ = op.rk4(mdl, lambda v: olr.apply_lowrank(d, U, S, V, v), op.half_step_samples(pulse, w.dt, steps),
+                    w.dt, steps, direction=(pulse.dir_x, pulse.dir_y))
+    return ref, time.perf_counter() - t0
+
+
+def bench_precision(tg, torch, stream, sh, hbm, split_steps=300, fp32_steps=30, full_steps=6, oracle_steps=100):
+    """The precision study: four-band 48 x 48 model (N = 36864), rank 2048 from the GPU's
+    randomised SVD (oversampling 64, two power iterations, FP64 orthogonalisation; setup
+    outside the timed regions), B = 64 trajectories of the sweep distributions.  Timed:
+    split-FP16 (tensor cores, Kahan-compensated RK4), plain FP32 and the dense kernel.
+    Accuracy: split-FP16 and FP32 (with and without compensation) against each other over
+    the FP32 run, and against the FP64 oracle with the same factors over an `oracle_steps`
+    prefix of the widest pulse, computed in a spawned process while later legs run; returns
+    (result, finish) where finish() joins the oracle and fills in its errors."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import tempfile
     w = wl.prec_nb4_l48()
     ctx = tg.Context(w.model, tg.C64, stream=sh)
-    U, S, V, d = wl.random_factors(w.model.N, w.rank, seed=3)
-    tg.tdagw_set_factors(ctx.h, U, S, V, d)
-    del U, V
+    t0 = time.perf_counter()
+    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED, precision=1)
+    tg.tdagw_sync(ctx.h)
+    setup = time.perf_counter() - t0
     fields = [tg.make_field(p) for p in w.pulses]
     N, r, B = w.model.N, w.rank, w.B
-    out = {"workload": "prec_nb4_l48", "N": N, "B": B, "rank": r, "factors": "seeded synthetic"}
+    out = {"workload": "prec_nb4_l48", "N": N, "B": B, "rank": r,
+           "factors": f"GPU randomised SVD (p = {w.oversample}, q = {w.power_iters}), split-FP16 tiles",
+           "setup_s": setup}
     obs = {}
     legs = (("lowrank_split_f16", tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16, split_steps),
             ("lowrank", tg.LOWRANK, tg.FLAG_RESET, fp32_steps),
@@ -356,12 +385,40 @@ def bench_precision(tg, torch, stream, sh, hbm, split_steps=300, fp32_steps=30, 
                      "factor_gbs": gbs, "hbm_frac": gbs / hbm}
     out["speedup_split_f16_vs_full"] = out["lowrank_split_f16"]["value"] / out["full"]["value"]
     out["speedup_split_f16_vs_fp32_lowrank"] = out["lowrank_split_f16"]["value"] / out["lowrank"]["value"]
-    # the FP32 run is a prefix of the same trajectories
-    tg.tdagw_propagate(ctx.h, fields, [fp32_steps] * B, w.dt, tg.LOWRANK, tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
-    split_prefix = tg.tdagw_observables(ctx.h, B=B)
-    out["p_rel_err_split_f16_vs_fp32"] = _rel_errs(split_prefix, obs["lowrank"], [fp32_steps] * B)
+    # accuracy runs over the oracle prefix (untimed)
+    T = max(fp32_steps, oracle_steps)
+    runs = {}
+    for name, flags in (("split_f16_kahan", tg.FLAG_RESET | tg.FLAG_SPLIT_F16),
+                        ("split_f16_plain", tg.FLAG_RESET | tg.FLAG_SPLIT_F16 | tg.FLAG_NO_KAHAN),
+                        ("fp32_kahan", tg.FLAG_RESET), ("fp32_plain", tg.FLAG_RESET | tg.FLAG_NO_KAHAN)):
+        tg.tdagw_propagate(ctx.h, fields, [T] * B, w.dt, tg.LOWRANK, flags)
+        runs[name] = tg.tdagw_observables(ctx.h, B=B)
+    out["p_rel_err_split_f16_vs_fp32"] = _rel_errs(runs["split_f16_kahan"], runs["fp32_kahan"], [T] * B)
+    b = int(np.argmax([p.sigma for p in w.pulses]))
+    U, S, V, d = tg.tdagw_get_factors(ctx.h)
     ctx.close()
-    return out
+    tmp = tempfile.NamedTemporaryFile(suffix=".npz", delete=False)
+    tmp.close()
+    np.savez(tmp.name, U=U.astype(np.complex64), V=V.astype(np.complex64), S=S, d=d, b=b)
+    del U, V
+    pool = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+    fut = pool.submit(precision_oracle_job, tmp.name, oracle_steps)
+
+    def finish():
+        try:
+            ref, secs = fut.result()
+        finally:
+            pool.shutdown()
+            os.unlink(tmp.name)
+        n = oracle_steps
+        acc = {"trajectory": b, "steps": n, "oracle_s": secs}
+        for name, o in runs.items():
+            acc[name] = float(np.linalg.norm(o[:n + 1, b, 0] - ref[:, 0]) / np.linalg.norm(ref[:, 0]))
+        acc["within_1e-4"] = acc["split_f16_kahan"] <= 1e-4
+        acc["fp32_within_1e-5"] = acc["fp32_kahan"] <= 1e-5
+        out["p_rel_err_vs_fp64_oracle"] = acc
+        return out
+    return out, finish
 
 
 def bench_adjoint(tg, torch, stream, sh, T=1000):
@@ -537,7 +594,8 @@ def run_leg(a):
     if a.leg == "sweep":
         out = bench_batched(tg, torch, stream, sh, tflops)
     elif a.leg == "precision":
-        out = bench_precision(tg, torch, stream, sh, hbm, *( (n, n, n) if n else ()))
+        _, finish = bench_precision(tg, torch, stream, sh, hbm, *((n, n, n) if n else ()))
+        out = finish()
     elif a.leg == "adjoint":
         out = bench_adjoint(tg, torch, stream, sh, n or 1000)
     elif a.leg == "channel":
@@ -697,7 +755,7 @@ def run_ours(a):
         line["cpu_baseline"] = cpu
     if not a.no_batched:
         line["batched_sweep"] = bench_batched(tg, torch, stream, sh, tflops)
-        line["precision_study"] = bench_precision(tg, torch, stream, sh, hbm)
+        prec, prec_finish = bench_precision(tg, torch, stream, sh, hbm)
         line["adjoint"] = bench_adjoint(tg, torch, stream, sh)
         line["channel_wise"] = bench_channel(tg, torch, stream, sh, hbm)
         ch = line["channel_wise"]
@@ -712,6 +770,7 @@ def run_ours(a):
         line["channel_wise_sweep"] = bench_channel_sweep(tg, torch, stream, sh)
         line["angle_hhg"] = bench_angle_hhg(tg, torch, stream, sh)
         line["kdiag_split"] = bench_kblock_split(tg, torch, stream, sh, hbm)
+        line["precision_study"] = prec_finish()
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -62,7 +62,10 @@ constexpr int kSyncThreads = kWorkers + 32;  // grid-barrier participants: MMA w
 #define TDAGW_TC_RING 5
 #endif
 constexpr int kRing = TDAGW_TC_RING;       // ring slots of one factor tile each
-constexpr int kAbuf = 4;                   // small-operand blocks in tensor memory
+#ifndef TDAGW_TC_ABUF
+#define TDAGW_TC_ABUF 4
+#endif
+constexpr int kAbuf = TDAGW_TC_ABUF;       // small-operand blocks in tensor memory
 constexpr int kCmb = 16;                   // chunk-completion barriers; every wait on one
                                            // targets a chunk < kCmb chunks behind the
                                            // waiter's next chunk, so parities cannot alias
@@ -143,14 +146,15 @@ __device__ unsigned long long g_trace_tc[160 * kTraceStages * 9];
     } while (0)
 // wait/issue time accumulators per CTA and traced stage: [0] MMA thread waiting for tiles,
 // [1] for operand blocks, [2] for the accumulator, [3] issuing MMAs and commits, [4] copy
-// thread waiting for a free slot, [5] issuing copies
-__device__ unsigned long long g_trace_w[160 * kTraceStages * 6];
+// thread waiting for a free slot, [5] issuing copies; worker 0: [6] waiting for a free
+// operand block, [7] waiting for its source values, [8] storing to tensor memory
+__device__ unsigned long long g_trace_w[160 * kTraceStages * 9];
 #define TC_W_BEGIN(id) const uint64_t tw_##id = gtimer()
 #define TC_W_END(id, k)                                                                          \
     do {                                                                                         \
         const int ts_ = tr_gs - kTraceFirst;                                                     \
         if (blockIdx.x < 160 && ts_ >= 0 && ts_ < kTraceStages)                                  \
-            g_trace_w[(blockIdx.x * kTraceStages + ts_) * 6 + (k)] += gtimer() - tw_##id;         \
+            g_trace_w[(blockIdx.x * kTraceStages + ts_) * 9 + (k)] += gtimer() - tw_##id;         \
     } while (0)
 #else
 #define TC_TRACE(who, k) \
@@ -246,13 +250,38 @@ __device__ __forceinline__ void mma_chunk(uint32_t d, uint32_t a_tm, uint32_t f_
     }
 }
 
+// Observable sums in double-float: (hi, lo) pairs of FP32 updated with error-free
+// products (FMA) and sums (TwoSum), the compensated dot product of Ogita, Rump and Oishi
+// (2005).  FP64 arithmetic is slow on this GPU; the per-thread sums of the epilogue stay
+// within a few units of 2^-44 of the FP64 sums and are widened once per thread.
+struct DF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float e;
+        hi = two_sum(hi, v, e);
+        lo += e;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);
+        float e;
+        hi = two_sum(hi, p, e);
+        lo += e + ep;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct DF3 {
+    DF p, j, o;
+};
+
 // Commutator + RK4 stage update of one (k, trajectory) block (Eq. tdagw; the arithmetic of
 // the FP32 batched path), with the low-rank part of dSigma read from the staged quarter
 // tile (block rows row0 .. row0 + NB^2 - 1, trajectory column bl) and K^diag o X added here.
-// xm: running max(|Re|, |Im|) of the values written to X (the next stage input).
+// xm: running max(|Re|, |Im|) of the values written to X (the next stage input); ob: the
+// thread's running sums of the observables (last stage).
 template <int NB>
-__device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
-                            const float2* sDS, int row0, int bl, float& xm) {
+__device__ void stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
+                            const float2* sDS, int row0, int bl, float& xm, DF3& ob) {
     constexpr int NB2 = NB * NB;
     const int64_t Bp = a.Bp;
     float2 X[NB2], M[NB2];
@@ -264,7 +293,6 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
         const float2 ds = cfma(a.diag[i], X[g], sDS[ds_index(row0 + g, bl)]);
         M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
     }
-    Obs3 ob{0.0, 0.0, 0.0};
     // state loads of RB rows at a time, issued before any store of those rows (all rows
     // for two bands, one row for four: register budget)
     constexpr int RB = NB == 2 ? 2 : 1;
@@ -320,15 +348,16 @@ __device__ Obs3 stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
                 Xn = cadd(ns, nc);
                 const float2 rho = (n == m) ? make_float2(Xn.x + a.occ[n], Xn.y) : Xn;
                 const float2 d1 = a.dx[i], v1 = a.vx[i];
-                ob.p += (double)rho.x * (double)d1.x + (double)rho.y * (double)d1.y;
-                ob.j += (double)rho.x * (double)v1.x + (double)rho.y * (double)v1.y;
-                if (n == m && n == a.c1) ob.o += (double)rho.x;
+                ob.p.add_prod(rho.x, d1.x);
+                ob.p.add_prod(rho.y, d1.y);
+                ob.j.add_prod(rho.x, v1.x);
+                ob.j.add_prod(rho.y, v1.y);
+                if (n == m && n == a.c1) ob.o.add(rho.x);
             }
             a.X[e] = Xn;
             xm = fmaxf(xm, fmaxf(fabsf(Xn.x), fabsf(Xn.y)));
         }
     }
-    return ob;
 }
 
 // Trajectory groups of phase C: at most kGroup trajectories each and, where the row tiles
@@ -500,7 +529,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     //   U Y:    row 2b: (re, -im), row 2b + 1: (im, re)
     auto build_block = [&](const float2 (&v)[8], bool vhx) {
         const uint32_t bs = bu % kAbuf;
+        TC_W_BEGIN(w6);
         if (!*vabort && !chunk_done(buf_ch[bs])) fail();
+        if (wt == 0) TC_W_END(w6, 6);
         buf_ch[bs] = gch;
         if (!warp_abort()) {
             uint32_t hi[8], lo[8];
@@ -514,15 +545,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     p0 = ocomp ? v[u].y : v[u].x;
                     p1 = ocomp ? v[u].x : -v[u].y;
                 }
-                __half h0, l0, h1, l1;
-                split16(p0, h0, l0);
-                split16(p1, h1, l1);
-                hi[u] = pack2(h0, h1);
-                lo[u] = pack2(l0, l1);
+                // split both values at once (paired conversions): hi = fp16(p), lo = fp16(p - hi)
+                const __half2 h = __floats2half2_rn(p0, p1);
+                const float2 hb = __half22float2(h);
+                const __half2 l = __floats2half2_rn(p0 - hb.x, p1 - hb.y);
+                hi[u] = *reinterpret_cast<const uint32_t*>(&h);
+                lo[u] = *reinterpret_cast<const uint32_t*>(&l);
             }
             const uint32_t ta = tm + ((uint32_t)(32 * wq) << 16) + kAcol + 32 * bs + 8 * wh;
+            TC_W_BEGIN(w8);
             tc::tmem_st8(ta, hi);
             tc::tmem_st8(ta + 16, lo);
+            if (wt == 0) TC_W_END(w8, 8);
         }
         tc::fence_before_sync();
         __syncwarp();
@@ -551,8 +585,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     // workers: wait for the source values of the chunk in slot k (kSrcAhead - 1 newer
     // groups may stay in flight) and read the pair's 8 values, scaled
     auto src_read = [&](float2 (&v)[8], int k, float sc) {
+        TC_W_BEGIN(w7);
         cp_async_wait<kSrcAhead - 1>();
         __syncwarp();
+        if (wt == 0) TC_W_END(w7, 7);
         const float2* src = srcbuf + (k % kSrcSlots) * 1024 + (warp - 2) * 128 + (obl & 15) * 8;
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = make_float2(src[u].x * sc, src[u].y * sc);
@@ -739,7 +775,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     tc::fence_after_sync();
                     const int kgroups = kWorkers / nbg;
                     const int bl = wt % nbg, kg = wt / nbg;
-                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    DF3 obs;
                     float xm = 0.f;
                     for (int qq = 0; qq < kRows / 64; ++qq) {
                         // accumulator columns 64 qq .. + 63 (the warp's 32 of them) -> staged
@@ -767,12 +803,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             const int b = b0 + bl;
                             const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
                             const float2 dr = a.dir[b];
-                            for (int kl = kg; kl < kt; kl += kgroups) {
-                                const Obs3 ob = stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm);
-                                s0 += ob.p;
-                                s1 += ob.j;
-                                s2 += ob.o;
-                            }
+                            for (int kl = kg; kl < kt; kl += kgroups)
+                                stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs);
                         }
                         workers_sync();  // the staged quarter is consumed before it is rewritten
                     }
@@ -782,9 +814,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     if (kg < kgroups) {
                         atomicMax(smx + bl, __float_as_uint(xm));
                         if (st == 3) {
-                            sred[(kg * nbg + bl) * 3] = s0;
-                            sred[(kg * nbg + bl) * 3 + 1] = s1;
-                            sred[(kg * nbg + bl) * 3 + 2] = s2;
+                            sred[(kg * nbg + bl) * 3] = obs.p.value();
+                            sred[(kg * nbg + bl) * 3 + 1] = obs.j.value();
+                            sred[(kg * nbg + bl) * 3 + 2] = obs.o.value();
                         }
                     }
                     workers_sync();
@@ -928,7 +960,7 @@ extern "C" int tdagw_debug_trace_tc(unsigned long long* out, int n) {
     return cudaMemcpyFromSymbol(out, g_trace_tc, sizeof(unsigned long long) * (size_t)n) == cudaSuccess ? 0 : -3;
 }
 extern "C" int tdagw_debug_trace_tc_w(unsigned long long* out) {
-    return cudaMemcpyFromSymbol(out, g_trace_w, sizeof(unsigned long long) * 160 * kTraceStages * 6) == cudaSuccess ? 0 : -3;
+    return cudaMemcpyFromSymbol(out, g_trace_w, sizeof(unsigned long long) * 160 * kTraceStages * 9) == cudaSuccess ? 0 : -3;
 }
 #endif
 
