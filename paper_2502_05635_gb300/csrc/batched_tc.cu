@@ -59,7 +59,7 @@ constexpr int kWorkers = 256;
 constexpr int kTcThreads = kWorkers + 64;  // warp 0: copies, warp 1: MMAs, warps 2-9: workers
 constexpr int kSyncThreads = kWorkers + 32;  // grid-barrier participants: MMA warp + workers
 #ifndef TDAGW_TC_RING
-#define TDAGW_TC_RING 5
+#define TDAGW_TC_RING 4
 #endif
 constexpr int kRing = TDAGW_TC_RING;       // ring slots of one factor tile each
 #ifndef TDAGW_TC_ABUF
@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* ring = smem;
     float2* sDS = reinterpret_cast<float2*>(ring + kRing * kTile);
-    double* sred = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(sDS) + kStg);
-    float* ssc = reinterpret_cast<float*>(sred + kWorkers * 3);
+    // per-thread observable sums of an item: written after its last staged quarter is
+    // consumed, read before the next item's operand sources are copied (they share memory)
+    double* sred = reinterpret_cast<double*>(sDS);
+    float* ssc = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sDS) + kStg);
     unsigned* smx = reinterpret_cast<unsigned*>(ssc + kGroup);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smx + kGroup);
     uint64_t* full = bars;
@@ -949,8 +951,9 @@ TcDims tc_dims(int64_t N, int r) {
 }
 
 size_t tc_smem_bytes() {
-    return (size_t)kRing * kTile + kStg + (size_t)kWorkers * 3 * sizeof(double) + kGroup * sizeof(float) +
-           kGroup * sizeof(unsigned) + (kRing + kCmb + kAbuf + 3) * sizeof(uint64_t);
+    static_assert(kWorkers * 3 * sizeof(double) <= kStg, "observable sums fit the staging buffer");
+    return (size_t)kRing * kTile + kStg + kGroup * sizeof(float) + kGroup * sizeof(unsigned) +
+           (kRing + kCmb + kAbuf + 3) * sizeof(uint64_t);
 }
 
 }  // namespace

@@ -5,17 +5,21 @@
 //
 //   V pass   for each input pair q:  y_c = sum_{k' of this CTA} conj(V_q[k']) x[k' P + q]
 //   grid barrier; x by pair (Xt[p][k]) from this CTA's rows; S o sum_c y_c (column slice)
-//   grid barrier; U pass  for each output pair p:
-//            dSigma[k P + p] = U_p[k] . [S o y of the channels out of p ; x_p]   (own k)
-//   commutator, RK4 stage update, observables for the same k
+//   grid barrier; U pass  for the rows (p, k) of this CTA's share of the U segments:
+//            dSigma[k P + p] = U_p[k] . [S o y of the channels out of p ; x_p]
+//   grid barrier; commutator, RK4 stage update, observables for the CTA's own k
 //
-// Each CTA owns a contiguous range of k-points with all their pair elements, so the
-// commutators use only rows it computed and the next V pass needs only its own stage
-// input.  The dense diagonal channels need all of x_p: every CTA publishes its rows of the
-// stage input by pair after the first barrier (when no CTA still reads the previous
-// stage's), and reads x_p after the second.  A producer warp streams the CTA's rows of the
-// 2 P factor segments through a shared-memory ring with 1D bulk copies (L2 evict-first:
-// the factors are read once per stage), sixteen consumer warps compute from shared memory.
+// Each CTA owns a contiguous range of k-points with all their pair elements: its V pass
+// reads only its own stage input and its commutators write it, so no barrier separates
+// them.  The U pass instead splits the stacked U segments (rows (p, k), p-major, one
+// contiguous array) into byte-balanced contiguous shares: a CTA streams one range of
+// rows touching one or two pairs (two vectors z_p instead of all P), and the dSigma rows
+// reach their k-point's owner through L2 across a third barrier.  The dense diagonal
+// channels need all of x_p: every CTA publishes its rows of the stage input by pair after
+// the first barrier (when no CTA still reads the previous stage's), and reads x_p after
+// the second.  A producer warp streams the CTA's V rows and its U share through a
+// shared-memory ring with 1D bulk copies (L2 evict-first: the factors are read once per
+// stage), sixteen consumer warps compute from shared memory.
 // Every wait is bounded; on expiry the CTA records an error word and returns.
 #include <algorithm>
 
@@ -67,10 +71,25 @@ struct CHArgs {
     float2* Xt;    // P x Nk, stage input by pair
     unsigned long long* bar_count;
     int* err;
-    int T, nslots, slot_bytes, kmax, zs_len;
+    int T, nslots, slot_bytes, kmax, zs_len, upart_len;
     int extra_arrivals;  // > 0 only for the timeout test: the barrier can never complete
     unsigned long long wait_ns;
 };
+
+// First U-pass row of CTA c (global row p Nk + k of the stacked U segments, which are
+// contiguous and p-major): the first row that starts at or after c/G of the U elements,
+// so that the shares are balanced to a row.
+__host__ __device__ inline int urow_start(const ChMeta& m, int c, int G) {
+    const long long t = (long long)c * m.utot / G;
+    for (int p = 0; p < m.P; ++p) {
+        const long long end = m.ubase[p] + (long long)m.Nk * m.ldw[p];
+        if (t < end) {
+            const long long k = (t - m.ubase[p] + m.ldw[p] - 1) / m.ldw[p];
+            return p * m.Nk + (int)k;
+        }
+    }
+    return m.P * m.Nk;
+}
 
 // rows of a segment per ring slot: the largest power of two (<= 64) whose rows fit
 __device__ __forceinline__ int seg_rps(int ld, int slot_bytes) {
@@ -115,13 +134,17 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
     const int nk = kb - ka;
     const int64_t ra = (int64_t)ka * P, rb = (int64_t)kb * P;
     const int ns = a.nslots;
+    // this CTA's share of the U pass: rows [ur0, ur1) of the stacked U segments, pairs
+    // pA .. pB (pB < pA when the share is empty)
+    const int ur0 = urow_start(a.m, cta, G), ur1 = urow_start(a.m, cta + 1, G);
+    const int pA = ur0 / Nk, pB = ur1 > ur0 ? (ur1 - 1) / Nk : pA - 1;
 
     unsigned char* ring = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * a.slot_bytes);
     uint64_t* empty = full + ns;
     float2* zbuf = reinterpret_cast<float2*>(empty + ns);  // 2 x zs_len U-pass vectors
-    float2* ubuf = zbuf + 2 * a.zs_len;                    // 2 x kmax x kCW partial dots
-    float2* xs = ubuf + 2 * a.kmax * kCW;                  // kmax x P, this CTA's stage input
+    float2* ubuf = zbuf + 2 * a.zs_len;                    // 2 x upart_len partial dots
+    float2* xs = ubuf + 2 * a.upart_len;                   // kmax x P, this CTA's stage input
     float2* yred = xs + a.kmax * P;                         // kCons partial sums of S o y
     double* wred = reinterpret_cast<double*>(yred + kCons);
     volatile int* abort_s = reinterpret_cast<volatile int*>(wred + 3 * kCW);
@@ -178,18 +201,20 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                         ++issued;
                         pos.advance(1, ns);
                     }
-                    // U pass: one chunk of rows per slot
-                    for (int e = 0; e < P && ok; ++e) {
+                    // U pass: this CTA's share, one chunk of rows of one pair per slot
+                    for (int e = pA; e <= pB && ok; ++e) {
                         const int ld = a.m.ldw[e];
-                        const float2* base = a.U + a.m.ubase[e] + (int64_t)ka * ld;
+                        const int k0 = e == pA ? ur0 - pA * Nk : 0, k1 = e == pB ? ur1 - pB * Nk : Nk;
+                        const int nkp = k1 - k0;
+                        const float2* base = a.U + a.m.ubase[e] + (int64_t)k0 * ld;
                         const int rps = seg_rps(ld, a.slot_bytes);
-                        for (int r0 = 0; r0 < nk; r0 += rps) {
+                        for (int r0 = 0; r0 < nkp; r0 += rps) {
                             if (issued >= (uint64_t)ns &&
                                 !mbar_wait(empty + pos.slot, pos.phase ^ 1u, abort_s, a.wait_ns)) {
                                 ok = false;
                                 break;
                             }
-                            const int nr = min(rps, nk - r0);
+                            const int nr = min(rps, nkp - r0);
                             const uint32_t bytes = (uint32_t)nr * ld * 8u;
                             mbar_expect_tx(full + pos.slot, bytes);
                             bulk_g2s_hint(ring + (size_t)pos.slot * a.slot_bytes, base + (int64_t)r0 * ld, bytes,
@@ -358,24 +383,28 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                         if (c < ld) dst[c] = zr[j];
                     }
                 };
-                zload(0);
-                zstore(zbuf, a.m.ldw[0]);
+                if (pA <= pB) {
+                    zload(pA);
+                    zstore(zbuf, a.m.ldw[pA]);
+                }
                 named_sync<kCons>();
                 CH_TRACE(5);
-                for (int p = 0; p < P; ++p) {
+                for (int p = pA; p <= pB; ++p) {
                     const int ld = a.m.ldw[p];
-                    const float2* zs = zbuf + (p & 1) * a.zs_len;
-                    float2* upart = ubuf + (p & 1) * a.kmax * kCW;
-                    if (p + 1 < P) zload(p + 1);
+                    const int k0 = p == pA ? ur0 - pA * Nk : 0, k1 = p == pB ? ur1 - pB * Nk : Nk;
+                    const int nkp = k1 - k0;
+                    const float2* zs = zbuf + ((p - pA) & 1) * a.zs_len;
+                    float2* upart = ubuf + ((p - pA) & 1) * a.upart_len;
+                    if (p + 1 <= pB) zload(p + 1);
                     const int rps = seg_rps(ld, a.slot_bytes);
                     const int cp = rps >= kCW ? 1 : kCW / rps;
                     const int pw = ((ld + cp - 1) / cp + 1) / 2 * 2;
                     const int myq = warp % cp, myr = warp / cp, rstride = kCW / cp;
                     const int c0 = myq * pw, c1 = min(ld, c0 + pw);
-                    for (int r0 = 0; r0 < nk; r0 += rps) {
+                    for (int r0 = 0; r0 < nkp; r0 += rps) {
                         if (!warp_wait_full(full, pos, abort_s, a.wait_ns, lane)) break;
                         const float2* tile = reinterpret_cast<const float2*>(ring + (size_t)pos.slot * a.slot_bytes);
-                        const int nr = min(rps, nk - r0);
+                        const int nr = min(rps, nkp - r0);
                         for (int rr = myr; rr < nr; rr += rstride) {
                             const float2* ur = tile + (size_t)rr * ld;
                             float2 d = make_float2(0.f, 0.f), d1 = d;
@@ -394,18 +423,20 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                         if (lane == 0) mbar_arrive(empty + pos.slot);
                         pos.advance(1, ns);
                     }
-                    if (p + 1 < P) zstore(zbuf + ((p + 1) & 1) * a.zs_len, a.m.ldw[p + 1]);
+                    if (p + 1 <= pB) zstore(zbuf + ((p + 1 - pA) & 1) * a.zs_len, a.m.ldw[p + 1]);
                     // every part of every row of pair p is in, and the vector of p + 1; the
                     // buffers written next (pair p + 2) were last read before this barrier's
                     // predecessor
                     named_sync<kCons>();
-                    for (int kk = tid; kk < nk; kk += kCons) {
+                    for (int kk = tid; kk < nkp; kk += kCons) {
                         float2 s = upart[kk * cp];
                         for (int qq = 1; qq < cp; ++qq) s = cadd(s, upart[kk * cp + qq]);
-                        a.dSw[(int64_t)(ka + kk) * P + p] = s;
+                        a.dSw[(int64_t)(k0 + kk) * P + p] = s;
                     }
                 }
-                named_sync<kCons>();  // this CTA's dSigma rows are complete
+                // every CTA's dSigma rows are complete (the own k-points' rows came from
+                // the CTAs whose U shares hold them)
+                if (!(ok = grid_sync<kCons>(a.bar_count, a.err, a.extra_arrivals, a.wait_ns, lgen, abort_s))) break;
                 CH_TRACE(6);
                 // ---- commutator + RK4 stage update for k in [ka, kb)
                 const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
@@ -502,16 +533,39 @@ bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     const int row_max = std::max(maxv, maxw) * 8;
     const int zs_len = maxw;  // even
     if (zs_len > kZPre * kCons) return false;  // the U-pass vector prefetch covers 4096 entries
-    const size_t extras = 2 * (size_t)zs_len * 8 + 2 * (size_t)kmax * kCW * 8 + (size_t)kmax * P * 8 +
-                          (size_t)kCons * 8 + 3 * kCW * 8 + 16;
+    const size_t extras_fixed = 2 * (size_t)zs_len * 8 + (size_t)kmax * P * 8 + (size_t)kCons * 8 + 3 * kCW * 8 + 16;
     const size_t avail = (size_t)smem_max - 1024;
-    if (avail < extras) return false;
     // slots of up to four U rows (fewer partial dot products per row), as long as at least
     // four slots fit; at least one whole row
-    int slot_bytes = 0;
+    auto slot_for = [&](int rows) {
+        return (std::max(kSlotMin, std::max(row_max, std::min(rows * maxw * 8, kSlotMax))) + 127) / 128 * 128;
+    };
+    // partial dot products of one pair of a U share: rows x column parts (per slot size)
+    auto upart_need = [&](int sb) {
+        int need = 1;
+        for (int c = 0; c < G; ++c) {
+            const int u0 = urow_start(m, c, G), u1 = urow_start(m, c + 1, G);
+            for (int p = u0 / h.Nk; u1 > u0 && p <= (u1 - 1) / h.Nk; ++p) {
+                const int k0 = std::max(u0, p * h.Nk), k1 = std::min(u1, (p + 1) * h.Nk);
+                int rps = 1;
+                while (rps < 64 && 2 * rps * m.ldw[p] * 8 <= sb) rps *= 2;
+                const int cp = rps >= kCW ? 1 : kCW / rps;
+                need = std::max(need, (k1 - k0) * cp);
+            }
+        }
+        return need;
+    };
+    int slot_bytes = 0, upart_len = 0;
+    size_t extras = 0;
     for (int rows = 4; rows >= 1 && !slot_bytes; rows /= 2) {
-        const int sb = (std::max(kSlotMin, std::max(row_max, std::min(rows * maxw * 8, kSlotMax))) + 127) / 128 * 128;
-        if ((avail - extras) / ((size_t)sb + 16) >= 4) slot_bytes = sb;
+        const int sb = slot_for(rows);
+        const int ul = upart_need(sb);
+        const size_t ex = extras_fixed + 2 * (size_t)ul * 8;
+        if (avail > ex && (avail - ex) / ((size_t)sb + 16) >= 4) {
+            slot_bytes = sb;
+            upart_len = ul;
+            extras = ex;
+        }
     }
     if (!slot_bytes) return false;
     const int nslots = (int)std::min<size_t>(64, (avail - extras) / (slot_bytes + 16));
@@ -564,6 +618,7 @@ bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.slot_bytes = slot_bytes;
     a.kmax = kmax;
     a.zs_len = zs_len;
+    a.upart_len = upart_len;
     a.extra_arrivals = test_timeout ? 1 : 0;
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};
