@@ -423,26 +423,34 @@ def bench_precision(tg, torch, stream, sh, hbm, split_steps=300, fp32_steps=30, 
 
 def bench_adjoint(tg, torch, stream, sh, T=1000):
     """Differentiation size: two-band 36 x 36 model (N = 5184), rank 512, B = 32 equal
-    lengths: the checkpointed forward and the discrete adjoint (objective 1/2 sum P_x^2)."""
+    lengths: the checkpointed forward and the discrete adjoint (objective 1/2 sum P_x^2),
+    with the forward and the segment recomputes in FP32 and on the tensor cores (split-FP16
+    factors; the reverse stages use the FP32 factors in both)."""
     w = wl.adj_nb2_l36()
     ctx = tg.Context(w.model, tg.C64, stream=sh)
-    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED)
+    tg.tdagw_compress_svd(ctx.h, w.rank, w.oversample, w.power_iters, wl.SKETCH_SEED, precision=1)
     fields = [tg.make_field(p) for p in w.pulses]
     B = w.B
-    ms_fwd = _time_propagate(tg, torch, stream, ctx, fields, [T] * B, w.dt, tg.LOWRANK,
-                             tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
-    P = tg.tdagw_observables(ctx.h, B=B)
-    d = np.zeros((T + 1, B, 3))
-    d[:, :, 0] = P[:, :, 0]
-    t0 = time.perf_counter()
-    gE, gp = tg.tdagw_adjoint(ctx.h, d, T, B)
-    s_adj = time.perf_counter() - t0
+    out = {"workload": "adj_nb2_l36", "N": w.model.N, "B": B, "rank": w.rank, "steps": T}
+    grads = {}
+    for name, extra in (("fp32", 0), ("split_f16", tg.FLAG_SPLIT_F16)):
+        ms_fwd = _time_propagate(tg, torch, stream, ctx, fields, [T] * B, w.dt, tg.LOWRANK,
+                                 tg.FLAG_RESET | tg.FLAG_CHECKPOINT | extra)
+        P = tg.tdagw_observables(ctx.h, B=B)
+        d = np.zeros((T + 1, B, 3))
+        d[:, :, 0] = P[:, :, 0]
+        t0 = time.perf_counter()
+        gE, gp = tg.tdagw_adjoint(ctx.h, d, T, B)
+        s_adj = time.perf_counter() - t0
+        grads[name] = gE
+        out[name] = {"forward_checkpointed": {"value": T * B / (ms_fwd * 1e-3), "unit": "traj*steps/s", "ms": ms_fwd},
+                     "adjoint": {"value": T * B / s_adj, "unit": "traj*steps/s", "ms": s_adj * 1e3},
+                     "forward_plus_adjoint": {"value": T * B / (ms_fwd * 1e-3 + s_adj), "unit": "traj*steps/s"},
+                     "gradients_finite": bool(np.all(np.isfinite(gE)) and np.all(np.isfinite(gp)))}
+    out["grad_rel_err_split_f16_vs_fp32"] = float(np.linalg.norm(grads["split_f16"] - grads["fp32"]) /
+                                                  np.linalg.norm(grads["fp32"]))
     ctx.close()
-    return {"workload": "adj_nb2_l36", "N": w.model.N, "B": B, "rank": w.rank, "steps": T,
-            "forward_checkpointed": {"value": T * B / (ms_fwd * 1e-3), "unit": "traj*steps/s", "ms": ms_fwd},
-            "adjoint": {"value": T * B / s_adj, "unit": "traj*steps/s", "ms": s_adj * 1e3},
-            "forward_plus_adjoint": {"value": T * B / (ms_fwd * 1e-3 + s_adj), "unit": "traj*steps/s"},
-            "gradients_finite": bool(np.all(np.isfinite(gE)) and np.all(np.isfinite(gp)))}
+    return out
 
 
 def bench_tc_mid(tg, torch, stream, sh, hbm, steps=20):

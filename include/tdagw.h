@@ -68,8 +68,9 @@ enum {
                                      path, also for B = 1; needs TDAGW_FLAG_RESET)           */
     TDAGW_FLAG_SPLIT_F16 = 64     /* low-rank c64 (any B, needs TDAGW_FLAG_RESET): factors as
                                      split FP16 pairs (hi + lo) on the tensor cores with FP32
-                                     accumulation (three products per term); not combinable
-                                     with TDAGW_FLAG_CHECKPOINT                              */
+                                     accumulation (three products per term); with
+                                     TDAGW_FLAG_CHECKPOINT the checkpointed run and the
+                                     adjoint's segment recomputes run on the tensor cores    */
 };
 
 typedef struct tdagw_ctx tdagw_ctx;
@@ -227,9 +228,11 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * Errors: NO_FACTORS for LOWRANK or CHANNEL without the matching factors; NOT_BUILT before
  * tdagw_build_kernel;
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
- * TDAGW_FLAG_SPLIT_F16 with TDAGW_FLAG_CHECKPOINT, and for CHANNEL with
- * TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16; INVALID_ARG for TDAGW_FLAG_SPLIT_F16 with
- * FULL. */
+ * CHANNEL with TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16; INVALID_ARG for
+ * TDAGW_FLAG_SPLIT_F16 with FULL.
+ * The work split of a tensor-core launch (trajectory groups of the U product, K-ranges of
+ * V^H X) is tuned by timing six steps of each candidate on the first call of at least
+ * eight steps for a batch size and rank, and kept on the context. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
 
@@ -241,7 +244,8 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
  * E(j dt/2) of each trajectory (the amplitude along its direction); dJdparams (B x 4):
  * dJ/d(E0, omega, t0, sigma) for TDAGW_FIELD_GAUSS_COS pulses (zeros otherwise).  The
  * backward sweep recomputes the forward run segment by segment from checkpoints taken
- * every ceil(sqrt(steps)) steps.  Synchronises.  Errors: INVALID_ARG without a
+ * every ceil(sqrt(steps)) steps (on the tensor cores when the forward ran with
+ * TDAGW_FLAG_SPLIT_F16; the reverse stages use the FP32 factors).  Synchronises.  Errors: INVALID_ARG without a
  * checkpointed run; UNSUPPORTED on complex128 contexts; TIMEOUT if a bounded wait gave up. */
 int tdagw_adjoint(tdagw_ctx* ctx, const double* dJdobs, double* dJdE, double* dJdparams);
 

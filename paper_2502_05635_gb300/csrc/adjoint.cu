@@ -349,11 +349,16 @@ void adjoint_batched(Ctx& c, const double* dJdobs, double* dJdE, double* dJdpara
         ck_restore_kernel<<<152 * 4, 256, 0, s>>>(c.ckS.as<float2>() + slot, c.ckC.as<float2>() + slot,
                                                   c.bS.as<float2>(), c.bC.as<float2>(), c.bX.as<float2>(), N * Bp);
         check_launch("ck_restore_kernel");
-        fa.n0 = n0;
-        fa.Tmax = len;
-        TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
-        void* fargs[] = {&fa};
-        TDAGW_CUDA(cudaLaunchCooperativeKernel(ffn, grid, dim3(kBThreads), fargs, smem, s));
+        if (st.tc) {
+            // the forward ran on the tensor cores: recompute the segment there too
+            tc_recompute_segment(c, n0, len, fa.recX, fa.recDS, fa.obs);
+        } else {
+            fa.n0 = n0;
+            fa.Tmax = len;
+            TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+            void* fargs[] = {&fa};
+            TDAGW_CUDA(cudaLaunchCooperativeKernel(ffn, grid, dim3(kBThreads), fargs, smem, s));
+        }
         aa.seg0 = n0;
         aa.seglen = len;
         TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));

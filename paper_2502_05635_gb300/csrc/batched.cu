@@ -680,3 +680,106 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
 }
 
 }  // namespace tdagw
+
+namespace tdagw {
+
+// The backward sweep of the adjoint after a checkpointed split-FP16 (tensor-core) forward
+// run uses the FP32 batched partition: the low-rank plan cached for this batch size and
+// rank, else the first candidate shape (at most kTileB trajectories per block, CTAs <=
+// SMs).  Fills c.adj like a checkpointed FP32 run; the caller adds the tensor-core fields.
+void prepare_adjoint_fp32(Ctx& c, const BatchSetup& bs, const tdagw_field* fields, int B, const int* steps,
+                          double dt, int flags) {
+    const HostModel& h = c.hm;
+    const int64_t N = h.N;
+    const int Bp = bs.Bp;
+    const int r = c.rank, ldu = r + (r & 1);
+    int dev = 0, nsm = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = (size_t)kGemmSmem * sizeof(float2) +
+                        (size_t)(kBThreads / kTileB) * kTileB * 3 * sizeof(double);
+    const void* fn = h.Nb == 2 ? (const void*)batched_kernel<2, false> : (const void*)batched_kernel<4, false>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBThreads, smem));
+    TDAGW_REQUIRE(per_sm >= 1, TDAGW_ERR_UNSUPPORTED, "batched kernel does not fit on this device");
+    const int max_ctas = nsm * per_sm;
+    const uint64_t key = ((uint64_t)TDAGW_LOWRANK << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
+    const int tg_min = (B + kTileB - 1) / kTileB;
+    BatchPlan plan;
+    auto it = c.batch_plans.find(key);
+    if (it != c.batch_plans.end() && it->second.second >= tg_min && it->second.first >= 1 &&
+        it->second.first <= h.Nk && it->second.first * it->second.second <= max_ctas) {
+        plan.Rg = it->second.first;
+        plan.Tg = it->second.second;
+    } else {
+        plan.Tg = tg_min;
+        plan.Rg = std::min(h.Nk, max_ctas / tg_min);
+        TDAGW_REQUIRE(plan.Rg >= 1, TDAGW_ERR_UNSUPPORTED, "too many trajectories for one launch");
+    }
+    BatchArgs a{};
+    a.U = c.U.as<float2>();
+    a.V = c.V.as<float2>();
+    a.S = c.S.as<float>();
+    a.diag = c.diagF.as<float2>();
+    a.kblk = c.kdiag ? c.kblkF.as<float2>() : nullptr;
+    a.K = c.K.as<float2>();
+    a.dx = c.dx.as<float2>();
+    a.dy = c.dy.as<float2>();
+    a.vx = c.vx.as<float2>();
+    a.gap = c.gap.as<float2>();
+    a.X = c.bX.as<float2>();
+    a.Ssum = c.bS.as<float2>();
+    a.Ccomp = c.bC.as<float2>();
+    a.acc = c.bA.as<float2>();
+    a.dS = c.bdS.as<float2>();
+    a.Etab = c.bEtab.as<double>();
+    a.dir = c.bdir.as<float2>();
+    a.act = c.bact.as<int>();
+    a.obs = c.bobs.as<double>();
+    a.N = N;
+    a.ldE = bs.ldE;
+    a.Nk = h.Nk;
+    a.Nb = h.Nb;
+    a.r = r;
+    a.ldu = ldu;
+    a.Bp = Bp;
+    a.B = B;
+    a.mode = TDAGW_LOWRANK;
+    a.kahan = (flags & TDAGW_FLAG_NO_KAHAN) ? 0 : 1;
+    a.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) a.occ[q] = (float)h.occ[q];
+    a.dt = (float)dt;
+    a.wait_ns = 2000000000ull;
+    c.sync.ensure(4 * sizeof(unsigned));
+    a.bar = reinterpret_cast<unsigned long long*>(c.sync.p);
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.Rg = plan.Rg;
+    a.Tg = plan.Tg;
+    a.Tmax = bs.Tmax;
+    c.bP.ensure((size_t)std::max(1, plan.Rg * std::max(r, 1)) * Bp * sizeof(float2));
+    c.bY.ensure((size_t)std::max(r, 1) * Bp * sizeof(float2));
+    c.bred.ensure((size_t)plan.Rg * Bp * 3 * sizeof(double));
+    a.P = c.bP.as<float2>();
+    a.Y = c.bY.as<float2>();
+    a.red = c.bred.as<double>();
+    AdjointState& st = c.adj;
+    st = AdjointState{};
+    st.valid = true;
+    st.B = B;
+    st.Bp = Bp;
+    st.Tmax = bs.Tmax;
+    st.Rg = plan.Rg;
+    st.Tg = plan.Tg;
+    st.mode = TDAGW_LOWRANK;
+    st.dt = dt;
+    st.perm = bs.perm;
+    st.steps.assign(steps, steps + B);
+    st.fields.assign(fields, fields + B);
+    for (tdagw_field& f : st.fields) f.table = nullptr;
+    st.fwd_args.resize(sizeof(BatchArgs));
+    std::memcpy(st.fwd_args.data(), &a, sizeof(BatchArgs));
+    st.fwd_fn = fn;
+}
+
+}  // namespace tdagw

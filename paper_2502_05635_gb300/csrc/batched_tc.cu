@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "batched_common.cuh"
@@ -123,6 +124,14 @@ struct TcArgs {
     int Nk, r, rp, Nt, Mt, nchU, nchV, Bp, B, Tmax, kahan, c1;
     int gc_max;     // phase C trajectory groups at most (1 .. B / 8); 0: fill the CTAs
     int ks_max;     // phase A K-ranges at most; 0: fill the CTAs
+    // adjoint support: global step of this launch's first step, checkpoints of the
+    // compensated state every ck_period steps, per-stage records of (X_s, dSigma_s) for the
+    // steps of this launch ([step * 4 + stage][N][Bp]); null pointers: off
+    int n0, ck_period;
+    float2* ckS;
+    float2* ckC;
+    float2* recX;
+    float2* recDS;
     float occ[4];
     float dt;
     float su, sv;   // power-of-two scales of the U and V tiles
@@ -281,7 +290,7 @@ struct DF3 {
 // thread's running sums of the observables (last stage).
 template <int NB>
 __device__ void stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, float2 dr,
-                            const float2* sDS, int row0, int bl, float& xm, DF3& ob) {
+                            const float2* sDS, int row0, int bl, float& xm, DF3& ob, int64_t rec) {
     constexpr int NB2 = NB * NB;
     const int64_t Bp = a.Bp;
     float2 X[NB2], M[NB2];
@@ -291,6 +300,10 @@ __device__ void stage_kb_tc(const TcArgs& a, int k, int b, int st, float E, floa
         X[g] = __ldcg(a.X + i * Bp + b);
         const float2 d1 = a.dx[i], d2 = a.dy[i];
         const float2 ds = cfma(a.diag[i], X[g], sDS[ds_index(row0 + g, bl)]);
+        if (rec >= 0) {  // stage input and dSigma, for the adjoint's backward sweep
+            a.recX[rec + i * Bp + b] = X[g];
+            a.recDS[rec + i * Bp + b] = ds;
+        }
         M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
     }
     // state loads of RB rows at a time, issued before any store of those rows (all rows
@@ -598,7 +611,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     };
 
     for (int n = 0; n < a.Tmax && ok && (in_sync || producer); ++n) {
-        const int Bact = a.act[n];
+        const int Bact = a.act[a.n0 + n];
         const Groups q = stage_groups(a, Bact);
         for (int st = 0; st < 4 && ok; ++st) {
             const int gs = 4 * n + st;
@@ -608,6 +621,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             TC_TRACE(worker && wt == 0, 0);
             if (blockIdx.x == 0 && worker)
                 for (int b = wt; b < a.Bp; b += kWorkers) xout[b] = 0u;
+            if (st == 0 && a.ckS && worker && (a.n0 + n) % a.ck_period == 0) {
+                // checkpoint of the compensated state at the start of step n0 + n (stable
+                // until the last stage's epilogue of this step, two grid barriers away)
+                const int64_t slot = (int64_t)((a.n0 + n) / a.ck_period) * a.N * a.Bp;
+                const int64_t tot = a.N * Bact;
+                for (int64_t e = (int64_t)blockIdx.x * kWorkers + wt; e < tot; e += (int64_t)gridDim.x * kWorkers) {
+                    const int64_t off = (e / Bact) * a.Bp + e % Bact;
+                    a.ckS[slot + off] = __ldcg(a.Ssum + off);
+                    a.ckC[slot + off] = __ldcg(a.Ccomp + off);
+                }
+            }
 
             // ---------------- A: partials of V^H X ----------------
             const int nA = q.G * a.Mt * q.KS;
@@ -707,7 +731,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 }
                 if (st == 0 && n > 0) {
                     // observables of step n (written by the last stage of step n - 1)
-                    for (int64_t b = gt; b < a.act[n - 1]; b += total) {
+                    for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
                         double s0 = 0, s1 = 0, s2 = 0;
                         for (int t = 0; t < a.Nt; ++t) {
                             const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
@@ -803,10 +827,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         const int kt = min(64 / NB2, a.Nk - kbase);
                         if (kg < kgroups && !*vabort) {
                             const int b = b0 + bl;
-                            const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * n + eoff];
+                            const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
                             const float2 dr = a.dir[b];
+                            const int64_t rec = a.recX ? (int64_t)(4 * n + st) * a.N * a.Bp : -1;
                             for (int kl = kg; kl < kt; kl += kgroups)
-                                stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs);
+                                stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, rec);
                         }
                         workers_sync();  // the staged quarter is consumed before it is rewritten
                     }
@@ -848,7 +873,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     if (worker && ok && a.Tmax > 0) {
         const int n = a.Tmax;
         const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
-        for (int64_t b = gt; b < a.act[n - 1]; b += total) {
+        for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
             double s0 = 0, s1 = 0, s2 = 0;
             for (int t = 0; t < a.Nt; ++t) {
                 const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
@@ -878,6 +903,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tm, kTmemCols);
     }
+}
+
+// max(|Re|, |Im|) of each trajectory's stage input X (N x Bp) as float bits, into xmax
+// (zeroed by the caller): the split-FP16 scale of a launch that starts from a restored state.
+__global__ void xmax_kernel(const float2* __restrict__ X, int64_t N, int Bp, unsigned* __restrict__ xmax) {
+    const int b = blockIdx.y;
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = X[i * Bp + b];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(xmax + b, __float_as_uint(m));
 }
 
 // Per column j: max(|Re|, |Im|) of U and of V, and ||v_j||^2.
@@ -1021,8 +1059,6 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "split-FP16 propagation needs a complex64 context");
     TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
                   "split-FP16 propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
-    TDAGW_REQUIRE(!(flags & TDAGW_FLAG_CHECKPOINT), TDAGW_ERR_UNSUPPORTED,
-                  "checkpoints for the adjoint are kept by the FP32 path only");
     pack_factors_tc(c);
     const HostModel& h = c.hm;
     cudaStream_t s = c.stream;
@@ -1094,6 +1130,17 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.sv = c.tc_sv;
     a.ybound = c.tc_ybound;
     a.wait_ns = 2000000000ull;
+    a.n0 = 0;
+    a.ck_period = 1;
+    const bool ckpt = (flags & TDAGW_FLAG_CHECKPOINT) != 0;
+    int period = 1;
+    if (ckpt) {
+        // compensated state every ceil(sqrt(Tmax)) steps for the adjoint's recomputes
+        period = std::max(1, (int)std::ceil(std::sqrt((double)bs.Tmax)));
+        const int nck = (bs.Tmax + period - 1) / period;
+        c.ckS.ensure((size_t)nck * sbytes);
+        c.ckC.ensure((size_t)nck * sbytes);
+    }
     auto run = [&](int gc_max, int ks_max, int T, bool graph) {
         a.gc_max = gc_max;
         a.ks_max = ks_max;
@@ -1159,10 +1206,56 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
             c.batch_plans[key] = {gc_max, ks_max};
         }
     }
+    c.adj.valid = false;
+    if (ckpt) {
+        a.ckS = c.ckS.as<float2>();
+        a.ckC = c.ckC.as<float2>();
+        a.ck_period = period;
+    }
     run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
     c.persistent_launched = true;
-    c.adj.valid = false;
+    if (ckpt) {
+        // the backward sweep: FP32 partition and arguments; segment recomputes on the
+        // tensor cores from the checkpoints, with this launch's arguments
+        prepare_adjoint_fp32(c, bs, fields, B, steps, dt, flags);
+        AdjointState& st = c.adj;
+        st.period = period;
+        st.tc = true;
+        a.ckS = nullptr;
+        a.ckC = nullptr;
+        st.tc_args.resize(sizeof(TcArgs));
+        std::memcpy(st.tc_args.data(), &a, sizeof(TcArgs));
+        st.tc_fn = fn;
+        st.tc_smem = smem;
+        st.tc_grid = nctas;
+    }
     finish_batch(c, bs, B);
+}
+
+// Segment recompute of the adjoint's backward sweep (see the declaration): the checkpointed
+// launch's arguments with the segment's first step and length, records on, checkpoints off,
+// observables into scratch, the first stage's scales from the restored state, no resets.
+void tc_recompute_segment(Ctx& c, int n0, int len, float2* recX, float2* recDS, double* obs) {
+    AdjointState& st = c.adj;
+    TDAGW_REQUIRE(st.valid && st.tc && st.tc_args.size() == sizeof(TcArgs), TDAGW_ERR_INVALID_ARG,
+                  "no checkpointed tensor-core propagation to recompute");
+    cudaStream_t s = c.stream;
+    TcArgs a;
+    std::memcpy(&a, st.tc_args.data(), sizeof(TcArgs));
+    a.n0 = n0;
+    a.Tmax = len;
+    a.ckS = nullptr;
+    a.ckC = nullptr;
+    a.recX = recX;
+    a.recDS = recDS;
+    a.obs = obs;
+    TDAGW_CUDA(cudaMemsetAsync(a.xmax, 0, 3 * (size_t)a.Bp * sizeof(unsigned), s));
+    xmax_kernel<<<dim3(64, (unsigned)a.Bp), 256, 0, s>>>(a.X, a.N, a.Bp, a.xmax);
+    check_launch("xmax_kernel");
+    TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
+    void* args[] = {&a};
+    TDAGW_CUDA(cudaLaunchCooperativeKernel(st.tc_fn, dim3(st.tc_grid), dim3(kTcThreads), args, st.tc_smem, s));
+    c.persistent_launched = true;
 }
 
 }  // namespace tdagw

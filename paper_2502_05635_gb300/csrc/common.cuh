@@ -147,8 +147,15 @@ struct AdjointState {
     double dt = 0.0;
     std::vector<int> perm, steps;          // sorted -> caller order; caller-order lengths
     std::vector<tdagw_field> fields;       // caller order
-    std::vector<unsigned char> fwd_args;   // argument block of the forward kernel launch
-    const void* fwd_fn = nullptr;          // the forward kernel (for segment recomputes)
+    std::vector<unsigned char> fwd_args;   // argument block of the FP32 batched kernel
+    const void* fwd_fn = nullptr;          // the FP32 forward kernel (for segment recomputes)
+    // split-FP16 forward (tensor cores): its segment recomputes run the tensor-core kernel
+    // (argument block, function, shared memory, CTAs); the backward sweep uses fwd_args
+    bool tc = false;
+    std::vector<unsigned char> tc_args;
+    const void* tc_fn = nullptr;
+    size_t tc_smem = 0;
+    int tc_grid = 0;
 };
 
 
@@ -322,6 +329,13 @@ void finish_batch(Ctx& c, const BatchSetup& bs, int B);
 
 // Backward sweep of the last checkpointed batched propagation (host arrays).
 void adjoint_batched(Ctx& c, const double* dJdobs, double* dJdE, double* dJdparams);
+// After a checkpointed tensor-core forward: the FP32 batched partition, launch arguments
+// and intermediates of the adjoint's backward sweep, recorded in c.adj.
+void prepare_adjoint_fp32(Ctx& c, const BatchSetup& bs, const tdagw_field* fields, int B, const int* steps,
+                          double dt, int flags);
+// Recompute steps [n0, n0 + len) of the last checkpointed tensor-core forward from the
+// restored state (c.bS, c.bC, c.bX), recording every stage's input and dSigma.
+void tc_recompute_segment(Ctx& c, int n0, int len, float2* recX, float2* recDS, double* obs);
 
 // Persistent single-trajectory low-rank propagation (complex64); false if not applicable.
 bool launch_lr_persistent(Ctx& c, int T, double dt, double dirx, double diry, bool kahan,

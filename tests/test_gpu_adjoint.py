@@ -39,9 +39,12 @@ PULSES = [wl.Pulse(E0=0.02, omega=0.15, t0=6.0, sigma=3.0),
           wl.Pulse(E0=0.01, omega=0.13, t0=5.0, sigma=4.0)]
 
 
-@pytest.mark.parametrize("mode", [tg.LOWRANK, tg.FULL])
+@pytest.mark.parametrize("mode,split", [(tg.LOWRANK, False), (tg.FULL, False), (tg.LOWRANK, True)],
+                         ids=["lowrank", "full", "lowrank-split-f16"])
 @pytest.mark.parametrize("L,nc,rank", [(4, 1, 9), (3, 2, 20)])
-def test_adjoint_matches_oracle(mode, L, nc, rank):
+def test_adjoint_matches_oracle(mode, split, L, nc, rank):
+    """split: the checkpointed forward and the segment recomputes on the tensor cores
+    (split-FP16 factors), the reverse stages with the FP32 factors."""
     p, mdl, K, d, U, S, V = _case(L, nc, rank)
     if mode == tg.LOWRANK:
         apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
@@ -52,14 +55,14 @@ def test_adjoint_matches_oracle(mode, L, nc, rank):
     ctx = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
     tg.tdagw_set_factors(ctx.h, U, S, V, d)
     tg.tdagw_propagate(ctx.h, [tg.make_field(q) for q in PULSES], steps, dt, mode,
-                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
+                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT | (tg.FLAG_SPLIT_F16 if split else 0))
     got_obs = tg.tdagw_observables(ctx.h, B=3)
     dJ = np.zeros((61, 3, 3))
     refs = []
     for b, (q, T) in enumerate(zip(PULSES, steps)):
         s = op.half_step_samples(q, dt, T)
         obs, _ = op.rk4(mdl, apply, s, dt, T, direction=(q.dir_x, q.dir_y))
-        assert op.rel_l2(got_obs[:T + 1, b, 0], obs[:, 0]) < 1e-5
+        assert op.rel_l2(got_obs[:T + 1, b, 0], obs[:, 0]) < (1e-4 if split else 1e-5)
         _, dJdP = oa.spectral_objective(obs[:, 0], dt, q.omega)
         dJ[:T + 1, b, 0] = dJdP
         gE = oa.adjoint(mdl, apply, applyH, s, dt, T, (q.dir_x, q.dir_y), dJdP)
@@ -135,10 +138,12 @@ def test_adjoint_all_observables(mode):
         assert e < 1e-4, (b, e)
 
 
-def test_adjoint_full_size_vs_oracle():
+@pytest.mark.parametrize("split", [False, True], ids=["fp32", "split-f16"])
+def test_adjoint_full_size_vs_oracle(split):
     """The differentiation workload's size (two-band 36 x 36, N = 5184, rank 512, B = 32) with
     pulses that act inside a 60-step window: field-sample and pulse-parameter gradients of
-    two trajectories against the FP64 oracle adjoint (seeded factors on both sides)."""
+    two trajectories against the FP64 oracle adjoint (seeded factors on both sides); split:
+    the checkpointed forward and its recomputes on the tensor cores."""
     w = wl.adj_nb2_l36()
     mdl = om.Model(w.model)
     U, S, V, d = wl.random_factors(mdl.N, w.rank, seed=29)
@@ -150,7 +155,7 @@ def test_adjoint_full_size_vs_oracle():
               for _ in range(w.B)]
     T, dt = 60, w.dt
     tg.tdagw_propagate(ctx.h, [tg.make_field(q) for q in pulses], [T] * w.B, dt, tg.LOWRANK,
-                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT)
+                       tg.FLAG_RESET | tg.FLAG_CHECKPOINT | (tg.FLAG_SPLIT_F16 if split else 0))
     apply = lambda v: olr.apply_lowrank(d, U, S, V, v)
     applyH = lambda v: np.conj(d) * v + V @ (S * (U.conj().T @ v))
     dJ = np.zeros((T + 1, w.B, 3))

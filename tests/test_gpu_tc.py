@@ -134,9 +134,6 @@ def test_split_f16_errors():
     ctx = _ctx(p, U, S, V, d)
     q = wl.Pulse()
     with pytest.raises(tg.TdagwError) as e:
-        tg.tdagw_propagate(ctx.h, [tg.make_field(q)], [5], 0.2, tg.LOWRANK, SPLIT | tg.FLAG_CHECKPOINT)
-    assert e.value.code == tg.ERR_UNSUPPORTED
-    with pytest.raises(tg.TdagwError) as e:
         tg.tdagw_propagate(ctx.h, [tg.make_field(q)], [5], 0.2, tg.FULL, SPLIT)
     assert e.value.code == tg.ERR_INVALID_ARG
     with pytest.raises(tg.TdagwError) as e:
