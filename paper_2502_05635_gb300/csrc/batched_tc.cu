@@ -259,26 +259,8 @@ __device__ __forceinline__ void mma_chunk(uint32_t d, uint32_t a_tm, uint32_t f_
     }
 }
 
-// Observable sums in double-float: (hi, lo) pairs of FP32 updated with error-free
-// products (FMA) and sums (TwoSum), the compensated dot product of Ogita, Rump and Oishi
-// (2005).  FP64 arithmetic is slow on this GPU; the per-thread sums of the epilogue stay
-// within a few units of 2^-44 of the FP64 sums and are widened once per thread.
-struct DF {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        float e;
-        hi = two_sum(hi, v, e);
-        lo += e;
-    }
-    __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = a * b;
-        const float ep = fmaf(a, b, -p);
-        float e;
-        hi = two_sum(hi, p, e);
-        lo += e + ep;
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
+// Observable sums of the epilogue in double-float (DF, FP32 pipes; FP64 arithmetic is
+// slow on this GPU), widened to FP64 once per thread.
 struct DF3 {
     DF p, j, o;
 };

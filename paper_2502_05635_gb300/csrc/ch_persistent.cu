@@ -441,40 +441,47 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                 // ---- commutator + RK4 stage update for k in [ka, kb)
                 const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
                 const float E = (float)a.sp.Etab[2 * (int64_t)n + eoff];
-                double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+                ObsDF ob;  // double-float sums (FP64 is slow on this GPU)
                 for (int64_t b = ra; b < rb; b += kCons) {
                     const int64_t i = b + tid;
-                    const Obs3 ob = stage_element<float, NB>(a.sp, i, i < rb, lane, st, E);
-                    o0 += ob.p;
-                    o1 += ob.j;
-                    o2 += ob.o;
+                    stage_element<float, NB>(a.sp, i, i < rb, lane, st, E, ob);
                 }
                 if (st == 3) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        o0 += __shfl_xor_sync(0xffffffffu, o0, o);
-                        o1 += __shfl_xor_sync(0xffffffffu, o1, o);
-                        o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+                        ob.p = ob.p.shfl_xor_sum(o);
+                        ob.j = ob.j.shfl_xor_sum(o);
+                        ob.o = ob.o.shfl_xor_sum(o);
                     }
+                    float* wf = reinterpret_cast<float*>(wred);  // 6 floats per warp
                     if (lane == 0) {
-                        wred[3 * warp] = o0;
-                        wred[3 * warp + 1] = o1;
-                        wred[3 * warp + 2] = o2;
+                        wf[6 * warp] = ob.p.hi;
+                        wf[6 * warp + 1] = ob.p.lo;
+                        wf[6 * warp + 2] = ob.j.hi;
+                        wf[6 * warp + 3] = ob.j.lo;
+                        wf[6 * warp + 4] = ob.o.hi;
+                        wf[6 * warp + 5] = ob.o.lo;
                     }
                     named_sync<kCons>();
                     if (tid == 0) {
-                        double s0 = 0, s1 = 0, s2 = 0;
+                        ObsDF s;
                         for (int w = 0; w < kCW; ++w) {
-                            s0 += wred[3 * w];
-                            s1 += wred[3 * w + 1];
-                            s2 += wred[3 * w + 2];
+                            DF t;
+                            t.hi = wf[6 * w];
+                            t.lo = wf[6 * w + 1];
+                            s.p.add(t);
+                            t.hi = wf[6 * w + 2];
+                            t.lo = wf[6 * w + 3];
+                            s.j.add(t);
+                            t.hi = wf[6 * w + 4];
+                            t.lo = wf[6 * w + 5];
+                            s.o.add(t);
                         }
-                        a.sp.red[3 * cta] = s0;
-                        a.sp.red[3 * cta + 1] = s1;
-                        a.sp.red[3 * cta + 2] = s2;
+                        a.sp.red[3 * cta] = s.p.value();
+                        a.sp.red[3 * cta + 1] = s.j.value();
+                        a.sp.red[3 * cta + 2] = s.o.value();
                     }
                 }
-                named_sync<kCons>();
                 CH_TRACE(7);
                 for (int e = tid; e < nk * P; e += kCons) xs[e] = __ldcg(a.sp.X + ra + e);
                 named_sync<kCons>();

@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<R> p) {
     const int64_t nstep = *p.step;
     const int eoff = p.stage == 0 ? 0 : (p.stage == 3 ? 2 : 1);
     const R E = (R)p.Etab[2 * nstep + eoff];
-    const Obs3 ob = stage_element<R, NB>(p, i, i < p.N, threadIdx.x & 31, p.stage, E);
+    Obs3 ob{0.0, 0.0, 0.0};
+    stage_element<R, NB>(p, i, i < p.N, threadIdx.x & 31, p.stage, E, ob);
     if (p.stage == 3)
         reduce_observables(ob.p, ob.j, ob.o, p.red, p.counter, p.obs + (nstep + 1) * 3,
                            1.0 / (double)p.Nk, p.step, nstep + 1);

@@ -3,6 +3,8 @@
 // classical RK4 combination, the compensated state update, and the observables.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tdagw {
@@ -64,16 +66,60 @@ struct Obs3 {
     double p, j, o;
 };
 
+// Double-float sums (hi, lo) in FP32: error-free products (FMA) and sums (TwoSum), the
+// compensated dot product of Ogita, Rump and Oishi (2005).  FP64 arithmetic is slow on this
+// GPU; double-float keeps a few units of 2^-44 of the FP64 result and runs on FP32 pipes.
+struct DF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = hi + v, bp = s - hi;
+        lo += (hi - (s - bp)) + (v - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);
+        add(p);
+        lo += ep;
+    }
+    __device__ __forceinline__ void add(const DF& o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ DF shfl_xor_sum(int m) const {
+        DF r = *this;
+        DF t;
+        t.hi = __shfl_xor_sync(0xffffffffu, hi, m);
+        t.lo = __shfl_xor_sync(0xffffffffu, lo, m);
+        r.add(t);
+        return r;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+// observable sums of P_x, J_x and the occupation: FP64 (Obs3) or double-float (ObsDF)
+struct ObsDF {
+    DF p, j, o;
+};
+__device__ __forceinline__ void obs_add_prod(Obs3& ob, int w, double a, double b) {
+    (w == 0 ? ob.p : ob.j) += a * b;
+}
+__device__ __forceinline__ void obs_add_prod(ObsDF& ob, int w, float a, float b) {
+    (w == 0 ? ob.p : ob.j).add_prod(a, b);
+}
+__device__ __forceinline__ void obs_add_occ(Obs3& ob, double v) { ob.o += v; }
+__device__ __forceinline__ void obs_add_occ(ObsDF& ob, float v) { ob.o.add(v); }
+
 // Element i = (k Nb + n) Nb + m of stage `stage` at field amplitude E.  All NB^2 lanes of a
 // k block must call this together (act = false for padding lanes).  Computes
 //   k_s = -i [diag(eps) + E d + dSigma, rho0 + X_s]_nm
 //       = -i ( (eps_n - eps_m) X_nm + M_nm (f_m - f_n) + sum_l (M_nl X_lm - X_nl M_lm) ),
 // M = E d + dSigma, updates the RK4 accumulator and writes the next stage input; on the
 // last stage advances the state (TwoSum compensation) and returns the element's share of
-// Re Tr(rho d^x), Re Tr(rho v^x) and the first-conduction-band occupation.
-template <typename R, int NB>
-__device__ __forceinline__ Obs3 stage_element(const StageParams<R>& p, int64_t i, bool act,
-                                              int lane, int stage, R E) {
+// Re Tr(rho d^x), Re Tr(rho v^x) and the first-conduction-band occupation, added to ob
+// (FP64 sums: Obs3, double-float sums of FP32 values: ObsDF).
+template <typename R, int NB, typename OB>
+__device__ __forceinline__ void stage_element(const StageParams<R>& p, int64_t i, bool act,
+                                              int lane, int stage, R E, OB& ob) {
     using C = cplx_t<R>;
     constexpr int NB2 = NB * NB;
     const int base = lane - (lane % NB2);
@@ -96,7 +142,6 @@ __device__ __forceinline__ Obs3 stage_element(const StageParams<R>& p, int64_t i
         comm = cfma(Mnl, Xlm, comm);
         comm = csub(comm, cmul(Xnl, Mlm));
     }
-    Obs3 ob{0.0, 0.0, 0.0};
     if (act) {
         const C h0 = gap_times(p.gap[i], X);
         const C s = cadd(h0, comm);
@@ -127,13 +172,15 @@ __device__ __forceinline__ Obs3 stage_element(const StageParams<R>& p, int64_t i
             // Re(rho_nm conj(d_nm)) summed over n, m is Re Tr(rho d) for Hermitian d
             const C rho = (n == m) ? cadd(Xn, mk(p.occ[n], (R)0)) : Xn;
             const C vxv = p.vx[i];
-            ob.p = (double)rho.x * (double)dxv.x + (double)rho.y * (double)dxv.y;
-            ob.j = (double)rho.x * (double)vxv.x + (double)rho.y * (double)vxv.y;
-            ob.o = (n == m && n == p.c1) ? (double)rho.x : 0.0;
+            using A = typename std::conditional<std::is_same<OB, Obs3>::value, double, float>::type;
+            obs_add_prod(ob, 0, (A)rho.x, (A)dxv.x);
+            obs_add_prod(ob, 0, (A)rho.y, (A)dxv.y);
+            obs_add_prod(ob, 1, (A)rho.x, (A)vxv.x);
+            obs_add_prod(ob, 1, (A)rho.y, (A)vxv.y);
+            if (n == m && n == p.c1) obs_add_occ(ob, (A)rho.x);
         }
         p.Xnext[i] = Xn;
     }
-    return ob;
 }
 
 }  // namespace tdagw
