@@ -62,7 +62,15 @@ __device__ double vjp_local(const AdjArgs& a, int k, int b, int slot, float E, f
     constexpr int NB2 = NB * NB;
     const BatchArgs& m = a.b;
     const int64_t Bp = m.Bp;
-    float2 G[NB2], X[NB2], M[NB2], D[NB2];
+    float2 G[NB2], X[NB2], M[NB2];
+    // D = dir . d of the k-point, recomputed where it is used from the (L1-resident)
+    // dipoles instead of held in registers
+    const float2* dxk = m.dx + (int64_t)k * NB2;
+    const float2* dyk = m.dy + (int64_t)k * NB2;
+    auto Dq = [&](int q) {
+        const float2 d1 = __ldg(dxk + q), d2 = __ldg(dyk + q);
+        return make_float2(dr.x * d1.x + dr.y * d2.x, dr.x * d1.y + dr.y * d2.y);
+    };
 #pragma unroll
     for (int q = 0; q < NB2; ++q) {
         const int64_t i = (int64_t)k * NB2 + q;
@@ -73,9 +81,8 @@ __device__ double vjp_local(const AdjArgs& a, int k, int b, int slot, float E, f
         G[q] = g;
         X[q] = __ldcg(a.recX + (int64_t)slot * m.N * Bp + e);
         const float2 ds = __ldcg(a.recDS + (int64_t)slot * m.N * Bp + e);
-        const float2 d1 = m.dx[i], d2 = m.dy[i];
-        D[q] = make_float2(dr.x * d1.x + dr.y * d2.x, dr.x * d1.y + dr.y * d2.y);
-        M[q] = make_float2(ds.x + E * D[q].x, ds.y + E * D[q].y);
+        const float2 D = Dq(q);
+        M[q] = make_float2(ds.x + E * D.x, ds.y + E * D.y);
     }
     double ebar = 0.0;
 #pragma unroll
@@ -89,15 +96,15 @@ __device__ double vjp_local(const AdjArgs& a, int k, int b, int slot, float E, f
             // (g rho^+ - rho^+ g)_nm = g_nm (f_m - f_n) + sum_l (g_nl conj(X_ml) - conj(X_ln) g_lm)
             float2 t2 = cscale(G[q], m.occ[mm] - m.occ[n]);
             // [D, rho]_nm = D_nm (f_m - f_n) + sum_l (D_nl X_lm - X_nl D_lm)
-            float2 t3 = cscale(D[q], m.occ[mm] - m.occ[n]);
+            float2 t3 = cscale(Dq(q), m.occ[mm] - m.occ[n]);
 #pragma unroll
             for (int l = 0; l < NB; ++l) {
                 t1 = cadd(t1, cmul(cconj(M[l * NB + n]), G[l * NB + mm]));
                 t1 = csub(t1, cmul(G[n * NB + l], cconj(M[mm * NB + l])));
                 t2 = cadd(t2, cmul(G[n * NB + l], cconj(X[mm * NB + l])));
                 t2 = csub(t2, cmul(cconj(X[l * NB + n]), G[l * NB + mm]));
-                t3 = cadd(t3, cmul(D[n * NB + l], X[l * NB + mm]));
-                t3 = csub(t3, cmul(X[n * NB + l], D[l * NB + mm]));
+                t3 = cadd(t3, cmul(Dq(n * NB + l), X[l * NB + mm]));
+                t3 = csub(t3, cmul(X[n * NB + l], Dq(l * NB + mm)));
             }
             const int64_t e = i * Bp + b;
             a.c1[e] = mul_i(t1);

@@ -34,9 +34,10 @@ using namespace batched;
 namespace {
 
 // Commutator + RK4 stage update of one (k, trajectory) block, all NB^2 elements in
-// registers (the same arithmetic as stage_element, Eq. tdagw).  Returns the observables.
+// registers (the same arithmetic as stage_element, Eq. tdagw).  The observables (last
+// stage) are added to ob in double-float (FP64 arithmetic is slow on this GPU).
 template <int NB>
-__device__ Obs3 stage_kb(const BatchArgs& a, int k, int b, int st, float E, float2 dr) {
+__device__ void stage_kb(const BatchArgs& a, int k, int b, int st, float E, float2 dr, ObsDF& ob) {
     constexpr int NB2 = NB * NB;
     const int64_t Bp = a.Bp;
     float2 X[NB2], M[NB2];
@@ -48,7 +49,6 @@ __device__ Obs3 stage_kb(const BatchArgs& a, int k, int b, int st, float E, floa
         const float2 ds = __ldcg(a.dS + i * Bp + b);
         M[g] = make_float2(ds.x + E * (dr.x * d1.x + dr.y * d2.x), ds.y + E * (dr.x * d1.y + dr.y * d2.y));
     }
-    Obs3 ob{0.0, 0.0, 0.0};
 #pragma unroll
     for (int n = 0; n < NB; ++n)
 #pragma unroll
@@ -90,13 +90,14 @@ __device__ Obs3 stage_kb(const BatchArgs& a, int k, int b, int st, float E, floa
                 Xn = cadd(ns, nc);
                 const float2 rho = (n == m) ? make_float2(Xn.x + a.occ[n], Xn.y) : Xn;
                 const float2 d1 = a.dx[i], v1 = a.vx[i];
-                ob.p += (double)rho.x * (double)d1.x + (double)rho.y * (double)d1.y;
-                ob.j += (double)rho.x * (double)v1.x + (double)rho.y * (double)v1.y;
-                if (n == m && n == a.c1) ob.o += (double)rho.x;
+                ob.p.add_prod(rho.x, d1.x);
+                ob.p.add_prod(rho.y, d1.y);
+                ob.j.add_prod(rho.x, v1.x);
+                ob.j.add_prod(rho.y, v1.y);
+                if (n == m && n == a.c1) ob.o.add(rho.x);
             }
             a.X[e] = Xn;
         }
-    return ob;
 }
 
 // CH: the channel-wise mode (a separate instantiation, so the other modes' code is unchanged)
@@ -254,22 +255,17 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
             const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
             {
                 const int bl = tid % kTileB, kg = tid / kTileB;  // 16 k-groups x 32 trajectories
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                ObsDF ob;
                 if (bl < nb) {
                     const int b = b0 + bl;
                     const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
                     const float2 dr = a.dir[b];
-                    for (int k = ka + kg; k < kb; k += kBThreads / kTileB) {
-                        const Obs3 ob = stage_kb<NB>(a, k, b, st, E, dr);
-                        s0 += ob.p;
-                        s1 += ob.j;
-                        s2 += ob.o;
-                    }
+                    for (int k = ka + kg; k < kb; k += kBThreads / kTileB) stage_kb<NB>(a, k, b, st, E, dr, ob);
                 }
                 if (st == 3) {
-                    sred[(kg * kTileB + bl) * 3] = s0;
-                    sred[(kg * kTileB + bl) * 3 + 1] = s1;
-                    sred[(kg * kTileB + bl) * 3 + 2] = s2;
+                    sred[(kg * kTileB + bl) * 3] = ob.p.value();
+                    sred[(kg * kTileB + bl) * 3 + 1] = ob.j.value();
+                    sred[(kg * kTileB + bl) * 3 + 2] = ob.o.value();
                 }
             }
             __syncthreads();
