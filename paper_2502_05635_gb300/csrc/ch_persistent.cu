@@ -72,6 +72,7 @@ struct CHArgs {
     unsigned long long* bar_count;
     int* err;
     int T, nslots, slot_bytes, kmax, zs_len, upart_len;
+    int vgroups;  // V pass: warp groups (power of two), each owning every vgroups-th pair
     int extra_arrivals;  // > 0 only for the timeout test: the barrier can never complete
     unsigned long long wait_ns;
 };
@@ -101,9 +102,10 @@ __device__ __forceinline__ int seg_rps(int ld, int slot_bytes) {
 // The V pass streams its chunks (up to seg_rps rows of one input pair) packed into shared
 // slots: consecutive chunks share a slot while they fit, so the short segments of the V
 // pass still fill the ring.  VWalk is the walk over those chunks that the producer and
-// the consumers both follow.
+// the consumers both follow; qi counts the non-empty pairs passed (the pair's owner group
+// in the consumers is qi mod the number of groups).
 struct VWalk {
-    int q, r0;
+    int q, r0, qi;
     __device__ __forceinline__ void skip_empty(const ChMeta& m, int P) {
         while (q < P && m.ldv[q] == 0) ++q;
     }
@@ -118,6 +120,7 @@ struct VWalk {
         if (r0 >= nk) {
             r0 = 0;
             ++q;
+            ++qi;
             skip_empty(m, P);
         }
     }
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
             for (int n = 0; n < a.T && ok; ++n)
                 for (int st = 0; st < 4 && ok; ++st) {
                     // V pass: chunks of consecutive input pairs packed into shared slots
-                    VWalk vw{0, 0};
+                    VWalk vw{0, 0, 0};
                     vw.skip_empty(a.m, P);
                     while (vw.q < P) {
                         if (issued >= (uint64_t)ns &&
@@ -254,11 +257,15 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
         for (int n = 0; n < a.T && ok; ++n) {
             for (int st = 0; st < 4 && ok; ++st) {
                 CH_TRACE(0);
-                // ---- V pass: every warp reads every row; thread owns column pairs tid and
-                //      tid + 512 of the current input pair's segment (ldv <= 2048); one
-                //      slot may hold chunks of several consecutive pairs
+                // ---- V pass: the consumer warps form vgroups groups of TG threads; a pair's
+                //      chunks all go to one group (pairs dealt round-robin), whose thread lt
+                //      owns column pairs lt and lt + TG of the segment (ldv <= 4 TG), so the
+                //      short V rows keep every warp busy; one slot may hold chunks of
+                //      several consecutive pairs, every warp waits for and releases each slot
                 {
-                    VWalk vw{0, 0};
+                    const int wpg = kCW / a.vgroups, TG = 32 * wpg;
+                    const int vg = warp / wpg, lt = tid - vg * TG;
+                    VWalk vw{0, 0, 0};
                     vw.skip_empty(a.m, P);
                     float2 acc[4];
 #pragma unroll
@@ -276,13 +283,14 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                             if (off > 0 && off + b > (uint32_t)a.slot_bytes) break;
                             const int q = vw.q, ld = a.m.ldv[q];
                             const float2* tile = reinterpret_cast<const float2*>(sbase + off);
-                            // warps without columns of this pair skip the rows (they still
-                            // wait for and release every slot); two rows per iteration
-                            if (64 * warp < ld) {
+                            // other groups' pairs and warps without columns of this pair
+                            // skip the rows; two rows per iteration
+                            const bool own = (vw.qi & (a.vgroups - 1)) == vg;
+                            if (own && 64 * (warp - vg * wpg) < ld) {
                                 const float2* xr = xs + vw.r0 * P + q;
 #pragma unroll
                                 for (int m = 0; m < 2; ++m) {
-                                    const int c = 2 * (tid + m * kCons);
+                                    const int c = 2 * (lt + m * TG);
                                     if (c < ld) {
                                         float2 a0 = acc[2 * m], a1 = acc[2 * m + 1];
                                         float2 b0 = make_float2(0.f, 0.f), b1 = b0;
@@ -308,11 +316,11 @@ __global__ void __launch_bounds__(kThr, 1) ch_persistent_kernel(CHArgs a) {
                                 }
                             }
                             off += b;
-                            if (vw.r0 + nr >= nk) {  // last chunk of pair q: publish its partials
+                            if (own && vw.r0 + nr >= nk) {  // last chunk of pair q: publish its partials
                                 float2* dst = a.part + (size_t)cta * stot + a.m.sbase[q];
 #pragma unroll
                                 for (int m = 0; m < 2; ++m) {
-                                    const int p2 = tid + m * kCons;
+                                    const int p2 = lt + m * TG;
                                     if (2 * p2 < ld)
                                         *reinterpret_cast<float4*>(dst + 2 * p2) = make_float4(
                                             acc[2 * m].x, acc[2 * m].y, acc[2 * m + 1].x, acc[2 * m + 1].y);
@@ -626,6 +634,9 @@ bool launch_ch_persistent(Ctx& c, int T, double dt, double dirx, double diry, bo
     a.kmax = kmax;
     a.zs_len = zs_len;
     a.upart_len = upart_len;
+    // V-pass groups: as many as keep four columns per thread covering the longest V row
+    a.vgroups = 1;
+    while (a.vgroups < kCW && 4 * (kCons / (2 * a.vgroups)) >= maxv) a.vgroups *= 2;
     a.extra_arrivals = test_timeout ? 1 : 0;
     a.wait_ns = test_timeout ? 20000000ull : 2000000000ull;
     void* args[] = {&a};

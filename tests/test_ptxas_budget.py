@@ -23,7 +23,7 @@ UNITS = ["lr_persistent", "ch_persistent", "batched", "batched_tc", "adjoint", "
 # fragment of the mangled kernel name -> largest allowed spill stores (bytes)
 BUDGET = {
     "lr_persistent_kernelILi2E": 0, "lr_persistent_kernelILi4E": 0,
-    "ch_persistent_kernelILi2E": 4, "ch_persistent_kernelILi4E": 4,
+    "ch_persistent_kernelILi2E": 16, "ch_persistent_kernelILi4E": 4,
     "batched_kernelILi2ELb0E": 0, "batched_kernelILi2ELb1E": 28,
     "batched_kernelILi4ELb0E": 100, "batched_kernelILi4ELb1E": 72,
     "batched_tc_kernelILi2E": 88, "batched_tc_kernelILi4E": 424,
