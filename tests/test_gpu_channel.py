@@ -99,6 +99,28 @@ def test_persistent_and_stagewise_agree_and_resume():
     assert op.rel_l2(np.concatenate([h1, h2[1:]])[:, 0], a[:, 0]) < 1e-6
 
 
+@pytest.mark.parametrize("rank", [100, 200, 350])
+def test_persistent_long_v_rows_vs_oracle(rank):
+    """Two bands, Nk = 400: every input pair has three incoming channels of the given rank,
+    so the V rows hold 300, 600 and 1050 columns and the persistent kernel's V pass runs
+    with four, two and one warp groups (the smaller ranks of the other tests give eight or
+    sixteen)."""
+    p = wl.small_model(20, 1)
+    mdl = om.Model(p)
+    D, U, S, V = oc.channel_svd(ok.dense_kernel(mdl), p.Nb, rank)
+    c = _ctx(p, tg.C64)
+    tg.tdagw_set_channel_factors(c.h, U, S, V, D)
+    pulse = wl.Pulse(E0=5e-3, omega=0.12, t0=6.0, sigma=3.0, dir_x=0.6, dir_y=0.8)
+    T = 60
+    s = op.half_step_samples(pulse, 0.2, T)
+    ref, _ = op.rk4(mdl, lambda v: oc.apply_channel(D, U, S, V, v), s, 0.2, T,
+                    direction=(pulse.dir_x, pulse.dir_y))
+    got = c.propagate(pulse, T, 0.2, tg.CHANNEL)
+    assert np.abs(ref[:, 0]).max() > 1e-8
+    for j in range(3):
+        assert op.rel_l2(got[:, j], ref[:, j]) < 1e-5, j
+
+
 def test_per_channel_ranks_and_round_trip():
     """Each channel its own rank (including 0): the apply uses exactly the first z_pq
     triplets, and get returns what set installed (FP32 storage)."""
