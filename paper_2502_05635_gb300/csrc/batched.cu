@@ -211,22 +211,28 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                         if (nb > 0) kblock_term<NB, false>(a.kblk, a.X, a.dS, a.Bp, ra, nrows, b0, nb);
                     }
                 } else {
-                    // D (channel-wise), per output pair p, rows k P + p of this row group: the
-                    // dense diagonal channel with x_p over all k, then each off-diagonal
-                    // channel's U^pq with its block of S o Y added
+                    // D (channel-wise) by p-major shares: row group rg takes the rows
+                    // [u0, u1) of the order p Nk + k (one or two output pairs), so each pair
+                    // is one product over many k-points instead of the group's few: the dense
+                    // diagonal channel with x_p over all k, then each off-diagonal channel's
+                    // U^pq with its block of S o Y added.  The rows reach their k-point's
+                    // owner through global memory across the barrier below.
                     const int64_t ldo = (int64_t)NB2 * a.Bp;
+                    const int u0 = (int)((int64_t)rg * a.N / a.Rg), u1 = (int)((int64_t)(rg + 1) * a.N / a.Rg);
                     if (nb > 0)
-                        for (int p = 0; p < NB2; ++p) {
+                        for (int p = u0 / a.Nk; p < NB2 && p * a.Nk < u1; ++p) {
+                            const int k0 = max(u0 - p * a.Nk, 0), k1 = min(u1 - p * a.Nk, a.Nk);
+                            if (k1 <= k0) continue;
                             const int ldw = a.chm->ldw[p], nl = a.chm->nlr[p];
-                            const float2* Ub = a.Uch + a.chm->ubase[p] + (int64_t)ka * ldw;
-                            float2* o = a.dS + (ra + p) * a.Bp + b0;
-                            block_gemm<false>(Ub + nl, ldw, kb - ka, a.Nk, a.X + (int64_t)p * a.Bp + b0, ldo, nb, o,
+                            const float2* Ub = a.Uch + a.chm->ubase[p] + (int64_t)k0 * ldw;
+                            float2* o = a.dS + ((int64_t)k0 * NB2 + p) * a.Bp + b0;
+                            block_gemm<false>(Ub + nl, ldw, k1 - k0, a.Nk, a.X + (int64_t)p * a.Bp + b0, ldo, nb, o,
                                               ldo, false, nullptr, nullptr, sA, sB);
                             for (int q = 0; q < NB2; ++q) {
                                 const int z = a.choff[2 * NB2 * NB2 + p * NB2 + q];
                                 if (q == p || z == 0) continue;
                                 const int64_t yrow = a.chm->sbase[q] + a.choff[NB2 * NB2 + q * NB2 + p];
-                                block_gemm<false, true>(Ub + a.choff[p * NB2 + q], ldw, kb - ka, z,
+                                block_gemm<false, true>(Ub + a.choff[p * NB2 + q], ldw, k1 - k0, z,
                                                         a.Y + yrow * a.Bp + b0, a.Bp, nb, o, ldo, false, nullptr,
                                                         nullptr, sA, sB);
                             }

@@ -117,6 +117,20 @@ def mos2size_nb4_l36(steps: int = 10000) -> Workload:
     return Workload("mos2size_nb4_l36", mp, 0.2, (steps,), (Pulse(),), rank=1024)
 
 
+def early_pulses(B: int, seed: int = TRAJ_SEED):
+    """Seeded Gaussian*cos pulses that peak within the first 12 time units (t0 = 6,
+    sigma 1.5-3), amplitudes 1e-4 .. 1e-2 (log-uniform), frequencies 0.06-0.16 and field
+    directions spread over the plane: short runs that still see the whole pulse, for
+    comparing kernel forms over a few dozen steps."""
+    rng = np.random.default_rng(seed + 7)
+    E0 = 10.0 ** rng.uniform(-4.0, -2.0, size=B)
+    omega = rng.uniform(0.06, 0.16, size=B)
+    sigma = rng.uniform(1.5, 3.0, size=B)
+    ang = rng.uniform(0.0, np.pi, size=B)
+    return tuple(Pulse(E0=float(E0[b]), omega=float(omega[b]), t0=6.0, sigma=float(sigma[b]),
+                       dir_x=float(np.cos(ang[b])), dir_y=float(np.sin(ang[b])), kind=0) for b in range(B))
+
+
 def mos2size_channel(steps: int = 10000) -> Workload:
     """The mos2-size model with the channel-wise compression: dense diagonal channels and
     every off-diagonal channel truncated to 5 % of Nk (65 of 1296 singular values), the
