@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
             }
         }
         for (int st = 0; st < 4 && ok; ++st) {
-            const bool need_x_barrier = (a.mode == TDAGW_FULL) ? !(n == 0 && st == 0)
-                                                               : (st == 0 && Bact != prev_act && n > 0);
+            // the dense product and the channel-wise row shares read every CTA's rows of X
+            const bool need_x_barrier = (a.mode == TDAGW_FULL || CH) ? !(n == 0 && st == 0)
+                                                                     : (st == 0 && Bact != prev_act && n > 0);
             if (need_x_barrier && !(ok = bgrid_sync(a, gen, &abort_s))) break;
             if (st == 0 && n > 0 && rg == 0 && a.mode == TDAGW_FULL) {
                 // observables of step n-1 for this group's trajectories at that step
@@ -164,11 +165,16 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                                          a.P + (int64_t)rg * a.r * a.Bp + b0, a.Bp, false, nullptr, nullptr,
                                          sA, sB);
                 } else if (nb > 0) {
-                    for (int q = 0; q < NB2; ++q) {
+                    // channel-wise: q-major row shares as in D below (rows q Nk + k' of the
+                    // V segments, one or two input pairs per row group); the group writes the
+                    // partials of those pairs' columns only
+                    const int u0 = (int)((int64_t)rg * a.N / a.Rg), u1 = (int)((int64_t)(rg + 1) * a.N / a.Rg);
+                    for (int q = u0 / a.Nk; q < NB2 && q * a.Nk < u1; ++q) {
                         const int ldv = a.chm->ldv[q];
-                        if (ldv == 0) continue;
-                        block_gemm<true>(a.Vch + a.chm->vbase[q] + (int64_t)ka * ldv, ldv, ldv, kb - ka,
-                                         a.X + (ra + q) * a.Bp + b0, (int64_t)NB2 * a.Bp, nb,
+                        const int k0 = max(u0 - q * a.Nk, 0), k1 = min(u1 - q * a.Nk, a.Nk);
+                        if (ldv == 0 || k1 <= k0) continue;
+                        block_gemm<true>(a.Vch + a.chm->vbase[q] + (int64_t)k0 * ldv, ldv, ldv, k1 - k0,
+                                         a.X + ((int64_t)k0 * NB2 + q) * a.Bp + b0, (int64_t)NB2 * a.Bp, nb,
                                          a.P + ((int64_t)rg * a.r + a.chm->sbase[q]) * a.Bp + b0, a.Bp, false,
                                          nullptr, nullptr, sA, sB);
                     }
@@ -190,11 +196,20 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(BatchArgs a) {
                         o[2] = s2 / a.Nk;
                     }
                 }
-                // C: Y[j][b] = S_j sum over row groups, j in this CTA's slice
+                // C: Y[j][b] = S_j sum over row groups, j in this CTA's slice (channel-wise:
+                // over the row groups whose share touches the input pair of column j)
                 for (int e = tid; e < (jr1 - jr0) * nb; e += kBThreads) {
                     const int j = jr0 + e / nb, b = b0 + e % nb;
+                    int g0 = 0, g1 = a.Rg - 1;
+                    if constexpr (CH) {
+                        int q = 0;
+                        while (q + 1 < NB2 && a.chm->sbase[q + 1] <= j) ++q;
+                        const int64_t NR = a.N, RG = a.Rg, lo = (int64_t)q * a.Nk;
+                        g0 = max(0, (int)(((lo + 1) * RG + NR - 1) / NR) - 1);
+                        g1 = min(a.Rg - 1, (int)(((lo + a.Nk) * RG + NR - 1) / NR) - 1);
+                    }
                     float2 s = make_float2(0.f, 0.f);
-                    for (int g2 = 0; g2 < a.Rg; ++g2)
+                    for (int g2 = g0; g2 <= g1; ++g2)
                         s = cadd(s, __ldcg(a.P + ((int64_t)g2 * a.r + j) * a.Bp + b));
                     a.Y[(int64_t)j * a.Bp + b] = cscale(s, a.S[j]);
                 }

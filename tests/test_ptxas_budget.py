@@ -24,7 +24,7 @@ UNITS = ["lr_persistent", "ch_persistent", "batched", "batched_tc", "adjoint", "
 BUDGET = {
     "lr_persistent_kernelILi2E": 0, "lr_persistent_kernelILi4E": 0,
     "ch_persistent_kernelILi2E": 16, "ch_persistent_kernelILi4E": 4,
-    "batched_kernelILi2ELb0E": 0, "batched_kernelILi2ELb1E": 28,
+    "batched_kernelILi2ELb0E": 0, "batched_kernelILi2ELb1E": 52,
     "batched_kernelILi4ELb0E": 100, "batched_kernelILi4ELb1E": 72,
     "batched_tc_kernelILi2E": 88, "batched_tc_kernelILi4E": 424,
     "adjoint_kernelILi2E": 0, "adjoint_kernelILi4E": 780,
