@@ -541,16 +541,29 @@ def bench_channel_batched(tg, torch, stream, sh, B=64, steps=60):
     T = [steps] * B
     ms_ch = _time_propagate(tg, torch, stream, ctx, fields, T, w.dt, tg.CHANNEL, tg.FLAG_RESET)
     ch = tg.tdagw_observables(ctx.h, B=B)
+    ms_sp = _time_propagate(tg, torch, stream, ctx, fields, T, w.dt, tg.CHANNEL,
+                            tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    sp = tg.tdagw_observables(ctx.h, B=B)
     ms_full = _time_propagate(tg, torch, stream, ctx, fields, T, w.dt, tg.FULL, tg.FLAG_RESET)
     full = tg.tdagw_observables(ctx.h, B=B)
     ctx.close()
-    err = _rel_errs(ch, full, T)
+    err, err_sp = _rel_errs(ch, full, T), _rel_errs(sp, full, T)
+    # factor bytes streamed per stage by the tensor-core path: split tiles of the V and U
+    # segments (8 bytes per complex entry, as complex64)
+    ranks = 2 * 65 * 48
+    per_stage = 8 * (w.model.Nk * ranks + w.model.N * w.model.Nk)
     return {"workload": "mos2size_nb4_l36, channel-wise rank 65, early pulses", "N": w.model.N, "B": B,
             "steps": steps,
-            "channel_wise": {"value": B * steps / (ms_ch * 1e-3), "unit": "traj*steps/s", "ms": ms_ch},
+            "channel_wise": {"value": B * steps / (ms_ch * 1e-3), "unit": "traj*steps/s", "ms": ms_ch,
+                             "speedup_vs_full": ms_full / ms_ch, "p_rel_err_vs_full_gpu": err},
+            "channel_wise_split_f16": {"value": B * steps / (ms_sp * 1e-3), "unit": "traj*steps/s", "ms": ms_sp,
+                                       "speedup_vs_full": ms_full / ms_sp, "p_rel_err_vs_full_gpu": err_sp,
+                                       "factor_gbs": 4 * steps * per_stage / (ms_sp * 1e-3) / 1e9,
+                                       "p_rel_err_vs_fp32_channel": _rel_errs(sp, ch, T)},
             "full": {"value": B * steps / (ms_full * 1e-3), "unit": "traj*steps/s", "ms": ms_full},
-            "speedup_vs_full": ms_full / ms_ch, "p_rel_err_vs_full_gpu": err,
-            "within_1e-4": err["max"] <= 1e-4}
+            "speedup_vs_full": ms_full / min(ms_ch, ms_sp),
+            "p_rel_err_vs_full_gpu": err_sp if ms_sp < ms_ch else err,
+            "within_1e-4": max(err["max"], err_sp["max"]) <= 1e-4}
 
 
 def bench_angle_hhg(tg, torch, stream, sh, steps=2000, nfreq=512):
@@ -806,8 +819,13 @@ def run_ours(a):
             "within_1e-4_of_full_kernel": ch["p_rel_err_vs_full_gpu"] <= 1e-4,
             "speedup_vs_full": ch["value"] / (nf / (ms_full * 1e-3))}
         line["channel_wise_batched"] = bench_channel_batched(tg, torch, stream, sh)
+        cb = line["channel_wise_batched"]
         line["accuracy_qualified"]["batched"] = {
-            k: line["channel_wise_batched"][k] for k in ("B", "p_rel_err_vs_full_gpu", "within_1e-4", "speedup_vs_full")}
+            "form": "channel-wise, split-FP16 segment tiles on the tensor cores",
+            "value": cb["channel_wise_split_f16"]["value"], "unit": "traj*steps/s", "B": cb["B"],
+            "p_rel_err_vs_full_gpu": cb["channel_wise_split_f16"]["p_rel_err_vs_full_gpu"],
+            "within_1e-4": cb["channel_wise_split_f16"]["p_rel_err_vs_full_gpu"]["max"] <= 1e-4,
+            "speedup_vs_full": cb["channel_wise_split_f16"]["speedup_vs_full"]}
         line["channel_wise_sweep"] = bench_channel_sweep(tg, torch, stream, sh)
         line["angle_hhg"] = bench_angle_hhg(tg, torch, stream, sh)
         line["kdiag_split"] = bench_kblock_split(tg, torch, stream, sh, hbm)

@@ -66,7 +66,8 @@ enum {
                                      with TDAGW_ERR_TIMEOUT at the next synchronising call   */
     TDAGW_FLAG_CHECKPOINT = 32,   /* keep checkpoints for tdagw_adjoint (runs the batched
                                      path, also for B = 1; needs TDAGW_FLAG_RESET)           */
-    TDAGW_FLAG_SPLIT_F16 = 64     /* low-rank c64 (any B, needs TDAGW_FLAG_RESET): factors as
+    TDAGW_FLAG_SPLIT_F16 = 64     /* low-rank or channel-wise c64 (any B, needs
+                                     TDAGW_FLAG_RESET): factors as
                                      split FP16 pairs (hi + lo) on the tensor cores with FP32
                                      accumulation (three products per term); with
                                      TDAGW_FLAG_CHECKPOINT the checkpointed run and the
@@ -221,15 +222,17 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * With TDAGW_FLAG_SPLIT_F16 (LOWRANK, complex64, any B) the two products of Eq. svd_acc run
  * on the tensor cores with the factors split into FP16 hi + lo pairs and FP32
  * accumulation; P(t) then agrees with the FP32 path to about 1e-6 relative.
- * Mode CHANNEL (channel-wise factors) runs without TDAGW_FLAG_CHECKPOINT and
- * TDAGW_FLAG_SPLIT_F16; for B = 1 one persistent launch for complex64 when every input
+ * Mode CHANNEL (channel-wise factors, Eq. svd-channel-wise) runs without
+ * TDAGW_FLAG_CHECKPOINT; for B = 1 one persistent launch for complex64 when every input
  * pair's channels hold at most 2048 columns in all (else stage-wise kernels), for B > 1 the
- * batched FP32 launch.
+ * batched FP32 launch; with TDAGW_FLAG_SPLIT_F16 (complex64, any B, TDAGW_FLAG_RESET) the
+ * V segments and the U segments (low-rank columns and the dense diagonal channel of each
+ * output pair) run on the tensor cores as split FP16 tiles, made at the first such call
+ * after new channel factors.
  * Errors: NO_FACTORS for LOWRANK or CHANNEL without the matching factors; NOT_BUILT before
  * tdagw_build_kernel;
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
- * CHANNEL with TDAGW_FLAG_CHECKPOINT or TDAGW_FLAG_SPLIT_F16; INVALID_ARG for
- * TDAGW_FLAG_SPLIT_F16 with FULL.
+ * CHANNEL with TDAGW_FLAG_CHECKPOINT; INVALID_ARG for TDAGW_FLAG_SPLIT_F16 with FULL.
  * The work split of a tensor-core launch (trajectory groups of the U product, K-ranges of
  * V^H X) is tuned by timing six steps of each candidate on the first call of at least
  * eight steps for a batch size and rank, and kept on the context. */

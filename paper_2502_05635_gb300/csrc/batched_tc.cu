@@ -137,6 +137,20 @@ struct TcArgs {
     float su, sv;   // power-of-two scales of the U and V tiles
     float ybound;   // max|S| max_j ||v_j|| sqrt(2N): |(S o Y)_jb| <= ybound max|X_b|
     unsigned long long wait_ns;
+    int Nred;       // row tiles of the per-tile observable sums (red)
+    // Channel-wise mode (Eq. svd-channel-wise; a separate instantiation).  Phase A runs
+    // over the V segments (segment q: its Mt_q 256-column tiles, mtq0[q] the first of them
+    // in the padded column order, K over the Nk k-points in nchV chunks), phase C over the
+    // U segments (segment p = [U^pq of the channels out of p | K^pp]: NtK 256-row tiles of
+    // k-points, nchw[p] chunks of its columns), with the operand z_p = [S o y of those
+    // channels (padded rows gpad) ; x_p]; phase C writes dSigma to dS and a fourth phase
+    // runs the commutator + RK4 epilogue over the nte 256-row tiles of all N rows.
+    const int* gpad;
+    float2* dS;
+    int npair, NtK, nte;
+    float zbound;   // |z_p| <= zbound max|X_b|
+    long long tvoff[kMaxPairs], tuoff[kMaxPairs];
+    int mtq0[kMaxPairs + 1], ldvq[kMaxPairs], sbq[kMaxPairs], nlrq[kMaxPairs], gbq[kMaxPairs], nchw[kMaxPairs];
 };
 
 // Optional phase timestamps (build with -DTDAGW_TRACE): one thread per CTA records
@@ -390,7 +404,14 @@ __device__ __forceinline__ ItemA item_a(const TcArgs& a, const Groups& q, int it
     return it;
 }
 
-template <int NB>
+// phase A tile index mt (padded column order) -> V segment q and its tile m (channel-wise)
+__device__ __forceinline__ void seg_of_mt(const TcArgs& a, int mt, int& q, int& m) {
+    q = 0;
+    while (q + 1 < a.npair && a.mtq0[q + 1] <= mt) ++q;
+    m = mt - a.mtq0[q];
+}
+
+template <int NB, bool CHT>
 __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* ring = smem;
@@ -579,6 +600,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         }
         cp_async_commit();
     };
+    // the same with the rows given by rowp(i): the row's base pointer, or null for a zero
+    // row (channel-wise mode: gathered rows of X and of S o Y)
+    auto src_issue_rows = [&](auto rowp, int c, int c_end, bool live, int b0, int k) {
+        if (c < c_end) {
+            float2* dst = srcbuf + (k % kSrcSlots) * 1024 + (warp - 2) * 128 + (obl & 15) * 8 + 4 * ocomp;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = (int64_t)c * 16 + 8 * wh + 4 * ocomp + u;
+                const float2* row = live ? rowp(i) : nullptr;
+                cp_async8(dst + u, row ? (const void*)(row + b0 + obl) : (const void*)a.X, row ? 8u : 0u);
+            }
+        }
+        cp_async_commit();
+    };
     // workers: wait for the source values of the chunk in slot k (kSrcAhead - 1 newer
     // groups may stay in flight) and read the pair's 8 values, scaled
     auto src_read = [&](float2 (&v)[8], int k, float sc) {
@@ -620,10 +655,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             if (producer) {
                 for (int item = blockIdx.x; item < nA; item += gridDim.x) {
                     const ItemA it = item_a(a, q, item);
-                    for (int c = it.c0; c < it.c1; ++c, ++gch) {
-                        TC_W_BEGIN(p0);
-                        issue(a.tV + ((int64_t)it.m * a.nchV + c) * kTile);
-                        TC_W_END(p0, 4);
+                    if constexpr (CHT) {
+                        int qs, m;
+                        seg_of_mt(a, it.m, qs, m);
+                        const unsigned char* tv = a.tV + (a.tvoff[qs] + (int64_t)m * a.nchV) * kTile;
+                        for (int c = it.c0; c < it.c1; ++c, ++gch) {
+                            TC_W_BEGIN(p0);
+                            issue(tv + (int64_t)c * kTile);
+                            TC_W_END(p0, 4);
+                        }
+                    } else {
+                        for (int c = it.c0; c < it.c1; ++c, ++gch) {
+                            TC_W_BEGIN(p0);
+                            issue(a.tV + ((int64_t)it.m * a.nchV + c) * kTile);
+                            TC_W_END(p0, 4);
+                        }
                     }
                 }
             } else if (mma) {
@@ -647,12 +693,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     const float sx = ssc[obl];
                     const bool live = obl < nbg;
                     // X values of the warp's columns of chunk c, kSrcAhead chunks ahead
-                    for (int c = it.c0; c < it.c0 + kSrcAhead; ++c) src_issue(a.X, c, it.c1, live, b0, c - it.c0);
-                    for (int c = it.c0; c < it.c1; ++c) {
-                        float2 v[8];
-                        src_read(v, c - it.c0, sx);
-                        build_block(v, true);
-                        src_issue(a.X, c + kSrcAhead, it.c1, live, b0, c + kSrcAhead - it.c0);
+                    if constexpr (CHT) {
+                        // rows k' P + q of X for the V segment q of this item
+                        int qs, m;
+                        seg_of_mt(a, it.m, qs, m);
+                        const int P = a.npair, Nk = a.Nk;
+                        auto rowx = [&](int64_t i) -> const float2* {
+                            return i < Nk ? a.X + (i * P + qs) * a.Bp : nullptr;
+                        };
+                        for (int c = it.c0; c < it.c0 + kSrcAhead; ++c)
+                            src_issue_rows(rowx, c, it.c1, live, b0, c - it.c0);
+                        for (int c = it.c0; c < it.c1; ++c) {
+                            float2 v[8];
+                            src_read(v, c - it.c0, sx);
+                            build_block(v, true);
+                            src_issue_rows(rowx, c + kSrcAhead, it.c1, live, b0, c + kSrcAhead - it.c0);
+                        }
+                    } else {
+                        for (int c = it.c0; c < it.c0 + kSrcAhead; ++c) src_issue(a.X, c, it.c1, live, b0, c - it.c0);
+                        for (int c = it.c0; c < it.c1; ++c) {
+                            float2 v[8];
+                            src_read(v, c - it.c0, sx);
+                            build_block(v, true);
+                            src_issue(a.X, c + kSrcAhead, it.c1, live, b0, c + kSrcAhead - it.c0);
+                        }
                     }
                     cp_async_wait<0>();
                     // accumulator -> raw partials P[ks][j][b]: lanes 2 bl and 2 bl + 1 hold the
@@ -684,38 +748,81 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             // ---------------- B: S o sum of the partials, scaled for FP16 ----------------
             if (worker) {
                 const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
-                const int64_t tot_el = (int64_t)a.rp * Bact;
-                for (int64_t e = gt; e < tot_el; e += total) {
-                    const int j = (int)(e / Bact), b = (int)(e % Bact);
-                    float2 v = make_float2(0.f, 0.f);
-                    if (j < a.r) {
-                        // eight independent partial sums (loads in flight), fixed order
-                        const float2* pp = a.P + (int64_t)j * a.Bp + b;
-                        const int64_t pstride = (int64_t)a.rp * a.Bp;
-                        float2 s8[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
-                        int k2 = 0;
-                        for (; k2 + 8 <= q.KS; k2 += 8) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                if constexpr (CHT) {
+                    const int64_t tot_el = (int64_t)a.rp * Bact;
+                    for (int64_t e = gt; e < tot_el; e += total) {
+                        const int j = (int)(e / Bact), b = (int)(e % Bact);
+                        float2 v = make_float2(0.f, 0.f);
+                        // column of S (channel-wise: the padded column j of V segment qs)
+                        int sj = j < a.r ? j : -1;
+                        if constexpr (CHT) {
+                            int qs, m;
+                            seg_of_mt(a, j / kRows, qs, m);
+                            const int jj = m * kRows + j % kRows;
+                            sj = jj < a.ldvq[qs] ? a.sbq[qs] + jj : -1;
                         }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
-                        const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
-                                              cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
-                        const float mx = __uint_as_float(__ldcg(xin + b));
-                        const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
-                        v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
+                        if (sj >= 0) {
+                            // eight independent partial sums (loads in flight), fixed order
+                            const float2* pp = a.P + (int64_t)j * a.Bp + b;
+                            const int64_t pstride = (int64_t)a.rp * a.Bp;
+                            float2 s8[8];
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
+                            int k2 = 0;
+                            for (; k2 + 8 <= q.KS; k2 += 8) {
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                            }
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                            const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
+                                                  cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
+                            const float mx = __uint_as_float(__ldcg(xin + b));
+                            if constexpr (CHT) {
+                                // unscaled: the U-pass operand mixes S o y and x, scaled together
+                                v = cscale(s, a.S[sj] * (1.f / (a.sv * pow2_scale(mx))));
+                            } else {
+                                const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
+                                v = cscale(s, a.S[sj] * (sy / (a.sv * sx)));
+                            }
+                        }
+                        a.Ys[(int64_t)j * a.Bp + b] = v;
                     }
-                    a.Ys[(int64_t)j * a.Bp + b] = v;
+                } else {
+                    const int64_t tot_el = (int64_t)a.rp * Bact;
+                    for (int64_t e = gt; e < tot_el; e += total) {
+                        const int j = (int)(e / Bact), b = (int)(e % Bact);
+                        float2 v = make_float2(0.f, 0.f);
+                        if (j < a.r) {
+                            // eight independent partial sums (loads in flight), fixed order
+                            const float2* pp = a.P + (int64_t)j * a.Bp + b;
+                            const int64_t pstride = (int64_t)a.rp * a.Bp;
+                            float2 s8[8];
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
+                            int k2 = 0;
+                            for (; k2 + 8 <= q.KS; k2 += 8) {
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                            }
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
+                            const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
+                                                  cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
+                            const float mx = __uint_as_float(__ldcg(xin + b));
+                            const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
+                            v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
+                        }
+                        a.Ys[(int64_t)j * a.Bp + b] = v;
+                    }
                 }
                 if (st == 0 && n > 0) {
                     // observables of step n (written by the last stage of step n - 1)
                     for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
                         double s0 = 0, s1 = 0, s2 = 0;
-                        for (int t = 0; t < a.Nt; ++t) {
+                        for (int t = 0; t < a.Nred; ++t) {
                             const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                             s0 += __ldcg(rr);
                             s1 += __ldcg(rr + 1);
@@ -734,114 +841,253 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 
             // ---------------- C: dSigma = U (S o Y) + K^diag o X, commutator, RK4 ----------------
             const int eoff = st == 0 ? 0 : (st == 3 ? 2 : 1);
-            const int nC = a.Nt * q.GC;
-            if (producer) {
-                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                    const int t = item % a.Nt;
-                    for (int c = 0; c < a.nchU; ++c, ++gch) {
-                        TC_W_BEGIN(p1);
-                        issue(a.tU + ((int64_t)t * a.nchU + c) * kTile);
-                        TC_W_END(p1, 4);
-                    }
-                }
-                TC_TRACE(true, 8);
-            } else if (mma) {
-                const uint32_t idesc = tc::idesc_f16(128, kRows);
-                for (int item = blockIdx.x; item < nC && !*vabort; item += gridDim.x) {
-                    wait_acc_free();
-                    for (int c = 0; c < a.nchU && !*vabort; ++c) mma_step(idesc, c == 0);
-                    tc::mma_commit(accf);
-                    ++acnt;
-                }
-                TC_TRACE(true, 7);
-            } else if (worker) {
-                for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                    const int t = item % a.Nt, g = item / a.Nt;
-                    int b0, b1;
-                    group_range(Bact, q.GC, g, b0, b1);
-                    const int nbg = b1 - b0;
-                    workers_sync();  // the previous item's readers of ssc, smx, sred are done
-                    if (wt < kGroup) {
-                        if (wt < nbg) {
-                            const float mx = __uint_as_float(__ldcg(xin + b0 + wt));
-                            ssc[wt] = 1.f / (a.su * pow2_scale(a.ybound * mx));
+            if constexpr (!CHT) {
+                const int nC = a.Nt * q.GC;
+                if (producer) {
+                    for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                        const int t = item % a.Nt;
+                        for (int c = 0; c < a.nchU; ++c, ++gch) {
+                            TC_W_BEGIN(p1);
+                            issue(a.tU + ((int64_t)t * a.nchU + c) * kTile);
+                            TC_W_END(p1, 4);
                         }
-                        smx[wt] = 0u;
                     }
-                    workers_sync();
-                    const bool live = obl < nbg;
-                    // S o Y values of the warp's columns of chunk c, kSrcAhead chunks ahead
-                    for (int c = 0; c < kSrcAhead; ++c) src_issue(a.Ys, c, a.nchU, live, b0, c);
-                    for (int c = 0; c < a.nchU; ++c) {
-                        float2 v[8];
-                        src_read(v, c, 1.f);
-                        build_block(v, false);
-                        src_issue(a.Ys, c + kSrcAhead, a.nchU, live, b0, c + kSrcAhead);
+                    TC_TRACE(true, 8);
+                } else if (mma) {
+                    const uint32_t idesc = tc::idesc_f16(128, kRows);
+                    for (int item = blockIdx.x; item < nC && !*vabort; item += gridDim.x) {
+                        wait_acc_free();
+                        for (int c = 0; c < a.nchU && !*vabort; ++c) mma_step(idesc, c == 0);
+                        tc::mma_commit(accf);
+                        ++acnt;
                     }
-                    cp_async_wait<0>();
-                    if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
-                    tc::fence_after_sync();
-                    const int kgroups = kWorkers / nbg;
-                    const int bl = wt % nbg, kg = wt / nbg;
-                    DF3 obs;
-                    float xm = 0.f;
-                    for (int qq = 0; qq < kRows / 64; ++qq) {
-                        // accumulator columns 64 qq .. + 63 (the warp's 32 of them) -> staged
-                        // quarter, unscaled; lanes 2 bl and 2 bl + 1 hold re and im
-                        if (!warp_abort()) {
-#pragma unroll
-                            for (int u = 0; u < 2; ++u) {
-                                float v[16];
-                                const int col = 64 * qq + 32 * wh + 16 * u;
-                                tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
-                                const float sc = live ? ssc[obl] : 0.f;
-#pragma unroll
-                                for (int e = 0; e < 16; ++e) {
-                                    const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
-                                    if (!ocomp && live)
-                                        sDS[ds_index(32 * wh + 16 * u + e, obl)] = make_float2(v[e] * sc, im * sc);
+                    TC_TRACE(true, 7);
+                } else if (worker) {
+                    for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                        const int t = item % a.Nt, g = item / a.Nt;
+                        int b0, b1;
+                        group_range(Bact, q.GC, g, b0, b1);
+                        const int nbg = b1 - b0;
+                        workers_sync();  // the previous item's readers of ssc, smx, sred are done
+                        if (wt < kGroup) {
+                            if (wt < nbg) {
+                                const float mx = __uint_as_float(__ldcg(xin + b0 + wt));
+                                ssc[wt] = 1.f / (a.su * pow2_scale(a.ybound * mx));
+                            }
+                            smx[wt] = 0u;
+                        }
+                        workers_sync();
+                        const bool live = obl < nbg;
+                        // S o Y values of the warp's columns of chunk c, kSrcAhead chunks ahead
+                        for (int c = 0; c < kSrcAhead; ++c) src_issue(a.Ys, c, a.nchU, live, b0, c);
+                        for (int c = 0; c < a.nchU; ++c) {
+                            float2 v[8];
+                            src_read(v, c, 1.f);
+                            build_block(v, false);
+                            src_issue(a.Ys, c + kSrcAhead, a.nchU, live, b0, c + kSrcAhead);
+                        }
+                        cp_async_wait<0>();
+                        if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
+                        tc::fence_after_sync();
+                        const int kgroups = kWorkers / nbg;
+                        const int bl = wt % nbg, kg = wt / nbg;
+                        DF3 obs;
+                        float xm = 0.f;
+                        for (int qq = 0; qq < kRows / 64; ++qq) {
+                            // accumulator columns 64 qq .. + 63 (the warp's 32 of them) -> staged
+                            // quarter, unscaled; lanes 2 bl and 2 bl + 1 hold re and im
+                            if (!warp_abort()) {
+    #pragma unroll
+                                for (int u = 0; u < 2; ++u) {
+                                    float v[16];
+                                    const int col = 64 * qq + 32 * wh + 16 * u;
+                                    tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
+                                    const float sc = live ? ssc[obl] : 0.f;
+    #pragma unroll
+                                    for (int e = 0; e < 16; ++e) {
+                                        const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
+                                        if (!ocomp && live)
+                                            sDS[ds_index(32 * wh + 16 * u + e, obl)] = make_float2(v[e] * sc, im * sc);
+                                    }
                                 }
+                            }
+                            workers_sync();
+                            // commutator + RK4 for the k-blocks of these 64 rows
+                            const int kbase = (t * kRows + 64 * qq) / NB2;
+                            const int kt = min(64 / NB2, a.Nk - kbase);
+                            if (kg < kgroups && !*vabort) {
+                                const int b = b0 + bl;
+                                const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
+                                const float2 dr = a.dir[b];
+                                const int64_t rec = a.recX ? (int64_t)(4 * n + st) * a.N * a.Bp : -1;
+                                for (int kl = kg; kl < kt; kl += kgroups)
+                                    stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, rec);
+                            }
+                            workers_sync();  // the staged quarter is consumed before it is rewritten
+                        }
+                        tc::fence_before_sync();
+                        mbar_arrive(acce);
+                        ++acnt;
+                        if (kg < kgroups) {
+                            atomicMax(smx + bl, __float_as_uint(xm));
+                            if (st == 3) {
+                                sred[(kg * nbg + bl) * 3] = obs.p.value();
+                                sred[(kg * nbg + bl) * 3 + 1] = obs.j.value();
+                                sred[(kg * nbg + bl) * 3 + 2] = obs.o.value();
                             }
                         }
                         workers_sync();
-                        // commutator + RK4 for the k-blocks of these 64 rows
-                        const int kbase = (t * kRows + 64 * qq) / NB2;
-                        const int kt = min(64 / NB2, a.Nk - kbase);
-                        if (kg < kgroups && !*vabort) {
-                            const int b = b0 + bl;
-                            const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
-                            const float2 dr = a.dir[b];
-                            const int64_t rec = a.recX ? (int64_t)(4 * n + st) * a.N * a.Bp : -1;
-                            for (int kl = kg; kl < kt; kl += kgroups)
-                                stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, rec);
-                        }
-                        workers_sync();  // the staged quarter is consumed before it is rewritten
-                    }
-                    tc::fence_before_sync();
-                    mbar_arrive(acce);
-                    ++acnt;
-                    if (kg < kgroups) {
-                        atomicMax(smx + bl, __float_as_uint(xm));
-                        if (st == 3) {
-                            sred[(kg * nbg + bl) * 3] = obs.p.value();
-                            sred[(kg * nbg + bl) * 3 + 1] = obs.j.value();
-                            sred[(kg * nbg + bl) * 3 + 2] = obs.o.value();
-                        }
-                    }
-                    workers_sync();
-                    if (wt < nbg && !*vabort) {
-                        atomicMax(xout + b0 + wt, smx[wt]);
-                        if (st == 3) {
-                            double r0 = 0.0, r1 = 0.0, r2 = 0.0;
-                            for (int k2 = 0; k2 < kgroups; ++k2) {
-                                r0 += sred[(k2 * nbg + wt) * 3];
-                                r1 += sred[(k2 * nbg + wt) * 3 + 1];
-                                r2 += sred[(k2 * nbg + wt) * 3 + 2];
+                        if (wt < nbg && !*vabort) {
+                            atomicMax(xout + b0 + wt, smx[wt]);
+                            if (st == 3) {
+                                double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+                                for (int k2 = 0; k2 < kgroups; ++k2) {
+                                    r0 += sred[(k2 * nbg + wt) * 3];
+                                    r1 += sred[(k2 * nbg + wt) * 3 + 1];
+                                    r2 += sred[(k2 * nbg + wt) * 3 + 2];
+                                }
+                                double* rr = a.red + ((int64_t)t * a.Bp + b0 + wt) * 3;
+                                rr[0] = r0;
+                                rr[1] = r1;
+                                rr[2] = r2;
                             }
-                            double* rr = a.red + ((int64_t)t * a.Bp + b0 + wt) * 3;
-                            rr[0] = r0;
-                            rr[1] = r1;
-                            rr[2] = r2;
+                        }
+                    }
+                }
+            } else {
+                // ---- C (channel-wise): dSigma rows k P + p of U segment p's row tile t ----
+                const int nC = a.Nt * q.GC;  // a.Nt: P NtK segment tiles
+                if (producer) {
+                    for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                        const int si = item % a.Nt, p = si / a.NtK, t = si % a.NtK;
+                        const unsigned char* tu = a.tU + (a.tuoff[p] + (int64_t)t * a.nchw[p]) * kTile;
+                        for (int c = 0; c < a.nchw[p]; ++c, ++gch) {
+                            TC_W_BEGIN(p1);
+                            issue(tu + (int64_t)c * kTile);
+                            TC_W_END(p1, 4);
+                        }
+                    }
+                    TC_TRACE(true, 8);
+                } else if (mma) {
+                    const uint32_t idesc = tc::idesc_f16(128, kRows);
+                    for (int item = blockIdx.x; item < nC && !*vabort; item += gridDim.x) {
+                        const int p = (item % a.Nt) / a.NtK;
+                        wait_acc_free();
+                        for (int c = 0; c < a.nchw[p] && !*vabort; ++c) mma_step(idesc, c == 0);
+                        tc::mma_commit(accf);
+                        ++acnt;
+                    }
+                    TC_TRACE(true, 7);
+                } else if (worker) {
+                    for (int item = blockIdx.x; item < nC; item += gridDim.x) {
+                        const int si = item % a.Nt, g = item / a.Nt, p = si / a.NtK, t = si % a.NtK;
+                        int b0, b1;
+                        group_range(Bact, q.GC, g, b0, b1);
+                        const int nbg = b1 - b0;
+                        workers_sync();  // the previous item's readers of ssc are done
+                        if (wt < kGroup && wt < nbg) ssc[wt] = pow2_scale(a.zbound * __uint_as_float(__ldcg(xin + b0 + wt)));
+                        workers_sync();
+                        const bool live = obl < nbg;
+                        const float sz = live ? ssc[obl] : 0.f;
+                        // operand z_p: the S o y rows of the channels out of p, then x_p
+                        const int nl = a.nlrq[p], P = a.npair, Nk = a.Nk;
+                        const int* gp = a.gpad + a.gbq[p];
+                        auto rowz = [&](int64_t j) -> const float2* {
+                            if (j < nl) return a.Ys + (int64_t)__ldg(gp + j) * a.Bp;
+                            return j < nl + Nk ? a.X + ((j - nl) * P + p) * a.Bp : nullptr;
+                        };
+                        const int nch = a.nchw[p];
+                        for (int c = 0; c < kSrcAhead; ++c) src_issue_rows(rowz, c, nch, live, b0, c);
+                        for (int c = 0; c < nch; ++c) {
+                            float2 v[8];
+                            src_read(v, c, sz);
+                            build_block(v, false);
+                            src_issue_rows(rowz, c + kSrcAhead, nch, live, b0, c + kSrcAhead);
+                        }
+                        cp_async_wait<0>();
+                        // accumulator -> dSigma rows k P + p (unscaled); lanes 2 bl and 2 bl + 1
+                        // hold the real and imaginary parts
+                        if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
+                        tc::fence_after_sync();
+                        if (!warp_abort()) {
+                            const float osc = live ? 1.f / (a.su * sz) : 0.f;
+                            for (int u = 0; u < 8; ++u) {
+                                float v[16];
+                                const int col = 128 * wh + 16 * u;
+                                tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) {
+                                    const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
+                                    const int k = t * kRows + col + e;
+                                    if (!ocomp && live && k < Nk)
+                                        a.dS[((int64_t)k * P + p) * a.Bp + b0 + obl] = make_float2(v[e] * osc, im * osc);
+                                }
+                            }
+                        }
+                        tc::fence_before_sync();
+                        mbar_arrive(acce);
+                        ++acnt;
+                    }
+                }
+                // every dSigma row is written before the epilogue reads it
+                if (in_sync && !(ok = tc_grid_sync(a, gen, &abort_s))) break;
+                // ---- E (channel-wise): commutator + RK4 for the 256-row tiles of all N rows,
+                //      dSigma staged from global memory by 64-row quarters ----
+                if (worker) {
+                    const int nE = a.nte * q.GC;
+                    for (int item = blockIdx.x; item < nE; item += gridDim.x) {
+                        const int te = item % a.nte, g = item / a.nte;
+                        int b0, b1;
+                        group_range(Bact, q.GC, g, b0, b1);
+                        const int nbg = b1 - b0;
+                        workers_sync();  // the previous item's readers of smx and sred are done
+                        if (wt < kGroup) smx[wt] = 0u;
+                        workers_sync();
+                        const int kgroups = kWorkers / nbg;
+                        const int bl = wt % nbg, kg = wt / nbg;
+                        DF3 obs;
+                        float xm = 0.f;
+                        for (int qq = 0; qq < kRows / 64; ++qq) {
+                            const int64_t r0 = (int64_t)te * kRows + 64 * qq;
+                            for (int e = wt; e < 64 * nbg; e += kWorkers) {
+                                const int rr = e / nbg, bb = e % nbg;
+                                if (r0 + rr < a.N) sDS[ds_index(rr, bb)] = __ldcg(a.dS + (r0 + rr) * a.Bp + b0 + bb);
+                            }
+                            workers_sync();
+                            const int kbase = (int)(r0 / NB2);
+                            const int kt = min(64 / NB2, a.Nk - kbase);
+                            if (kg < kgroups && !*vabort) {
+                                const int b = b0 + bl;
+                                const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
+                                const float2 dr = a.dir[b];
+                                for (int kl = kg; kl < kt; kl += kgroups)
+                                    stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, -1);
+                            }
+                            workers_sync();  // the staged quarter is consumed before it is rewritten
+                        }
+                        if (kg < kgroups) {
+                            atomicMax(smx + bl, __float_as_uint(xm));
+                            if (st == 3) {
+                                sred[(kg * nbg + bl) * 3] = obs.p.value();
+                                sred[(kg * nbg + bl) * 3 + 1] = obs.j.value();
+                                sred[(kg * nbg + bl) * 3 + 2] = obs.o.value();
+                            }
+                        }
+                        workers_sync();
+                        if (wt < nbg && !*vabort) {
+                            atomicMax(xout + b0 + wt, smx[wt]);
+                            if (st == 3) {
+                                double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+                                for (int k2 = 0; k2 < kgroups; ++k2) {
+                                    r0 += sred[(k2 * nbg + wt) * 3];
+                                    r1 += sred[(k2 * nbg + wt) * 3 + 1];
+                                    r2 += sred[(k2 * nbg + wt) * 3 + 2];
+                                }
+                                double* rr = a.red + ((int64_t)te * a.Bp + b0 + wt) * 3;
+                                rr[0] = r0;
+                                rr[1] = r1;
+                                rr[2] = r2;
+                            }
                         }
                     }
                 }
@@ -857,7 +1103,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
         for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
             double s0 = 0, s1 = 0, s2 = 0;
-            for (int t = 0; t < a.Nt; ++t) {
+            for (int t = 0; t < a.Nred; ++t) {
                 const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
                 s0 += __ldcg(rr);
                 s1 += __ldcg(rr + 1);
@@ -1054,7 +1300,7 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     TDAGW_CUDA(cudaGetDevice(&dev));
     TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const size_t smem = tc_smem_bytes();
-    const void* fn = h.Nb == 2 ? (const void*)batched_tc_kernel<2> : (const void*)batched_tc_kernel<4>;
+    const void* fn = h.Nb == 2 ? (const void*)batched_tc_kernel<2, false> : (const void*)batched_tc_kernel<4, false>;
     TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
@@ -1099,6 +1345,7 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.r = r;
     a.rp = d.rp;
     a.Nt = d.Nt;
+    a.Nred = d.Nt;
     a.Mt = d.Mt;
     a.nchU = d.nchU;
     a.nchV = d.nchV;
@@ -1238,6 +1485,281 @@ void tc_recompute_segment(Ctx& c, int n0, int len, float2* recX, float2* recDS, 
     void* args[] = {&a};
     TDAGW_CUDA(cudaLaunchCooperativeKernel(st.tc_fn, dim3(st.tc_grid), dim3(kTcThreads), args, st.tc_smem, s));
     c.persistent_launched = true;
+}
+
+
+// Split-FP16 tiles of the channel-wise factors (Eq. svd-channel-wise): V segment q as
+// Mt_q = ceil(ldv_q / 256) column tiles x ceil(Nk / 16) chunks of k-points, U segment p
+// (its low-rank columns, then the dense diagonal channel K^pp) as ceil(Nk / 256) row tiles
+// x ceil(ldw_p / 16) chunks; power-of-two scales from the largest entries; the bound of
+// the U-pass operand z_p = [S o y ; x_p]; the padded S o Y row of every gathered channel
+// column.  Made once per set of channel factors.
+void pack_channel_tc(Ctx& c) {
+    ChannelFactors& f = c.ch;
+    if (f.tc_valid) return;
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "split-FP16 factors need a complex64 context");
+    TDAGW_REQUIRE(f.valid, TDAGW_ERR_NO_FACTORS, "no channel factors installed");
+    cudaStream_t s = c.stream;
+    const ChMeta& m = f.m;
+    const int P = m.P, Nk = m.Nk;
+    const int nchK = (Nk + 15) / 16, NtK = (Nk + kRows - 1) / kRows;
+    int maxc = 1;
+    for (int e = 0; e < P; ++e) maxc = std::max(maxc, std::max(m.ldv[e], m.ldw[e]));
+    DevBuf stats;
+    stats.ensure((size_t)3 * maxc * sizeof(float));
+    std::vector<float> st(3 * (size_t)maxc);
+    float mu = 0.f, mv = 0.f, nv = 0.f, smax = 0.f;
+    auto seg_stats = [&](const float2* A, int cols, bool isv) {
+        factor_stats_kernel<<<(cols + 127) / 128, 128, 0, s>>>(A, A, Nk, cols, cols, stats.as<float>());
+        check_launch("factor_stats_kernel");
+        TDAGW_CUDA(cudaMemcpyAsync(st.data(), stats.p, 3 * (size_t)cols * sizeof(float), cudaMemcpyDeviceToHost, s));
+        TDAGW_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < cols; ++j) {
+            if (isv) {
+                mv = std::max(mv, st[j]);
+                nv = std::max(nv, st[2 * (size_t)cols + j]);
+            } else {
+                mu = std::max(mu, st[j]);
+            }
+        }
+    };
+    f.tc_mtq0.assign(P + 1, 0);
+    f.tc_nchw.assign(P, 0);
+    f.tc_tvoff.assign(P, 0);
+    f.tc_tuoff.assign(P, 0);
+    long long tv = 0, tu = 0;
+    for (int q = 0; q < P; ++q) {
+        const int mt = (m.ldv[q] + kRows - 1) / kRows;
+        f.tc_mtq0[q + 1] = f.tc_mtq0[q] + mt;
+        f.tc_tvoff[q] = tv;
+        tv += (long long)mt * nchK;
+        if (m.ldv[q] > 0) seg_stats(f.V.as<float2>() + m.vbase[q], m.ldv[q], true);
+    }
+    for (int p = 0; p < P; ++p) {
+        f.tc_nchw[p] = (m.ldw[p] + 15) / 16;
+        f.tc_tuoff[p] = tu;
+        tu += (long long)NtK * f.tc_nchw[p];
+        seg_stats(f.U.as<float2>() + m.ubase[p], m.ldw[p], false);
+    }
+    std::vector<float> S((size_t)std::max<long long>(m.stot, 1), 0.f);
+    if (m.stot > 0) {
+        TDAGW_CUDA(cudaMemcpyAsync(S.data(), f.S.p, m.stot * sizeof(float), cudaMemcpyDeviceToHost, s));
+        TDAGW_CUDA(cudaStreamSynchronize(s));
+    }
+    for (float v : S) smax = std::max(smax, std::fabs(v));
+    TDAGW_REQUIRE(std::isfinite(mu) && std::isfinite(mv) && std::isfinite(nv) && std::isfinite(smax),
+                  TDAGW_ERR_INVALID_ARG, "factors are not finite");
+    auto p2 = [](float bound) {
+        if (!(bound > 0.f)) return 1.f;
+        int e = 0;
+        std::frexp(bound, &e);
+        return std::ldexp(1.f, 13 - std::max(e, -100));
+    };
+    f.tc_su = p2(mu);
+    f.tc_sv = p2(mv);
+    // |y_c| <= ||v_c|| ||x_q|| <= ||v_c|| sqrt(2 Nk) max|x| for the channel columns, and
+    // z_p also holds x_p itself
+    f.tc_zbound = std::max(1.f, smax * std::sqrt(nv) * (float)std::sqrt(2.0 * (double)Nk));
+    f.tcV.ensure((size_t)std::max<long long>(tv, 1) * kTile);
+    f.tcU.ensure((size_t)std::max<long long>(tu, 1) * kTile);
+    for (int q = 0; q < P; ++q) {
+        if (m.ldv[q] == 0) continue;
+        const int rp = (f.tc_mtq0[q + 1] - f.tc_mtq0[q]) * kRows;
+        const int64_t total = (int64_t)nchK * 16 * rp;
+        pack_v_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+            f.V.as<float2>() + m.vbase[q], Nk, m.ldv[q], m.ldv[q], rp, nchK, f.tc_sv,
+            f.tcV.as<unsigned char>() + f.tc_tvoff[q] * kTile, total);
+        check_launch("pack_v_kernel");
+    }
+    for (int p = 0; p < P; ++p) {
+        const int rp = f.tc_nchw[p] * 16;
+        const int64_t total = (int64_t)NtK * kRows * rp;
+        pack_u_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+            f.U.as<float2>() + m.ubase[p], Nk, m.ldw[p], m.ldw[p], rp, f.tc_nchw[p], f.tc_su,
+            f.tcU.as<unsigned char>() + f.tc_tuoff[p] * kTile, total);
+        check_launch("pack_u_kernel");
+    }
+    // padded S o Y row of each gathered column (its V segment's tiles start at mtq0 256)
+    std::vector<int> gpad((size_t)std::max<long long>(m.gtot, 1), 0);
+    for (long long e = 0; e < m.gtot; ++e) {
+        const long long col = f.gidx_host[e];
+        int q = 0;
+        while (q + 1 < P && m.sbase[q + 1] <= col) ++q;
+        gpad[e] = f.tc_mtq0[q] * kRows + (int)(col - m.sbase[q]);
+    }
+    f.tcGpad.ensure(gpad.size() * sizeof(int));
+    TDAGW_CUDA(cudaMemcpyAsync(f.tcGpad.p, gpad.data(), gpad.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    f.tcZero.ensure((size_t)c.hm.N * sizeof(float2));
+    TDAGW_CUDA(cudaMemsetAsync(f.tcZero.p, 0, (size_t)c.hm.N * sizeof(float2), s));
+    TDAGW_CUDA(cudaStreamSynchronize(s));
+    f.tc_valid = true;
+}
+
+void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt, int flags) {
+    TDAGW_REQUIRE(c.dtype == TDAGW_C64, TDAGW_ERR_UNSUPPORTED, "split-FP16 propagation needs a complex64 context");
+    TDAGW_REQUIRE(flags & TDAGW_FLAG_RESET, TDAGW_ERR_UNSUPPORTED,
+                  "split-FP16 propagation starts from drho = 0 (TDAGW_FLAG_RESET)");
+    TDAGW_REQUIRE(!(flags & TDAGW_FLAG_CHECKPOINT), TDAGW_ERR_UNSUPPORTED,
+                  "the channel-wise kernel runs without checkpoints");
+    pack_channel_tc(c);
+    const ChannelFactors& f = c.ch;
+    const ChMeta& m = f.m;
+    const HostModel& h = c.hm;
+    cudaStream_t s = c.stream;
+    const int64_t N = h.N;
+    const int P = m.P, Nk = m.Nk;
+    const int nchK = (Nk + 15) / 16, NtK = (Nk + kRows - 1) / kRows;
+    const int nsegA = f.tc_mtq0[P];
+    const int rp = std::max(1, nsegA) * kRows;
+    const int nte = (int)((N + kRows - 1) / kRows);
+    const BatchSetup bs = prepare_batch(c, fields, B, steps, dt);
+    const int Bp = bs.Bp;
+
+    int dev = 0, nsm = 0;
+    TDAGW_CUDA(cudaGetDevice(&dev));
+    TDAGW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = tc_smem_bytes();
+    const void* fn = h.Nb == 2 ? (const void*)batched_tc_kernel<2, true> : (const void*)batched_tc_kernel<4, true>;
+    TDAGW_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TDAGW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
+    TDAGW_REQUIRE(per_sm == 1, TDAGW_ERR_UNSUPPORTED, "tensor-core batched kernel needs exactly one CTA per SM");
+    const int nctas = nsm;
+
+    const int KSmax = std::max(1, std::min(nctas / std::max(1, nsegA), nchK));
+    c.tcP.ensure((size_t)KSmax * rp * Bp * sizeof(float2));
+    c.tcY.ensure((size_t)rp * Bp * sizeof(float2));
+    c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
+    c.tcRed.ensure((size_t)nte * Bp * 3 * sizeof(double));
+    const size_t sbytes = (size_t)N * Bp * sizeof(float2);
+    c.bdS.ensure(sbytes);
+    c.sync.ensure(4 * sizeof(unsigned));
+
+    TcArgs a{};
+    a.tU = f.tcU.as<unsigned char>();
+    a.tV = f.tcV.as<unsigned char>();
+    a.Ys = c.tcY.as<float2>();
+    a.P = c.tcP.as<float2>();
+    a.xmax = c.tcMax.as<unsigned>();
+    a.S = f.S.as<float>();
+    a.diag = f.tcZero.as<float2>();  // the diagonal channels are products of phase C
+    a.dx = c.dx.as<float2>();
+    a.dy = c.dy.as<float2>();
+    a.vx = c.vx.as<float2>();
+    a.gap = c.gap.as<float2>();
+    a.X = c.bX.as<float2>();
+    a.Ssum = c.bS.as<float2>();
+    a.Ccomp = c.bC.as<float2>();
+    a.acc = c.bA.as<float2>();
+    a.Etab = c.bEtab.as<double>();
+    a.dir = c.bdir.as<float2>();
+    a.act = c.bact.as<int>();
+    a.red = c.tcRed.as<double>();
+    a.obs = c.bobs.as<double>();
+    a.bar = reinterpret_cast<unsigned long long*>(c.sync.p);
+    a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.N = N;
+    a.ldE = bs.ldE;
+    a.Nk = Nk;
+    a.r = rp;
+    a.rp = rp;
+    a.Nt = P * NtK;  // phase C items per trajectory group
+    a.Mt = nsegA;    // phase A column tiles per K-range
+    a.nchU = 0;
+    a.nchV = nchK;
+    a.Bp = Bp;
+    a.B = B;
+    a.kahan = (flags & TDAGW_FLAG_NO_KAHAN) ? 0 : 1;
+    a.c1 = h.c1;
+    for (int q = 0; q < 4; ++q) a.occ[q] = (float)h.occ[q];
+    a.dt = (float)dt;
+    a.su = f.tc_su;
+    a.sv = f.tc_sv;
+    a.ybound = 0.f;
+    a.wait_ns = 2000000000ull;
+    a.n0 = 0;
+    a.ck_period = 1;
+    a.Nred = nte;
+    a.gpad = f.tcGpad.as<int>();
+    a.dS = c.bdS.as<float2>();
+    a.npair = P;
+    a.NtK = NtK;
+    a.nte = nte;
+    a.zbound = f.tc_zbound;
+    for (int e = 0; e < P; ++e) {
+        a.tvoff[e] = f.tc_tvoff[e];
+        a.tuoff[e] = f.tc_tuoff[e];
+        a.mtq0[e] = f.tc_mtq0[e];
+        a.ldvq[e] = m.ldv[e];
+        a.sbq[e] = (int)m.sbase[e];
+        a.nlrq[e] = m.nlr[e];
+        a.gbq[e] = (int)m.gbase[e];
+        a.nchw[e] = f.tc_nchw[e];
+    }
+    a.mtq0[P] = f.tc_mtq0[P];
+    auto run = [&](int gc_max, int ks_max, int T, bool graph) {
+        a.gc_max = gc_max;
+        a.ks_max = ks_max;
+        a.Tmax = T;
+        launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
+                       {{c.bX.p, sbytes},
+                        {c.bS.p, sbytes},
+                        {c.bC.p, sbytes},
+                        {c.tcMax.p, 3 * Bp * sizeof(unsigned)},
+                        {c.sync.p, 4 * sizeof(unsigned)}},
+                       graph);
+    };
+    // work split tuned once per (B, channel columns) as for the low-rank kernel
+    const uint64_t key = (0xF1ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)m.stot;
+    int gc_max = 0, ks_max = 0;
+    auto it = c.batch_plans.find(key);
+    if (it != c.batch_plans.end()) {
+        gc_max = it->second.first;
+        ks_max = it->second.second;
+    } else {
+        const int g_min = (B + kGroup - 1) / kGroup;
+        const int g_fill = group_count(B, a.Nt, nctas, 0);
+        std::vector<int> gcs;
+        for (int gcand = g_min; gcand < g_fill; gcand *= 2) gcs.push_back(gcand);
+        gcs.push_back(0);
+        const int ks_fill = std::max(1, std::min(nctas / (g_min * std::max(1, nsegA)), nchK));
+        std::vector<int> kss = {0};
+        if (ks_fill >= 4) kss.push_back(ks_fill / 2);
+        if (gcs.size() * kss.size() == 1) {
+            c.batch_plans[key] = {0, 0};
+        } else if (bs.Tmax >= 8) {
+            cudaEvent_t e0, e1;
+            TDAGW_CUDA(cudaEventCreate(&e0));
+            TDAGW_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (int gcand : gcs)
+                for (int kcand : kss) {
+                    run(gcand, kcand, 2, false);  // warm
+                    TDAGW_CUDA(cudaEventRecord(e0, s));
+                    run(gcand, kcand, 6, false);
+                    TDAGW_CUDA(cudaEventRecord(e1, s));
+                    TDAGW_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    TDAGW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        gc_max = gcand;
+                        ks_max = kcand;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            int err = 0;
+            TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
+            TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the tensor-core kernel");
+            reset_batch_observables(c, bs, B);
+            c.batch_plans[key] = {gc_max, ks_max};
+        }
+    }
+    c.adj.valid = false;
+    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
+    c.persistent_launched = true;
+    finish_batch(c, bs, B);
 }
 
 }  // namespace tdagw

@@ -594,8 +594,8 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
         TDAGW_REQUIRE(mode != TDAGW_CHANNEL || ctx->c.ch.valid, TDAGW_ERR_NO_FACTORS,
                       "channel mode needs channel factors (tdagw_compress_channels or "
                       "tdagw_set_channel_factors)");
-        TDAGW_REQUIRE(mode != TDAGW_CHANNEL || !(flags & (TDAGW_FLAG_CHECKPOINT | TDAGW_FLAG_SPLIT_F16)),
-                      TDAGW_ERR_UNSUPPORTED, "channel mode runs without checkpoints or split-FP16 factors");
+        TDAGW_REQUIRE(mode != TDAGW_CHANNEL || !(flags & TDAGW_FLAG_CHECKPOINT), TDAGW_ERR_UNSUPPORTED,
+                      "channel mode runs without checkpoints");
         for (int b = 0; b < B; ++b) {
             const tdagw_field& f = fields[b];
             TDAGW_REQUIRE(f.kind >= 0 && f.kind <= 3, TDAGW_ERR_INVALID_ARG, "bad field kind");
@@ -606,15 +606,18 @@ int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int*
             TDAGW_REQUIRE(f.kind != TDAGW_FIELD_SIN2_SIN || f.T_pulse > 0, TDAGW_ERR_INVALID_ARG,
                           "T_pulse must be positive");
         }
-        TDAGW_REQUIRE(!(flags & TDAGW_FLAG_SPLIT_F16) || mode == TDAGW_LOWRANK, TDAGW_ERR_INVALID_ARG,
-                      "TDAGW_FLAG_SPLIT_F16 applies to the low-rank kernel");
+        TDAGW_REQUIRE(!(flags & TDAGW_FLAG_SPLIT_F16) || mode == TDAGW_LOWRANK || mode == TDAGW_CHANNEL,
+                      TDAGW_ERR_INVALID_ARG, "TDAGW_FLAG_SPLIT_F16 applies to the low-rank and channel-wise kernels");
         TDAGW_REQUIRE(mode != TDAGW_LOWRANK || !ctx->c.kdiag || !(flags & TDAGW_FLAG_SPLIT_F16),
                       TDAGW_ERR_UNSUPPORTED, "split-FP16 factors need the strict-diagonal reading of K^diag");
         if (flags & TDAGW_FLAG_SPLIT_F16) {
             int tmax = 0;
             for (int b = 0; b < B; ++b) tmax = std::max(tmax, steps[b]);
             TDAGW_REQUIRE(tmax > 0, TDAGW_ERR_INVALID_ARG, "at least one trajectory needs steps");
-            propagate_batched_tc(ctx->c, fields, B, steps, dt, flags);
+            if (mode == TDAGW_CHANNEL)
+                propagate_channel_tc(ctx->c, fields, B, steps, dt, flags);
+            else
+                propagate_batched_tc(ctx->c, fields, B, steps, dt, flags);
         } else if (B == 1 && !(flags & TDAGW_FLAG_CHECKPOINT)) {
             DISPATCH(ctx, propagate, ctx->c, fields[0], steps[0], dt, mode, flags);
             ctx->c.obs_B = 1;

@@ -95,6 +95,7 @@ void ch_layout(Ctx& c, const std::vector<int>& z) {
     const int P = h.Nb * h.Nb, Nk = h.Nk;
     ChannelFactors& f = c.ch;
     f.valid = false;
+    f.tc_valid = false;
     f.z = z;
     f.zmax = 0;
     for (int p = 0; p < P; ++p) f.z[p * P + p] = 0;

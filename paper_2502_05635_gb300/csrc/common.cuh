@@ -183,6 +183,13 @@ struct ChannelFactors {
     std::vector<int> gidx_host;
     ChMeta m{};
     DevBuf V, U, S, Y, gidx, part, Xt;
+    // split-FP16 tiles of the segments for the tensor-core batched path, and whether they
+    // match the installed factors
+    bool tc_valid = false;
+    DevBuf tcU, tcV, tcZero, tcGpad;
+    float tc_su = 1.f, tc_sv = 1.f, tc_zbound = 0.f;
+    std::vector<long long> tc_tvoff, tc_tuoff;
+    std::vector<int> tc_mtq0, tc_nchw;
 };
 
 struct Ctx {
@@ -303,6 +310,8 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
                           int flags);
 // Split-FP16 tiled copies of the installed factors (made once per set of factors).
 void pack_factors_tc(Ctx& c);
+// The channel-wise kernel with split-FP16 segment tiles on the tensor cores.
+void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* steps, double dt, int flags);
 
 // One persistent cooperative launch of a batched kernel (argument block `args` of
 // `args_size` bytes, a single by-value struct) after zeroing `resets` (pointer, bytes); with

@@ -236,8 +236,8 @@ def test_channel_errors():
         tg.tdagw_compress_channels(c.h, 17, 8, 1)
     assert e.value.code == tg.ERR_INVALID_ARG
     tg.tdagw_compress_channels(c.h, 3, 8, 1)
-    for flags, B in ((tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 1), (tg.FLAG_RESET | tg.FLAG_SPLIT_F16, 1),
-                     (tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 3)):
+    for flags, B in ((tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 1), (tg.FLAG_RESET | tg.FLAG_CHECKPOINT, 3),
+                     (tg.FLAG_SPLIT_F16, 2), (tg.FLAG_RESET | tg.FLAG_SPLIT_F16 | tg.FLAG_CHECKPOINT, 2)):
         with pytest.raises(tg.TdagwError) as e:
             tg.tdagw_propagate(c.h, [tg.make_field(q)] * B, [5] * B, 0.2, tg.CHANNEL, flags)
         assert e.value.code == tg.ERR_UNSUPPORTED
