@@ -148,6 +148,7 @@ struct TcArgs {
     const int* gpad;
     float2* dS;
     int npair, NtK, nte;
+    int kcu;        // K-ranges of a U segment tile (partial dSigma slots dS + kc N Bp)
     float zbound;   // |z_p| <= zbound max|X_b|
     long long tvoff[kMaxPairs], tuoff[kMaxPairs];
     int mtq0[kMaxPairs + 1], ldvq[kMaxPairs], sbq[kMaxPairs], nlrq[kMaxPairs], gbq[kMaxPairs], nchw[kMaxPairs];
@@ -402,6 +403,33 @@ __device__ __forceinline__ ItemA item_a(const TcArgs& a, const Groups& q, int it
     it.c0 = (int)((int64_t)it.ks * a.nchV / q.KS);
     it.c1 = (int)((int64_t)(it.ks + 1) * a.nchV / q.KS);
     return it;
+}
+
+// Observables of step n from the Nred per-tile partial sums (channel-wise mode, where
+// Nred is large): one warp per trajectory, the lanes take every 32nd tile and a butterfly
+// sums the lanes, in a fixed order.  gw, nw: the calling warp and the number of warps.
+__device__ void tc_obs_warp(const TcArgs& a, int n, int gw, int nw, int lane) {
+    for (int b = gw; b < a.act[a.n0 + n - 1]; b += nw) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int t = lane; t < a.Nred; t += 32) {
+            const double* rr = a.red + ((int64_t)t * a.Bp + b) * 3;
+            s0 += __ldcg(rr);
+            s1 += __ldcg(rr + 1);
+            s2 += __ldcg(rr + 2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            double* o = a.obs + ((int64_t)n * a.B + b) * 3;
+            o[0] = s0 / a.Nk;
+            o[1] = s1 / a.Nk;
+            o[2] = s2 / a.Nk;
+        }
+    }
 }
 
 // phase A tile index mt (padded column order) -> V segment q and its tile m (channel-wise)
@@ -818,7 +846,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         a.Ys[(int64_t)j * a.Bp + b] = v;
                     }
                 }
-                if (st == 0 && n > 0) {
+                if (CHT && st == 0 && n > 0) {
+                    tc_obs_warp(a, n, blockIdx.x * (kWorkers / 32) + (warp - 2), gridDim.x * (kWorkers / 32), lane);
+                } else if (st == 0 && n > 0) {
                     // observables of step n (written by the last stage of step n - 1)
                     for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
                         double s0 = 0, s1 = 0, s2 = 0;
@@ -956,12 +986,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 }
             } else {
                 // ---- C (channel-wise): dSigma rows k P + p of U segment p's row tile t ----
-                const int nC = a.Nt * q.GC;  // a.Nt: P NtK segment tiles
+                // items: (segment tile si = p NtK + t, trajectory group g, K-range kc)
+                const int nC = a.Nt * q.GC * a.kcu;  // a.Nt: P NtK segment tiles
+                auto item_c = [&](int item, int& p, int& t, int& g, int& kc, int& c0, int& c1) {
+                    const int si = item % a.Nt, rest = item / a.Nt;
+                    p = si / a.NtK;
+                    t = si % a.NtK;
+                    g = rest % q.GC;
+                    kc = rest / q.GC;
+                    c0 = a.nchw[p] * kc / a.kcu;
+                    c1 = a.nchw[p] * (kc + 1) / a.kcu;
+                };
                 if (producer) {
                     for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                        const int si = item % a.Nt, p = si / a.NtK, t = si % a.NtK;
+                        int p, t, g, kc, c0, c1;
+                        item_c(item, p, t, g, kc, c0, c1);
                         const unsigned char* tu = a.tU + (a.tuoff[p] + (int64_t)t * a.nchw[p]) * kTile;
-                        for (int c = 0; c < a.nchw[p]; ++c, ++gch) {
+                        for (int c = c0; c < c1; ++c, ++gch) {
                             TC_W_BEGIN(p1);
                             issue(tu + (int64_t)c * kTile);
                             TC_W_END(p1, 4);
@@ -971,16 +1012,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 } else if (mma) {
                     const uint32_t idesc = tc::idesc_f16(128, kRows);
                     for (int item = blockIdx.x; item < nC && !*vabort; item += gridDim.x) {
-                        const int p = (item % a.Nt) / a.NtK;
+                        int p, t, g, kc, c0, c1;
+                        item_c(item, p, t, g, kc, c0, c1);
                         wait_acc_free();
-                        for (int c = 0; c < a.nchw[p] && !*vabort; ++c) mma_step(idesc, c == 0);
+                        for (int c = c0; c < c1 && !*vabort; ++c) mma_step(idesc, c == c0);
                         tc::mma_commit(accf);
                         ++acnt;
                     }
-                    TC_TRACE(true, 7);
                 } else if (worker) {
                     for (int item = blockIdx.x; item < nC; item += gridDim.x) {
-                        const int si = item % a.Nt, g = item / a.Nt, p = si / a.NtK, t = si % a.NtK;
+                        int p, t, g, kc, c0, c1;
+                        item_c(item, p, t, g, kc, c0, c1);
                         int b0, b1;
                         group_range(Bact, q.GC, g, b0, b1);
                         const int nbg = b1 - b0;
@@ -996,21 +1038,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             if (j < nl) return a.Ys + (int64_t)__ldg(gp + j) * a.Bp;
                             return j < nl + Nk ? a.X + ((j - nl) * P + p) * a.Bp : nullptr;
                         };
-                        const int nch = a.nchw[p];
-                        for (int c = 0; c < kSrcAhead; ++c) src_issue_rows(rowz, c, nch, live, b0, c);
-                        for (int c = 0; c < nch; ++c) {
+                        for (int c = c0; c < c0 + kSrcAhead; ++c) src_issue_rows(rowz, c, c1, live, b0, c - c0);
+                        for (int c = c0; c < c1; ++c) {
                             float2 v[8];
-                            src_read(v, c, sz);
+                            src_read(v, c - c0, sz);
                             build_block(v, false);
-                            src_issue_rows(rowz, c + kSrcAhead, nch, live, b0, c + kSrcAhead);
+                            src_issue_rows(rowz, c + kSrcAhead, c1, live, b0, c + kSrcAhead - c0);
                         }
                         cp_async_wait<0>();
-                        // accumulator -> dSigma rows k P + p (unscaled); lanes 2 bl and 2 bl + 1
-                        // hold the real and imaginary parts
+                        // accumulator -> partial dSigma rows k P + p of K-range kc (unscaled);
+                        // lanes 2 bl and 2 bl + 1 hold the real and imaginary parts
                         if (!*vabort && !mb_wait(accf, acnt & 1u, vabort, budget)) fail();
                         tc::fence_after_sync();
                         if (!warp_abort()) {
-                            const float osc = live ? 1.f / (a.su * sz) : 0.f;
+                            // an empty K-range (fewer chunks than ranges) contributes zeros
+                            const float osc = live && c1 > c0 ? 1.f / (a.su * sz) : 0.f;
                             for (int u = 0; u < 8; ++u) {
                                 float v[16];
                                 const int col = 128 * wh + 16 * u;
@@ -1020,7 +1062,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                     const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
                                     const int k = t * kRows + col + e;
                                     if (!ocomp && live && k < Nk)
-                                        a.dS[((int64_t)k * P + p) * a.Bp + b0 + obl] = make_float2(v[e] * osc, im * osc);
+                                        a.dS[((int64_t)kc * a.N + (int64_t)k * P + p) * a.Bp + b0 + obl] =
+                                            make_float2(v[e] * osc, im * osc);
                                 }
                             }
                         }
@@ -1031,40 +1074,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 }
                 // every dSigma row is written before the epilogue reads it
                 if (in_sync && !(ok = tc_grid_sync(a, gen, &abort_s))) break;
-                // ---- E (channel-wise): commutator + RK4 for the 256-row tiles of all N rows,
-                //      dSigma staged from global memory by 64-row quarters ----
+                TC_TRACE(worker && wt == 0, 7);
+                // ---- E (channel-wise): commutator + RK4 by 64-row quarters of all N rows
+                //      (items: quarter, trajectory group), dSigma summed over the K-range
+                //      partials of phase C in a fixed order into the staging buffer ----
                 if (worker) {
-                    const int nE = a.nte * q.GC;
+                    const int nq = 4 * a.nte;
+                    const int nE = nq * q.GC;
                     for (int item = blockIdx.x; item < nE; item += gridDim.x) {
-                        const int te = item % a.nte, g = item / a.nte;
+                        const int tq = item % nq, g = item / nq;
                         int b0, b1;
                         group_range(Bact, q.GC, g, b0, b1);
                         const int nbg = b1 - b0;
                         workers_sync();  // the previous item's readers of smx and sred are done
                         if (wt < kGroup) smx[wt] = 0u;
+                        const int64_t r0 = (int64_t)tq * 64;
+                        for (int e = wt; e < 64 * nbg; e += kWorkers) {
+                            const int rr = e / nbg, bb = e % nbg;
+                            if (r0 + rr < a.N) {
+                                const float2* src = a.dS + (r0 + rr) * a.Bp + b0 + bb;
+                                float2 v = __ldcg(src);
+                                for (int kc = 1; kc < a.kcu; ++kc) v = cadd(v, __ldcg(src + (int64_t)kc * a.N * a.Bp));
+                                sDS[ds_index(rr, bb)] = v;
+                            }
+                        }
                         workers_sync();
                         const int kgroups = kWorkers / nbg;
                         const int bl = wt % nbg, kg = wt / nbg;
                         DF3 obs;
                         float xm = 0.f;
-                        for (int qq = 0; qq < kRows / 64; ++qq) {
-                            const int64_t r0 = (int64_t)te * kRows + 64 * qq;
-                            for (int e = wt; e < 64 * nbg; e += kWorkers) {
-                                const int rr = e / nbg, bb = e % nbg;
-                                if (r0 + rr < a.N) sDS[ds_index(rr, bb)] = __ldcg(a.dS + (r0 + rr) * a.Bp + b0 + bb);
-                            }
-                            workers_sync();
-                            const int kbase = (int)(r0 / NB2);
-                            const int kt = min(64 / NB2, a.Nk - kbase);
-                            if (kg < kgroups && !*vabort) {
-                                const int b = b0 + bl;
-                                const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
-                                const float2 dr = a.dir[b];
-                                for (int kl = kg; kl < kt; kl += kgroups)
-                                    stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, -1);
-                            }
-                            workers_sync();  // the staged quarter is consumed before it is rewritten
+                        const int kbase = (int)(r0 / NB2);
+                        const int kt = min(64 / NB2, a.Nk - kbase);
+                        if (kg < kgroups && !*vabort) {
+                            const int b = b0 + bl;
+                            const float E = (float)a.Etab[(int64_t)b * a.ldE + 2 * (a.n0 + n) + eoff];
+                            const float2 dr = a.dir[b];
+                            for (int kl = kg; kl < kt; kl += kgroups)
+                                stage_kb_tc<NB>(a, kbase + kl, b, st, E, dr, sDS, kl * NB2, bl, xm, obs, -1);
                         }
+                        workers_sync();  // the staged quarter is consumed before sred reuses it
                         if (kg < kgroups) {
                             atomicMax(smx + bl, __float_as_uint(xm));
                             if (st == 3) {
@@ -1077,16 +1125,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         if (wt < nbg && !*vabort) {
                             atomicMax(xout + b0 + wt, smx[wt]);
                             if (st == 3) {
-                                double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+                                double r0s = 0.0, r1s = 0.0, r2s = 0.0;
                                 for (int k2 = 0; k2 < kgroups; ++k2) {
-                                    r0 += sred[(k2 * nbg + wt) * 3];
-                                    r1 += sred[(k2 * nbg + wt) * 3 + 1];
-                                    r2 += sred[(k2 * nbg + wt) * 3 + 2];
+                                    r0s += sred[(k2 * nbg + wt) * 3];
+                                    r1s += sred[(k2 * nbg + wt) * 3 + 1];
+                                    r2s += sred[(k2 * nbg + wt) * 3 + 2];
                                 }
-                                double* rr = a.red + ((int64_t)te * a.Bp + b0 + wt) * 3;
-                                rr[0] = r0;
-                                rr[1] = r1;
-                                rr[2] = r2;
+                                double* rr = a.red + ((int64_t)tq * a.Bp + b0 + wt) * 3;
+                                rr[0] = r0s;
+                                rr[1] = r1s;
+                                rr[2] = r2s;
                             }
                         }
                     }
@@ -1098,7 +1146,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
         }
     }
     // observables of the last step (workers: they passed the last grid barrier)
-    if (worker && ok && a.Tmax > 0) {
+    if (CHT && worker && ok && a.Tmax > 0) {
+        tc_obs_warp(a, a.Tmax, blockIdx.x * (kWorkers / 32) + (warp - 2), gridDim.x * (kWorkers / 32), lane);
+    } else if (worker && ok && a.Tmax > 0) {
         const int n = a.Tmax;
         const int64_t gt = (int64_t)blockIdx.x * kWorkers + wt, total = (int64_t)gridDim.x * kWorkers;
         for (int64_t b = gt; b < a.act[a.n0 + n - 1]; b += total) {
@@ -1630,9 +1680,10 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     c.tcP.ensure((size_t)KSmax * rp * Bp * sizeof(float2));
     c.tcY.ensure((size_t)rp * Bp * sizeof(float2));
     c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
-    c.tcRed.ensure((size_t)nte * Bp * 3 * sizeof(double));
+    c.tcRed.ensure((size_t)4 * nte * Bp * 3 * sizeof(double));
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
-    c.bdS.ensure(sbytes);
+    constexpr int kKcMax = 4;  // K-ranges of a phase C tile at most (partial dSigma slots)
+    c.bdS.ensure(kKcMax * sbytes);
     c.sync.ensure(4 * sizeof(unsigned));
 
     TcArgs a{};
@@ -1679,7 +1730,7 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.wait_ns = 2000000000ull;
     a.n0 = 0;
     a.ck_period = 1;
-    a.Nred = nte;
+    a.Nred = 4 * nte;  // per-quarter observable sums
     a.gpad = f.tcGpad.as<int>();
     a.dS = c.bdS.as<float2>();
     a.npair = P;
@@ -1697,9 +1748,10 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         a.nchw[e] = f.tc_nchw[e];
     }
     a.mtq0[P] = f.tc_mtq0[P];
-    auto run = [&](int gc_max, int ks_max, int T, bool graph) {
+    auto run = [&](int gc_max, int kc, int T, bool graph) {
         a.gc_max = gc_max;
-        a.ks_max = ks_max;
+        a.ks_max = 0;
+        a.kcu = kc;
         a.Tmax = T;
         launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
                        {{c.bX.p, sbytes},
@@ -1709,31 +1761,31 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
                         {c.sync.p, 4 * sizeof(unsigned)}},
                        graph);
     };
-    // work split tuned once per (B, channel columns) as for the low-rank kernel
+    // work split tuned once per (B, channel columns) by timing six steps of each candidate:
+    // the trajectory groups of phase C (as for the low-rank kernel) and the K-ranges of a
+    // phase C tile (more ranges spread the U segments' tiles over more CTAs, at the cost of
+    // partial dSigma sums in the epilogue)
     const uint64_t key = (0xF1ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)m.stot;
-    int gc_max = 0, ks_max = 0;
+    int gc_max = 0, kc = 1;
     auto it = c.batch_plans.find(key);
     if (it != c.batch_plans.end()) {
         gc_max = it->second.first;
-        ks_max = it->second.second;
+        kc = it->second.second;
     } else {
         const int g_min = (B + kGroup - 1) / kGroup;
         const int g_fill = group_count(B, a.Nt, nctas, 0);
         std::vector<int> gcs;
         for (int gcand = g_min; gcand < g_fill; gcand *= 2) gcs.push_back(gcand);
         gcs.push_back(0);
-        const int ks_fill = std::max(1, std::min(nctas / (g_min * std::max(1, nsegA)), nchK));
-        std::vector<int> kss = {0};
-        if (ks_fill >= 4) kss.push_back(ks_fill / 2);
-        if (gcs.size() * kss.size() == 1) {
-            c.batch_plans[key] = {0, 0};
-        } else if (bs.Tmax >= 8) {
+        std::vector<int> kcs;
+        for (int kcand = 1; kcand <= kKcMax; ++kcand) kcs.push_back(kcand);
+        if (bs.Tmax >= 8) {
             cudaEvent_t e0, e1;
             TDAGW_CUDA(cudaEventCreate(&e0));
             TDAGW_CUDA(cudaEventCreate(&e1));
             float best = 1e30f;
             for (int gcand : gcs)
-                for (int kcand : kss) {
+                for (int kcand : kcs) {
                     run(gcand, kcand, 2, false);  // warm
                     TDAGW_CUDA(cudaEventRecord(e0, s));
                     run(gcand, kcand, 6, false);
@@ -1744,7 +1796,7 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
                     if (ms < best) {
                         best = ms;
                         gc_max = gcand;
-                        ks_max = kcand;
+                        kc = kcand;
                     }
                 }
             cudaEventDestroy(e0);
@@ -1753,11 +1805,11 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
             TDAGW_CUDA(cudaMemcpy(&err, c.sync.as<unsigned>() + 2, sizeof(int), cudaMemcpyDeviceToHost));
             TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the tensor-core kernel");
             reset_batch_observables(c, bs, B);
-            c.batch_plans[key] = {gc_max, ks_max};
+            c.batch_plans[key] = {gc_max, kc};
         }
     }
     c.adj.valid = false;
-    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
+    run(gc_max, kc, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
     c.persistent_launched = true;
     finish_batch(c, bs, B);
 }
