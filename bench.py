@@ -486,12 +486,18 @@ def bench_channel_sweep(tg, torch, stream, sh):
     total = int(sum(w.steps))
     ms = _time_propagate(tg, torch, stream, ctx, fields, w.steps, w.dt, tg.CHANNEL, tg.FLAG_RESET)
     ch = tg.tdagw_observables(ctx.h, B=w.B)
+    ms_sp = _time_propagate(tg, torch, stream, ctx, fields, w.steps, w.dt, tg.CHANNEL,
+                            tg.FLAG_RESET | tg.FLAG_SPLIT_F16)
+    sp = tg.tdagw_observables(ctx.h, B=w.B)
     tg.tdagw_propagate(ctx.h, fields, list(w.steps), w.dt, tg.FULL, tg.FLAG_RESET)
     full = tg.tdagw_observables(ctx.h, B=w.B)
     ctx.close()
     return {"workload": "sweep_nb2_l24, channel-wise rank 29", "N": w.model.N, "B": w.B, "traj_steps": total,
             "value": total / (ms * 1e-3), "unit": "traj*steps/s", "ms": ms,
-            "p_rel_err_vs_full_gpu": _rel_errs(ch, full, w.steps)}
+            "p_rel_err_vs_full_gpu": _rel_errs(ch, full, w.steps),
+            "split_f16": {"value": total / (ms_sp * 1e-3), "unit": "traj*steps/s", "ms": ms_sp,
+                          "p_rel_err_vs_full_gpu": _rel_errs(sp, full, w.steps),
+                          "p_rel_err_vs_fp32_channel": _rel_errs(sp, ch, w.steps)}}
 
 
 def bench_channel(tg, torch, stream, sh, hbm, steps=1000, cmp_steps=200):
