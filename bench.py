@@ -51,6 +51,8 @@ METRIC = ("RK4 steps x trajectories / s (rank-1024 low-rank kernel vs full kerne
           "single trajectory; P(t) within 1e-5 of the FP64 oracle with the same factors)")
 UNIT = "steps*traj/s"
 CLOCK_WINDOW_S = 1.5
+# FP32 (non-tensor) peak of the GPU: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _args():
@@ -534,7 +536,7 @@ def bench_channel(tg, torch, stream, sh, hbm, steps=1000, cmp_steps=200):
             "steps_compared": cmp_steps, "setup_s": setup}
 
 
-def bench_channel_batched(tg, torch, stream, sh, B=64, steps=60):
+def bench_channel_batched(tg, torch, stream, sh, hbm=6780.0, B=64, steps=60):
     """Batched propagation at the mos2 size (N = 20736) in the channel-wise form (dense
     diagonal channels, off-diagonal channels at rank 65 from the GPU's randomised channel
     SVDs) against the batched dense kernel on the same GPU: B trajectories of pulses that
@@ -558,6 +560,7 @@ def bench_channel_batched(tg, torch, stream, sh, B=64, steps=60):
     # segments (8 bytes per complex entry, as complex64)
     ranks = 2 * 65 * 48
     per_stage = 8 * (w.model.Nk * ranks + w.model.N * w.model.Nk)
+    full_bound_s = max(8.0 * w.model.N ** 2 / (hbm * 1e9), 8.0 * w.model.N ** 2 * B / (FP32_SIMT_TFLOPS * 1e12))
     return {"workload": "mos2size_nb4_l36, channel-wise rank 65, early pulses", "N": w.model.N, "B": B,
             "steps": steps,
             "channel_wise": {"value": B * steps / (ms_ch * 1e-3), "unit": "traj*steps/s", "ms": ms_ch,
@@ -567,6 +570,11 @@ def bench_channel_batched(tg, torch, stream, sh, B=64, steps=60):
                                        "factor_gbs": 4 * steps * per_stage / (ms_sp * 1e-3) / 1e9,
                                        "p_rel_err_vs_fp32_channel": _rel_errs(sp, ch, T)},
             "full": {"value": B * steps / (ms_full * 1e-3), "unit": "traj*steps/s", "ms": ms_full},
+            # the fastest any FP32 (non-tensor) dense step could be on this GPU: K streamed at
+            # the measured copy peak, or 8 N^2 B FLOPs at the FP32 SIMT peak, whichever is
+            # slower; the split-FP16 channel-wise speed-up against that bound
+            "full_fp32_bound_ms": 4 * steps * full_bound_s * 1e3,
+            "speedup_split_f16_vs_full_fp32_bound": 4 * steps * full_bound_s * 1e3 / ms_sp,
             "speedup_vs_full": ms_full / min(ms_ch, ms_sp),
             "p_rel_err_vs_full_gpu": err_sp if ms_sp < ms_ch else err,
             "within_1e-4": max(err["max"], err_sp["max"]) <= 1e-4}
@@ -658,7 +666,7 @@ def run_leg(a):
     elif a.leg == "channel_sweep":
         out = bench_channel_sweep(tg, torch, stream, sh)
     elif a.leg == "channel_batched":
-        out = bench_channel_batched(tg, torch, stream, sh, steps=n or 60)
+        out = bench_channel_batched(tg, torch, stream, sh, hbm, steps=n or 60)
     elif a.leg == "angle_hhg":
         out = bench_angle_hhg(tg, torch, stream, sh, n or 2000)
     elif a.leg == "kblock":
@@ -824,7 +832,7 @@ def run_ours(a):
             "p_rel_err_vs_full_gpu": ch["p_rel_err_vs_full_gpu"], "steps_compared": ch["steps_compared"],
             "within_1e-4_of_full_kernel": ch["p_rel_err_vs_full_gpu"] <= 1e-4,
             "speedup_vs_full": ch["value"] / (nf / (ms_full * 1e-3))}
-        line["channel_wise_batched"] = bench_channel_batched(tg, torch, stream, sh)
+        line["channel_wise_batched"] = bench_channel_batched(tg, torch, stream, sh, hbm)
         cb = line["channel_wise_batched"]
         line["accuracy_qualified"]["batched"] = {
             "form": "channel-wise, split-FP16 segment tiles on the tensor cores",

@@ -60,8 +60,10 @@ enum {
     TDAGW_FLAG_NO_KAHAN = 4,      /* plain (uncompensated) RK4 accumulation                 */
     TDAGW_FLAG_STAGEWISE = 8,     /* low-rank or channel-wise c64: stage-wise kernels
                                      instead of the persistent single-launch kernel         */
-    TDAGW_FLAG_TEST_TIMEOUT = 16, /* fault-injection hook for tests: the persistent kernel's
-                                     grid barrier waits for one block that does not exist,
+    TDAGW_FLAG_TEST_TIMEOUT = 16, /* fault-injection hook for tests: the grid barrier of the
+                                     persistent single-trajectory kernels and of the
+                                     tensor-core batched kernel (no tuning runs then) waits
+                                     for one block that does not exist,
                                      every wait runs out a 20 ms budget and the call ends
                                      with TDAGW_ERR_TIMEOUT at the next synchronising call   */
     TDAGW_FLAG_CHECKPOINT = 32,   /* keep checkpoints for tdagw_adjoint (runs the batched

@@ -138,6 +138,7 @@ struct TcArgs {
     float ybound;   // max|S| max_j ||v_j|| sqrt(2N): |(S o Y)_jb| <= ybound max|X_b|
     unsigned long long wait_ns;
     int Nred;       // row tiles of the per-tile observable sums (red)
+    int extra_arrivals;  // > 0 only for the timeout test: the grid barrier can never complete
     // Channel-wise mode (Eq. svd-channel-wise; a separate instantiation).  Phase A runs
     // over the V segments (segment q: its Mt_q 256-column tiles, mtq0[q] the first of them
     // in the padded column order, K over the Nk k-points in nchV chunks), phase C over the
@@ -244,7 +245,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 __device__ bool tc_grid_sync(const TcArgs& a, unsigned& gen, int* abort_s) {
     participants_sync();
     if (threadIdx.x == 64 && !*abort_s) {
-        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x + a.extra_arrivals;
         red_release_add64(a.bar, 1ull);
         const uint64_t t0 = gtimer();
         while (ld_acquire64(a.bar) < target) {
@@ -1440,8 +1441,11 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     // half the partial sums).
     const uint64_t key = (0xF0ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
     int gc_max = 0, ks_max = 0;
+    const bool test_timeout = (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0;
     auto it = c.batch_plans.find(key);
-    if (it != c.batch_plans.end()) {
+    if (test_timeout) {
+        // timeout test: no tuning; the launch below waits for an arrival that never comes
+    } else if (it != c.batch_plans.end()) {
         gc_max = it->second.first;
         ks_max = it->second.second;
     } else {
@@ -1491,7 +1495,13 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         a.ckC = c.ckC.as<float2>();
         a.ck_period = period;
     }
-    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
+    if (test_timeout) {
+        a.extra_arrivals = 1;
+        a.wait_ns = 20000000ull;
+    }
+    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH) && !test_timeout);
+    a.extra_arrivals = 0;
+    a.wait_ns = 2000000000ull;
     c.persistent_launched = true;
     if (ckpt) {
         // the backward sweep: FP32 partition and arguments; segment recomputes on the
@@ -1767,8 +1777,11 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     // partial dSigma sums in the epilogue)
     const uint64_t key = (0xF1ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)m.stot;
     int gc_max = 0, kc = 1;
+    const bool test_timeout = (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0;
     auto it = c.batch_plans.find(key);
-    if (it != c.batch_plans.end()) {
+    if (test_timeout) {
+        // timeout test: no tuning; the launch below waits for an arrival that never comes
+    } else if (it != c.batch_plans.end()) {
         gc_max = it->second.first;
         kc = it->second.second;
     } else {
@@ -1809,7 +1822,11 @@ void propagate_channel_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         }
     }
     c.adj.valid = false;
-    run(gc_max, kc, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH));
+    if (test_timeout) {
+        a.extra_arrivals = 1;
+        a.wait_ns = 20000000ull;
+    }
+    run(gc_max, kc, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH) && !test_timeout);
     c.persistent_launched = true;
     finish_batch(c, bs, B);
 }

@@ -15,6 +15,7 @@ import pytest
 import workloads as wl
 from oracle import channel as oc
 from oracle import kernel as ok
+from oracle import lowrank as olr
 from oracle import model as om
 from oracle import propagate as op
 
@@ -167,3 +168,38 @@ def test_full_size_channel_split_f16():
         ref, _ = op.rk4(mdl, apply, s, w.dt, T, direction=(q.dir_x, q.dir_y))
         for j in range(3):
             assert op.rel_l2(got[:, b, j], ref[:, j]) < TOL, (b, j)
+
+
+@pytest.mark.parametrize("mode", ["lowrank", "channel"])
+def test_tensor_core_timeout_is_reported_and_context_survives(mode):
+    """Fault injection on the host side of a bounded wait (no GPU fault): the tensor-core
+    kernel's grid barrier waits for an arrival that never comes; every wait gives up after
+    its 20 ms budget, the copies and MMAs in flight drain, tensor memory is freed, the call
+    reports TDAGW_ERR_TIMEOUT at the next synchronisation, and the same context then runs
+    the same propagation correctly (against the oracle)."""
+    p = wl.small_model(6, 2)
+    mdl, fac, _ = _factors(p, 5)
+    D, U, S, V = fac
+    c = _ctx(p)
+    pulses = _pulses(3, 11)
+    steps = [20, 12, 20]
+    if mode == "channel":
+        tg.tdagw_set_channel_factors(c.h, U, S, V, D)
+        m, apply = tg.CHANNEL, (lambda v: oc.apply_channel(D, U, S, V, v))  # noqa: E731
+    else:
+        K = ok.dense_kernel(mdl)
+        d, Koff = ok.split_diag_off(K)
+        Ul, Sl, Vl = olr.truncated_svd(Koff, 40)
+        tg.tdagw_set_factors(c.h, Ul, Sl, Vl, d)
+        m = tg.LOWRANK
+        apply = lambda v: d * v + Ul @ (Sl * (Vl.conj().T @ v))  # noqa: E731
+    tg.tdagw_propagate(c.h, [tg.make_field(q) for q in pulses], steps, 0.2, m,
+                       SPLIT | tg.FLAG_TEST_TIMEOUT)
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_sync(c.h)
+    assert e.value.code == tg.ERR_TIMEOUT
+    got = c.propagate_batch(pulses, steps, 0.2, m, SPLIT)
+    for b, (q, T) in enumerate(zip(pulses, steps)):
+        s = op.half_step_samples(q, 0.2, T)
+        ref, _ = op.rk4(mdl, apply, s, 0.2, T, direction=(q.dir_x, q.dir_y))
+        assert op.rel_l2(got[:T + 1, b, 0], ref[:, 0]) < TOL, b
