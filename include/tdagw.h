@@ -62,7 +62,7 @@ enum {
                                      instead of the persistent single-launch kernel         */
     TDAGW_FLAG_TEST_TIMEOUT = 16, /* fault-injection hook for tests: the grid barrier of the
                                      persistent single-trajectory kernels and of the
-                                     tensor-core batched kernel (no tuning runs then) waits
+                                     batched kernels (no tuning runs then) waits
                                      for one block that does not exist,
                                      every wait runs out a 20 ms budget and the call ends
                                      with TDAGW_ERR_TIMEOUT at the next synchronising call   */

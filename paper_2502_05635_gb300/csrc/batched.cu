@@ -607,15 +607,20 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         a.red = c.bred.as<double>();
         launch_batched(c, fn, dim3(pl.Rg * pl.Tg), dim3(kBThreads), smem, &a, sizeof(a),
                        {{c.bX.p, sbytes}, {c.bS.p, sbytes}, {c.bC.p, sbytes}, {c.sync.p, 4 * sizeof(unsigned)}},
-                       !(flags & TDAGW_FLAG_NO_GRAPH));
+                       !(flags & TDAGW_FLAG_NO_GRAPH) && !a.extra_arrivals);
         c.persistent_launched = true;
     };
 
     const uint64_t key = ((uint64_t)mode << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
     const int tg_min = (B + kTileB - 1) / kTileB;  // at most kTileB trajectories per block
     BatchPlan plan;
+    const bool test_timeout = (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0;
     auto it = c.batch_plans.find(key);
-    if (it != c.batch_plans.end()) {
+    if (test_timeout) {
+        // timeout test: the first candidate untuned; the launch below waits for an arrival
+        // that never comes
+        plan = {std::min(h.Nk, max_ctas / tg_min), tg_min};
+    } else if (it != c.batch_plans.end()) {
         plan.Rg = it->second.first;
         plan.Tg = it->second.second;
         TDAGW_REQUIRE(plan.Tg >= tg_min && plan.Rg >= 1 && plan.Rg <= h.Nk && plan.Rg * plan.Tg <= max_ctas,
@@ -670,7 +675,13 @@ void propagate_batched(Ctx& c, const tdagw_field* fields, int B, const int* step
         a.ckC = c.ckC.as<float2>();
         a.ck_period = period;
     }
+    if (test_timeout) {
+        a.extra_arrivals = 1;
+        a.wait_ns = 20000000ull;
+    }
     run(plan, Tmax);
+    a.extra_arrivals = 0;
+    a.wait_ns = 2000000000ull;
     if (ckpt) {
         AdjointState& st = c.adj;
         st.valid = true;

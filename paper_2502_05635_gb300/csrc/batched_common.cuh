@@ -68,13 +68,14 @@ struct BatchArgs {
     float2* ckC;
     float2* recX;
     float2* recDS;
+    int extra_arrivals;  // > 0 only for the timeout test: the grid barrier can never complete
 };
 
 // grid barrier with a monotonic arrival counter (see persist::grid_sync); all threads call
 static __device__ bool bgrid_sync(const BatchArgs& a, unsigned& gen, int* abort_s) {
     __syncthreads();
     if (threadIdx.x == 0 && !*abort_s) {
-        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x + a.extra_arrivals;
         persist::red_release_add64(a.bar, 1ull);
         const uint64_t t0 = persist::gtimer();
         while (persist::ld_acquire64(a.bar) < target) {

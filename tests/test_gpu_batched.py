@@ -174,3 +174,31 @@ def test_zero_step_trajectories_inside_a_batch(mode, flags):
         assert op.rel_l2(got[:T + 1, b, 0], ref[:, 0]) < tol, b
         assert np.all(np.isnan(got[T + 1:, b]))
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", [tg.LOWRANK, tg.FULL])
+def test_batched_timeout_is_reported_and_context_survives(mode):
+    """Fault injection on the host side of a bounded wait (no GPU fault): the FP32 batched
+    kernel's grid barrier waits for an arrival that never comes; the call reports
+    TDAGW_ERR_TIMEOUT at the next synchronisation and the same context then runs the same
+    batch correctly (against the oracle)."""
+    p = wl.small_model(6, 1)
+    mdl = om.Model(p)
+    K = ok.dense_kernel(mdl)
+    d, Koff = ok.split_diag_off(K)
+    U, S, V = olr.truncated_svd(Koff, 20)
+    c = tg.Context(p, tg.C64, stream=torch.cuda.current_stream().cuda_stream)
+    tg.tdagw_set_factors(c.h, U, S, V, d)
+    pulses = _pulses(5, 21)
+    steps = [30, 9, 30, 17, 1]
+    tg.tdagw_propagate(c.h, [tg.make_field(q) for q in pulses], steps, 0.2, mode,
+                       tg.FLAG_RESET | tg.FLAG_TEST_TIMEOUT)
+    with pytest.raises(tg.TdagwError) as e:
+        tg.tdagw_sync(c.h)
+    assert e.value.code == tg.ERR_TIMEOUT
+    got = c.propagate_batch(pulses, steps, 0.2, mode)
+    if mode == tg.FULL:
+        apply = lambda v: K @ v  # noqa: E731
+    else:
+        apply = lambda v: d * v + U @ (S * (V.conj().T @ v))  # noqa: E731
+    _check(got, mdl, apply, pulses, steps, 0.2, 1e-5)
