@@ -139,6 +139,11 @@ struct TcArgs {
     unsigned long long wait_ns;
     int Nred;       // row tiles of the per-tile observable sums (red)
     int extra_arrivals;  // > 0 only for the timeout test: the grid barrier can never complete
+    // low-rank mode: per 256-row tile, the epilogue items completed so far (monotonic) and
+    // max(|Re|, |Im|) of the new stage input per trajectory (float bits): a phase A item
+    // waits only for the tiles of its K-range instead of a grid barrier
+    unsigned long long* tdone;
+    unsigned* xtile;
     // Channel-wise mode (Eq. svd-channel-wise; a separate instantiation).  Phase A runs
     // over the V segments (segment q: its Mt_q 256-column tiles, mtq0[q] the first of them
     // in the padded column order, K over the Nk k-points in nchV chunks), phase C over the
@@ -504,6 +509,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     for (int q = 0; q < kAbuf; ++q) buf_ch[q] = -1;
     unsigned gen = 0;
     bool ok = true;
+    unsigned long long tdone_target = 0;  // low-rank mode: epilogue items per tile so far
     int tr_gs = 0;  // stage of the phase timestamps (traced builds)
     (void)tr_gs;
     auto fail = [&]() {
@@ -667,17 +673,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             TC_TRACE(worker && wt == 0, 0);
             if (blockIdx.x == 0 && worker)
                 for (int b = wt; b < a.Bp; b += kWorkers) xout[b] = 0u;
-            if (st == 0 && a.ckS && worker && (a.n0 + n) % a.ck_period == 0) {
-                // checkpoint of the compensated state at the start of step n0 + n (stable
-                // until the last stage's epilogue of this step, two grid barriers away)
-                const int64_t slot = (int64_t)((a.n0 + n) / a.ck_period) * a.N * a.Bp;
-                const int64_t tot = a.N * Bact;
-                for (int64_t e = (int64_t)blockIdx.x * kWorkers + wt; e < tot; e += (int64_t)gridDim.x * kWorkers) {
-                    const int64_t off = (e / Bact) * a.Bp + e % Bact;
-                    a.ckS[slot + off] = __ldcg(a.Ssum + off);
-                    a.ckC[slot + off] = __ldcg(a.Ccomp + off);
-                }
-            }
 
             // ---------------- A: partials of V^H X ----------------
             const int nA = q.G * a.Mt * q.KS;
@@ -717,7 +712,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     group_range(Bact, q.G, it.g, b0, b1);
                     const int nbg = b1 - b0;
                     workers_sync();  // the previous item's readers of ssc are done
-                    if (wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
+                    if constexpr (CHT) {
+                        if (wt < kGroup) ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(__ldcg(xin + b0 + wt))) : 0.f;
+                    } else {
+                        // the rows of this K-range: wait until every epilogue item of their row
+                        // tiles has finished the previous stage, then this item's FP16 scale
+                        // from the tiles' maxima
+                        const int t0 = it.c0 * 16 / kRows, t1 = (it.c1 * 16 - 1) / kRows;
+                        if (wt == 0 && tdone_target > 0 && !*vabort) {
+                            const uint64_t tw = gtimer();
+                            for (int t = t0; t <= t1 && !*vabort; ++t)
+                                while (ld_acquire64(a.tdone + t) < tdone_target) {
+                                    if (gtimer() - tw > budget || *(volatile int*)a.err) {
+                                        fail();
+                                        break;
+                                    }
+                                    __nanosleep(32);
+                                }
+                        }
+                        workers_sync();
+                        if (wt < kGroup) {
+                            unsigned mx = 0u;
+                            if (wt < nbg)
+                                for (int t = t0; t <= t1; ++t) mx = max(mx, __ldcg(a.xtile + (int64_t)t * a.Bp + b0 + wt));
+                            ssc[wt] = wt < nbg ? pow2_scale(__uint_as_float(mx)) : 0.f;
+                        }
+                    }
                     workers_sync();
                     const float sx = ssc[obl];
                     const bool live = obl < nbg;
@@ -754,6 +774,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     tc::fence_after_sync();
                     if (!warp_abort()) {
                         float2* pbase = a.P + ((int64_t)it.ks * a.rp + (int64_t)it.m * kRows) * a.Bp + b0 + obl;
+                        // low-rank mode: partials unscaled (each item has its own X scale)
+                        const float ps = CHT ? 1.f : (live ? 1.f / (a.sv * sx) : 0.f);
                         for (int u = 0; u < 8; ++u) {
                             float v[16];
                             const int col = 128 * wh + 16 * u;
@@ -761,7 +783,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {
                                 const float im = __shfl_xor_sync(0xffffffffu, v[t], 1);
-                                if (!ocomp && live) pbase[(int64_t)(col + t) * a.Bp] = make_float2(v[t], im);
+                                if (!ocomp && live) pbase[(int64_t)(col + t) * a.Bp] = make_float2(v[t] * ps, im * ps);
                             }
                         }
                     }
@@ -773,6 +795,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
             TC_TRACE(worker && wt == 0, 1);
             if (in_sync && !(ok = tc_grid_sync(a, gen, &abort_s))) break;
             TC_TRACE(worker && wt == 0, 2);
+            if (st == 0 && a.ckS && worker && (a.n0 + n) % a.ck_period == 0) {
+                // checkpoint of the compensated state at the start of step n0 + n (every
+                // epilogue of the previous step is complete after the first barrier; stable
+                // until the last stage's epilogue of this step)
+                const int64_t slot = (int64_t)((a.n0 + n) / a.ck_period) * a.N * a.Bp;
+                const int64_t tot = a.N * Bact;
+                for (int64_t e = (int64_t)blockIdx.x * kWorkers + wt; e < tot; e += (int64_t)gridDim.x * kWorkers) {
+                    const int64_t off = (e / Bact) * a.Bp + e % Bact;
+                    a.ckS[slot + off] = __ldcg(a.Ssum + off);
+                    a.ckC[slot + off] = __ldcg(a.Ccomp + off);
+                }
+            }
 
             // ---------------- B: S o sum of the partials, scaled for FP16 ----------------
             if (worker) {
@@ -841,8 +875,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
                                                   cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
                             const float mx = __uint_as_float(__ldcg(xin + b));
-                            const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
-                            v = cscale(s, a.S[j] * (sy / (a.sv * sx)));
+                            v = cscale(s, a.S[j] * pow2_scale(a.ybound * mx));
                         }
                         a.Ys[(int64_t)j * a.Bp + b] = v;
                     }
@@ -970,6 +1003,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         workers_sync();
                         if (wt < nbg && !*vabort) {
                             atomicMax(xout + b0 + wt, smx[wt]);
+                            a.xtile[(int64_t)t * a.Bp + b0 + wt] = smx[wt];
                             if (st == 3) {
                                 double r0 = 0.0, r1 = 0.0, r2 = 0.0;
                                 for (int k2 = 0; k2 < kgroups; ++k2) {
@@ -983,6 +1017,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                                 rr[2] = r2;
                             }
                         }
+                        // every row of this item is written: count it for the tile (release)
+                        workers_sync();
+                        if (wt == 0) red_release_add64(a.tdone + t, 1ull);
                     }
                 }
             } else {
@@ -1142,11 +1179,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 }
             }
             TC_TRACE(worker && wt == 0, 5);
-            if (in_sync) ok = tc_grid_sync(a, gen, &abort_s);
+            if constexpr (CHT) {
+                if (in_sync) ok = tc_grid_sync(a, gen, &abort_s);
+            } else {
+                // no grid barrier: the next stage's phase A items wait for their row tiles (an
+                // abort is seen uniformly at the next stage's first barrier)
+                tdone_target += (unsigned long long)q.GC;
+            }
             TC_TRACE(worker && wt == 0, 6);
         }
     }
     // observables of the last step (workers: they passed the last grid barrier)
+    // low-rank mode: every CTA's last epilogue is complete before the last observables
+    if (!CHT && in_sync && ok && a.Tmax > 0) ok = tc_grid_sync(a, gen, &abort_s);
     if (CHT && worker && ok && a.Tmax > 0) {
         tc_obs_warp(a, a.Tmax, blockIdx.x * (kWorkers / 32) + (warp - 2), gridDim.x * (kWorkers / 32), lane);
     } else if (worker && ok && a.Tmax > 0) {
@@ -1181,6 +1226,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tm, kTmemCols);
+    }
+}
+
+// max(|Re|, |Im|) of each trajectory's stage input X over each 256-row tile, as float bits
+// (block (t, b)): the per-tile maxima of a launch that starts from a restored state
+__global__ void xtile_kernel(const float2* __restrict__ X, int64_t N, int Bp, unsigned* __restrict__ xtile) {
+    const int t = blockIdx.x, b = blockIdx.y;
+    float m = 0.f;
+    for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+        const int64_t i = (int64_t)t * kRows + r;
+        if (i < N) {
+            const float2 v = X[i * Bp + b];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        m = fmaxf(m, wm[0]);
+        xtile[(int64_t)t * Bp + b] = __float_as_uint(m);
     }
 }
 
@@ -1364,6 +1432,8 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     c.tcY.ensure((size_t)d.rp * Bp * sizeof(float2));
     c.tcMax.ensure((size_t)3 * Bp * sizeof(unsigned));
     c.tcRed.ensure((size_t)d.Nt * Bp * 3 * sizeof(double));
+    c.tcDone.ensure((size_t)d.Nt * sizeof(unsigned long long));
+    c.tcXt.ensure((size_t)d.Nt * Bp * sizeof(unsigned));
     const size_t sbytes = (size_t)N * Bp * sizeof(float2);
     c.sync.ensure(4 * sizeof(unsigned));
 
@@ -1390,6 +1460,8 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
     a.obs = c.bobs.as<double>();
     a.bar = reinterpret_cast<unsigned long long*>(c.sync.p);
     a.err = reinterpret_cast<int*>(c.sync.as<unsigned>() + 2);
+    a.tdone = c.tcDone.as<unsigned long long>();
+    a.xtile = c.tcXt.as<unsigned>();
     a.N = N;
     a.ldE = bs.ldE;
     a.Nk = h.Nk;
@@ -1430,6 +1502,8 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
                         {c.bS.p, sbytes},
                         {c.bC.p, sbytes},
                         {c.tcMax.p, 3 * Bp * sizeof(unsigned)},
+                        {c.tcDone.p, d.Nt * sizeof(unsigned long long)},
+                        {c.tcXt.p, d.Nt * Bp * sizeof(unsigned)},
                         {c.sync.p, 4 * sizeof(unsigned)}},
                        graph);
     };
@@ -1541,6 +1615,9 @@ void tc_recompute_segment(Ctx& c, int n0, int len, float2* recX, float2* recDS, 
     TDAGW_CUDA(cudaMemsetAsync(a.xmax, 0, 3 * (size_t)a.Bp * sizeof(unsigned), s));
     xmax_kernel<<<dim3(64, (unsigned)a.Bp), 256, 0, s>>>(a.X, a.N, a.Bp, a.xmax);
     check_launch("xmax_kernel");
+    TDAGW_CUDA(cudaMemsetAsync(a.tdone, 0, (size_t)a.Nt * sizeof(unsigned long long), s));
+    xtile_kernel<<<dim3((unsigned)a.Nt, (unsigned)a.Bp), 256, 0, s>>>(a.X, a.N, a.Bp, a.xtile);
+    check_launch("xtile_kernel");
     TDAGW_CUDA(cudaMemsetAsync(c.sync.p, 0, 4 * sizeof(unsigned), s));
     void* args[] = {&a};
     TDAGW_CUDA(cudaLaunchCooperativeKernel(st.tc_fn, dim3(st.tc_grid), dim3(kTcThreads), args, st.tc_smem, s));

@@ -230,7 +230,7 @@ struct Ctx {
     int obs_B = 1;           // trajectories in the recorded observables
     // split-FP16 tiled factors for the tensor-core batched path, its intermediates, and
     // whether the tiles match the installed factors
-    DevBuf tcU, tcV, tcY, tcP, tcMax, tcRed;
+    DevBuf tcU, tcV, tcY, tcP, tcMax, tcRed, tcDone, tcXt;
     bool tc_valid = false;
     float tc_su = 1.f, tc_sv = 1.f, tc_ybound = 0.f;
     // checkpoints (compensated state every `period` steps) and adjoint work buffers

@@ -27,7 +27,7 @@ BUDGET = {
     "batched_kernelILi2ELb0E": 0, "batched_kernelILi2ELb1E": 52,
     "batched_kernelILi4ELb0E": 100, "batched_kernelILi4ELb1E": 72,
     "batched_tc_kernelILi2ELb0E": 96, "batched_tc_kernelILi4ELb0E": 424,
-    "batched_tc_kernelILi2ELb1E": 16, "batched_tc_kernelILi4ELb1E": 380,
+    "batched_tc_kernelILi2ELb1E": 16, "batched_tc_kernelILi4ELb1E": 392,
     "adjoint_kernelILi2E": 0, "adjoint_kernelILi4E": 780,
     "stage_kernelIfLi2E": 0, "stage_kernelIfLi4E": 0,
     "gemv_kernelIfLi4ELi256E": 0, "vcols_kernelIfE": 0, "yreduce_kernelIfE": 0,
