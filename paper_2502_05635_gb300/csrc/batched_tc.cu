@@ -30,8 +30,13 @@
 //   C  items (256-row tile of U, trajectory group): the U tiles stream through the ring,
 //      the workers write the expanded split S o Y blocks into tensor memory; the
 //      accumulator (128 lanes x 256 rows) is staged through shared memory in quarters and
-//      the commutator + RK4 epilogue (Eq. tdagw) runs per (k, b) block.
-//   -- grid barrier --
+//      the commutator + RK4 epilogue (Eq. tdagw) runs per (k, b) block; each item then
+//      counts its row tile (release), and the next stage's phase A items wait only for
+//      the tiles of their K-ranges instead of a grid barrier.
+// The channel-wise mode (Eq. svd-channel-wise, a second instantiation) runs phase A per V
+// segment and phase C per U segment (low-rank columns and the dense diagonal channel of an
+// output pair) with gathered operand rows, writes dSigma to global memory, and runs the
+// epilogue as a fourth phase by 64-row quarters, with grid barriers between all phases.
 // Roles: warp 0 streams the factor tiles into the ring (it only reads static tiles, so it
 // stays out of the grid barriers and keeps copies in flight across them), warp 1 issues
 // the MMAs, warps 2-9 build the tensor-memory operands and drain the accumulator.  Every
