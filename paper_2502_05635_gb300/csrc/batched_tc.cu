@@ -821,39 +821,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                     for (int64_t e = gt; e < tot_el; e += total) {
                         const int j = (int)(e / Bact), b = (int)(e % Bact);
                         float2 v = make_float2(0.f, 0.f);
-                        // column of S (channel-wise: the padded column j of V segment qs)
-                        int sj = j < a.r ? j : -1;
-                        if constexpr (CHT) {
-                            int qs, m;
-                            seg_of_mt(a, j / kRows, qs, m);
-                            const int jj = m * kRows + j % kRows;
-                            sj = jj < a.ldvq[qs] ? a.sbq[qs] + jj : -1;
-                        }
+                        // column of S: the padded column j is column jj of V segment qs
+                        int qs, m;
+                        seg_of_mt(a, j / kRows, qs, m);
+                        const int jj = m * kRows + j % kRows;
+                        const int sj = jj < a.ldvq[qs] ? a.sbq[qs] + jj : -1;
                         if (sj >= 0) {
                             // eight independent partial sums (loads in flight), fixed order
                             const float2* pp = a.P + (int64_t)j * a.Bp + b;
                             const int64_t pstride = (int64_t)a.rp * a.Bp;
                             float2 s8[8];
-    #pragma unroll
+#pragma unroll
                             for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
                             int k2 = 0;
                             for (; k2 + 8 <= q.KS; k2 += 8) {
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
                             }
-    #pragma unroll
+#pragma unroll
                             for (int u = 0; u < 8; ++u)
                                 if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
                             const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
                                                   cadd(cadd(s8[4], s8[5]), cadd(s8[6], s8[7])));
+                            // unscaled: the U-pass operand mixes S o y and x, scaled together
                             const float mx = __uint_as_float(__ldcg(xin + b));
-                            if constexpr (CHT) {
-                                // unscaled: the U-pass operand mixes S o y and x, scaled together
-                                v = cscale(s, a.S[sj] * (1.f / (a.sv * pow2_scale(mx))));
-                            } else {
-                                const float sx = pow2_scale(mx), sy = pow2_scale(a.ybound * mx);
-                                v = cscale(s, a.S[sj] * (sy / (a.sv * sx)));
-                            }
+                            v = cscale(s, a.S[sj] * (1.f / (a.sv * pow2_scale(mx))));
                         }
                         a.Ys[(int64_t)j * a.Bp + b] = v;
                     }
@@ -867,14 +859,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             const float2* pp = a.P + (int64_t)j * a.Bp + b;
                             const int64_t pstride = (int64_t)a.rp * a.Bp;
                             float2 s8[8];
-    #pragma unroll
+#pragma unroll
                             for (int u = 0; u < 8; ++u) s8[u] = make_float2(0.f, 0.f);
                             int k2 = 0;
                             for (; k2 + 8 <= q.KS; k2 += 8) {
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < 8; ++u) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
                             }
-    #pragma unroll
+#pragma unroll
                             for (int u = 0; u < 8; ++u)
                                 if (k2 + u < q.KS) s8[u] = cadd(s8[u], __ldcg(pp + (k2 + u) * pstride));
                             const float2 s = cadd(cadd(cadd(s8[0], s8[1]), cadd(s8[2], s8[3])),
@@ -966,13 +958,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                             // accumulator columns 64 qq .. + 63 (the warp's 32 of them) -> staged
                             // quarter, unscaled; lanes 2 bl and 2 bl + 1 hold re and im
                             if (!warp_abort()) {
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < 2; ++u) {
                                     float v[16];
                                     const int col = 64 * qq + 32 * wh + 16 * u;
                                     tc::tmem_ld16(tm + ((uint32_t)(32 * wq) << 16) + col, v);
                                     const float sc = live ? ssc[obl] : 0.f;
-    #pragma unroll
+#pragma unroll
                                     for (int e = 0; e < 16; ++e) {
                                         const float im = __shfl_xor_sync(0xffffffffu, v[e], 1);
                                         if (!ocomp && live)
