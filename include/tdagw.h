@@ -236,8 +236,10 @@ int tdagw_apply(tdagw_ctx* ctx, int mode, const void* x, void* y);
  * UNSUPPORTED for B > 1 on a complex128 context or without TDAGW_FLAG_RESET, and for
  * CHANNEL with TDAGW_FLAG_CHECKPOINT; INVALID_ARG for TDAGW_FLAG_SPLIT_F16 with FULL.
  * The work split of a tensor-core launch (trajectory groups of the U product, K-ranges of
- * V^H X) is tuned by timing six steps of each candidate on the first call of at least
- * eight steps for a batch size and rank, and kept on the context. */
+ * V^H X, and per-tile counters or a grid barrier between a stage's epilogue and the next
+ * V^H X; channel-wise: trajectory groups and K-ranges of the U segments) is tuned by
+ * timing six steps of each candidate on the first call of at least eight steps for a
+ * batch size and rank, and kept on the context. */
 int tdagw_propagate(tdagw_ctx* ctx, const tdagw_field* fields, int B, const int* steps,
                     double dt, int mode, int flags);
 

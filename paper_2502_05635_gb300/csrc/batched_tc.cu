@@ -149,6 +149,7 @@ struct TcArgs {
     // waits only for the tiles of its K-range instead of a grid barrier
     unsigned long long* tdone;
     unsigned* xtile;
+    int use_flags;  // low-rank mode: 1 the per-tile counters, 0 a grid barrier after the epilogue
     // Channel-wise mode (Eq. svd-channel-wise; a separate instantiation).  Phase A runs
     // over the V segments (segment q: its Mt_q 256-column tiles, mtq0[q] the first of them
     // in the padded column order, K over the Nk k-points in nchV chunks), phase C over the
@@ -724,7 +725,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                         // tiles has finished the previous stage, then this item's FP16 scale
                         // from the tiles' maxima
                         const int t0 = it.c0 * 16 / kRows, t1 = (it.c1 * 16 - 1) / kRows;
-                        if (wt == 0 && tdone_target > 0 && !*vabort) {
+                        if (wt == 0 && a.use_flags && tdone_target > 0 && !*vabort) {
                             const uint64_t tw = gtimer();
                             for (int t = t0; t <= t1 && !*vabort; ++t)
                                 while (ld_acquire64(a.tdone + t) < tdone_target) {
@@ -1176,7 +1177,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batched_tc_kernel(TcArgs a) {
                 }
             }
             TC_TRACE(worker && wt == 0, 5);
-            if constexpr (CHT) {
+            if (CHT || !a.use_flags) {
                 if (in_sync) ok = tc_grid_sync(a, gen, &abort_s);
             } else {
                 // no grid barrier: the next stage's phase A items wait for their row tiles (an
@@ -1490,9 +1491,10 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         c.ckS.ensure((size_t)nck * sbytes);
         c.ckC.ensure((size_t)nck * sbytes);
     }
-    auto run = [&](int gc_max, int ks_max, int T, bool graph) {
+    auto run = [&](int gc_max, int ks_max, int fl, int T, bool graph) {
         a.gc_max = gc_max;
         a.ks_max = ks_max;
+        a.use_flags = fl;
         a.Tmax = T;
         launch_batched(c, fn, dim3(nctas), dim3(kTcThreads), smem, &a, sizeof(a),
                        {{c.bX.p, sbytes},
@@ -1507,18 +1509,20 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
 
     // Work split of the launch, tuned once per (B, rank) on this context by timing a few
     // steps of each candidate: the trajectory groups of the U product (fewer groups stream
-    // U fewer times and waste fewer MMA rows; more groups fill more CTAs when N is small)
-    // and the K-ranges of the V^H X product (all CTAs, or half as many longer ranges with
-    // half the partial sums).
+    // U fewer times and waste fewer MMA rows; more groups fill more CTAs when N is small),
+    // the K-ranges of the V^H X product (all CTAs, or half as many longer ranges with half
+    // the partial sums), and whether the next stage's V^H X items wait for their row tiles
+    // through per-tile counters or all CTAs meet at a grid barrier after the epilogue.
     const uint64_t key = (0xF0ull << 56) | ((uint64_t)B << 32) | (uint64_t)(uint32_t)r;
-    int gc_max = 0, ks_max = 0;
+    int gc_max = 0, ks_max = 0, flags_on = 1;
     const bool test_timeout = (flags & TDAGW_FLAG_TEST_TIMEOUT) != 0;
     auto it = c.batch_plans.find(key);
     if (test_timeout) {
         // timeout test: no tuning; the launch below waits for an arrival that never comes
     } else if (it != c.batch_plans.end()) {
         gc_max = it->second.first;
-        ks_max = it->second.second;
+        ks_max = it->second.second & 0xFFFFF;
+        flags_on = it->second.second >> 20;
     } else {
         const int g_min = (B + kGroup - 1) / kGroup;
         const int g_fill = group_count(B, d.Nt, nctas, 0);
@@ -1528,28 +1532,28 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         const int ks_fill = std::max(1, std::min(nctas / (g_min * d.Mt), d.nchV));
         std::vector<int> kss = {0};
         if (ks_fill >= 4) kss.push_back(ks_fill / 2);
-        if (gcs.size() * kss.size() == 1) {
-            c.batch_plans[key] = {0, 0};
-        } else if (bs.Tmax >= 8) {
+        if (bs.Tmax >= 8) {
             cudaEvent_t e0, e1;
             TDAGW_CUDA(cudaEventCreate(&e0));
             TDAGW_CUDA(cudaEventCreate(&e1));
             float best = 1e30f;
             for (int gcand : gcs)
-                for (int kcand : kss) {
-                    run(gcand, kcand, 2, false);  // warm
-                    TDAGW_CUDA(cudaEventRecord(e0, s));
-                    run(gcand, kcand, 6, false);
-                    TDAGW_CUDA(cudaEventRecord(e1, s));
-                    TDAGW_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    TDAGW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (ms < best) {
-                        best = ms;
-                        gc_max = gcand;
-                        ks_max = kcand;
+                for (int kcand : kss)
+                    for (int fcand = 1; fcand >= 0; --fcand) {
+                        run(gcand, kcand, fcand, 2, false);  // warm
+                        TDAGW_CUDA(cudaEventRecord(e0, s));
+                        run(gcand, kcand, fcand, 6, false);
+                        TDAGW_CUDA(cudaEventRecord(e1, s));
+                        TDAGW_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        TDAGW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        if (ms < best) {
+                            best = ms;
+                            gc_max = gcand;
+                            ks_max = kcand;
+                            flags_on = fcand;
+                        }
                     }
-                }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             int err = 0;
@@ -1557,7 +1561,7 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
             TDAGW_REQUIRE(!err, TDAGW_ERR_TIMEOUT, "a bounded wait gave up while tuning the tensor-core kernel");
             // the tuning runs overwrote the observables: restore the first row
             reset_batch_observables(c, bs, B);
-            c.batch_plans[key] = {gc_max, ks_max};
+            c.batch_plans[key] = {gc_max, ks_max | (flags_on << 20)};
         }
     }
     c.adj.valid = false;
@@ -1570,7 +1574,7 @@ void propagate_batched_tc(Ctx& c, const tdagw_field* fields, int B, const int* s
         a.extra_arrivals = 1;
         a.wait_ns = 20000000ull;
     }
-    run(gc_max, ks_max, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH) && !test_timeout);
+    run(gc_max, ks_max, flags_on, bs.Tmax, !(flags & TDAGW_FLAG_NO_GRAPH) && !test_timeout);
     a.extra_arrivals = 0;
     a.wait_ns = 2000000000ull;
     c.persistent_launched = true;
