@@ -39,3 +39,19 @@ def test_angle_sweep_directions_are_unit_vectors():
     assert np.allclose([p.dir_x ** 2 + p.dir_y ** 2 for p in w.pulses], 1.0)
     assert abs(ang[0] - 1.0) < 1e-9 and abs(ang[-1] - 60.0) < 1e-9
     assert all(p.kind == 2 and p.T_pulse == w.steps[0] * w.dt for p in w.pulses)
+
+
+def test_early_pulses_recipe():
+    """The early pulses of the batched comparisons: seeded, peaking within 60 steps of
+    dt = 0.2, log-uniform amplitudes, unit field directions over a half turn."""
+    a, b = wl.early_pulses(2048), wl.early_pulses(2048)
+    assert a == b
+    E0 = np.array([p.E0 for p in a])
+    sg = np.array([p.sigma for p in a])
+    ang = np.array([np.arctan2(p.dir_y, p.dir_x) for p in a])
+    assert np.all((E0 >= 1e-4) & (E0 <= 1e-2)) and abs(np.log10(E0).mean() + 3.0) < 0.05
+    assert np.all((sg >= 1.5) & (sg <= 3.0)) and all(p.t0 == 6.0 and p.kind == 0 for p in a)
+    assert np.all((ang >= 0.0) & (ang <= np.pi)) and ang.max() - ang.min() > 3.0
+    assert all(abs(p.dir_x ** 2 + p.dir_y ** 2 - 1.0) < 1e-12 for p in a)
+    # the envelope has decayed by the end of 60 steps: t0 + 4 sigma <= 12 = 60 dt
+    assert np.all(6.0 + 4.0 * sg <= 60 * 0.2)
