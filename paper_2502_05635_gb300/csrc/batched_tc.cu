@@ -142,7 +142,7 @@ struct TcArgs {
     float su, sv;   // power-of-two scales of the U and V tiles
     float ybound;   // max|S| max_j ||v_j|| sqrt(2N): |(S o Y)_jb| <= ybound max|X_b|
     unsigned long long wait_ns;
-    int Nred;       // row tiles of the per-tile observable sums (red)
+    int Nred;       // tiles of the per-tile observable sums (red): row tiles, or quarters
     int extra_arrivals;  // > 0 only for the timeout test: the grid barrier can never complete
     // low-rank mode: per 256-row tile, the epilogue items completed so far (monotonic) and
     // max(|Re|, |Im|) of the new stage input per trajectory (float bits): a phase A item
@@ -155,8 +155,9 @@ struct TcArgs {
     // in the padded column order, K over the Nk k-points in nchV chunks), phase C over the
     // U segments (segment p = [U^pq of the channels out of p | K^pp]: NtK 256-row tiles of
     // k-points, nchw[p] chunks of its columns), with the operand z_p = [S o y of those
-    // channels (padded rows gpad) ; x_p]; phase C writes dSigma to dS and a fourth phase
-    // runs the commutator + RK4 epilogue over the nte 256-row tiles of all N rows.
+    // channels (padded rows gpad) ; x_p]; phase C writes dSigma to dS (one partial slot per
+    // K-range) and a fourth phase runs the commutator + RK4 epilogue by 64-row quarters of
+    // the nte 256-row tiles of all N rows.
     const int* gpad;
     float2* dS;
     int npair, NtK, nte;
